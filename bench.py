@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral-element Poisson CG solve on GB300.
+
+One step = one complete mixed-precision solve (FP32 Jacobi-PCG inside FP64
+iterative refinement, every kernel of the hot path) of the 16x16x16 deformed
+box, N = 9 (4,096,000 local / 3,048,625 unique nodes), right-hand side
+U[-1,1) per unique node, to a true FP64 relative residual of 1e-10.
+
+value = unique degrees of freedom solved to 1e-10 per second, summed over
+ranks (each rank solves its own replica: weak scaling).  The same line
+reports the plain FP64 PCG time on the same GPU (the paper's Gain), the
+operator throughput with its HBM roofline, an end-to-end number through the
+host-buffer entry point, and the FP64 CPU oracle as a baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "CG time-to-solution & ax GDOF/s: mixed vs FP64 on 1 GB300 at equal residual"
+UNIT = "GDOF/s (unique DOFs solved to FP64 rel. residual 1e-10 per second)"
+BOX = W.MIXED_16CUBE_N9
+WORKLOAD = ("mixed-precision Jacobi-PCG (FP32 operator and vectors, FP64 dots, FP64 iterative "
+            "refinement) on the 16x16x16 deformed box, N=9, to FP64 relative residual 1e-10")
+RTOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=40,
+                    help="oracle iterations timed for the CPU baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def oracle_iterations():
+    p = os.path.join(ROOT, "oracle", "iteration_counts.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)["mixed_16cube_n9"]
+
+
+def cpu_baseline(iters: int):
+    """The FP64 oracle as it stands, single-threaded on a host core: a
+    bounded sample of Jacobi-PCG iterations on the same problem, scaled to a
+    full solve with the oracle's own iteration count to 1e-10."""
+    import oracle
+    P = oracle.Problem(BOX)
+    b = P.to_local(W.rhs_global(BOX, 0))
+    t0 = time.perf_counter()
+    P.pcg(b, tol=0.0, maxit=iters)
+    dt = time.perf_counter() - t0
+    per_it = dt / iters
+    full = oracle_iterations()
+    if full is None:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{iters} oracle iterations, {per_it * 1e3:.1f} ms/iteration; "
+                          "iteration count to 1e-10 not yet recorded"}
+    t_solve = per_it * full["iterations"]
+    return {
+        "value": BOX.n_global / t_solve / 1e9,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"{iters} FP64 Jacobi-PCG iterations of the C oracle (1 thread) on the same "
+                   f"E=4096 N=9 problem, {per_it * 1e3:.1f} ms/iteration, scaled to the "
+                   f"{full['iterations']} iterations the oracle needs for 1e-10 "
+                   f"(oracle/iteration_counts.json): {t_solve:.1f} s per solve"),
+        "seconds_per_solve": t_solve,
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        args = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                "-lms", "200"]
+        if device_uuid:
+            args += ["-i", device_uuid]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(args, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_impl.cuh", "paper_2405_11065_gb300/csrc/nb_ax_f32.cu"]
+
+
+def profiled_traffic(sha):
+    """DRAM bytes per launch of the FP32 CG-step operator from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ax_fp32_cg_step_E4096_N9.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    P = oracle.Problem(BOX)
+    b = P.to_local(W.rhs_global(BOX, 0))
+    full = oracle_iterations()
+    per_step_iters = 8
+    for _ in range(args.warmup):
+        P.pcg(b, tol=0.0, maxit=2)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        P.pcg(b, tol=0.0, maxit=per_step_iters)
+        times.append(time.perf_counter() - t0)
+    per_it = sum(times) / (args.steps * per_step_iters)
+    t_solve = per_it * full["iterations"]
+    value = BOX.n_global / t_solve / 1e9
+    sample = (f"each step: {per_step_iters} FP64 Jacobi-PCG iterations of the C oracle "
+              f"(1 thread) on the E=4096 N=9 problem; scaled to the {full['iterations']} "
+              f"iterations the oracle needs for 1e-10")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "E": BOX.E, "N": BOX.N,
+                       "n_local": BOX.n_local, "n_global": BOX.n_global},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_iters)  # host only, before the first GPU call
+
+    import torch
+    import paper_2405_11065_gb300 as nb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)  # legacy default stream: events are ordered
+    ctx = nb.Context(local)                  # with the library's own blocking stream
+    mesh = nb.Mesh.from_box(ctx, BOX)
+    bg = torch.from_numpy(W.rhs_global(BOX, rank)).to(dev)
+    b = torch.empty(BOX.n_local, dtype=torch.float64, device=dev)
+    mesh.to_local(nb.NB_FP64, bg, b, masked=True)
+    x = torch.zeros_like(b)
+    flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
+
+    # autotune the operator (per precision, this order) before timing
+    tune = {}
+    for pname, prec in (("fp32", nb.NB_FP32), ("fp64", nb.NB_FP64)):
+        v, ms = mesh.autotune(prec, reps=3, flush=flush)
+        tune[pname] = {"variant": v, "ms": ms}
+
+    opts = nb.default_opts(prec=nb.NB_FP32, rtol=RTOL)
+    for _ in range(args.warmup):
+        x.zero_()
+        mesh.solve(b, x, opts)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    dev_uuid = None
+    try:
+        dev_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(dev_uuid)
+    barrier()
+    evs = []
+    stats = []
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # evict L2 between steps, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = mesh.solve(b, x, opts)
+        e1.record(stream)
+        evs.append((e0, e1))
+        stats.append(out)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in evs]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    ok = all(s["status"] == 0 and s["rel_res"] < RTOL for s in stats)
+
+    # correctness of the last solve on the device: FP64 residual
+    w = torch.empty_like(b)
+    mesh.ax(nb.NB_FP64, x, w, assemble=True)
+    r = b - w
+    c = torch.from_numpy(mesh.geom()[2]).to(dev)
+    true_rel = float(torch.sqrt((c * r * r).sum() / (c * b * b).sum()))
+
+    # plain FP64 PCG on the same GPU, same problem (the paper's comparison)
+    o64 = nb.default_opts(prec=nb.NB_FP64, rtol=RTOL)
+    x64 = torch.zeros_like(b)
+    mesh.solve(b, x64, o64)
+    fp64_ms, fp64_stats = [], None
+    for _ in range(2):
+        flush.fill_(1)
+        x64.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fp64_stats = mesh.solve(b, x64, o64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_ms.append(e0.elapsed_time(e1))
+    t64 = statistics.median(fp64_ms)
+    tm = statistics.median(step_ms)
+    sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+
+    # operator throughput and roofline of the dominant kernel
+    hbm_peak, peak_kind = measured_peaks()
+    nL = BOX.n_local
+    ax = {}
+    for pname, prec, elt in (("fp32", nb.NB_FP32, 4), ("fp64", nb.NB_FP64, 8)):
+        ms_cg = mesh.time_ax(prec, cg_step=True, reps=20, flush=flush)
+        ms_ax = mesh.time_ax(prec, cg_step=False, reps=20, flush=flush)
+        ax[pname] = {"cg_step_ms": ms_cg, "ax_ms": ms_ax,
+                     "ax_gdofs_local": nL / (ms_ax * 1e-3) / 1e9,
+                     "ax_gdofs_unique": BOX.n_global / (ms_ax * 1e-3) / 1e9,
+                     "ax_gbs_algorithmic": 8 * elt * nL / (ms_ax * 1e-3) / 1e9,
+                     "cg_step_gbs_algorithmic": 11 * elt * nL / (ms_cg * 1e-3) / 1e9,
+                     "variant": tune[pname]["variant"]}
+    n = BOX.n
+    ax["fp64"]["ax_gflops"] = (12 * n + 15) * nL / (ax["fp64"]["ax_ms"] * 1e-3) / 1e9
+    sha = source_sha(AX_SOURCES)
+    bytes_cg = 11 * 4 * nL
+    achieved = bytes_cg / (ax["fp32"]["cg_step_ms"] * 1e-3) / 1e9
+    traffic = profiled_traffic(sha)
+    roofline = {"kernel": "k_ax_cc<float,10,*,PUPD> (fused p-update + operator, FP32)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} (STREAM copy)",
+                "traffic": traffic, "algorithmic_bytes_per_launch": bytes_cg,
+                "bytes_per_local_node": 44, "kernel_source_sha": sha}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if rank == 0 or world > 1:
+        bh = torch.from_numpy(W.rhs_global(BOX, rank)).pin_memory()
+        xh = torch.zeros(BOX.n_global, dtype=torch.float64).pin_memory()
+        mesh.solve_host(bh, xh, opts)
+        e2e_ms = []
+        for _ in range(max(2, min(args.steps, 5))):
+            flush.fill_(2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outh = mesh.solve_host(bh, xh, opts)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            e2e_ms.append(e0.elapsed_time(e1))
+        te = statistics.median(e2e_ms)
+        e2e = {"value": world * BOX.n_global / (te * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * BOX.n_global, "d2h_bytes_per_step": 8 * BOX.n_global,
+               "ms_per_step": te, "status": outh["status"]}
+
+    launches = int(sum(s["launches"] for s in stats))
+    value = world * BOX.n_global * args.steps / (max_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 refinement)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "E": BOX.E, "N": BOX.N, "n_local": BOX.n_local,
+                       "n_global": BOX.n_global, "deform": BOX.deform, "rhs": "U[-1,1) per unique node, seed = rank",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "time_to_solution_ms": {"mixed_fp32_refined": tm, "fp64_pcg": t64},
+            "gain_vs_fp64": (t64 - tm) / t64,
+            "speedup_vs_fp64": t64 / tm,
+            "iterations": {"mixed_inner": stats[-1]["iters"], "mixed_outer": stats[-1]["outer_iters"],
+                           "fp64": fp64_stats["iters"]},
+            "rel_res": {"mixed": stats[-1]["rel_res"], "fp64": fp64_stats["rel_res"],
+                        "mixed_recomputed": true_rel},
+            "mixed_vs_fp64_solution_rel_diff": sol_diff,
+            "all_steps_converged": ok,
+            "ax": ax,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0 if ok else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * nekbone_gb300.h -- C ABI of the GB300 (sm_103a) spectral-element Poisson
+ * conjugate-gradient library.
+ *
+ * The method is the conjugate-gradient (CG) solve of the Nekbone mini-app as
+ * profiled in the mixed-precision case study (Section 4.1, Table 1): each
+ * iteration applies the preconditioner (solveM), three weighted dot products
+ * (glsc3), two kinds of vector updates (add2s1, add2s2) and the matrix-free
+ * spectral-element operator ax, whose "accumulations before and after"
+ * (Table 1, note b) are the direct-stiffness summation over shared nodes.
+ * Section 6 of the paper runs that loop in single precision with the set-up
+ * kept in double; this library adds FP64 iterative refinement around an FP32
+ * (or tensor-core) inner solve.
+ *
+ * Conventions for every function below:
+ *  - Return value: NB_OK (0) on success; a negative nb_status on an error (no
+ *    output is valid); a positive nb_status is a solver outcome with a valid
+ *    solution (not converged, stagnated, breakdown, fell back).
+ *    nb_last_error() returns a message for the last error of the calling
+ *    thread.
+ *  - "_dev" pointers are CUDA device pointers on the context's device; "_host"
+ *    pointers are ordinary host memory.  The caller owns every buffer it
+ *    passes and must keep it alive until the call returns (device work is
+ *    complete when a call returns unless stated otherwise).  The library owns
+ *    what it allocates and frees it in the matching *_destroy call.
+ *  - All work is issued on the context's stream (set at nb_create or with
+ *    nb_set_stream).  Functions synchronise that stream before returning.
+ *  - Vector layout: an "L-vector" holds E*(N+1)^3 values, element-major,
+ *    [e][k][j][i] with i fastest; a "G-vector" holds one value per unique
+ *    (global) node, index gx + (nx*N+1)*(gy + (ny*N+1)*gz).
+ *  - Element e of an nx*ny*nz box is (ex, ey, ez) with e = ex + nx*(ey + ny*ez).
+ *  - The precision argument selects the value type of vector arguments:
+ *    NB_FP64 -> double; NB_FP32, NB_TC_F16, NB_TC_BF16 -> float.
+ *  - The library validates sizes and pointers on the host, never aborts and
+ *    bounds every device loop by an iteration limit.
+ */
+#ifndef NEKBONE_GB300_H
+#define NEKBONE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx;   /* device, stream, error state */
+typedef struct nb_mesh nb_mesh; /* device geometry, numbering, gather-scatter, workspaces */
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = -1,        /* invalid argument (size, pointer, enum, NaN input) */
+    NB_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    NB_ERR_OOM = -3,        /* device allocation failed */
+    NB_ERR_MESH = -4,       /* invalid mesh: non-positive Jacobian, bad order */
+    NB_ERR_STATE = -5,      /* call out of order (e.g. solve before setup_gs) */
+    NB_NOT_CONVERGED = 1,   /* iteration limit reached; x holds the last iterate */
+    NB_STAGNATED = 2,       /* refinement stopped reducing the residual */
+    NB_BREAKDOWN = 3,       /* p^T A p <= 0 or a non-finite scalar */
+    NB_FELL_BACK = 4        /* learned preconditioner abandoned for Jacobi */
+} nb_status;
+
+typedef enum {
+    NB_FP64 = 0,      /* operator and vectors in double */
+    NB_FP32 = 1,      /* operator and vectors in float, dots accumulated in double */
+    NB_TC_F16 = 2,    /* float vectors, derivative contractions on FP16 tensor cores */
+    NB_TC_BF16 = 3    /* float vectors, derivative contractions on BF16 tensor cores */
+} nb_prec;
+
+typedef enum {
+    NB_PC_NONE = 0,    /* solveM is a copy (the paper's no-multigrid case) */
+    NB_PC_JACOBI = 1,  /* z = diag(A)^-1 r */
+    NB_PC_LEARNED = 2  /* per-element network inside flexible CG */
+} nb_pc;
+
+typedef struct {
+    nb_prec prec;       /* NB_FP64: plain FP64 PCG.  Others: FP64 iterative
+                           refinement around an inner solve in that precision */
+    nb_pc pc;           /* preconditioner */
+    double rtol;        /* stop when ||b - A x||_c / ||b||_c < rtol (FP64) */
+    int maxiter;        /* iteration limit (inner iterations summed) */
+    double inner_rtol;  /* relative tolerance of each inner solve (refinement) */
+    int max_outer;      /* refinement step limit */
+    int use_graph;      /* 1: the iteration is a CUDA graph with a device-side
+                           while loop; 0: host-launched kernels */
+    int record_history; /* 1: keep the recursive residual of each iteration */
+    int use_x0;         /* 1: x_dev holds the initial guess; 0: start from zero */
+} nb_opts;
+
+typedef struct {
+    int iters;              /* CG iterations (inner iterations summed) */
+    int outer_iters;        /* refinement steps (0 for plain FP64 PCG) */
+    double rel_res;         /* final relative residual ||b - A x||/||b|| in FP64 */
+    double seconds;         /* wall time of the solve on the device */
+    nb_status status;
+    int history_len;        /* entries written to history_host */
+    double *history_host;   /* caller-provided, history_cap entries, or NULL */
+    int history_cap;
+    int64_t launches;       /* kernels launched by the solve (graph nodes included) */
+} nb_stats;
+
+/* Library version string. */
+const char *nb_version(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *nb_last_error(void);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on, or NULL for a stream owned by the context; that stream is
+ * a blocking stream, so it is ordered with work on the legacy default stream.
+ * The solver captures CUDA graphs on the context's stream, so it must not be
+ * the legacy default stream itself (pass NULL instead).
+ * Errors: NB_ERR_ARG (bad device), NB_ERR_CUDA. */
+nb_status nb_create(nb_ctx **ctx, int device, void *cuda_stream);
+
+/* Replace the stream used by later calls (NULL: the context's own stream). */
+nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
+
+nb_status nb_destroy(nb_ctx *ctx);
+
+/* Build the box mesh of nx*ny*nz hexahedral elements of order N (1 <= N <= 15)
+ * on the unit cube, nodes at the Gauss-Lobatto-Legendre points, displaced by
+ * a*sin(pi x)sin(pi y)sin(pi z) in each coordinate with a = deform/max(nx,ny,nz),
+ * and compute on the device the six geometric factors per node (FP64 and FP32
+ * copies).  The paper keeps this initialisation in double (Section 6, step 3).
+ * Errors: NB_ERR_ARG (sizes), NB_ERR_MESH (a non-positive Jacobian),
+ * NB_ERR_OOM. */
+nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N,
+                        double deform, nb_mesh **out);
+
+/* Build the global numbering, multiplicities, Dirichlet mask (homogeneous on
+ * the box boundary), the gather-scatter lists of shared or masked nodes, the
+ * dot-product weights c = 1/multiplicity and the Jacobi inverse diagonal.
+ * Must follow nb_setup_mesh.  Errors: NB_ERR_STATE, NB_ERR_OOM, NB_ERR_CUDA. */
+nb_status nb_setup_gs(nb_mesh *mesh);
+
+nb_status nb_mesh_destroy(nb_mesh *mesh);
+
+/* Sizes: out[0]=E, out[1]=N, out[2]=n_local, out[3]=n_global,
+ * out[4]=number of gather-scatter rows (shared or masked global nodes),
+ * out[5]=total local copies in those rows, out[6..8]=nx,ny,nz. */
+nb_status nb_mesh_sizes(const nb_mesh *mesh, int64_t out[9]);
+
+/* Copy the index maps to host buffers for inspection (any may be NULL):
+ * gid[n_local] global node of each local node; mult[n_global];
+ * mask[n_global] (1 free, 0 Dirichlet); gs_row_gid[rows] global node of each
+ * gather-scatter row (ascending); gs_off[rows+1] row offsets; gs_loc[copies]
+ * local copies of each row in ascending order; gs_mask[rows]. */
+nb_status nb_get_maps(const nb_mesh *mesh, int32_t *gid, int32_t *mult,
+                      uint8_t *mask, int32_t *gs_row_gid, int32_t *gs_off,
+                      int32_t *gs_loc, uint8_t *gs_mask);
+
+/* Copy geometry to host buffers (any may be NULL): G[E][6][n^3] in FP64,
+ * order (rr, rs, rt, ss, st, tt); dinv[n_local] Jacobi inverse diagonal
+ * (0 on Dirichlet nodes); c[n_local] = 1/multiplicity. */
+nb_status nb_get_geom(const nb_mesh *mesh, double *G, double *dinv, double *c);
+
+/* u_L = Q u_G: copy each global value to all its local copies; masked != 0
+ * also zeroes Dirichlet nodes.  Both vectors in the precision's type. */
+nb_status nb_to_local(nb_mesh *mesh, nb_prec prec, const void *ug_dev,
+                      void *uL_dev, int masked);
+
+/* u_G = value of a continuous L-vector at each global node (first copy). */
+nb_status nb_to_global(nb_mesh *mesh, nb_prec prec, const void *uL_dev,
+                       void *ug_dev);
+
+/* Matrix-free operator ax (Table 1 line 5): w_L = A_L u_L element by element,
+ * A_e = D^T G D over the n^3 GLL nodes with six geometric factors per node
+ * (local_grad3, geometric factors, local_grad3_t).  assemble != 0 follows
+ * with the direct-stiffness summation and the Dirichlet mask (dssum), giving
+ * the assembled operator on continuous vectors.  u_dev and w_dev must not
+ * overlap.  prec: NB_FP64 (double), NB_FP32 (float), NB_TC_F16/NB_TC_BF16
+ * (float vectors; derivative contractions on tensor cores, FP32 accumulate). */
+nb_status nb_ax(nb_mesh *mesh, nb_prec prec, int assemble, const void *u_dev,
+                void *w_dev);
+
+/* Direct-stiffness summation in place (gather-scatter over shared nodes, sum
+ * in ascending local index), then the Dirichlet mask if masked != 0.
+ * Deterministic: the same input gives bit-identical output. */
+nb_status nb_dssum(nb_mesh *mesh, nb_prec prec, void *u_dev, int masked);
+
+/* glsc3 (Table 1 lines 3, 6, 9): *out_host = sum_l a_l b_l c_l with
+ * c = 1/multiplicity; products in the precision's type, accumulated in FP64
+ * in a fixed order (deterministic). */
+nb_status nb_glsc3(nb_mesh *mesh, nb_prec prec, const void *a_dev,
+                   const void *b_dev, double *out_host);
+
+/* Fill opts with defaults: FP32 inner solve with FP64 refinement, Jacobi,
+ * rtol 1e-10, maxiter 10000, inner_rtol 1e-4, max_outer 30, use_graph 1,
+ * record_history 0, use_x0 0. */
+void nb_default_opts(nb_opts *opts);
+
+/* Solve A x = b for the assembled, masked operator.  b_dev and x_dev are FP64
+ * L-vectors; b must be continuous and zero on Dirichlet nodes; with use_x0 = 1
+ * x_dev holds the initial guess on entry (continuous, masked); it holds the
+ * solution on exit.
+ * NB_FP64: preconditioned CG in the order of Table 1, all in FP64.
+ * With use_x0 = 0 the initial guess is zero and x_dev is only written.
+ * Other precisions: FP64 iterative refinement -- r = b - A x in FP64, an inner
+ * PCG (or flexible CG with NB_PC_LEARNED) in the reduced precision with FP64
+ * dot-product accumulation, then x += correction in FP64 -- until the FP64
+ * residual meets rtol.  stats may be NULL.
+ * Returns NB_OK, a positive outcome, or a negative error. */
+nb_status nb_solve(nb_mesh *mesh, const nb_opts *opts, const double *b_dev,
+                   double *x_dev, nb_stats *stats);
+
+/* nb_solve with host G-vectors: bg_host[n_global] right-hand side (masked on
+ * the device), xg_host[n_global] solution (initial guess zero).  Copies
+ * host->device and device->host inside the call. */
+nb_status nb_solve_host(nb_mesh *mesh, const nb_opts *opts,
+                        const double *bg_host, double *xg_host, nb_stats *stats);
+
+/* Measure the operator kernel: `reps` launches on the context's stream, each
+ * bracketed by CUDA events, with `flush_bytes` of `flush_dev` overwritten
+ * between launches (outside the events) to evict the L2 cache; flush_dev may
+ * be NULL.  cg_step = 0 times ax (u -> w, the nb_ax kernel); cg_step = 1 times
+ * the fused CG-step kernel of the solver (p = dinv*r + beta*p, w = A_L p,
+ * partial p.w) on the mesh's solve workspace.  variant: -1 for the current
+ * choice, else a kernel variant index (see nb_autotune).  *ms_out = mean
+ * milliseconds per launch.  Errors: NB_ERR_ARG, NB_ERR_STATE, NB_ERR_CUDA. */
+nb_status nb_time_ax(nb_mesh *mesh, nb_prec prec, int cg_step, int variant, int reps,
+                     void *flush_dev, size_t flush_bytes, double *ms_out);
+
+/* Number of operator kernel variants available for (mesh order, prec). */
+int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
+
+/* Autotuner: time every operator variant for this mesh's order and
+ * precision with nb_time_ax (cg_step = 1, `reps` launches each) and keep the
+ * fastest for later calls.  *best_variant and *best_ms (may be NULL) receive
+ * the choice.  Variants differ only in launch shape and in how sums inside
+ * one element are associated, so their results agree to rounding. */
+nb_status nb_autotune(nb_mesh *mesh, nb_prec prec, int reps, void *flush_dev,
+                      size_t flush_bytes, int *best_variant, double *best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEKBONE_GB300_H */

@@ -1,0 +1,276 @@
+"""Python binding of the sm_103a spectral-element CG library.
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+``_build/libnekbone_gb300.so`` (C ABI in ``include/nekbone_gb300.h``).  The
+functions below carry the C names; ``Mesh`` bundles them for convenience.
+Device vectors are ``torch`` CUDA tensors (PyTorch provides memory and
+streams only).  If the library has not been built, importing this module
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnekbone_gb300.so")
+
+NB_OK, NB_ERR_ARG, NB_ERR_CUDA, NB_ERR_OOM, NB_ERR_MESH, NB_ERR_STATE = 0, -1, -2, -3, -4, -5
+NB_NOT_CONVERGED, NB_STAGNATED, NB_BREAKDOWN, NB_FELL_BACK = 1, 2, 3, 4
+NB_FP64, NB_FP32, NB_TC_F16, NB_TC_BF16 = 0, 1, 2, 3
+NB_PC_NONE, NB_PC_JACOBI, NB_PC_LEARNED = 0, 1, 2
+STATUS_NAMES = {0: "ok", -1: "invalid argument", -2: "cuda error", -3: "out of memory",
+                -4: "invalid mesh", -5: "bad state", 1: "not converged", 2: "stagnated",
+                3: "breakdown", 4: "fell back"}
+PREC_NAMES = {"fp64": NB_FP64, "fp32": NB_FP32, "tc_f16": NB_TC_F16, "tc_bf16": NB_TC_BF16}
+
+
+class NbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nb_opts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("pc", C.c_int), ("rtol", C.c_double), ("maxiter", C.c_int),
+                ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("use_graph", C.c_int),
+                ("record_history", C.c_int), ("use_x0", C.c_int)]
+
+
+class nb_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("rel_res", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int), ("history_len", C.c_int),
+                ("history_host", C.POINTER(C.c_double)), ("history_cap", C.c_int),
+                ("launches", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"CUDA library not built ({LIB_PATH}); run `python -c 'import __graft_entry__ as g; "
+            f"g.build()'` on a machine with nvcc")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "nb_version": (C.c_char_p, []),
+        "nb_last_error": (C.c_char_p, []),
+        "nb_create": (i32, [C.POINTER(vp), i32, vp]),
+        "nb_set_stream": (i32, [vp, vp]),
+        "nb_destroy": (i32, [vp]),
+        "nb_setup_mesh": (i32, [vp, i32, i32, i32, i32, dbl, C.POINTER(vp)]),
+        "nb_setup_gs": (i32, [vp]),
+        "nb_mesh_destroy": (i32, [vp]),
+        "nb_mesh_sizes": (i32, [vp, C.POINTER(i64)]),
+        "nb_get_maps": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "nb_get_geom": (i32, [vp, vp, vp, vp]),
+        "nb_to_local": (i32, [vp, i32, vp, vp, i32]),
+        "nb_to_global": (i32, [vp, i32, vp, vp]),
+        "nb_ax": (i32, [vp, i32, i32, vp, vp]),
+        "nb_dssum": (i32, [vp, i32, vp, i32]),
+        "nb_glsc3": (i32, [vp, i32, vp, vp, C.POINTER(dbl)]),
+        "nb_default_opts": (None, [C.POINTER(nb_opts)]),
+        "nb_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
+        "nb_solve_host": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
+        "nb_time_ax": (i32, [vp, i32, i32, i32, i32, vp, C.c_size_t, C.POINTER(dbl)]),
+        "nb_ax_variants": (i32, [vp, i32]),
+        "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+def check(status, allow_positive=True):
+    if status < 0 or (status > 0 and not allow_positive):
+        raise NbError(status, lib.nb_last_error().decode())
+    return status
+
+
+def nb_version() -> str:
+    return lib.nb_version().decode()
+
+
+def default_opts(**kw) -> nb_opts:
+    o = nb_opts()
+    lib.nb_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC_NAMES[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """nb_create/nb_destroy.  With ``stream=None`` (or torch's legacy default
+    stream) the library issues work on a stream of its own that is ordered
+    with the legacy default stream, so tensors produced by ordinary torch
+    calls are ready when the library reads them."""
+
+    def __init__(self, device: int = 0, stream=None):
+        handle = None
+        if stream is not None and stream.cuda_stream:
+            handle = C.c_void_p(stream.cuda_stream)
+        self.stream = stream
+        h = C.c_void_p()
+        check(lib.nb_create(C.byref(h), device, handle))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            lib.nb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """A box mesh with its gather-scatter set up (nb_setup_mesh + nb_setup_gs)."""
+
+    def __init__(self, ctx: Context, nx, ny, nz, N, deform=0.0, setup_gs=True):
+        h = C.c_void_p()
+        check(lib.nb_setup_mesh(ctx.h, nx, ny, nz, N, float(deform), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        if setup_gs:
+            check(lib.nb_setup_gs(self.h))
+        s = (C.c_int64 * 9)()
+        check(lib.nb_mesh_sizes(self.h, s))
+        self.E, self.N, self.n_local, self.n_global, self.gs_rows, self.gs_copies = list(s)[:6]
+        self.nx, self.ny, self.nz = list(s)[6:9]
+
+    @classmethod
+    def from_box(cls, ctx, box, **kw):
+        return cls(ctx, box.nx, box.ny, box.nz, box.N, box.deform, **kw)
+
+    def close(self):
+        if self.h:
+            lib.nb_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- inspection
+    def maps(self):
+        gid = np.zeros(self.n_local, np.int32)
+        mult = np.zeros(self.n_global, np.int32)
+        mask = np.zeros(self.n_global, np.uint8)
+        rgid = np.zeros(max(self.gs_rows, 1), np.int32)
+        roff = np.zeros(self.gs_rows + 1, np.int32)
+        rloc = np.zeros(max(self.gs_copies, 1), np.int32)
+        rmask = np.zeros(max(self.gs_rows, 1), np.uint8)
+        check(lib.nb_get_maps(self.h, _ptr(gid), _ptr(mult), _ptr(mask), _ptr(rgid), _ptr(roff),
+                              _ptr(rloc), _ptr(rmask)))
+        return dict(gid=gid, mult=mult, mask=mask, gs_gid=rgid[:self.gs_rows], gs_off=roff,
+                    gs_loc=rloc[:self.gs_copies], gs_mask=rmask[:self.gs_rows])
+
+    def geom(self):
+        G = np.zeros(6 * self.n_local)
+        dinv = np.zeros(self.n_local)
+        c = np.zeros(self.n_local)
+        check(lib.nb_get_geom(self.h, _ptr(G), _ptr(dinv), _ptr(c)))
+        return G.reshape(self.E, 6, -1), dinv, c
+
+    # --- operations on torch CUDA tensors
+    def _vec(self, t, prec, n=None):
+        import torch
+        n = self.n_local if n is None else n
+        want = torch.float64 if prec == NB_FP64 else torch.float32
+        if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.numel() == n):
+            raise NbError(NB_ERR_ARG, f"expected contiguous CUDA {want} tensor of {n} values")
+        return _ptr(t)
+
+    def to_local(self, prec, ug, uL, masked=True):
+        check(lib.nb_to_local(self.h, prec, self._vec(ug, prec, self.n_global),
+                              self._vec(uL, prec), int(masked)))
+
+    def to_global(self, prec, uL, ug):
+        check(lib.nb_to_global(self.h, prec, self._vec(uL, prec), self._vec(ug, prec, self.n_global)))
+
+    def ax(self, prec, u, w, assemble=False):
+        check(lib.nb_ax(self.h, prec, int(assemble), self._vec(u, prec), self._vec(w, prec)))
+
+    def dssum(self, prec, u, masked=True):
+        check(lib.nb_dssum(self.h, prec, self._vec(u, prec), int(masked)))
+
+    def glsc3(self, prec, a, b) -> float:
+        out = C.c_double()
+        check(lib.nb_glsc3(self.h, prec, self._vec(a, prec), self._vec(b, prec), C.byref(out)))
+        return out.value
+
+    def solve(self, b, x, opts: nb_opts | None = None, history_cap=0, raise_on_outcome=False):
+        opts = opts or default_opts()
+        st = nb_stats()
+        hist = None
+        if history_cap:
+            hist = np.zeros(history_cap)
+            st.history_host = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.history_cap = history_cap
+            opts.record_history = 1
+        r = check(lib.nb_solve(self.h, C.byref(opts), self._vec(b, NB_FP64), self._vec(x, NB_FP64),
+                               C.byref(st)), allow_positive=not raise_on_outcome)
+        out = dict(status=r, iters=st.iters, outer_iters=st.outer_iters, rel_res=st.rel_res,
+                   seconds=st.seconds, launches=st.launches)
+        if hist is not None:
+            out["history"] = hist[:st.history_len].copy()
+        return out
+
+    def solve_host(self, bg: np.ndarray, xg: np.ndarray, opts: nb_opts | None = None):
+        """bg, xg: host float64 arrays of n_global values (pinned or pageable)."""
+        opts = opts or default_opts()
+        st = nb_stats()
+        if hasattr(bg, "data_ptr"):
+            pb, px = C.c_void_p(bg.data_ptr()), C.c_void_p(xg.data_ptr())
+        else:
+            assert bg.dtype == np.float64 and xg.dtype == np.float64
+            pb, px = _ptr(bg), _ptr(xg)
+        r = check(lib.nb_solve_host(self.h, C.byref(opts), pb, px, C.byref(st)))
+        return dict(status=r, iters=st.iters, outer_iters=st.outer_iters, rel_res=st.rel_res,
+                    seconds=st.seconds, launches=st.launches)
+
+    # --- measurement
+    def time_ax(self, prec, cg_step=True, variant=-1, reps=10, flush=None) -> float:
+        """Mean milliseconds per operator launch (CUDA events, L2 flushed
+        between launches by overwriting ``flush``, a CUDA byte tensor)."""
+        ms = C.c_double()
+        fp, fb = (_ptr(flush), flush.numel() * flush.element_size()) if flush is not None else (None, 0)
+        check(lib.nb_time_ax(self.h, prec, int(cg_step), variant, reps, fp, fb, C.byref(ms)))
+        return ms.value
+
+    def ax_variants(self, prec) -> int:
+        return lib.nb_ax_variants(self.h, prec)
+
+    def autotune(self, prec, reps=5, flush=None):
+        v, ms = C.c_int(), C.c_double()
+        fp, fb = (_ptr(flush), flush.numel() * flush.element_size()) if flush is not None else (None, 0)
+        check(lib.nb_autotune(self.h, prec, reps, fp, fb, C.byref(v), C.byref(ms)))
+        return v.value, ms.value
+
+
+__all__ = ["lib", "LIB_PATH", "NbError", "Context", "Mesh", "default_opts", "check",
+           "nb_opts", "nb_stats", "nb_version", "PREC_NAMES",
+           "NB_FP64", "NB_FP32", "NB_TC_F16", "NB_TC_BF16", "NB_PC_NONE", "NB_PC_JACOBI",
+           "NB_PC_LEARNED", "NB_OK", "NB_NOT_CONVERGED", "NB_STAGNATED", "NB_BREAKDOWN",
+           "NB_FELL_BACK"]

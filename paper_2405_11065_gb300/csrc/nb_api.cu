@@ -1,0 +1,461 @@
+// The C ABI (include/nekbone_gb300.h): argument validation, object lifetime,
+// and dispatch to the device code.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nb_internal.h"
+
+namespace nb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static nb_status arg_error(const char *what)
+{
+    set_error("invalid argument: %s", what);
+    return NB_ERR_ARG;
+}
+
+static bool prec_ok(nb_prec p) { return p >= NB_FP64 && p <= NB_TC_BF16; }
+
+static void free_ws(Workspace &ws)
+{
+    if (ws.exec) cudaGraphExecDestroy(ws.exec);
+    if (ws.graph) cudaGraphDestroy(ws.graph);
+    cudaFree(ws.x);
+    cudaFree(ws.r);
+    cudaFree(ws.p);
+    cudaFree(ws.w);
+    cudaFree(ws.z);
+    cudaFree(ws.aux);
+    cudaFree(ws.part);
+    cudaFree(ws.scal);
+    cudaFree(ws.hist);
+    if (ws.scal_host) cudaFreeHost(ws.scal_host);
+    ws = Workspace();
+}
+
+void learned_free(nb_mesh *m);  // nb_learned.cu
+
+}  // namespace nb
+
+using namespace nb;
+
+extern "C" {
+
+const char *nb_version(void) { return "nekbone-gb300 0.1 (sm_103a)"; }
+
+const char *nb_last_error(void) { return g_err; }
+
+nb_status nb_create(nb_ctx **ctx, int device, void *cuda_stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    *ctx = nullptr;
+    int count = 0;
+    NB_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return arg_error("device index out of range");
+    NB_CUDA(cudaSetDevice(device));
+    nb_ctx *c = new nb_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        NB_CUDA(e);
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        // a blocking stream: ordered with work on the legacy default stream
+        e = cudaStreamCreate(&c->own_stream);
+        if (e != cudaSuccess) {
+            delete c;
+            NB_CUDA(e);
+        }
+        c->stream = c->own_stream;
+    }
+    *ctx = c;
+    return NB_OK;
+}
+
+nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return arg_error("ctx is NULL");
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (!ctx->own_stream) NB_CUDA(cudaStreamCreate(&ctx->own_stream));
+        ctx->stream = ctx->own_stream;
+    }
+    return NB_OK;
+}
+
+nb_status nb_destroy(nb_ctx *ctx)
+{
+    if (!ctx) return NB_OK;
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return NB_OK;
+}
+
+nb_status nb_mesh_destroy(nb_mesh *m)
+{
+    if (!m) return NB_OK;
+    cudaSetDevice(m->ctx->device);
+    cudaStreamSynchronize(m->ctx->stream);
+    learned_free(m);
+    free_ws(m->ws64);
+    free_ws(m->ws32);
+    void *bufs[] = {m->D64, m->D32, m->G64, m->G32, m->gid, m->gs_off, m->gs_loc, m->gs_gid,
+                    m->gs_mask, m->g_first, m->mask_g, m->c32, m->dinv64, m->dinv32,
+                    m->ones64, m->ones32, m->r64, m->w64, m->x64, m->b64, m->g64, m->part64,
+                    m->red_out};
+    for (void *b : bufs) cudaFree(b);
+    if (m->red_host) cudaFreeHost(m->red_host);
+    delete m;
+    return NB_OK;
+}
+
+nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double deform,
+                        nb_mesh **out)
+{
+    if (!ctx || !out) return arg_error("NULL ctx or out");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return arg_error("element counts must be >= 1");
+    if (N < 1 || N > kMaxN) {
+        set_error("order N=%d outside [1, %d]", N, kMaxN);
+        return NB_ERR_MESH;
+    }
+    if (!(deform >= 0.0) || !isfinite(deform)) return arg_error("deform must be finite, >= 0");
+    const int64_t n = N + 1;
+    const int64_t E = (int64_t)nx * ny * nz;
+    const int64_t nL = E * n * n * n;
+    const int64_t nG = ((int64_t)nx * N + 1) * ((int64_t)ny * N + 1) * ((int64_t)nz * N + 1);
+    if (nL >= (int64_t)1 << 31 || nG >= (int64_t)1 << 31)
+        return arg_error("mesh too large for 32-bit local/global indices");
+    NB_CUDA(cudaSetDevice(ctx->device));
+    nb_mesh *m = new nb_mesh();
+    m->ctx = ctx;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    m->N = N;
+    m->n = N + 1;
+    m->n3 = m->n * m->n * m->n;
+    m->deform = deform;
+    m->E = E;
+    m->nL = nL;
+    m->nG = nG;
+    nb_status st = build_geometry(m);
+    if (st != NB_OK) {
+        nb_mesh_destroy(m);
+        return st;
+    }
+    *out = m;
+    return NB_OK;
+}
+
+nb_status nb_setup_gs(nb_mesh *m)
+{
+    if (!m) return arg_error("mesh is NULL");
+    if (m->gs_ready) return NB_OK;
+    if (!m->G64) {
+        set_error("nb_setup_gs before nb_setup_mesh");
+        return NB_ERR_STATE;
+    }
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    return build_gs(m);
+}
+
+nb_status nb_mesh_sizes(const nb_mesh *m, int64_t out[9])
+{
+    if (!m || !out) return arg_error("NULL mesh or out");
+    out[0] = m->E;
+    out[1] = m->N;
+    out[2] = m->nL;
+    out[3] = m->nG;
+    out[4] = m->gs_rows;
+    out[5] = m->gs_copies;
+    out[6] = m->nx;
+    out[7] = m->ny;
+    out[8] = m->nz;
+    return NB_OK;
+}
+
+static nb_status need_gs(const nb_mesh *m)
+{
+    if (!m) return arg_error("mesh is NULL");
+    if (!m->gs_ready) {
+        set_error("call nb_setup_gs first");
+        return NB_ERR_STATE;
+    }
+    return NB_OK;
+}
+
+nb_status nb_get_maps(const nb_mesh *m, int32_t *gid, int32_t *mult, uint8_t *mask,
+                      int32_t *gs_row_gid, int32_t *gs_off, int32_t *gs_loc, uint8_t *gs_mask)
+{
+    NB_TRY(need_gs(m));
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    if (gid) NB_CUDA(cudaMemcpy(gid, m->gid, sizeof(int32_t) * m->nL, cudaMemcpyDeviceToHost));
+    if (mult) memcpy(mult, m->mult_host.data(), sizeof(int32_t) * m->nG);
+    if (mask) memcpy(mask, m->mask_host.data(), m->nG);
+    if (gs_row_gid && m->gs_rows)
+        NB_CUDA(cudaMemcpy(gs_row_gid, m->gs_gid, sizeof(int32_t) * m->gs_rows,
+                           cudaMemcpyDeviceToHost));
+    if (gs_off)
+        NB_CUDA(cudaMemcpy(gs_off, m->gs_off, sizeof(int32_t) * (m->gs_rows + 1),
+                           cudaMemcpyDeviceToHost));
+    if (gs_loc && m->gs_copies)
+        NB_CUDA(cudaMemcpy(gs_loc, m->gs_loc, sizeof(int32_t) * m->gs_copies,
+                           cudaMemcpyDeviceToHost));
+    if (gs_mask && m->gs_rows)
+        NB_CUDA(cudaMemcpy(gs_mask, m->gs_mask, m->gs_rows, cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+nb_status nb_get_geom(const nb_mesh *m, double *G, double *dinv, double *c)
+{
+    if (!m) return arg_error("mesh is NULL");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    if (G) NB_CUDA(cudaMemcpy(G, m->G64, sizeof(double) * 6 * m->nL, cudaMemcpyDeviceToHost));
+    if (dinv || c) NB_TRY(need_gs(m));
+    if (dinv)
+        NB_CUDA(cudaMemcpy(dinv, m->dinv64, sizeof(double) * m->nL, cudaMemcpyDeviceToHost));
+    if (c) {
+        float *tmp = (float *)malloc(sizeof(float) * m->nL);
+        if (!tmp) return NB_ERR_OOM;
+        cudaError_t e = cudaMemcpy(tmp, m->c32, sizeof(float) * m->nL, cudaMemcpyDeviceToHost);
+        for (int64_t l = 0; e == cudaSuccess && l < m->nL; ++l) c[l] = tmp[l];
+        free(tmp);
+        NB_CUDA(e);
+    }
+    return NB_OK;
+}
+
+nb_status nb_to_local(nb_mesh *m, nb_prec prec, const void *ug, void *uL, int masked)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !ug || !uL) return arg_error("precision or NULL vector");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_TRY(to_local(m, prec, ug, uL, masked, m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+nb_status nb_to_global(nb_mesh *m, nb_prec prec, const void *uL, void *ug)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !ug || !uL) return arg_error("precision or NULL vector");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_TRY(to_global(m, prec, uL, ug, m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+nb_status nb_ax(nb_mesh *m, nb_prec prec, int assemble, const void *u, void *w)
+{
+    if (!m) return arg_error("mesh is NULL");
+    if (!prec_ok(prec) || !u || !w) return arg_error("precision or NULL vector");
+    if (u == w) return arg_error("u and w must not overlap");
+    if (assemble) NB_TRY(need_gs(m));
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    NB_TRY(ax_local(m, prec, u, w, nullptr, nullptr, s));
+    if (assemble) NB_TRY(dssum(m, prec, w, 1, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    return NB_OK;
+}
+
+nb_status nb_dssum(nb_mesh *m, nb_prec prec, void *u, int masked)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !u) return arg_error("precision or NULL vector");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_TRY(dssum(m, prec, u, masked, m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+nb_status nb_glsc3(nb_mesh *m, nb_prec prec, const void *a, const void *b, double *out)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !a || !b || !out) return arg_error("precision or NULL pointer");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    if (!m->red_out) {
+        NB_CUDA(cudaMalloc(&m->red_out, sizeof(double) * 8));
+        NB_CUDA(cudaMallocHost(&m->red_host, sizeof(double) * 8));
+    }
+    if (!m->part64) NB_CUDA(cudaMalloc(&m->part64, sizeof(double) * kMaxPartials * 2));
+    NB_TRY(glsc3_dev(m, prec, a, b, m->part64, m->red_out + 2, s));
+    NB_CUDA(cudaMemcpyAsync(m->red_host + 2, m->red_out + 2, sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    *out = m->red_host[2];
+    return NB_OK;
+}
+
+void nb_default_opts(nb_opts *o)
+{
+    if (!o) return;
+    o->prec = NB_FP32;
+    o->pc = NB_PC_JACOBI;
+    o->rtol = 1e-10;
+    o->maxiter = 10000;
+    o->inner_rtol = 1e-4;
+    o->max_outer = 30;
+    o->use_graph = 1;
+    o->record_history = 0;
+    o->use_x0 = 0;
+}
+
+static nb_status check_opts(const nb_opts *o)
+{
+    if (!o) return arg_error("opts is NULL");
+    if (!prec_ok(o->prec)) return arg_error("opts.prec");
+    if (o->pc < NB_PC_NONE || o->pc > NB_PC_LEARNED) return arg_error("opts.pc");
+    if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return arg_error("opts.rtol must be in (0,1)");
+    if (o->maxiter < 0) return arg_error("opts.maxiter");
+    if (o->prec != NB_FP64 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0)))
+        return arg_error("opts.inner_rtol must be in (0,1)");
+    if (o->max_outer < 0) return arg_error("opts.max_outer");
+    if (o->pc == NB_PC_LEARNED && o->prec == NB_FP64)
+        return arg_error("the learned preconditioner runs inside refinement (prec != NB_FP64)");
+    return NB_OK;
+}
+
+nb_status nb_solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_stats *st)
+{
+    NB_TRY(need_gs(m));
+    NB_TRY(check_opts(o));
+    if (!b || !x) return arg_error("NULL b or x");
+    if (o->pc == NB_PC_LEARNED && !m->learned) {
+        set_error("no learned preconditioner attached to this mesh");
+        return NB_ERR_STATE;
+    }
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    if (st) st->history_len = 0;
+    return solve(m, o, b, x, st);
+}
+
+nb_status nb_solve_host(nb_mesh *m, const nb_opts *o, const double *bg, double *xg, nb_stats *st)
+{
+    NB_TRY(need_gs(m));
+    NB_TRY(check_opts(o));
+    if (!bg || !xg) return arg_error("NULL host vector");
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    if (!m->b64) {
+        NB_CUDA(cudaMalloc(&m->b64, sizeof(double) * m->nL));
+        NB_CUDA(cudaMalloc(&m->x64, sizeof(double) * m->nL));
+    }
+    if (!m->g64) NB_CUDA(cudaMalloc(&m->g64, sizeof(double) * m->nG));
+    double *gbuf = m->g64;
+    NB_CUDA(cudaMemcpyAsync(gbuf, bg, sizeof(double) * m->nG, cudaMemcpyHostToDevice, s));
+    nb_status r = to_local(m, NB_FP64, gbuf, m->b64, 1, s);
+    nb_opts o2 = *o;
+    o2.use_x0 = 0;
+    if (r >= 0) r = solve(m, &o2, m->b64, m->x64, st);
+    if (r >= 0) {
+        nb_status r2 = to_global(m, NB_FP64, m->x64, gbuf, s);
+        if (r2 < 0) r = r2;
+    }
+    cudaError_t e = cudaSuccess;
+    if (r >= 0) e = cudaMemcpyAsync(xg, gbuf, sizeof(double) * m->nG, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        set_error("nb_solve_host: %s", cudaGetErrorString(e));
+        return NB_ERR_CUDA;
+    }
+    return r;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// operator timing and autotuning
+// ---------------------------------------------------------------------------
+
+extern "C" int nb_ax_variants(const nb_mesh *m, nb_prec prec)
+{
+    if (!m || !prec_ok(prec)) return 0;
+    return ax_variant_count(m, prec);
+}
+
+extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int variant, int reps,
+                                void *flush_dev, size_t flush_bytes, double *ms_out)
+{
+    if (!m || !ms_out || reps < 1 || !prec_ok(prec)) return arg_error("mesh, prec, reps or out");
+    if (variant >= ax_variant_count(m, prec)) return arg_error("variant index");
+    if (cg_step) NB_TRY(need_gs(m));
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    Workspace &ws = prec == NB_FP64 ? m->ws64 : m->ws32;
+    NB_TRY(ensure_ws(m, ws, prec == NB_FP64 ? 8 : 4, 0));
+    NB_CUDA(cudaMemsetAsync(ws.scal, 0, sizeof(CgScalars), s));  // beta = 0, not done
+    const int saved = m->ax_cfg[prec].variant;
+    if (variant >= 0) m->ax_cfg[prec].variant = variant;
+    const void *dinv = prec == NB_FP64 ? (const void *)m->dinv64 : (const void *)m->dinv32;
+    std::vector<cudaEvent_t> ev(2 * reps);
+    nb_status st = NB_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) st = NB_ERR_CUDA;
+    for (int r = 0; st == NB_OK && r < reps; ++r) {
+        if (flush_dev && flush_bytes) cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, s);
+        cudaEventRecord(ev[2 * r], s);
+        if (cg_step)
+            st = ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, nullptr, s);
+        else
+            st = ax_local(m, prec, ws.p, ws.w, nullptr, nullptr, s);
+        cudaEventRecord(ev[2 * r + 1], s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    double tot = 0.0;
+    for (int r = 0; st == NB_OK && e == cudaSuccess && r < reps; ++r) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+        tot += ms;
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    m->ax_cfg[prec].variant = saved;
+    if (st != NB_OK) return st;
+    NB_CUDA(e);
+    *ms_out = tot / reps;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_autotune(nb_mesh *m, nb_prec prec, int reps, void *flush_dev,
+                                 size_t flush_bytes, int *best_variant, double *best_ms)
+{
+    if (!m || !prec_ok(prec) || reps < 1) return arg_error("mesh, prec or reps");
+    NB_TRY(need_gs(m));
+    const int nv = ax_variant_count(m, prec);
+    int best = 0;
+    double bms = 1e300;
+    for (int v = 0; v < nv; ++v) {
+        double ms = 0.0;
+        NB_TRY(nb_time_ax(m, prec, 1, v, 1, flush_dev, flush_bytes, &ms));  // warm-up
+        NB_TRY(nb_time_ax(m, prec, 1, v, reps, flush_dev, flush_bytes, &ms));
+        if (ms < bms) {
+            bms = ms;
+            best = v;
+        }
+    }
+    m->ax_cfg[prec].variant = best;
+    if (best_variant) *best_variant = best;
+    if (best_ms) *best_ms = bms;
+    return NB_OK;
+}

@@ -1,0 +1,32 @@
+// CUDA-core operator instantiations for float (see nb_ax_impl.cuh).
+#include "nb_ax_impl.cuh"
+
+namespace nb {
+
+// Derivative matrices of every order: c_D[n][i][l] = D[i][l] for n = N+1.
+static __constant__ float c_D[kMaxn + 1][kMaxn][kMaxn];
+
+template <>
+__device__ __forceinline__ float dtab<float>(int n, int i, int l)
+{
+    return c_D[n][i][l];
+}
+
+nb_status upload_D_f32(int n, const double *D)
+{
+    float tab[kMaxn * kMaxn] = {};
+    for (int i = 0; i < n; ++i)
+        for (int l = 0; l < n; ++l) tab[i * kMaxn + l] = (float)D[i * n + l];
+    NB_CUDA(cudaMemcpyToSymbol(c_D, tab, sizeof(tab), sizeof(tab) * n, cudaMemcpyHostToDevice));
+    return NB_OK;
+}
+
+nb_status ax_cc_f32(int n, int mchoice, bool pupd, int sm_count, long long E, const float *G,
+                      const float *u, float *w, const float *r, const float *dinv, float *p,
+                      const CgScalars *scal, double *part, int *grid, cudaStream_t s)
+{
+    return dispatch_ax_cc<float>(n, mchoice, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part,
+                                grid, s);
+}
+
+}  // namespace nb

@@ -1,0 +1,169 @@
+// Internal declarations shared by the translation units of the library.
+// Not part of the public C ABI (include/nekbone_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nekbone_gb300.h"
+
+namespace nb {
+
+constexpr int kMaxN = 15;          // highest polynomial order supported
+constexpr int kMaxn = kMaxN + 1;   // GLL points per direction
+constexpr int kFinalizeThreads = 512;
+constexpr int kMaxPartials = 1 << 16;
+
+void set_error(const char *fmt, ...);
+
+#define NB_CUDA(call)                                                               \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::nb::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,              \
+                            cudaGetErrorString(e_));                                \
+            return e_ == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;      \
+        }                                                                           \
+    } while (0)
+
+#define NB_TRY(expr)                     \
+    do {                                 \
+        nb_status s_ = (expr);           \
+        if (s_ < 0) return s_;           \
+    } while (0)
+
+// Device-resident scalars of one CG solve.  Every kernel of the iteration
+// reads alpha/beta from here, so a captured graph needs no host values.
+struct CgScalars {
+    double rtz;       // (r, c, z) of the current iteration
+    double rtz_old;   // of the previous iteration
+    double pap;       // (w, c, p)
+    double rtr;       // (r, c, r)
+    double alpha, beta;
+    double bnorm2;    // (b, c, b) of the system being solved
+    double relres;    // sqrt(rtr / bnorm2)
+    double tol;       // relative tolerance
+    double fcg_zw;    // flexible CG: (z, c, w_prev)
+    double pap_prev;  // flexible CG: previous (p, c, A p)
+    double rp;        // flexible CG: (r, c, p)
+    int iter;         // iterations done
+    int maxit;        // iteration limit
+    int done;         // 1 when the loop must stop
+    int status;       // 0 running/converged, NB_NOT_CONVERGED, NB_BREAKDOWN
+    int hist_cap;     // capacity of hist
+    int pad_;
+    double *hist;     // device history (relres per iteration) or nullptr
+};
+
+// A preallocated set of vectors for one solve precision.
+struct Workspace {
+    size_t nL = 0;
+    int elt = 0;                  // bytes per value (4 or 8)
+    void *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr;
+    void *aux = nullptr;          // flexible CG: previous A p
+    double *part = nullptr;       // per-block partial sums (kMaxPartials * 3)
+    CgScalars *scal = nullptr;    // device scalars
+    CgScalars *scal_host = nullptr;  // pinned mirror
+    double *hist = nullptr;       // device history buffer
+    int hist_cap = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_key = -1;           // which configuration the graph holds
+};
+
+// Launch shape of the ax kernel for one (precision, order).
+struct AxConfig {
+    int variant = -1;          // kernel variant id chosen by the autotuner (-1: default)
+    int grid = 0;              // blocks (persistent grid)
+    int threads = 0;
+};
+
+}  // namespace nb
+
+struct nb_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+};
+
+struct nb_mesh {
+    nb_ctx *ctx = nullptr;
+    int nx = 0, ny = 0, nz = 0, N = 0, n = 0, n3 = 0;
+    double deform = 0.0;
+    int64_t E = 0, nL = 0, nG = 0;
+    bool gs_ready = false;
+    // geometry
+    double *D64 = nullptr;     // n*n, D[i][l] = l_l'(xi_i)
+    float *D32 = nullptr;
+    double *G64 = nullptr;     // [E][6][n3]
+    float *G32 = nullptr;
+    // numbering and gather-scatter
+    int32_t *gid = nullptr;    // [nL]
+    int64_t gs_rows = 0, gs_copies = 0;
+    int32_t *gs_off = nullptr;   // [rows+1]
+    int32_t *gs_loc = nullptr;   // [copies]
+    int32_t *gs_gid = nullptr;   // [rows]
+    uint8_t *gs_mask = nullptr;  // [rows]
+    int32_t *g_first = nullptr;  // [nG] first local copy of each global node
+    uint8_t *mask_g = nullptr;   // [nG]
+    // weights and preconditioner
+    float *c32 = nullptr;      // [nL] 1/multiplicity (exact in float)
+    double *dinv64 = nullptr;  // [nL]
+    float *dinv32 = nullptr;
+    double *ones64 = nullptr;  // [nL] identity preconditioner (mask)
+    float *ones32 = nullptr;
+    // host copies of the small maps
+    std::vector<int32_t> mult_host;  // [nG]
+    std::vector<uint8_t> mask_host;  // [nG]
+    // solve workspaces
+    nb::Workspace ws64, ws32;
+    double *r64 = nullptr, *w64 = nullptr, *x64 = nullptr, *b64 = nullptr, *g64 = nullptr;
+    double *part64 = nullptr;
+    double *red_out = nullptr;       // device scalar for glsc3/norms
+    double *red_host = nullptr;      // pinned mirror
+    nb::AxConfig ax_cfg[4];
+    int64_t launches = 0;            // kernels issued by the current solve
+    // learned preconditioner (optional)
+    void *learned = nullptr;
+};
+
+namespace nb {
+
+// ---- setup (nb_setup.cu)
+nb_status gll_host(int N, double *xi, double *w);
+void deriv_host(int N, const double *xi, double *D);
+nb_status build_geometry(nb_mesh *m);
+nb_status build_gs(nb_mesh *m);
+
+// ---- operator (nb_ax.cu)
+nb_status upload_deriv_tables(int n, const double *D64);
+// w = A_L u on all elements; if pap_part != nullptr also per-block partials
+// of sum(u*w) (FP64); pupd: if non-null, u is first formed as
+// u = dinv*r + beta*u_old (CG direction update, see ax_cg_step).
+nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap_part,
+                   int *nparts, cudaStream_t s);
+nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, void *p,
+                     void *w, const CgScalars *scal, double *pap_part, int *nparts,
+                     cudaStream_t s);
+int ax_variant_count(const nb_mesh *m, nb_prec prec);
+
+// ---- gather-scatter and vectors (nb_vec.cu)
+nb_status dssum(nb_mesh *m, nb_prec prec, void *u, int masked, cudaStream_t s);
+nb_status to_local(nb_mesh *m, nb_prec prec, const void *ug, void *uL, int masked,
+                   cudaStream_t s);
+nb_status to_global(nb_mesh *m, nb_prec prec, const void *uL, void *ug, cudaStream_t s);
+nb_status glsc3_dev(nb_mesh *m, nb_prec prec, const void *a, const void *b, double *part,
+                    double *out_dev, cudaStream_t s);
+nb_status sum_partials_dev(const double *part, int cnt, double *out_dev, cudaStream_t s);
+nb_status local_diag(nb_mesh *m, double *diag, cudaStream_t s);
+nb_status finish_jacobi(nb_mesh *m, double *diag, cudaStream_t s);
+
+// ---- solvers (nb_solve.cu)
+nb_status ensure_ws(nb_mesh *m, Workspace &ws, int elt, int hist_cap);
+nb_status solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_stats *st);
+
+}  // namespace nb

@@ -1,0 +1,550 @@
+// Conjugate-gradient solvers on the device.
+//
+// The iteration follows Table 1 of the case study: z = solveM(r);
+// rtz1 = glsc3(r,c,z); p = beta p + z (add2s1); w = ax(p) with dssum;
+// pap = glsc3(w,c,p); x += alpha p, r -= alpha w (add2s2); rtr = glsc3(r,c,r).
+// On the GPU the nine lines become five launches per iteration:
+//   1. ax_cg_step: p = dinv*r + beta*p, w_L = A_L p, partials of p.w_L (= pap)
+//   2. dssum + mask of w
+//   3. fin_pap: pap, alpha = rtz/pap (breakdown check)
+//   4. update: x += alpha p, r -= alpha w, partials of (r,c,dinv r), (r,c,r)
+//   5. fin_iter: rtz, rtr, beta = rtz/rtz_old, convergence, iteration limit
+// All scalars live in device memory, so the iteration is captured once in a
+// CUDA graph whose while-node repeats it until fin_iter clears the condition
+// (converged, iteration limit, or breakdown): one graph launch per solve.
+//
+// Mixed precision (Section 6 runs the CG loop in single precision, set-up in
+// double): the reduced-precision solve sits inside FP64 iterative refinement.
+// r = b - A x and x += s*d are FP64; the inner PCG runs its operator and
+// vectors in FP32 (or with tensor-core contractions), its dot products
+// accumulated in FP64.
+#include <math.h>
+
+#include <algorithm>
+
+#include "nb_reduce.cuh"
+
+namespace nb {
+
+nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
+                      cudaStream_t s);  // nb_learned.cu
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_cg_setup(CgScalars *sc, double tol, int maxit, double *hist, int hist_cap)
+{
+    sc->tol = tol;
+    sc->maxit = maxit;
+    sc->hist = hist;
+    sc->hist_cap = hist_cap;
+    sc->iter = 0;
+    sc->done = 0;
+    sc->status = 0;
+    sc->beta = 0.0;
+    sc->alpha = 0.0;
+}
+
+// p = 0; partials of (r, c, dinv r) and (r, c, r).
+template <typename T>
+__global__ void k_cg_init(int64_t nL, const T *__restrict__ r, const T *__restrict__ dinv,
+                          const float *__restrict__ c, T *__restrict__ p, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    double a = 0.0, b = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const T rl = r[l], cl = (T)c[l];
+        p[l] = T(0);
+        a += (double)(cl * rl * (dinv[l] * rl));
+        b += (double)(cl * rl * rl);
+    }
+    double ta = block_sum(a, sred);
+    double tb = block_sum(b, sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+}
+
+// bnorm_from_r: the system's right-hand side is the initial residual.
+__global__ void k_cg_init_fin(CgScalars *sc, const double *__restrict__ part, int cnt,
+                              int bnorm_from_r)
+{
+    __shared__ double sred[32];
+    double rtz = sum_partials(part, cnt, sred);
+    double rtr = sum_partials(part + cnt, cnt, sred);
+    if (threadIdx.x == 0) {
+        sc->rtz = rtz;
+        sc->rtz_old = rtz;
+        sc->rtr = rtr;
+        if (bnorm_from_r) sc->bnorm2 = rtr;
+        const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
+        sc->relres = sqrt(rtr / bn);
+        sc->beta = 0.0;
+        sc->pap_prev = 0.0;
+        if (!(sc->relres >= 0.0) || !isfinite(sc->relres)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else if (sc->relres < sc->tol || rtr == 0.0) {
+            sc->done = 1;
+        } else if (sc->maxit <= 0) {
+            sc->done = 1;
+            sc->status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+__global__ void k_cg_fin_pap(CgScalars *sc, const double *__restrict__ part, int cnt)
+{
+    __shared__ double sred[32];
+    if (sc->done) return;
+    double pap = sum_partials(part, cnt, sred);
+    if (threadIdx.x == 0) {
+        sc->pap = pap;
+        double alpha = sc->rtz / pap;
+        if (!(pap > 0.0) || !isfinite(alpha)) {
+            sc->alpha = 0.0;
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else {
+            sc->alpha = alpha;
+        }
+    }
+}
+
+// add2s2 twice, then solveM and the two dot products of the next iteration.
+template <typename T>
+__global__ void k_cg_update(int64_t nL, const CgScalars *__restrict__ sc, T *__restrict__ x,
+                            T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ w,
+                            const T *__restrict__ dinv, const float *__restrict__ c,
+                            double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    double a = 0.0, b = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        x[l] = x[l] + alpha * p[l];
+        const T rl = r[l] - alpha * w[l];
+        r[l] = rl;
+        const T cl = (T)c[l];
+        a += (double)(cl * rl * (dinv[l] * rl));
+        b += (double)(cl * rl * rl);
+    }
+    double ta = block_sum(a, sred);
+    double tb = block_sum(b, sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+}
+
+__global__ void k_cg_fin_iter(CgScalars *sc, const double *__restrict__ part, int cnt,
+                              cudaGraphConditionalHandle h, int use_cond)
+{
+    __shared__ double sred[32];
+    if (!sc->done) {
+        double rtz = sum_partials(part, cnt, sred);
+        double rtr = sum_partials(part + cnt, cnt, sred);
+        if (threadIdx.x == 0) {
+            sc->rtz_old = sc->rtz;
+            sc->rtz = rtz;
+            sc->rtr = rtr;
+            sc->beta = rtz / sc->rtz_old;
+            const int it = sc->iter + 1;
+            sc->iter = it;
+            const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
+            const double rel = sqrt(rtr / bn);
+            sc->relres = rel;
+            if (sc->hist && it <= sc->hist_cap) sc->hist[it - 1] = rel;
+            if (!isfinite(rel) || !isfinite(sc->beta)) {
+                sc->done = 1;
+                sc->status = NB_BREAKDOWN;
+            } else if (rel < sc->tol) {
+                sc->done = 1;
+            } else if (it >= sc->maxit) {
+                sc->done = 1;
+                sc->status = NB_NOT_CONVERGED;
+            }
+        }
+    }
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
+// r = b - w (FP64) and partials of (r, c, r).
+__global__ void k_residual64(int64_t nL, const double *__restrict__ b, const double *__restrict__ w,
+                             const float *__restrict__ c, double *__restrict__ r,
+                             double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    double a = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double v = b[l] - (w ? w[l] : 0.0);
+        r[l] = v;
+        a += (double)c[l] * v * v;
+    }
+    double t = block_sum(a, sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Inner right-hand side: r32 = r64 / s (rounded to FP32), x32 = 0.
+__global__ void k_demote(int64_t nL, const double *__restrict__ r64, const double *__restrict__ s2,
+                         float *__restrict__ r32, float *__restrict__ x32)
+{
+    const double inv = 1.0 / sqrt(*s2);
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        r32[l] = (float)(r64[l] * inv);
+        x32[l] = 0.0f;
+    }
+}
+
+// Solution update in FP64: x += s * d.
+__global__ void k_promote(int64_t nL, const double *__restrict__ s2, const float *__restrict__ d,
+                          double *__restrict__ x)
+{
+    const double sc = sqrt(*s2);
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x)
+        x[l] += sc * (double)d[l];
+}
+
+__global__ void k_fill0(int64_t n, double *__restrict__ x)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        x[l] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------
+
+nb_status ensure_ws(nb_mesh *m, Workspace &ws, int elt, int hist_cap)
+{
+    if (ws.x == nullptr) {
+        const size_t bytes = (size_t)elt * m->nL;
+        ws.nL = m->nL;
+        ws.elt = elt;
+        NB_CUDA(cudaMalloc(&ws.x, bytes));
+        NB_CUDA(cudaMalloc(&ws.r, bytes));
+        NB_CUDA(cudaMalloc(&ws.p, bytes));
+        NB_CUDA(cudaMalloc(&ws.w, bytes));
+        NB_CUDA(cudaMalloc(&ws.z, bytes));
+        NB_CUDA(cudaMalloc(&ws.aux, bytes));
+        NB_CUDA(cudaMalloc(&ws.part, sizeof(double) * kMaxPartials * 3));
+        NB_CUDA(cudaMalloc(&ws.scal, sizeof(CgScalars)));
+        NB_CUDA(cudaMallocHost(&ws.scal_host, sizeof(CgScalars)));
+        NB_CUDA(cudaMemset(ws.scal, 0, sizeof(CgScalars)));
+        NB_CUDA(cudaMemset(ws.r, 0, bytes));
+        NB_CUDA(cudaMemset(ws.p, 0, bytes));
+        NB_CUDA(cudaMemset(ws.x, 0, bytes));
+    }
+    if (hist_cap > ws.hist_cap) {
+        if (ws.hist) NB_CUDA(cudaFree(ws.hist));
+        ws.hist = nullptr;
+        NB_CUDA(cudaMalloc(&ws.hist, sizeof(double) * hist_cap));
+        ws.hist_cap = hist_cap;
+    }
+    return NB_OK;
+}
+
+static nb_status ensure_fp64_bufs(nb_mesh *m)
+{
+    if (m->r64 == nullptr) {
+        NB_CUDA(cudaMalloc(&m->r64, sizeof(double) * m->nL));
+        NB_CUDA(cudaMalloc(&m->w64, sizeof(double) * m->nL));
+        NB_CUDA(cudaMalloc(&m->part64, sizeof(double) * kMaxPartials * 2));
+    }
+    if (m->red_out == nullptr) {
+        NB_CUDA(cudaMalloc(&m->red_out, sizeof(double) * 8));
+        NB_CUDA(cudaMallocHost(&m->red_host, sizeof(double) * 8));
+    }
+    return NB_OK;
+}
+
+// The five launches of one iteration (see the file comment).
+template <typename T>
+static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
+                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
+{
+    int nparts = 0;
+    NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
+    NB_TRY(dssum(m, prec, ws.w, 1, s));
+    k_cg_fin_pap<<<1, kFinalizeThreads, 0, s>>>(ws.scal, ws.part, nparts);
+    NB_CUDA(cudaGetLastError());
+    const int g = vec_grid(m->ctx, m->nL);
+    double *up = ws.part + kMaxPartials;
+    k_cg_update<T><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, (T *)ws.x, (T *)ws.r,
+                                             (const T *)ws.p, (const T *)ws.w, dinv, m->c32, up);
+    NB_CUDA(cudaGetLastError());
+    k_cg_fin_iter<<<1, kFinalizeThreads, 0, s>>>(ws.scal, up, g, h, use_cond);
+    NB_CUDA(cudaGetLastError());
+    if (!use_cond) m->launches += 5;
+    return NB_OK;
+}
+
+// Initial scalars from ws.r: p = 0, rtz, rtr, relres, done.
+template <typename T>
+static nb_status cg_start(nb_mesh *m, Workspace &ws, const T *dinv, double tol, int maxit,
+                          int bnorm_from_r, bool hist, cudaStream_t s)
+{
+    k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tol, maxit, hist ? ws.hist : nullptr,
+                               hist ? ws.hist_cap : 0);
+    NB_CUDA(cudaGetLastError());
+    const int g = vec_grid(m->ctx, m->nL);
+    k_cg_init<T><<<g, kVecThreads, 0, s>>>(m->nL, (const T *)ws.r, dinv, m->c32, (T *)ws.p,
+                                           ws.part + kMaxPartials);
+    NB_CUDA(cudaGetLastError());
+    k_cg_init_fin<<<1, kFinalizeThreads, 0, s>>>(ws.scal, ws.part + kMaxPartials, g, bnorm_from_r);
+    NB_CUDA(cudaGetLastError());
+    m->launches += 3;
+    return NB_OK;
+}
+
+// Run iterations until the device scalars say stop.
+template <typename T>
+static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv, int key,
+                            int use_graph, int maxit, cudaStream_t s)
+{
+    if (use_graph) {
+        if (ws.exec == nullptr || ws.graph_key != key) {
+            if (ws.exec) {
+                NB_CUDA(cudaGraphExecDestroy(ws.exec));
+                ws.exec = nullptr;
+            }
+            if (ws.graph) {
+                NB_CUDA(cudaGraphDestroy(ws.graph));
+                ws.graph = nullptr;
+            }
+            cudaGraph_t g;
+            NB_CUDA(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle h;
+            NB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            NB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+            nb_status st = cg_body<T>(m, prec, ws, dinv, h, 1, s);
+            cudaGraph_t captured = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s, &captured);
+            if (st != NB_OK) {
+                cudaGraphDestroy(g);
+                return st;
+            }
+            if (ce != cudaSuccess) {
+                cudaGraphDestroy(g);
+                set_error("graph capture failed: %s", cudaGetErrorString(ce));
+                return NB_ERR_CUDA;
+            }
+            NB_CUDA(cudaGraphInstantiate(&ws.exec, g, 0));
+            ws.graph = g;
+            ws.graph_key = key;
+        }
+        NB_CUDA(cudaGraphLaunch(ws.exec, s));
+        return NB_OK;
+    }
+    // host-driven: launch a chunk of iterations, then look at the flag
+    const int chunk = 16;
+    for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
+        for (int t = 0; t < chunk; ++t) NB_TRY(cg_body<T>(m, prec, ws, dinv, 0, 0, s));
+        NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        if (ws.scal_host->done) break;
+    }
+    return NB_OK;
+}
+
+// ||b - A x||_c^2 in FP64 into m->red_out[slot]; r into m->r64.
+static nb_status fp64_residual(nb_mesh *m, const double *b, const double *x, int slot,
+                               cudaStream_t s)
+{
+    const double *w = nullptr;
+    if (x) {
+        NB_TRY(ax_local(m, NB_FP64, x, m->w64, nullptr, nullptr, s));
+        NB_TRY(dssum(m, NB_FP64, m->w64, 1, s));
+        w = m->w64;
+    }
+    const int g = vec_grid(m->ctx, m->nL);
+    k_residual64<<<g, kVecThreads, 0, s>>>(m->nL, b, w, m->c32, m->r64, m->part64);
+    NB_CUDA(cudaGetLastError());
+    m->launches += x ? 4 : 2;
+    return sum_partials_dev(m->part64, g, m->red_out + slot, s);
+}
+
+static void copy_history(const Workspace &ws, int count, int offset, nb_stats *st,
+                         cudaStream_t s)
+{
+    if (!st || !st->history_host || st->history_cap <= offset || count <= 0) return;
+    int nmax = std::min(count, std::min(ws.hist_cap, st->history_cap - offset));
+    if (nmax <= 0) return;
+    cudaMemcpyAsync(st->history_host + offset, ws.hist, sizeof(double) * nmax,
+                    cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    st->history_len = offset + nmax;
+}
+
+static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, double *x,
+                            nb_stats *st, cudaStream_t s)
+{
+    Workspace &ws = m->ws64;
+    const int hist_cap = o->record_history ? std::max(o->maxiter, 1) : 0;
+    NB_TRY(ensure_ws(m, ws, 8, hist_cap));
+    NB_TRY(ensure_fp64_bufs(m));
+    const double *dinv = o->pc == NB_PC_NONE ? m->ones64 : m->dinv64;
+    // bnorm2 -> scal (through red_out), r = b - A x0
+    NB_TRY(fp64_residual(m, b, nullptr, 0, s));  // (b, c, b)
+    NB_TRY(fp64_residual(m, b, o->use_x0 ? x : nullptr, 1, s));
+    NB_CUDA(cudaMemcpyAsync(ws.r, m->r64, sizeof(double) * m->nL, cudaMemcpyDeviceToDevice, s));
+    if (o->use_x0)
+        NB_CUDA(cudaMemcpyAsync(ws.x, x, sizeof(double) * m->nL, cudaMemcpyDeviceToDevice, s));
+    else
+        NB_CUDA(cudaMemsetAsync(ws.x, 0, sizeof(double) * m->nL, s));
+    NB_CUDA(cudaMemcpyAsync(&ws.scal->bnorm2, m->red_out, sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+    NB_TRY(cg_start<double>(m, ws, dinv, o->rtol, o->maxiter, 0, o->record_history, s));
+    NB_TRY(cg_iterate<double>(m, NB_FP64, ws, dinv, 10 + (int)o->pc, o->use_graph, o->maxiter, s));
+    NB_CUDA(cudaMemcpyAsync(x, ws.x, sizeof(double) * m->nL, cudaMemcpyDeviceToDevice, s));
+    // true FP64 residual of the result
+    NB_TRY(fp64_residual(m, b, x, 1, s));
+    NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(m->red_host, m->red_out, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    const CgScalars &h = *ws.scal_host;
+    if (!isfinite(m->red_host[0])) {
+        set_error("right-hand side has a non-finite entry");
+        return NB_ERR_ARG;
+    }
+    const double bn2 = m->red_host[0] > 0 ? m->red_host[0] : 1.0;
+    if (st) {
+        if (o->use_graph) m->launches += 5 * (int64_t)std::max(h.iter, 1);
+        st->iters = h.iter;
+        st->outer_iters = 0;
+        st->launches = m->launches;
+        st->rel_res = sqrt(m->red_host[1] / bn2);
+        st->status = (nb_status)h.status;
+        st->history_len = 0;
+    }
+    if (o->record_history) copy_history(ws, h.iter, 0, st, s);
+    return (nb_status)h.status;
+}
+
+static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, double *x,
+                               nb_stats *st, cudaStream_t s)
+{
+    Workspace &ws = m->ws32;
+    const int hist_cap = o->record_history ? std::max(o->maxiter, 1) : 0;
+    NB_TRY(ensure_ws(m, ws, 4, hist_cap));
+    NB_TRY(ensure_fp64_bufs(m));
+    const float *dinv = o->pc == NB_PC_NONE ? m->ones32 : m->dinv32;
+    const int g = vec_grid(m->ctx, m->nL);
+    NB_TRY(fp64_residual(m, b, nullptr, 0, s));  // (b, c, b) into red_out[0]
+    if (!o->use_x0) {
+        k_fill0<<<g, kVecThreads, 0, s>>>(m->nL, x);
+        NB_CUDA(cudaGetLastError());
+        m->launches += 1;
+    }
+    int used = 0, outer = 0, stagn = 0, hist_off = 0;
+    double prev = INFINITY, rel = INFINITY;
+    nb_status result = NB_NOT_CONVERGED;
+    for (outer = 0; outer <= o->max_outer; ++outer) {
+        // FP64 residual r = b - A x (skipped product for the zero start)
+        NB_TRY(fp64_residual(m, b, (outer == 0 && !o->use_x0) ? nullptr : x, 1, s));
+        NB_CUDA(cudaMemcpyAsync(m->red_host, m->red_out, sizeof(double) * 2,
+                                cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        const double bn2 = m->red_host[0];
+        if (!isfinite(bn2)) {
+            set_error("right-hand side has a non-finite entry");
+            return NB_ERR_ARG;
+        }
+        if (!(bn2 > 0.0)) {  // b = 0: x = 0 is exact
+            rel = 0.0;
+            result = NB_OK;
+            break;
+        }
+        rel = sqrt(m->red_host[1] / bn2);
+        if (!isfinite(rel)) { result = NB_BREAKDOWN; break; }
+        if (rel < o->rtol) { result = NB_OK; break; }
+        if (outer == o->max_outer || used >= o->maxiter) { result = NB_NOT_CONVERGED; break; }
+        if (rel > 0.5 * prev) {
+            if (++stagn >= 3) { result = NB_STAGNATED; break; }
+        } else {
+            stagn = 0;
+        }
+        prev = rel;
+        // inner solve on r32 = r64/||r64||, from zero
+        k_demote<<<g, kVecThreads, 0, s>>>(m->nL, m->r64, m->red_out + 1, (float *)ws.r,
+                                           (float *)ws.x);
+        NB_CUDA(cudaGetLastError());
+        const int remaining = o->maxiter - used;
+        if (o->pc == NB_PC_LEARNED) {
+            // flexible CG with the learned preconditioner (nb_learned.cu)
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, o->inner_rtol, remaining,
+                                       o->record_history ? ws.hist : nullptr,
+                                       o->record_history ? ws.hist_cap : 0);
+            NB_CUDA(cudaGetLastError());
+            NB_TRY(fcg_learned(m, o->prec, ws, o, s));
+        } else {
+            NB_TRY(cg_start<float>(m, ws, dinv, o->inner_rtol, remaining, 1, o->record_history, s));
+            NB_TRY(cg_iterate<float>(m, o->prec, ws, dinv, 20 * (int)o->prec + (int)o->pc,
+                                     o->use_graph, remaining, s));
+        }
+        k_promote<<<g, kVecThreads, 0, s>>>(m->nL, m->red_out + 1, (const float *)ws.x, x);
+        NB_CUDA(cudaGetLastError());
+        m->launches += 2;  // demote + promote
+        NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost,
+                                s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        const int it = ws.scal_host->iter;
+        if (o->use_graph && o->pc != NB_PC_LEARNED) m->launches += 5 * (int64_t)std::max(it, 1);
+        if (o->record_history) {
+            copy_history(ws, it, hist_off, st, s);
+            hist_off += it;
+        }
+        used += it;
+        if (ws.scal_host->status == NB_BREAKDOWN && it == 0) { result = NB_BREAKDOWN; break; }
+    }
+    if (st) {
+        st->iters = used;
+        st->outer_iters = outer;
+        st->launches = m->launches;
+        st->rel_res = rel;
+        st->status = result;
+        if (o->record_history) st->history_len = std::min(hist_off, st->history_cap);
+    }
+    return result;
+}
+
+nb_status solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_stats *st)
+{
+    cudaStream_t s = m->ctx->stream;
+    cudaEvent_t e0, e1;
+    NB_CUDA(cudaEventCreate(&e0));
+    NB_CUDA(cudaEventCreate(&e1));
+    NB_CUDA(cudaEventRecord(e0, s));
+    m->launches = 0;
+    nb_status r = o->prec == NB_FP64 ? solve_fp64(m, o, b, x, st, s)
+                                      : solve_refined(m, o, b, x, st, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) st->seconds = ms * 1e-3;
+    return r;
+}
+
+}  // namespace nb

@@ -1,0 +1,194 @@
+// Gather-scatter (dssum + Dirichlet mask), global<->local maps, glsc3, and the
+// Jacobi diagonal.
+#include <algorithm>
+
+#include "nb_reduce.cuh"
+
+namespace nb {
+
+// Direct-stiffness summation over the rows of shared or Dirichlet nodes: one
+// thread per row sums the local copies in ascending local index and writes
+// the (masked) sum back to every copy.  Rows are disjoint, so there are no
+// races and no atomics; the order of the sum is fixed, so the result is
+// bit-identical run to run.
+template <typename T>
+__global__ void k_gs(int64_t rows, const int32_t *__restrict__ off, const int32_t *__restrict__ loc,
+                     const uint8_t *__restrict__ rmask, T *__restrict__ u, int masked)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < rows;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int o0 = off[a], o1 = off[a + 1];
+        T s = T(0);
+        for (int o = o0; o < o1; ++o) s += u[loc[o]];
+        if (masked && rmask[a] == 0) s = T(0);
+        for (int o = o0; o < o1; ++o) u[loc[o]] = s;
+    }
+}
+
+nb_status dssum(nb_mesh *m, nb_prec prec, void *u, int masked, cudaStream_t s)
+{
+    if (m->gs_rows == 0) return NB_OK;
+    int grid = (int)std::min<int64_t>((m->gs_rows + 255) / 256, (int64_t)m->ctx->sm_count * 8);
+    if (prec == NB_FP64)
+        k_gs<double><<<grid, 256, 0, s>>>(m->gs_rows, m->gs_off, m->gs_loc, m->gs_mask,
+                                          (double *)u, masked);
+    else
+        k_gs<float><<<grid, 256, 0, s>>>(m->gs_rows, m->gs_off, m->gs_loc, m->gs_mask,
+                                         (float *)u, masked);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <typename T>
+__global__ void k_to_local(int64_t nL, const int32_t *__restrict__ gid,
+                           const uint8_t *__restrict__ mask, const T *__restrict__ ug,
+                           T *__restrict__ uL, int masked)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = gid[l];
+        T v = ug[g];
+        if (masked && mask[g] == 0) v = T(0);
+        uL[l] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_to_global(int64_t nG, const int32_t *__restrict__ first,
+                            const T *__restrict__ uL, T *__restrict__ ug)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nG;
+         g += (int64_t)gridDim.x * blockDim.x)
+        ug[g] = uL[first[g]];
+}
+
+nb_status to_local(nb_mesh *m, nb_prec prec, const void *ug, void *uL, int masked, cudaStream_t s)
+{
+    int grid = vec_grid(m->ctx, m->nL);
+    if (prec == NB_FP64)
+        k_to_local<double><<<grid, kVecThreads, 0, s>>>(m->nL, m->gid, m->mask_g,
+                                                        (const double *)ug, (double *)uL, masked);
+    else
+        k_to_local<float><<<grid, kVecThreads, 0, s>>>(m->nL, m->gid, m->mask_g,
+                                                       (const float *)ug, (float *)uL, masked);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status to_global(nb_mesh *m, nb_prec prec, const void *uL, void *ug, cudaStream_t s)
+{
+    int grid = vec_grid(m->ctx, m->nG);
+    if (prec == NB_FP64)
+        k_to_global<double><<<grid, kVecThreads, 0, s>>>(m->nG, m->g_first, (const double *)uL,
+                                                         (double *)ug);
+    else
+        k_to_global<float><<<grid, kVecThreads, 0, s>>>(m->nG, m->g_first, (const float *)uL,
+                                                        (float *)ug);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// glsc3: per-block partials of sum a*b*c (product in T, accumulated in FP64),
+// then one block sums the partials in index order.
+template <typename T>
+__global__ void k_glsc3_part(int64_t n, const T *__restrict__ a, const T *__restrict__ b,
+                             const float *__restrict__ c, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    double acc = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)(a[l] * b[l] * (T)c[l]);
+    double t = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_sum_partials(const double *__restrict__ part, int cnt, double *__restrict__ out)
+{
+    __shared__ double sred[32];
+    double t = sum_partials(part, cnt, sred);
+    if (threadIdx.x == 0) *out = t;
+}
+
+nb_status sum_partials_dev(const double *part, int cnt, double *out_dev, cudaStream_t s)
+{
+    k_sum_partials<<<1, kFinalizeThreads, 0, s>>>(part, cnt, out_dev);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+nb_status glsc3_dev(nb_mesh *m, nb_prec prec, const void *a, const void *b, double *part,
+                    double *out_dev, cudaStream_t s)
+{
+    int grid = vec_grid(m->ctx, m->nL);
+    if (prec == NB_FP64)
+        k_glsc3_part<double><<<grid, kVecThreads, 0, s>>>(m->nL, (const double *)a,
+                                                          (const double *)b, m->c32, part);
+    else
+        k_glsc3_part<float><<<grid, kVecThreads, 0, s>>>(m->nL, (const float *)a,
+                                                         (const float *)b, m->c32, part);
+    NB_CUDA(cudaGetLastError());
+    k_sum_partials<<<1, kFinalizeThreads, 0, s>>>(part, grid, out_dev);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// Diagonal of the local operator (set-up, FP64):
+//   sum_l D[l][i]^2 Grr(l,j,k) + D[l][j]^2 Gss(i,l,k) + D[l][k]^2 Gtt(i,j,l)
+//   + 2 (D[i][i] D[j][j] Grs + D[i][i] D[k][k] Grt + D[j][j] D[k][k] Gst)(i,j,k)
+__global__ void k_local_diag(int64_t E, int n, const double *__restrict__ D,
+                             const double *__restrict__ G, double *__restrict__ d)
+{
+    const int n3 = n * n * n;
+    const int64_t total = E * n3;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = t / n3;
+        const int q = (int)(t - e * n3);
+        const int i = q % n, j = (q / n) % n, k = q / (n * n);
+        const double *Ge = G + e * 6 * n3;
+        double s = 0.0;
+        for (int l = 0; l < n; ++l) {
+            s += D[l * n + i] * D[l * n + i] * Ge[0 * n3 + (k * n + j) * n + l];
+            s += D[l * n + j] * D[l * n + j] * Ge[3 * n3 + (k * n + l) * n + i];
+            s += D[l * n + k] * D[l * n + k] * Ge[5 * n3 + (l * n + j) * n + i];
+        }
+        s += 2.0 * D[i * n + i] * D[j * n + j] * Ge[1 * n3 + q];
+        s += 2.0 * D[i * n + i] * D[k * n + k] * Ge[2 * n3 + q];
+        s += 2.0 * D[j * n + j] * D[k * n + k] * Ge[4 * n3 + q];
+        d[t] = s;
+    }
+}
+
+nb_status local_diag(nb_mesh *m, double *diag, cudaStream_t s)
+{
+    int grid = vec_grid(m->ctx, m->nL);
+    k_local_diag<<<grid, kVecThreads, 0, s>>>(m->E, m->n, m->D64, m->G64, diag);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+__global__ void k_finish_jacobi(int64_t nL, const double *__restrict__ diag, double *dinv64,
+                                float *dinv32, double *ones64, float *ones32)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double d = diag[l];
+        const double v = d != 0.0 ? 1.0 / d : 0.0;
+        dinv64[l] = v;
+        dinv32[l] = (float)v;
+        ones64[l] = d != 0.0 ? 1.0 : 0.0;
+        ones32[l] = d != 0.0 ? 1.0f : 0.0f;
+    }
+}
+
+nb_status finish_jacobi(nb_mesh *m, double *diag, cudaStream_t s)
+{
+    int grid = vec_grid(m->ctx, m->nL);
+    k_finish_jacobi<<<grid, kVecThreads, 0, s>>>(m->nL, diag, m->dinv64, m->dinv32, m->ones64,
+                                                 m->ones32);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+}  // namespace nb

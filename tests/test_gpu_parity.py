@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle,
+element by element, on seeded inputs that span several blocks and ragged
+tails, plus edge cases and determinism."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import Box, rhs_global
+
+pytestmark = pytest.mark.gpu
+
+BOXES = [
+    Box(1, 1, 1, 1, 0.0),      # smallest: one element, N = 1
+    Box(2, 2, 2, 7, 0.0),      # the plain FP64 workload
+    Box(3, 2, 1, 4, 0.05),     # odd number of points per direction
+    Box(5, 3, 2, 5, 0.05),     # E = 30: ragged tail of element groups
+    Box(2, 3, 2, 9, 0.05),
+    Box(1, 1, 3, 15, 0.05),    # highest supported order (16 points)
+    Box(4, 4, 4, 11, 0.05),
+]
+IDS = [f"{b.nx}x{b.ny}x{b.nz}N{b.N}d{b.deform}" for b in BOXES]
+
+# FP64 operator tolerance: both sides evaluate the same sums in FP64; the
+# GPU fuses multiply-adds and orders the inner products differently, so the
+# difference is a few ulps times the O(n) terms of each contraction.
+TOL_AX64 = 1e-12
+# FP32 operator: three chained contractions of n terms plus the 3x3 factor
+# product; each output accumulates ~(6n + 9) roundings of unit 2^-24 relative
+# to the largest term, bounded here by 64 n 2^-24 relative to max |w|.
+def tol_ax32(n):
+    return 64 * n * 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2405_11065_gb300 as nb
+    return nb
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    return nb.Context(0)
+
+
+@pytest.fixture(scope="module", params=BOXES, ids=IDS)
+def case(request, nb, ctx):
+    box = request.param
+    return box, nb.Mesh.from_box(ctx, box), oracle.Problem(box)
+
+
+def _t(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def test_index_maps_bit_exact(case):
+    box, mesh, P = case
+    m = mesh.maps()
+    np.testing.assert_array_equal(m["gid"].astype(np.int64), P.gid)
+    np.testing.assert_array_equal(m["mult"], P.mult)
+    np.testing.assert_array_equal(m["mask"], P.mask)
+    off, loc = oracle.csr(P.gid, box.n_global)
+    active = np.nonzero((P.mult > 1) | (P.mask == 0))[0]
+    np.testing.assert_array_equal(m["gs_gid"].astype(np.int64), active)
+    rows = [loc[off[g]:off[g + 1]] for g in active]
+    ref_off = np.concatenate([[0], np.cumsum([len(r) for r in rows])])
+    np.testing.assert_array_equal(m["gs_off"].astype(np.int64), ref_off)
+    np.testing.assert_array_equal(m["gs_loc"].astype(np.int64), np.concatenate(rows))
+    np.testing.assert_array_equal(m["gs_mask"], P.mask[active])
+
+
+def test_geometry_and_jacobi(case):
+    box, mesh, P = case
+    G, dinv, c = mesh.geom()
+    scale = np.abs(P.G).max()
+    assert np.max(np.abs(G - P.G)) <= 1e-13 * scale
+    np.testing.assert_array_equal(c, P.c)
+    np.testing.assert_allclose(dinv, P.dinv, rtol=1e-12, atol=0)
+
+
+def test_ax_fp64_local_and_assembled(case, nb):
+    box, mesh, P = case
+    import torch
+    rng = np.random.default_rng(5)
+    u = rng.uniform(-1, 1, box.n_local)
+    w = torch.empty(box.n_local, dtype=torch.float64, device="cuda")
+    mesh.ax(nb.NB_FP64, _t(u), w, assemble=False)
+    ref = P.ax_local(u)
+    err = np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err <= TOL_AX64, err
+    uc = P.to_local(rhs_global(box, 1))
+    mesh.ax(nb.NB_FP64, _t(uc), w, assemble=True)
+    ref = P.apply(uc)
+    err = np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err <= TOL_AX64, err
+
+
+def test_ax_fp32_error_stated(case, nb):
+    box, mesh, P = case
+    import torch
+    rng = np.random.default_rng(6)
+    u = rng.uniform(-1, 1, box.n_local).astype(np.float32)
+    w = torch.empty(box.n_local, dtype=torch.float32, device="cuda")
+    mesh.ax(nb.NB_FP32, _t(u), w)
+    ref = P.ax_local(u.astype(np.float64))
+    err = np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    print(f"FP32 ax max relative error vs FP64 oracle: {err:.3e} (n={box.n})")
+    assert err <= tol_ax32(box.n), err
+
+
+def test_dssum_bit_exact_fp64(case, nb):
+    box, mesh, P = case
+    rng = np.random.default_rng(7)
+    v = rng.uniform(-1, 1, box.n_local)
+    t = _t(v)
+    mesh.dssum(nb.NB_FP64, t, masked=True)
+    np.testing.assert_array_equal(t.cpu().numpy(), P.dssum(v, masked=True))
+    t = _t(v)
+    mesh.dssum(nb.NB_FP64, t, masked=False)
+    np.testing.assert_array_equal(t.cpu().numpy(), P.dssum(v, masked=False))
+
+
+def test_glsc3_and_maps(case, nb):
+    box, mesh, P = case
+    import torch
+    rng = np.random.default_rng(8)
+    a, b = rng.uniform(-1, 1, box.n_local), rng.uniform(-1, 1, box.n_local)
+    got = mesh.glsc3(nb.NB_FP64, _t(a), _t(b))
+    ref = oracle.glsc3(a, b, P.c)
+    assert abs(got - ref) <= 1e-13 * np.sum(np.abs(a * b * P.c))
+    ug = rhs_global(box, 2)
+    uL = torch.empty(box.n_local, dtype=torch.float64, device="cuda")
+    mesh.to_local(nb.NB_FP64, _t(ug), uL, masked=True)
+    np.testing.assert_array_equal(uL.cpu().numpy(), P.to_local(ug))
+    back = torch.empty(box.n_global, dtype=torch.float64, device="cuda")
+    mesh.to_global(nb.NB_FP64, uL, back)
+    np.testing.assert_array_equal(back.cpu().numpy(), ug * P.mask)
+
+
+def test_fp64_pcg_matches_oracle(case, nb):
+    box, mesh, P = case
+    import torch
+    b = P.to_local(rhs_global(box, 0))
+    if not np.any(b):
+        pytest.skip("no interior unknowns")
+    xo, ito, relo, histo = P.pcg(b, tol=1e-12, maxit=5000, history=True)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, rtol=1e-12, maxiter=5000),
+                     history_cap=5000)
+    assert out["status"] == 0, out
+    assert abs(out["iters"] - ito) <= 1, (out["iters"], ito)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    h = out["history"]
+    k = min(len(h), len(histo), 20)
+    np.testing.assert_allclose(h[:k], histo[:k], rtol=1e-8)
+    assert P.true_relres(b, xg) < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_mixed_refinement_reaches_fp64_accuracy(case, nb, prec):
+    box, mesh, P = case
+    import torch
+    b = P.to_local(rhs_global(box, 0))
+    if not np.any(b):
+        pytest.skip("no interior unknowns")
+    xo, _, _, _ = P.pcg(b, tol=1e-13, maxit=5000)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.PREC_NAMES[prec], rtol=1e-10))
+    assert out["status"] == 0, out
+    assert out["rel_res"] < 1e-10
+    xg = x.cpu().numpy()
+    rel_oracle = P.true_relres(b, xg)
+    assert rel_oracle < 1.01e-10, rel_oracle
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print(f"{prec}+refinement: {out['iters']} inner its, {out['outer_iters']} outer, "
+          f"oracle residual {rel_oracle:.2e}, |x-x_oracle|/|x_oracle| {err:.2e}")
+    assert err <= 1e-8
+
+
+def test_identity_preconditioner_iterations(nb, ctx):
+    box = Box(2, 2, 2, 7, 0.0)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 0))
+    _, ito, _, _ = P.pcg(b, tol=1e-10, maxit=1000, precond="none")
+    import torch
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, pc=nb.NB_PC_NONE, rtol=1e-10))
+    assert abs(out["iters"] - ito) <= 1
+
+
+def test_determinism_and_graph_equivalence(nb, ctx):
+    import torch
+    box = Box(3, 3, 2, 7, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = _t(P.to_local(rhs_global(box, 4)))
+    xs = []
+    for use_graph in (1, 1, 0):
+        for prec in (nb.NB_FP64, nb.NB_FP32):
+            x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+            mesh.solve(b, x, nb.default_opts(prec=prec, use_graph=use_graph))
+            xs.append(x.cpu().numpy())
+    # same precision, graph or not, repeated: bit-identical
+    for k in (2, 4):
+        np.testing.assert_array_equal(xs[0], xs[k])
+        np.testing.assert_array_equal(xs[1], xs[k + 1])
+    w1 = torch.empty_like(b)
+    w2 = torch.empty_like(b)
+    mesh.ax(nb.NB_FP64, b, w1, assemble=True)
+    mesh.ax(nb.NB_FP64, b, w2, assemble=True)
+    assert torch.equal(w1, w2)
+
+
+def test_initial_guess_resume(nb, ctx):
+    """A solve split in two (restart from the first half's iterate) reaches
+    the same accuracy as one solve."""
+    import torch
+    box = Box(2, 2, 2, 7, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = _t(P.to_local(rhs_global(box, 9)))
+    x = torch.zeros_like(b)
+    out1 = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64, maxiter=20))
+    assert out1["status"] == nb.NB_NOT_CONVERGED and out1["iters"] == 20
+    out2 = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64, use_x0=1))
+    assert out2["status"] == 0 and out2["rel_res"] < 1e-10
+    assert P.true_relres(b.cpu().numpy(), x.cpu().numpy()) < 1e-10
+
+
+def test_host_entry_point(nb, ctx):
+    box = Box(2, 2, 3, 5, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    bg = rhs_global(box, 3)
+    xg = np.zeros(box.n_global)
+    out = mesh.solve_host(bg, xg, nb.default_opts(prec=nb.NB_FP32))
+    assert out["status"] == 0
+    b = P.to_local(bg)
+    assert P.true_relres(b, P.to_local(xg)) < 1.01e-10
+
+
+def test_failures_are_reported(nb, ctx):
+    import torch
+    box = Box(2, 2, 2, 5, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 0))
+    bad = b.copy()
+    bad[np.nonzero(bad)[0][3]] = np.nan
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    for prec in (nb.NB_FP64, nb.NB_FP32):
+        with pytest.raises(nb.NbError) as ei:
+            mesh.solve(_t(bad), x, nb.default_opts(prec=prec))
+        assert ei.value.status == nb.NB_ERR_ARG
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, maxiter=1))
+    assert out["status"] == nb.NB_NOT_CONVERGED and out["iters"] == 1
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, max_outer=1))
+    assert out["status"] == nb.NB_NOT_CONVERGED
+    with pytest.raises(nb.NbError) as ei:
+        nb.Mesh(ctx, 1, 1, 1, 5, 3.0)
+    assert ei.value.status == nb.NB_ERR_MESH
+    with pytest.raises(nb.NbError):
+        nb.Mesh(ctx, 1, 1, 1, 16, 0.0)
+    with pytest.raises(nb.NbError):
+        mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_LEARNED))
+    # zero right-hand side: x = 0 exactly
+    z = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    x.fill_(1.0)
+    for prec in (nb.NB_FP64, nb.NB_FP32):
+        out = mesh.solve(z, x, nb.default_opts(prec=prec))
+        assert out["status"] == 0 and float(x.abs().max()) == 0.0
