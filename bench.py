@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
+    ap.add_argument("--mode", choices=["full", "solve", "ax"], default="full",
+                    help="solve: only the timed solves (for a kernel launch list); "
+                         "ax: only a few launches of the operators (for a profiler capture)")
+    ap.add_argument("--prec", default="fp32", help="precision of --mode ax")
     return ap.parse_args()
 
 
@@ -249,6 +253,13 @@ def main():
     mesh.to_local(nb.NB_FP64, bg, b, masked=True)
     x = torch.zeros_like(b)
     flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
+    if args.mode == "ax":
+        prec = nb.PREC_NAMES[args.prec]
+        for _ in range(args.warmup):
+            mesh.time_ax(prec, cg_step=True, reps=1, flush=flush)
+        ms = mesh.time_ax(prec, cg_step=True, reps=max(args.steps, 1), flush=flush)
+        print(json.dumps({"mode": "ax", "prec": args.prec, "cg_step_ms": ms}), flush=True)
+        return 0
 
     # autotune the operator (per precision, this order) before timing
     tune = {}
@@ -298,6 +309,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
     ok = all(s["status"] == 0 and s["rel_res"] < RTOL for s in stats)
+    if args.mode == "solve":
+        if rank == 0:
+            print(json.dumps({"mode": "solve", "ms_per_step": max_ms / args.steps, "ok": ok,
+                              "iters": stats[-1]["iters"], "launches": stats[-1]["launches"]}),
+                  flush=True)
+        return 0 if ok else 1
 
     # correctness of the last solve on the device: FP64 residual
     w = torch.empty_like(b)

@@ -27,7 +27,7 @@ nb_status upload_deriv_tables(int n, const double *D64)
 int ax_variant_count(const nb_mesh *m, nb_prec prec)
 {
     (void)m;
-    return (prec == NB_FP64 || prec == NB_FP32) ? 2 : 1;
+    return (prec == NB_FP64 || prec == NB_FP32) ? 2 : 1;  // tensor-core kernel: one shape
 }
 
 // Default before any autotuning: the larger element group, except FP64 at
