@@ -54,6 +54,9 @@ def parse():
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture)")
     ap.add_argument("--prec", default="fp32", help="precision of --mode ax")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the iteration's kernels from the host instead of one CUDA graph "
+                         "(same kernels; lets a profiler list them one by one)")
     return ap.parse_args()
 
 
@@ -267,7 +270,7 @@ def main():
         v, ms = mesh.autotune(prec, reps=3, flush=flush)
         tune[pname] = {"variant": v, "ms": ms}
 
-    opts = nb.default_opts(prec=nb.NB_FP32, rtol=RTOL)
+    opts = nb.default_opts(prec=nb.NB_FP32, rtol=RTOL, use_graph=0 if args.no_graph else 1)
     for _ in range(args.warmup):
         x.zero_()
         mesh.solve(b, x, opts)
