@@ -232,6 +232,27 @@ int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
 nb_status nb_autotune(nb_mesh *mesh, nb_prec prec, int reps, void *flush_dev,
                       size_t flush_bytes, int *best_variant, double *best_ms);
 
+/* nb_glsc3 for callers that cannot let a library allocate memory: a
+ * framework whose caching allocator owns the device memory, a process under
+ * a hard memory budget, or a latency-critical loop that must not pay for
+ * cudaMalloc's device synchronisation.  (The paper has no counterpart: this is
+ * an interface variant of glsc3, not part of the method.)
+ * Same arguments and result as nb_glsc3; the only difference is where the
+ * scratch lives: the per-block partial sums and the final scalar use a fixed
+ * array of 2048 + 1 doubles (16 KB) in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.  No call
+ * to cudaMalloc, cudaFree, cudaMallocHost or any allocating routine is made.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  Every call shares the array: calls whose kernels overlap on the
+ * GPU (several streams, several host threads) race and may return wrong
+ * sums; issue them in order on one stream.  The array keeps the last call's
+ * contents; each call writes every slot it reads, so nothing is cleared.
+ * Errors: NB_ERR_ARG (NULL pointer, bad precision, or a launch that would
+ * need more than 2048 partial sums), NB_ERR_STATE, NB_ERR_CUDA. */
+nb_status nb_glsc3_noalloc(nb_mesh *mesh, nb_prec prec, const void *a_dev,
+                           const void *b_dev, double *out_host);
+
 #ifdef __cplusplus
 }
 #endif

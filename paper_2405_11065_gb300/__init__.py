@@ -70,6 +70,7 @@ def _load():
         "nb_ax": (i32, [vp, i32, i32, vp, vp]),
         "nb_dssum": (i32, [vp, i32, vp, i32]),
         "nb_glsc3": (i32, [vp, i32, vp, vp, C.POINTER(dbl)]),
+        "nb_glsc3_noalloc": (i32, [vp, i32, vp, vp, C.POINTER(dbl)]),
         "nb_default_opts": (None, [C.POINTER(nb_opts)]),
         "nb_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
         "nb_solve_host": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
