@@ -120,7 +120,7 @@ nb_status nb_mesh_destroy(nb_mesh *m)
     void *bufs[] = {m->D64, m->D32, m->G64, m->G32, m->gid, m->gs_off, m->gs_loc, m->gs_gid,
                     m->gs_mask, m->g_first, m->mask_g, m->c32, m->dinv64, m->dinv32,
                     m->ones64, m->ones32, m->r64, m->w64, m->x64, m->b64, m->g64, m->part64,
-                    m->red_out};
+                    m->red_out, m->kerr};
     for (void *b : bufs) cudaFree(b);
     if (m->red_host) cudaFreeHost(m->red_host);
     delete m;
@@ -193,6 +193,20 @@ nb_status nb_mesh_sizes(const nb_mesh *m, int64_t out[9])
     return NB_OK;
 }
 
+// A pipelined kernel whose bounded wait gave up sets m->kerr (it then exits
+// without finishing its elements): report it as a CUDA error.
+static nb_status check_kernel_flag(nb_mesh *m)
+{
+    int flag = 0;
+    NB_CUDA(cudaMemcpy(&flag, m->kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(m->kerr, 0, sizeof(int));
+        set_error("a bulk-copy wait in the operator timed out; results are incomplete");
+        return NB_ERR_CUDA;
+    }
+    return NB_OK;
+}
+
 static nb_status need_gs(const nb_mesh *m)
 {
     if (!m) return arg_error("mesh is NULL");
@@ -231,8 +245,10 @@ nb_status nb_get_geom(const nb_mesh *m, double *G, double *dinv, double *c)
     NB_CUDA(cudaSetDevice(m->ctx->device));
     if (G) NB_CUDA(cudaMemcpy(G, m->G64, sizeof(double) * 6 * m->nL, cudaMemcpyDeviceToHost));
     if (dinv || c) NB_TRY(need_gs(m));
-    if (dinv)
+    if (dinv) {
         NB_CUDA(cudaMemcpy(dinv, m->dinv64, sizeof(double) * m->nL, cudaMemcpyDeviceToHost));
+        for (int64_t l = 0; l < m->nL; ++l) dinv[l] = fabs(dinv[l]);  // drop the owner sign
+    }
     if (c) {
         float *tmp = (float *)malloc(sizeof(float) * m->nL);
         if (!tmp) return NB_ERR_OOM;
@@ -275,7 +291,7 @@ nb_status nb_ax(nb_mesh *m, nb_prec prec, int assemble, const void *u, void *w)
     NB_TRY(ax_local(m, prec, u, w, nullptr, nullptr, s));
     if (assemble) NB_TRY(dssum(m, prec, w, 1, s));
     NB_CUDA(cudaStreamSynchronize(s));
-    return NB_OK;
+    return check_kernel_flag(m);
 }
 
 nb_status nb_dssum(nb_mesh *m, nb_prec prec, void *u, int masked)
@@ -347,7 +363,10 @@ nb_status nb_solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_
     }
     NB_CUDA(cudaSetDevice(m->ctx->device));
     if (st) st->history_len = 0;
-    return solve(m, o, b, x, st);
+    nb_status r = solve(m, o, b, x, st);
+    if (r < 0) return r;
+    NB_TRY(check_kernel_flag(m));
+    return r;
 }
 
 nb_status nb_solve_host(nb_mesh *m, const nb_opts *o, const double *bg, double *xg, nb_stats *st)

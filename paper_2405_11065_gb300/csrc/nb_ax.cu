@@ -1,4 +1,14 @@
 // Host glue of the operator: precision and variant dispatch.
+//
+// Variants of the CUDA-core operator (chosen per mesh and precision by
+// nb_autotune, or by the default below):
+//   0, 1: k_ax_cc with the smaller / larger number of elements per block,
+//         every load issued by the computing threads;
+//   2:    k_ax_tma, element data streamed by bulk copies into a two-stage
+//         shared-memory ring (even n, when two stages fit in shared memory,
+//         and every vector 16-byte aligned).
+#include <stdint.h>
+
 #include "nb_internal.h"
 
 namespace nb {
@@ -7,12 +17,20 @@ nb_status upload_D_f32(int n, const double *D);
 nb_status upload_D_f64(int n, const double *D);
 nb_status ax_cc_f32(int n, int mchoice, bool pupd, int sm_count, long long E, const float *G,
                     const float *u, float *w, const float *r, const float *dinv, float *p,
-                    const CgScalars *scal, double *part, int *grid, cudaStream_t s);
+                    CgScalars *scal, double *part, int *grid, cudaStream_t s);
 nb_status ax_cc_f64(int n, int mchoice, bool pupd, int sm_count, long long E, const double *G,
                     const double *u, double *w, const double *r, const double *dinv, double *p,
-                    const CgScalars *scal, double *part, int *grid, cudaStream_t s);
+                    CgScalars *scal, double *part, int *grid, cudaStream_t s);
+nb_status ax_tma_f32(int n, bool pupd, int sm_count, long long E, const float *G, const float *u,
+                     float *w, const float *r, const float *dinv, float *p, CgScalars *scal,
+                     double *part, int *err, int *grid, cudaStream_t s);
+nb_status ax_tma_f64(int n, bool pupd, int sm_count, long long E, const double *G,
+                     const double *u, double *w, const double *r, const double *dinv, double *p,
+                     CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s);
+bool ax_tma_available_f32(int n, bool pupd);
+bool ax_tma_available_f64(int n, bool pupd);
 nb_status ax_tc(nb_mesh *m, nb_prec prec, bool pupd, const float *u, float *w, const float *r,
-                const float *dinv, float *p, const CgScalars *scal, double *part, int *grid,
+                const float *dinv, float *p, CgScalars *scal, double *part, int *grid,
                 cudaStream_t s);
 nb_status upload_D_tc(int n, const double *D);
 
@@ -24,33 +42,77 @@ nb_status upload_deriv_tables(int n, const double *D64)
     return NB_OK;
 }
 
-int ax_variant_count(const nb_mesh *m, nb_prec prec)
+static bool tma_ok(const nb_mesh *m, nb_prec prec)
 {
-    (void)m;
-    return (prec == NB_FP64 || prec == NB_FP32) ? 2 : 1;  // tensor-core kernel: one shape
+    // both the plain and the fused form must fit for the variant to be offered
+    if (prec == NB_FP32) return ax_tma_available_f32(m->n, true) && ax_tma_available_f32(m->n, false);
+    if (prec == NB_FP64) return ax_tma_available_f64(m->n, true) && ax_tma_available_f64(m->n, false);
+    return false;
 }
 
-// Default before any autotuning: the larger element group, except FP64 at
-// high order where two elements per block spill registers.
-static int default_mchoice(const nb_mesh *m, nb_prec prec)
+int ax_variant_count(const nb_mesh *m, nb_prec prec)
 {
+    if (prec == NB_FP64 || prec == NB_FP32) return tma_ok(m, prec) ? 3 : 2;
+    return 1;  // tensor-core kernel: one shape
+}
+
+// Default before any autotuning: the bulk-copy kernel where available, else
+// the larger element group, except FP64 at high order where two elements per
+// block spill registers.
+static int default_variant(const nb_mesh *m, nb_prec prec)
+{
+    if (tma_ok(m, prec)) return 2;
     if (prec == NB_FP64 && m->n >= 12) return 0;
     return 1;
+}
+
+static bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+static nb_status run_cc(nb_mesh *m, nb_prec prec, int v, bool pupd, const T *G, const T *u, T *w,
+                        const T *r, const T *dinv, T *p, CgScalars *scal, double *part,
+                        int *grid, cudaStream_t s)
+{
+    if (v == 2 && !(aligned16(u) && aligned16(w) && aligned16(r) && aligned16(dinv) &&
+                    aligned16(p)))
+        v = 1;  // the bulk copies need 16-byte aligned vectors
+    if (v == 2) {
+        if (prec == NB_FP64)
+            return ax_tma_f64(m->n, pupd, m->ctx->sm_count, m->E, (const double *)G,
+                              (const double *)u, (double *)w, (const double *)r,
+                              (const double *)dinv, (double *)p, scal, part, m->kerr, grid, s);
+        return ax_tma_f32(m->n, pupd, m->ctx->sm_count, m->E, (const float *)G, (const float *)u,
+                          (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal,
+                          part, m->kerr, grid, s);
+    }
+    if (prec == NB_FP64)
+        return ax_cc_f64(m->n, v, pupd, m->ctx->sm_count, m->E, (const double *)G,
+                         (const double *)u, (double *)w, (const double *)r, (const double *)dinv,
+                         (double *)p, scal, part, grid, s);
+    return ax_cc_f32(m->n, v, pupd, m->ctx->sm_count, m->E, (const float *)G, (const float *)u,
+                     (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal, part,
+                     grid, s);
+}
+
+static int variant_of(const nb_mesh *m, nb_prec prec)
+{
+    const int v = m->ax_cfg[prec].variant;
+    if (v >= 0 && v < ax_variant_count(m, prec)) return v;
+    return default_variant(m, prec);
 }
 
 nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap_part,
                    int *nparts, cudaStream_t s)
 {
-    const int choice = m->ax_cfg[prec].variant >= 0 ? m->ax_cfg[prec].variant : default_mchoice(m, prec);
     switch (prec) {
         case NB_FP64:
-            return ax_cc_f64(m->n, choice, false, m->ctx->sm_count, m->E, m->G64,
-                             (const double *)u, (double *)w, nullptr, nullptr, nullptr, nullptr,
-                             pap_part, nparts, s);
+            return run_cc<double>(m, prec, variant_of(m, prec), false, m->G64, (const double *)u,
+                                  (double *)w, nullptr, nullptr, nullptr, nullptr, pap_part,
+                                  nparts, s);
         case NB_FP32:
-            return ax_cc_f32(m->n, choice, false, m->ctx->sm_count, m->E, m->G32,
-                             (const float *)u, (float *)w, nullptr, nullptr, nullptr, nullptr,
-                             pap_part, nparts, s);
+            return run_cc<float>(m, prec, variant_of(m, prec), false, m->G32, (const float *)u,
+                                 (float *)w, nullptr, nullptr, nullptr, nullptr, pap_part, nparts,
+                                 s);
         case NB_TC_F16:
         case NB_TC_BF16:
             return ax_tc(m, prec, false, (const float *)u, (float *)w, nullptr, nullptr, nullptr,
@@ -61,18 +123,17 @@ nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap
 }
 
 nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, void *p, void *w,
-                     const CgScalars *scal, double *pap_part, int *nparts, cudaStream_t s)
+                     CgScalars *scal, double *pap_part, int *nparts, cudaStream_t s)
 {
-    const int choice = m->ax_cfg[prec].variant >= 0 ? m->ax_cfg[prec].variant : default_mchoice(m, prec);
     switch (prec) {
         case NB_FP64:
-            return ax_cc_f64(m->n, choice, true, m->ctx->sm_count, m->E, m->G64, nullptr,
-                             (double *)w, (const double *)r, (const double *)dinv, (double *)p,
-                             scal, pap_part, nparts, s);
+            return run_cc<double>(m, prec, variant_of(m, prec), true, m->G64, nullptr,
+                                  (double *)w, (const double *)r, (const double *)dinv,
+                                  (double *)p, scal, pap_part, nparts, s);
         case NB_FP32:
-            return ax_cc_f32(m->n, choice, true, m->ctx->sm_count, m->E, m->G32, nullptr,
-                             (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal,
-                             pap_part, nparts, s);
+            return run_cc<float>(m, prec, variant_of(m, prec), true, m->G32, nullptr, (float *)w,
+                                 (const float *)r, (const float *)dinv, (float *)p, scal,
+                                 pap_part, nparts, s);
         case NB_TC_F16:
         case NB_TC_BF16:
             return ax_tc(m, prec, true, nullptr, (float *)w, (const float *)r,

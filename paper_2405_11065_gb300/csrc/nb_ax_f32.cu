@@ -1,5 +1,6 @@
 // CUDA-core operator instantiations for float (see nb_ax_impl.cuh).
 #include "nb_ax_impl.cuh"
+#include "nb_ax_tma.cuh"
 
 namespace nb {
 
@@ -23,10 +24,20 @@ nb_status upload_D_f32(int n, const double *D)
 
 nb_status ax_cc_f32(int n, int mchoice, bool pupd, int sm_count, long long E, const float *G,
                       const float *u, float *w, const float *r, const float *dinv, float *p,
-                      const CgScalars *scal, double *part, int *grid, cudaStream_t s)
+                      CgScalars *scal, double *part, int *grid, cudaStream_t s)
 {
     return dispatch_ax_cc<float>(n, mchoice, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part,
                                 grid, s);
 }
+
+nb_status ax_tma_f32(int n, bool pupd, int sm_count, long long E, const float *G,
+                      const float *u, float *w, const float *r, const float *dinv, float *p,
+                      CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s)
+{
+    return dispatch_ax_tma<float>(n, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
+                                s);
+}
+
+bool ax_tma_available_f32(int n, bool pupd) { return tma_fits<float>(n, pupd); }
 
 }  // namespace nb

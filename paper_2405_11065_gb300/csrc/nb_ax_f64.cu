@@ -1,5 +1,6 @@
 // CUDA-core operator instantiations for double (see nb_ax_impl.cuh).
 #include "nb_ax_impl.cuh"
+#include "nb_ax_tma.cuh"
 
 namespace nb {
 
@@ -23,10 +24,20 @@ nb_status upload_D_f64(int n, const double *D)
 
 nb_status ax_cc_f64(int n, int mchoice, bool pupd, int sm_count, long long E, const double *G,
                       const double *u, double *w, const double *r, const double *dinv, double *p,
-                      const CgScalars *scal, double *part, int *grid, cudaStream_t s)
+                      CgScalars *scal, double *part, int *grid, cudaStream_t s)
 {
     return dispatch_ax_cc<double>(n, mchoice, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part,
                                 grid, s);
 }
+
+nb_status ax_tma_f64(int n, bool pupd, int sm_count, long long E, const double *G,
+                      const double *u, double *w, const double *r, const double *dinv, double *p,
+                      CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s)
+{
+    return dispatch_ax_tma<double>(n, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
+                                s);
+}
+
+bool ax_tma_available_f64(int n, bool pupd) { return tma_fits<double>(n, pupd); }
 
 }  // namespace nb

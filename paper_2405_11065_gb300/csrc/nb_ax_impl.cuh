@@ -24,7 +24,7 @@
 // glsc3(w, c, p) of the assembled w for a continuous masked p.
 #pragma once
 
-#include "nb_internal.h"
+#include "nb_cg_dev.cuh"
 
 namespace nb {
 
@@ -35,7 +35,7 @@ template <typename T, int n, int M, bool PUPD>
 __global__ void __launch_bounds__(M * n * n)
 k_ax_cc(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__restrict__ w,
         const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
-        const CgScalars *__restrict__ scal, double *__restrict__ part)
+        CgScalars *__restrict__ scal, double *__restrict__ part)
 {
     constexpr int n2 = n * n, n3 = n2 * n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -74,7 +74,7 @@ k_ax_cc(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__re
             T v = T(0);
             if (valid) {
                 if (PUPD) {
-                    v = dinv[base + k * n2] * r[base + k * n2] + beta * p[base + k * n2];
+                    v = fabs(dinv[base + k * n2]) * r[base + k * n2] + beta * p[base + k * n2];
                     p[base + k * n2] = v;
                 } else {
                     v = uin[base + k * n2];
@@ -125,18 +125,10 @@ k_ax_cc(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__re
         }
     }
     if (part) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        const int lane = tid & 31, wid = tid >> 5;
-        if (lane == 0) sred[wid] = acc;
-        __syncthreads();
-        if (wid == 0) {
-            const int nw = (blockDim.x + 31) >> 5;
-            double v = lane < nw ? sred[lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) part[blockIdx.x] = v;
-        }
+        const double v = block_sum(acc, sred);
+        if (tid == 0) part[blockIdx.x] = v;
+        // in the solver, the last block to finish turns the partials into alpha
+        if (PUPD && last_block(&scal->tick_ax)) cg_finish_pap(scal, part, gridDim.x, sred);
     }
 }
 
@@ -149,7 +141,7 @@ constexpr size_t ax_cc_smem()
 // Launch helper: computes a persistent grid once from the occupancy.
 template <typename T, int n, int M, bool PUPD>
 nb_status launch_ax_cc(int sm_count, long long E, const T *G, const T *u, T *w, const T *r,
-                       const T *dinv, T *p, const CgScalars *scal, double *part, int *grid_io,
+                       const T *dinv, T *p, CgScalars *scal, double *part, int *grid_io,
                        cudaStream_t s)
 {
     auto kern = k_ax_cc<T, n, M, PUPD>;
@@ -182,7 +174,7 @@ nb_status launch_ax_cc(int sm_count, long long E, const T *G, const T *u, T *w, 
 template <typename T>
 nb_status dispatch_ax_cc(int n, int mchoice, bool pupd, int sm_count, long long E, const T *G,
                          const T *u, T *w, const T *r, const T *dinv, T *p,
-                         const CgScalars *scal, double *part, int *grid, cudaStream_t s)
+                         CgScalars *scal, double *part, int *grid, cudaStream_t s)
 {
 #define NB_AX_CASE(NN, M0, M1)                                                                 \
     case NN:                                                                                   \

@@ -27,7 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "nb_reduce.cuh"
+#include "nb_cg_dev.cuh"
 
 namespace nb {
 
@@ -158,7 +158,7 @@ template <typename H, int n, bool PUPD>
 __global__ void __launch_bounds__(kTcThreads)
 k_ax_tc(long long E, const float *__restrict__ G, const float *__restrict__ uin,
         float *__restrict__ w, const float *__restrict__ r, const float *__restrict__ dinv,
-        float *__restrict__ p, const CgScalars *__restrict__ scal, double *__restrict__ part)
+        float *__restrict__ p, CgScalars *__restrict__ scal, double *__restrict__ part)
 {
     constexpr int n3 = n * n * n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -202,7 +202,7 @@ k_ax_tc(long long E, const float *__restrict__ G, const float *__restrict__ uin,
         for (int q = tid; q < n3; q += kTcThreads) {
             float v;
             if (PUPD) {
-                v = dinv[base + q] * r[base + q] + beta * p[base + q];
+                v = fabsf(dinv[base + q]) * r[base + q] + beta * p[base + q];
                 p[base + q] = v;
             } else {
                 v = uin[base + q];
@@ -285,12 +285,13 @@ k_ax_tc(long long E, const float *__restrict__ G, const float *__restrict__ uin,
     if (part) {
         double tsum = block_sum(acc, sredd);
         if (tid == 0) part[blockIdx.x] = tsum;
+        if (PUPD && last_block(&scal->tick_ax)) cg_finish_pap(scal, part, gridDim.x, sredd);
     }
 }
 
 template <typename H, int n, bool PUPD>
 static nb_status launch_tc(int sm_count, long long E, const float *G, const float *u, float *w,
-                           const float *r, const float *dinv, float *p, const CgScalars *scal,
+                           const float *r, const float *dinv, float *p, CgScalars *scal,
                            double *part, int *grid_io, cudaStream_t s)
 {
     auto kern = k_ax_tc<H, n, PUPD>;
@@ -315,7 +316,7 @@ static nb_status launch_tc(int sm_count, long long E, const float *G, const floa
 template <typename H>
 static nb_status dispatch_tc(int n, bool pupd, int sm_count, long long E, const float *G,
                              const float *u, float *w, const float *r, const float *dinv, float *p,
-                             const CgScalars *scal, double *part, int *grid, cudaStream_t s)
+                             CgScalars *scal, double *part, int *grid, cudaStream_t s)
 {
 #define NB_TC_CASE(NN)                                                                        \
     case NN:                                                                                  \
@@ -347,7 +348,7 @@ static nb_status dispatch_tc(int n, bool pupd, int sm_count, long long E, const 
 }
 
 nb_status ax_tc(nb_mesh *m, nb_prec prec, bool pupd, const float *u, float *w, const float *r,
-                const float *dinv, float *p, const CgScalars *scal, double *part, int *grid,
+                const float *dinv, float *p, CgScalars *scal, double *part, int *grid,
                 cudaStream_t s)
 {
     if (prec == NB_TC_F16)

@@ -1,0 +1,326 @@
+// The operator with its element data streamed by the Blackwell bulk-copy
+// engine (TMA, cp.async.bulk) into a two-stage shared-memory ring.
+//
+// Same arithmetic and thread mapping as k_ax_cc (nb_ax_impl.cuh): one thread
+// per (i,j) column, k layers fully unrolled, the thread's u and w columns in
+// registers, wr/ws of one layer exchanged through shared memory.  What
+// changes is how the 6 geometric factors and the input vectors reach the
+// SM: one elected thread issues bulk copies of the whole element (G: 6 n^3
+// values; u, or r/dinv/p for the fused CG step) into the stage that the
+// block will use for its next element, completing on an mbarrier, while the
+// block computes the current element from the other stage.  The loads are
+// no longer tied to registers or warps in flight, so the kernel keeps about
+// one element per resident block in flight from HBM.
+//
+// Every wait on an mbarrier is bounded by one second of %globaltimer; a block
+// that times out sets *err, waits (bounded) for its own copies and exits.
+#pragma once
+
+#include "nb_ax_impl.cuh"
+#include "nb_reduce.cuh"
+
+namespace nb {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy completing on bar (bytes: multiple of 16, both
+// addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity; false after one second.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+template <int n>
+constexpr int tma_threads()
+{
+    return ((n * n + 31) / 32) * 32;
+}
+
+template <typename T, int n, bool PUPD>
+constexpr size_t ax_tma_stage_elems()
+{
+    return (size_t)(6 + (PUPD ? 3 : 1)) * n * n * n;
+}
+
+template <typename T, int n, bool PUPD>
+constexpr size_t ax_tma_smem()
+{
+    return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + 2 * n * n);
+}
+
+template <typename T, int n, bool PUPD>
+__global__ void __launch_bounds__(tma_threads<n>())
+k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__restrict__ w,
+         const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
+         CgScalars *__restrict__ scal, double *__restrict__ part, int *__restrict__ err)
+{
+    constexpr int n2 = n * n, n3 = n2 * n;
+    constexpr int STAGE = (int)ax_tma_stage_elems<T, n, PUPD>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *stage = reinterpret_cast<T *>(smem_raw);  // [2][STAGE]: G[6][n3], then vectors
+    T *swr = stage + 2 * STAGE;                  // [n2]
+    T *sws = swr + n2;                           // [n2]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double sred[32];
+
+    if (PUPD && scal->done) return;
+    const int tid = threadIdx.x;
+    const bool act = tid < n2;
+    const int ij = act ? tid : 0;
+    const int i = ij % n, j = ij / n;
+
+    T Di[n], Dj[n], DTi[n], DTj[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+        Di[l] = dtab<T>(n, i, l);
+        Dj[l] = dtab<T>(n, j, l);
+        DTi[l] = dtab<T>(n, l, i);
+        DTj[l] = dtab<T>(n, l, j);
+    }
+    const T beta = PUPD ? (T)scal->beta : T(0);
+    const long long mine = E > blockIdx.x ? (E - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // the elected thread streams element number t of this block into stage t&1
+    auto issue = [&](long long t) {
+        const long long e = blockIdx.x + t * gridDim.x;
+        T *dst = stage + (t & 1) * STAGE;
+        uint64_t *b = &bar[t & 1];
+        mbar_expect_tx(b, (uint32_t)(STAGE * sizeof(T)));
+        bulk_g2s(dst, G + (size_t)e * 6 * n3, (uint32_t)(6 * n3 * sizeof(T)), b);
+        if (PUPD) {
+            bulk_g2s(dst + 6 * n3, r + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
+            bulk_g2s(dst + 7 * n3, dinv + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
+            bulk_g2s(dst + 8 * n3, p + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
+        } else {
+            bulk_g2s(dst + 6 * n3, uin + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
+        }
+    };
+    if (tid == 0 && mine > 0) issue(0);
+
+    double acc = 0.0;
+    long long t = 0;
+    for (; t < mine; ++t) {
+        if (tid == 0 && t + 1 < mine) issue(t + 1);  // its stage was released at the end of t-1
+        const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) break;
+        const long long e = blockIdx.x + t * gridDim.x;
+        const size_t base = (size_t)e * n3 + ij;
+        T *s = stage + (t & 1) * STAGE;
+        const T *Gs = s;
+        T *su = s + (PUPD ? 8 : 6) * n3;  // u, or p (overwritten in place with the new p)
+        T ru[n], rw[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            T v;
+            if (PUPD) {
+                v = fabs(s[7 * n3 + k * n2 + ij]) * s[6 * n3 + k * n2 + ij] + beta * su[k * n2 + ij];
+                if (act) {
+                    su[k * n2 + ij] = v;
+                    p[base + k * n2] = v;
+                }
+            } else {
+                v = su[k * n2 + ij];
+            }
+            ru[k] = v;
+            rw[k] = T(0);
+        }
+        if (PUPD) __syncthreads();
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            const T g0 = Gs[0 * n3 + k * n2 + ij], g1 = Gs[1 * n3 + k * n2 + ij];
+            const T g2 = Gs[2 * n3 + k * n2 + ij], g3 = Gs[3 * n3 + k * n2 + ij];
+            const T g4 = Gs[4 * n3 + k * n2 + ij], g5 = Gs[5 * n3 + k * n2 + ij];
+            T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+            for (int l = 0; l < n; ++l) {
+                ur += Di[l] * su[k * n2 + j * n + l];
+                us += Dj[l] * su[k * n2 + l * n + i];
+                ut += dtab<T>(n, k, l) * ru[l];
+            }
+            const T wr = g0 * ur + g1 * us + g2 * ut;
+            const T ws = g1 * ur + g3 * us + g4 * ut;
+            const T wt = g2 * ur + g4 * us + g5 * ut;
+            if (act) {
+                swr[ij] = wr;
+                sws[ij] = ws;
+            }
+            __syncthreads();
+            T a = T(0);
+#pragma unroll
+            for (int l = 0; l < n; ++l) {
+                a += DTi[l] * swr[j * n + l];
+                a += DTj[l] * sws[l * n + i];
+            }
+            rw[k] += a;
+#pragma unroll
+            for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
+            __syncthreads();
+        }
+        if (act) {
+            T sdot = T(0);
+#pragma unroll
+            for (int k = 0; k < n; ++k) {
+                w[base + k * n2] = rw[k];
+                sdot += ru[k] * rw[k];
+            }
+            acc += (double)sdot;
+        }
+        // the last __syncthreads of the layer loop released this stage
+    }
+    if (t < mine) {
+        // a wait timed out: record it, let this block's copies land, stop
+        if (tid == 0) {
+            atomicExch(err, 1);
+            if (PUPD) {  // stop the solver's loop: this iteration cannot complete
+                scal->status = NB_BREAKDOWN;
+                scal->done = 1;
+            }
+            mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+            if (t + 1 < mine) mbar_wait_bounded(&bar[(t + 1) & 1], (uint32_t)(((t + 1) >> 1) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    if (part) {
+        const double v = block_sum(acc, sred);
+        if (tid == 0) part[blockIdx.x] = v;
+        if (PUPD && last_block(&scal->tick_ax)) cg_finish_pap(scal, part, gridDim.x, sred);
+    }
+}
+
+template <typename T, int n, bool PUPD>
+nb_status launch_ax_tma(int sm_count, long long E, const T *G, const T *u, T *w, const T *r,
+                        const T *dinv, T *p, CgScalars *scal, double *part, int *err,
+                        int *grid_io, cudaStream_t s)
+{
+    auto kern = k_ax_tma<T, n, PUPD>;
+    constexpr size_t smem = ax_tma_smem<T, n, PUPD>();
+    constexpr int threads = tma_threads<n>();
+    static int grid_cache = 0;
+    static int sm_cached = 0;
+    if (grid_cache == 0 || sm_cached != sm_count) {
+        NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
+        sm_cached = sm_count;
+    }
+    int grid = (int)(E < grid_cache ? E : grid_cache);
+    if (grid < 1) grid = 1;
+    if (grid > kMaxPartials) grid = kMaxPartials;
+    kern<<<grid, threads, smem, s>>>(E, G, u, w, r, dinv, p, scal, part, err);
+    NB_CUDA(cudaGetLastError());
+    if (grid_io) *grid_io = grid;
+    return NB_OK;
+}
+
+// The bulk-copy variant needs 16-byte multiples (n even) and two stages in
+// the 227 KB of shared memory a block may use.
+template <typename T>
+constexpr bool tma_fits(int n, bool pupd)
+{
+    return (n % 2 == 0) &&
+           sizeof(T) * (2 * (size_t)(6 + (pupd ? 3 : 1)) * n * n * n + 2 * n * n) <= 227 * 1024;
+}
+
+template <typename T>
+nb_status dispatch_ax_tma(int n, bool pupd, int sm_count, long long E, const T *G, const T *u,
+                          T *w, const T *r, const T *dinv, T *p, CgScalars *scal,
+                          double *part, int *err, int *grid, cudaStream_t s)
+{
+    if (!tma_fits<T>(n, pupd)) {
+        set_error("bulk-copy operator variant unavailable for n=%d", n);
+        return NB_ERR_ARG;
+    }
+#define NB_TMA_CASE(NN)                                                                        \
+    case NN:                                                                                   \
+        if constexpr (tma_fits<T>(NN, true)) {                                                 \
+            if (pupd)                                                                          \
+                return launch_ax_tma<T, NN, true>(sm_count, E, G, u, w, r, dinv, p, scal, part, \
+                                                  err, grid, s);                               \
+        }                                                                                      \
+        if constexpr (tma_fits<T>(NN, false)) {                                                \
+            if (!pupd)                                                                         \
+                return launch_ax_tma<T, NN, false>(sm_count, E, G, u, w, r, dinv, p, scal,     \
+                                                   part, err, grid, s);                        \
+        }                                                                                      \
+        break;
+    switch (n) {
+        NB_TMA_CASE(2)
+        NB_TMA_CASE(4)
+        NB_TMA_CASE(6)
+        NB_TMA_CASE(8)
+        NB_TMA_CASE(10)
+        NB_TMA_CASE(12)
+        NB_TMA_CASE(14)
+        NB_TMA_CASE(16)
+        default:
+            break;
+    }
+#undef NB_TMA_CASE
+    set_error("bulk-copy operator variant unavailable for n=%d", n);
+    return NB_ERR_ARG;
+}
+
+}  // namespace nb

@@ -54,8 +54,10 @@ struct CgScalars {
     int done;         // 1 when the loop must stop
     int status;       // 0 running/converged, NB_NOT_CONVERGED, NB_BREAKDOWN
     int hist_cap;     // capacity of hist
-    int pad_;
+    int loops;        // executions of the graph's loop body (hard stop at maxit + 1)
     double *hist;     // device history (relres per iteration) or nullptr
+    unsigned int tick_ax;   // blocks of the operator kernel done (last block finalises)
+    unsigned int tick_upd;  // blocks of the update kernel done
 };
 
 // A preallocated set of vectors for one solve precision.
@@ -126,6 +128,7 @@ struct nb_mesh {
     double *red_out = nullptr;       // device scalar for glsc3/norms
     double *red_host = nullptr;      // pinned mirror
     nb::AxConfig ax_cfg[4];
+    int *kerr = nullptr;             // device flag: a pipelined kernel's wait timed out
     int64_t launches = 0;            // kernels issued by the current solve
     // learned preconditioner (optional)
     void *learned = nullptr;
@@ -147,7 +150,7 @@ nb_status upload_deriv_tables(int n, const double *D64);
 nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap_part,
                    int *nparts, cudaStream_t s);
 nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, void *p,
-                     void *w, const CgScalars *scal, double *pap_part, int *nparts,
+                     void *w, CgScalars *scal, double *pap_part, int *nparts,
                      cudaStream_t s);
 int ax_variant_count(const nb_mesh *m, nb_prec prec);
 

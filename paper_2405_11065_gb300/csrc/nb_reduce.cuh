@@ -36,6 +36,35 @@ __device__ __forceinline__ double sum_partials(const double *part, int cnt, doub
     return block_sum(v, sred);
 }
 
+// Per-thread accumulation of a dot product with FP64 accuracy.  For double
+// terms it is a plain FP64 sum.  For float terms it is a compensated FP32 sum
+// (Knuth's TwoSum: s + c carries the rounding error of every addition),
+// converted to FP64 once per thread: FP64-level accuracy for the FP32
+// products without an FP64 instruction per term, which matters on a GPU whose
+// FP64 rate is a small fraction of its FP32 rate.
+template <typename T>
+struct DotAcc;
+
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct DotAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 constexpr int kVecThreads = 256;
 
 inline int vec_grid(const nb_ctx *ctx, int64_t n)

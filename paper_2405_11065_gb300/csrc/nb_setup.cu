@@ -170,6 +170,8 @@ nb_status build_geometry(nb_mesh *m)
     cudaStream_t s = m->ctx->stream;
     double *dxi = nullptr, *dw = nullptr;
     int *dbad = nullptr;
+    NB_CUDA(cudaMalloc(&m->kerr, sizeof(int)));
+    NB_CUDA(cudaMemsetAsync(m->kerr, 0, sizeof(int), s));
     NB_CUDA(cudaMalloc(&m->D64, sizeof(double) * n * n));
     NB_CUDA(cudaMalloc(&m->D32, sizeof(float) * n * n));
     float D32h[kMaxn * kMaxn];

@@ -3,15 +3,16 @@
 // The iteration follows Table 1 of the case study: z = solveM(r);
 // rtz1 = glsc3(r,c,z); p = beta p + z (add2s1); w = ax(p) with dssum;
 // pap = glsc3(w,c,p); x += alpha p, r -= alpha w (add2s2); rtr = glsc3(r,c,r).
-// On the GPU the nine lines become five launches per iteration:
-//   1. ax_cg_step: p = dinv*r + beta*p, w_L = A_L p, partials of p.w_L (= pap)
+// On the GPU the nine lines become three kernels per iteration:
+//   1. ax_cg_step: p = dinv*r + beta*p, w_L = A_L p, partials of p.w_L (= pap);
+//      its last block sums them: alpha = rtz/pap (breakdown check)
 //   2. dssum + mask of w
-//   3. fin_pap: pap, alpha = rtz/pap (breakdown check)
-//   4. update: x += alpha p, r -= alpha w, partials of (r,c,dinv r), (r,c,r)
-//   5. fin_iter: rtz, rtr, beta = rtz/rtz_old, convergence, iteration limit
+//   3. update: x += alpha p, r -= alpha w, partials of (r,c,dinv r), (r,c,r);
+//      its last block sums them: beta, convergence, iteration limit
 // All scalars live in device memory, so the iteration is captured once in a
-// CUDA graph whose while-node repeats it until fin_iter clears the condition
-// (converged, iteration limit, or breakdown): one graph launch per solve.
+// CUDA graph whose while-node repeats it (a fourth, one-thread kernel sets the
+// loop condition) until converged, at the iteration limit, or on breakdown:
+// one graph launch per solve.
 //
 // Mixed precision (Section 6 runs the CG loop in single precision, set-up in
 // double): the reduced-precision solve sits inside FP64 iterative refinement.
@@ -22,7 +23,7 @@
 
 #include <algorithm>
 
-#include "nb_reduce.cuh"
+#include "nb_cg_dev.cuh"
 
 namespace nb {
 
@@ -44,24 +45,40 @@ __global__ void k_cg_setup(CgScalars *sc, double tol, int maxit, double *hist, i
     sc->status = 0;
     sc->beta = 0.0;
     sc->alpha = 0.0;
+    sc->loops = 0;
+    sc->tick_ax = 0u;
+    sc->tick_upd = 0u;
 }
 
-// p = 0; partials of (r, c, dinv r) and (r, c, r).
+// The weighted dot products glsc3(a, c, b) of the iteration, for continuous
+// vectors, equal plain sums over one "owner" copy of every global node.  The
+// solver's preconditioner array carries that ownership in its sign bit
+// (dinv >= +0 on the owner copy, <= -0 on the others; |dinv| is the Jacobi
+// factor), so the iteration reads no weight vector.
+template <typename T>
+__device__ __forceinline__ bool owner_copy(T d)
+{
+    return !signbit(d);
+}
+
+// p = 0; partials of (r, dinv r) and (r, r) over owner copies.
 template <typename T>
 __global__ void k_cg_init(int64_t nL, const T *__restrict__ r, const T *__restrict__ dinv,
-                          const float *__restrict__ c, T *__restrict__ p, double *__restrict__ part)
+                          T *__restrict__ p, double *__restrict__ part)
 {
     __shared__ double sred[32];
-    double a = 0.0, b = 0.0;
+    DotAcc<T> a, b;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
          l += (int64_t)gridDim.x * blockDim.x) {
-        const T rl = r[l], cl = (T)c[l];
+        const T rl = r[l], d = dinv[l];
         p[l] = T(0);
-        a += (double)(cl * rl * (dinv[l] * rl));
-        b += (double)(cl * rl * rl);
+        if (owner_copy(d)) {
+            a.add(rl * (d * rl));
+            b.add(rl * rl);
+        }
     }
-    double ta = block_sum(a, sred);
-    double tb = block_sum(b, sred);
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -96,82 +113,46 @@ __global__ void k_cg_init_fin(CgScalars *sc, const double *__restrict__ part, in
     }
 }
 
-__global__ void k_cg_fin_pap(CgScalars *sc, const double *__restrict__ part, int cnt)
-{
-    __shared__ double sred[32];
-    if (sc->done) return;
-    double pap = sum_partials(part, cnt, sred);
-    if (threadIdx.x == 0) {
-        sc->pap = pap;
-        double alpha = sc->rtz / pap;
-        if (!(pap > 0.0) || !isfinite(alpha)) {
-            sc->alpha = 0.0;
-            sc->done = 1;
-            sc->status = NB_BREAKDOWN;
-        } else {
-            sc->alpha = alpha;
-        }
-    }
-}
-
 // add2s2 twice, then solveM and the two dot products of the next iteration.
 template <typename T>
-__global__ void k_cg_update(int64_t nL, const CgScalars *__restrict__ sc, T *__restrict__ x,
+__global__ void k_cg_update(int64_t nL, CgScalars *__restrict__ sc, T *__restrict__ x,
                             T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ w,
-                            const T *__restrict__ dinv, const float *__restrict__ c,
-                            double *__restrict__ part)
+                            const T *__restrict__ dinv, double *__restrict__ part)
 {
     __shared__ double sred[32];
     if (sc->done) return;
     const T alpha = (T)sc->alpha;
-    double a = 0.0, b = 0.0;
+    DotAcc<T> a, b;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
          l += (int64_t)gridDim.x * blockDim.x) {
         x[l] = x[l] + alpha * p[l];
         const T rl = r[l] - alpha * w[l];
         r[l] = rl;
-        const T cl = (T)c[l];
-        a += (double)(cl * rl * (dinv[l] * rl));
-        b += (double)(cl * rl * rl);
+        const T d = dinv[l];
+        if (owner_copy(d)) {
+            a.add(rl * (d * rl));
+            b.add(rl * rl);
+        }
     }
-    double ta = block_sum(a, sred);
-    double tb = block_sum(b, sred);
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
     }
+    // the last block to finish: rtz, rtr, beta, convergence (nb_cg_dev.cuh)
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
-__global__ void k_cg_fin_iter(CgScalars *sc, const double *__restrict__ part, int cnt,
-                              cudaGraphConditionalHandle h, int use_cond)
+// The while-node condition of the captured iteration.  It counts executions
+// of the loop body itself, so the loop ends after maxit + 1 bodies even if
+// no other kernel of the body managed to set `done`.
+__global__ void k_cg_cond(CgScalars *sc, cudaGraphConditionalHandle h)
 {
-    __shared__ double sred[32];
-    if (!sc->done) {
-        double rtz = sum_partials(part, cnt, sred);
-        double rtr = sum_partials(part + cnt, cnt, sred);
-        if (threadIdx.x == 0) {
-            sc->rtz_old = sc->rtz;
-            sc->rtz = rtz;
-            sc->rtr = rtr;
-            sc->beta = rtz / sc->rtz_old;
-            const int it = sc->iter + 1;
-            sc->iter = it;
-            const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
-            const double rel = sqrt(rtr / bn);
-            sc->relres = rel;
-            if (sc->hist && it <= sc->hist_cap) sc->hist[it - 1] = rel;
-            if (!isfinite(rel) || !isfinite(sc->beta)) {
-                sc->done = 1;
-                sc->status = NB_BREAKDOWN;
-            } else if (rel < sc->tol) {
-                sc->done = 1;
-            } else if (it >= sc->maxit) {
-                sc->done = 1;
-                sc->status = NB_NOT_CONVERGED;
-            }
-        }
-    }
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+    const int loops = sc->loops + 1;
+    sc->loops = loops;
+    const bool stop = sc->done != 0 || loops > sc->maxit;
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
 // r = b - w (FP64) and partials of (r, c, r).
@@ -267,7 +248,9 @@ static nb_status ensure_fp64_bufs(nb_mesh *m)
     return NB_OK;
 }
 
-// The five launches of one iteration (see the file comment).
+// The launches of one iteration (see the file comment): operator (its last
+// block computes alpha), gather-scatter, update (its last block computes
+// beta and the stopping test), and inside a graph the loop condition.
 template <typename T>
 static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
                          cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
@@ -275,16 +258,17 @@ static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
     int nparts = 0;
     NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
     NB_TRY(dssum(m, prec, ws.w, 1, s));
-    k_cg_fin_pap<<<1, kFinalizeThreads, 0, s>>>(ws.scal, ws.part, nparts);
-    NB_CUDA(cudaGetLastError());
     const int g = vec_grid(m->ctx, m->nL);
     double *up = ws.part + kMaxPartials;
     k_cg_update<T><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, (T *)ws.x, (T *)ws.r,
-                                             (const T *)ws.p, (const T *)ws.w, dinv, m->c32, up);
+                                             (const T *)ws.p, (const T *)ws.w, dinv, up);
     NB_CUDA(cudaGetLastError());
-    k_cg_fin_iter<<<1, kFinalizeThreads, 0, s>>>(ws.scal, up, g, h, use_cond);
-    NB_CUDA(cudaGetLastError());
-    if (!use_cond) m->launches += 5;
+    if (use_cond) {
+        k_cg_cond<<<1, 1, 0, s>>>(ws.scal, h);
+        NB_CUDA(cudaGetLastError());
+    } else {
+        m->launches += 3;
+    }
     return NB_OK;
 }
 
@@ -297,7 +281,7 @@ static nb_status cg_start(nb_mesh *m, Workspace &ws, const T *dinv, double tol, 
                                hist ? ws.hist_cap : 0);
     NB_CUDA(cudaGetLastError());
     const int g = vec_grid(m->ctx, m->nL);
-    k_cg_init<T><<<g, kVecThreads, 0, s>>>(m->nL, (const T *)ws.r, dinv, m->c32, (T *)ws.p,
+    k_cg_init<T><<<g, kVecThreads, 0, s>>>(m->nL, (const T *)ws.r, dinv, (T *)ws.p,
                                            ws.part + kMaxPartials);
     NB_CUDA(cudaGetLastError());
     k_cg_init_fin<<<1, kFinalizeThreads, 0, s>>>(ws.scal, ws.part + kMaxPartials, g, bnorm_from_r);
@@ -428,7 +412,7 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
     }
     const double bn2 = m->red_host[0] > 0 ? m->red_host[0] : 1.0;
     if (st) {
-        if (o->use_graph) m->launches += 5 * (int64_t)std::max(h.iter, 1);
+        if (o->use_graph) m->launches += 4 * (int64_t)std::max(h.iter, 1);
         st->iters = h.iter;
         st->outer_iters = 0;
         st->launches = m->launches;
@@ -489,15 +473,18 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                            (float *)ws.x);
         NB_CUDA(cudaGetLastError());
         const int remaining = o->maxiter - used;
+        // the inner solve only has to close the remaining gap to rtol (with a
+        // factor 2 of margin), and never less than inner_rtol per step
+        const double tau = std::min(0.5, std::max(o->inner_rtol, 0.5 * o->rtol / rel));
         if (o->pc == NB_PC_LEARNED) {
             // flexible CG with the learned preconditioner (nb_learned.cu)
-            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, o->inner_rtol, remaining,
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, remaining,
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
             NB_TRY(fcg_learned(m, o->prec, ws, o, s));
         } else {
-            NB_TRY(cg_start<float>(m, ws, dinv, o->inner_rtol, remaining, 1, o->record_history, s));
+            NB_TRY(cg_start<float>(m, ws, dinv, tau, remaining, 1, o->record_history, s));
             NB_TRY(cg_iterate<float>(m, o->prec, ws, dinv, 20 * (int)o->prec + (int)o->pc,
                                      o->use_graph, remaining, s));
         }
@@ -508,7 +495,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         const int it = ws.scal_host->iter;
-        if (o->use_graph && o->pc != NB_PC_LEARNED) m->launches += 5 * (int64_t)std::max(it, 1);
+        if (o->use_graph && o->pc != NB_PC_LEARNED) m->launches += 4 * (int64_t)std::max(it, 1);
         if (o->record_history) {
             copy_history(ws, it, hist_off, st, s);
             hist_off += it;

@@ -168,25 +168,34 @@ nb_status local_diag(nb_mesh *m, double *diag, cudaStream_t s)
     return NB_OK;
 }
 
-__global__ void k_finish_jacobi(int64_t nL, const double *__restrict__ diag, double *dinv64,
-                                float *dinv32, double *ones64, float *ones32)
+// Inverse assembled diagonal (0 on Dirichlet nodes) and the identity
+// preconditioner (the mask).  The sign bit of both marks the copy that owns
+// its global node (+ on the first local copy, - on the others): the solver's
+// dot products sum over owner copies instead of weighting every copy by
+// 1/multiplicity, and the preconditioner applies |value|.
+__global__ void k_finish_jacobi(int64_t nL, const double *__restrict__ diag,
+                                const int32_t *__restrict__ gid,
+                                const int32_t *__restrict__ first, double *dinv64, float *dinv32,
+                                double *ones64, float *ones32)
 {
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
          l += (int64_t)gridDim.x * blockDim.x) {
         const double d = diag[l];
-        const double v = d != 0.0 ? 1.0 / d : 0.0;
+        const double sgn = first[gid[l]] == (int32_t)l ? 1.0 : -1.0;
+        const double v = sgn * (d != 0.0 ? 1.0 / d : 0.0);
+        const double one = sgn * (d != 0.0 ? 1.0 : 0.0);
         dinv64[l] = v;
         dinv32[l] = (float)v;
-        ones64[l] = d != 0.0 ? 1.0 : 0.0;
-        ones32[l] = d != 0.0 ? 1.0f : 0.0f;
+        ones64[l] = one;
+        ones32[l] = (float)one;
     }
 }
 
 nb_status finish_jacobi(nb_mesh *m, double *diag, cudaStream_t s)
 {
     int grid = vec_grid(m->ctx, m->nL);
-    k_finish_jacobi<<<grid, kVecThreads, 0, s>>>(m->nL, diag, m->dinv64, m->dinv32, m->ones64,
-                                                 m->ones32);
+    k_finish_jacobi<<<grid, kVecThreads, 0, s>>>(m->nL, diag, m->gid, m->g_first, m->dinv64,
+                                                 m->dinv32, m->ones64, m->ones32);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
