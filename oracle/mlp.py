@@ -1,0 +1,101 @@
+"""FP64 reference of the per-element network used as a learned preconditioner.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The network maps an element's residual, divided by its Euclidean norm, to a
+correction of the same length d = (N+1)^3, which the preconditioner scales
+back by that norm:
+
+    Z = X W1 + b1,  H = gelu(Z),  Y = H W2 + b2
+
+with the tanh form of GELU, gelu(z) = z/2 (1 + tanh(sqrt(2/pi)(z + 0.044715 z^3))).
+Training minimises the mean squared error L = sum((Y - T)^2) / (B d) over a
+batch of B pairs with Adam (Kingma and Ba, 2015).  The backward pass below is
+the chain rule written out; it is pinned against central finite differences
+of ``loss`` by the tests.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_C = math.sqrt(2.0 / math.pi)
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + np.tanh(_C * (z + 0.044715 * z ** 3)))
+
+
+def gelu_grad(z):
+    u = _C * (z + 0.044715 * z ** 3)
+    t = np.tanh(u)
+    du = _C * (1.0 + 3 * 0.044715 * z ** 2)
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * du
+
+
+def init_params(d: int, h: int, seed: int):
+    """Deterministic initialisation (uniform, scaled by 1/sqrt(fan-in))."""
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.uniform(-1, 1, (d, h)) / math.sqrt(d),
+        "b1": np.zeros(h),
+        "W2": rng.uniform(-1, 1, (h, d)) / math.sqrt(h),
+        "b2": np.zeros(d),
+    }
+
+
+def forward(params, X):
+    Z = X @ params["W1"] + params["b1"]
+    H = gelu(Z)
+    Y = H @ params["W2"] + params["b2"]
+    return Y, (X, Z, H)
+
+
+def loss(params, X, T):
+    Y, _ = forward(params, X)
+    return float(np.sum((Y - T) ** 2) / Y.size)
+
+
+def backward(params, X, T):
+    """Gradients of ``loss`` with respect to every parameter."""
+    Y, (X, Z, H) = forward(params, X)
+    dY = 2.0 * (Y - T) / Y.size
+    gW2 = H.T @ dY
+    gb2 = dY.sum(axis=0)
+    dH = dY @ params["W2"].T
+    dZ = dH * gelu_grad(Z)
+    gW1 = X.T @ dZ
+    gb1 = dZ.sum(axis=0)
+    return {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2}
+
+
+def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update in place; ``state`` holds m, v and the step count t."""
+    t = state.get("t", 0) + 1
+    state["t"] = t
+    for k in params:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[:] = b1 * m + (1 - b1) * grads[k]
+        v[:] = b2 * v + (1 - b2) * grads[k] ** 2
+        mhat = m / (1 - b1 ** t)
+        vhat = v / (1 - b2 ** t)
+        params[k] = params[k] - lr * mhat / (np.sqrt(vhat) + eps)
+    return params
+
+
+def make_pairs(r_elems: np.ndarray, e_elems: np.ndarray):
+    """Training pairs from element slices of residuals and errors (rows):
+    input r/|r|, target e/|r| (rows with |r| = 0 are dropped)."""
+    nrm = np.linalg.norm(r_elems, axis=1)
+    keep = nrm > 0
+    return r_elems[keep] / nrm[keep, None], e_elems[keep] / nrm[keep, None]
+
+
+def precondition(params, r_elems: np.ndarray):
+    """Element corrections |r_e| * MLP(r_e / |r_e|) (zero where r_e = 0)."""
+    nrm = np.linalg.norm(r_elems, axis=1)
+    safe = np.where(nrm > 0, nrm, 1.0)
+    Y, _ = forward(params, r_elems / safe[:, None])
+    return Y * nrm[:, None]

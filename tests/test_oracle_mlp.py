@@ -1,0 +1,68 @@
+"""Pins of the network oracle: backward pass against central finite
+differences of the loss, GELU against its closed form, Adam against a
+hand-computed first step."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_gelu_closed_form_and_derivative():
+    z = np.linspace(-4, 4, 81)
+    ref = 0.5 * z * (1 + np.tanh(math.sqrt(2 / math.pi) * (z + 0.044715 * z ** 3)))
+    np.testing.assert_allclose(mlp.gelu(z), ref, rtol=0, atol=0)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    np.testing.assert_allclose(mlp.gelu_grad(z), fd, rtol=1e-8, atol=1e-9)
+    assert abs(mlp.gelu(np.array([0.0]))[0]) == 0.0
+    assert abs(mlp.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+
+
+@pytest.mark.parametrize("shape", [(8, 4, 5), (27, 6, 3)])
+def test_backward_matches_finite_differences(shape):
+    d, h, B = shape
+    p = mlp.init_params(d, h, seed=3)
+    rng = np.random.default_rng(4)
+    p["b1"] = rng.uniform(-0.5, 0.5, h)
+    p["b2"] = rng.uniform(-0.5, 0.5, d)
+    X = rng.uniform(-1, 1, (B, d))
+    T = rng.uniform(-1, 1, (B, d))
+    g = mlp.backward(p, X, T)
+    eps = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(12, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp = mlp.loss(p, X, T)
+            flat[idx] = old - eps
+            lm = mlp.loss(p, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            got = g[k].reshape(-1)[idx]
+            assert abs(got - fd) <= 1e-7 * max(1.0, abs(fd)) + 1e-10, (k, idx, got, fd)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    p = {"w": np.array([1.0, -2.0, 3.0])}
+    g = {"w": np.array([0.5, -0.25, 0.0])}
+    st = {}
+    mlp.adam_step(p, g, st, lr=0.1)
+    # first step: mhat = g, vhat = g^2 -> update = lr * g / (|g| + eps)
+    np.testing.assert_allclose(p["w"], [1.0 - 0.1, -2.0 + 0.1, 3.0], atol=1e-9)
+
+
+def test_training_reduces_loss_on_a_linear_map():
+    rng = np.random.default_rng(0)
+    d, h = 16, 8
+    A = rng.normal(size=(d, d)) / 4
+    X = rng.normal(size=(256, d))
+    T = X @ A
+    p = mlp.init_params(d, h, seed=1)
+    st = {}
+    l0 = mlp.loss(p, X, T)
+    for _ in range(300):
+        mlp.adam_step(p, mlp.backward(p, X, T), st, lr=3e-3)
+    assert mlp.loss(p, X, T) < 0.5 * l0
