@@ -54,6 +54,9 @@ def parse():
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture)")
     ap.add_argument("--prec", default="fp32", help="precision of --mode ax")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default operator variants (profiler runs: timing under a "
+                         "profiler would steer the autotuner)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the iteration's kernels from the host instead of one CUDA graph "
                          "(same kernels; lets a profiler list them one by one)")
@@ -267,6 +270,9 @@ def main():
     # autotune the operator (per precision, this order) before timing
     tune = {}
     for pname, prec in (("fp32", nb.NB_FP32), ("fp64", nb.NB_FP64)):
+        if args.no_autotune:
+            tune[pname] = {"variant": -1, "ms": None}
+            continue
         v, ms = mesh.autotune(prec, reps=3, flush=flush)
         tune[pname] = {"variant": v, "ms": ms}
 

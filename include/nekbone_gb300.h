@@ -232,6 +232,105 @@ int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
 nb_status nb_autotune(nb_mesh *mesh, nb_prec prec, int reps, void *flush_dev,
                       size_t flush_bytes, int *best_variant, double *best_ms);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent Poisson problems of different size and
+ * order solved together, every CG iteration of all problems captured in one
+ * CUDA graph (the extension of Table 1's loop to a batch; the paper solves one
+ * problem per process).
+ * ------------------------------------------------------------------------ */
+typedef struct nb_batch nb_batch;
+
+/* Build nprob box meshes (arrays of length nprob: element counts, orders
+ * 1 <= N <= 15, deformations as in nb_setup_mesh) with their gather-scatter,
+ * and lay them out as one batch.  The batch L-vector stores the problems one
+ * after another, grouped by order (problems of equal order keep their
+ * relative order); nb_batch_layout reports where each problem sits.
+ * Errors: NB_ERR_ARG, NB_ERR_MESH, NB_ERR_OOM, NB_ERR_CUDA. */
+nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, const int *ny, const int *nz,
+                          const int *N, const double *deform, nb_batch **out);
+
+nb_status nb_batch_destroy(nb_batch *batch);
+
+/* Per problem p (caller's numbering): l_off[p] = offset of its L-vector in
+ * the batch L-vector, g_off[p] = offset of its G-vector in the batch G-vector
+ * (G-vectors concatenated in the caller's order), and if not NULL
+ * totals[0] = batch L length, totals[1] = batch G length. */
+nb_status nb_batch_layout(const nb_batch *batch, int64_t *l_off, int64_t *g_off,
+                          int64_t totals[2]);
+
+/* The mesh of problem p (owned by the batch), e.g. for nb_to_local on it. */
+nb_mesh *nb_batch_mesh(nb_batch *batch, int p);
+
+/* Batch L-vector from the concatenated G-vectors (FP64), masked. */
+nb_status nb_batch_to_local(nb_batch *batch, const double *ug_dev, double *uL_dev);
+
+/* Solve every problem of the batch: b_dev, x_dev are FP64 batch L-vectors
+ * (x: solution out; opts.use_x0 as in nb_solve).  opts.prec: NB_FP64 (plain
+ * PCG for all problems) or NB_FP32 (FP64 refinement around batched FP32 PCG,
+ * per-problem scaling and inner tolerances).  Each problem stops on its own
+ * criterion; the batch stops when all have.  stats[p] (array of nprob, may
+ * be NULL) receives each problem's outcome; *total (may be NULL) the batch's
+ * (iters = batched iterations, seconds = wall time, launches).
+ * Returns the worst outcome over the problems, or a negative error. */
+nb_status nb_batch_solve(nb_batch *batch, const nb_opts *opts, const double *b_dev,
+                         double *x_dev, nb_stats *stats, nb_stats *total);
+
+/* Autotuner for the batch: for every order present, time each operator
+ * variant on that order's elements (reps launches) and keep the fastest. */
+nb_status nb_batch_autotune(nb_batch *batch, int reps, void *flush_dev, size_t flush_bytes);
+
+/* ------------------------------------------------------------------------
+ * Learned preconditioner: a per-element network (one hidden layer with GELU,
+ * BF16 tensor-core products with FP32 accumulation, FP32 master weights)
+ * mapping an element's residual r_e / |r_e| to a correction, used as
+ * z = M Q Q^T(c |r_e| MLP(r_e/|r_e|)) inside flexible CG.  Not in the paper;
+ * it replaces the paper's multigrid solveM slot with a learned one.
+ * ------------------------------------------------------------------------ */
+typedef struct nb_model nb_model;
+
+/* A network for order N: d = (N+1)^3 inputs and outputs, `hidden` units,
+ * weights uniform(-1,1)/sqrt(fan-in) drawn from SplitMix64(seed), biases 0. */
+nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t seed, nb_model **out);
+nb_status nb_model_destroy(nb_model *model);
+
+/* Parameters as one FP32 host array [W1 (d x h, row-major), b1 (h),
+ * W2 (h x d), b2 (d)]: copied out to get_host and/or in from set_host (either
+ * may be NULL); *nparam (may be NULL) receives the count. */
+nb_status nb_model_params(nb_model *model, float *get_host, const float *set_host,
+                          int64_t *nparam);
+
+/* Loss sum((Y - T)^2) / (B d) and its gradient (same layout as the
+ * parameters) on B pairs X, T (device, B x d FP32, row-major). */
+nb_status nb_model_grad(nb_model *model, const float *X_dev, const float *T_dev, int B,
+                        double *loss_host, float *grad_host);
+
+/* Adam (lr, 0.9, 0.999, 1e-8) over `epochs` passes of consecutive minibatches
+ * of `batch` pairs; *final_loss (may be NULL) = mean loss of the last epoch. */
+nb_status nb_model_train(nb_model *model, const float *X_dev, const float *T_dev, int npairs,
+                         int epochs, int batch, float lr, double *final_loss);
+
+/* Training pairs from the solver itself: solves A x = b (b: FP64 L-vector,
+ * continuous, masked), then for each of nsnap iteration counts runs that many
+ * Jacobi-PCG iterations from zero and, for per_snap elements drawn with
+ * SplitMix64(seed), writes X = r_k|e / |r_k|e| and T = (x* - x_k)|e / |r_k|e|
+ * (device FP32, capacity nsnap * per_snap * d).  *count = pairs written. */
+nb_status nb_learned_collect(nb_mesh *mesh, const double *b_dev, int nsnap,
+                             const int *snap_iters, int per_snap, uint64_t seed,
+                             float *X_dev, float *T_dev, int *count);
+
+/* Pairs from given residual and error L-vectors (FP64, device) for the listed
+ * elements (device int32). */
+nb_status nb_learned_pairs(nb_mesh *mesh, const double *r_dev, const double *err_dev,
+                           const int32_t *elems_dev, int count, float *X_dev, float *T_dev);
+
+/* Use `model` (NULL detaches) as the mesh's NB_PC_LEARNED preconditioner;
+ * jacobi_add != 0 adds the Jacobi term dinv*r to its output.  The model must
+ * outlive its use. */
+nb_status nb_learned_attach(nb_mesh *mesh, nb_model *model, int jacobi_add);
+
+/* Apply the attached preconditioner once: z = B(r), FP32 L-vectors. */
+nb_status nb_learned_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
+
 /* nb_glsc3 for callers that cannot let a library allocate memory: a
  * framework whose caching allocator owns the device memory, a process under
  * a hard memory budget, or a latency-critical loop that must not pay for

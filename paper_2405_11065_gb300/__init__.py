@@ -71,6 +71,22 @@ def _load():
         "nb_dssum": (i32, [vp, i32, vp, i32]),
         "nb_glsc3": (i32, [vp, i32, vp, vp, C.POINTER(dbl)]),
         "nb_glsc3_noalloc": (i32, [vp, i32, vp, vp, C.POINTER(dbl)]),
+        "nb_batch_create": (i32, [vp, i32, vp, vp, vp, vp, vp, C.POINTER(vp)]),
+        "nb_batch_destroy": (i32, [vp]),
+        "nb_batch_layout": (i32, [vp, vp, vp, vp]),
+        "nb_batch_mesh": (vp, [vp, i32]),
+        "nb_batch_to_local": (i32, [vp, vp, vp]),
+        "nb_batch_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, vp, C.POINTER(nb_stats)]),
+        "nb_batch_autotune": (i32, [vp, i32, vp, C.c_size_t]),
+        "nb_model_create": (i32, [vp, i32, i32, C.c_uint64, C.POINTER(vp)]),
+        "nb_model_destroy": (i32, [vp]),
+        "nb_model_params": (i32, [vp, vp, vp, C.POINTER(i64)]),
+        "nb_model_grad": (i32, [vp, vp, vp, i32, C.POINTER(dbl), vp]),
+        "nb_model_train": (i32, [vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl)]),
+        "nb_learned_collect": (i32, [vp, vp, i32, vp, i32, C.c_uint64, vp, vp, C.POINTER(i32)]),
+        "nb_learned_pairs": (i32, [vp, vp, vp, vp, i32, vp, vp]),
+        "nb_learned_attach": (i32, [vp, vp, i32]),
+        "nb_learned_apply": (i32, [vp, vp, vp]),
         "nb_default_opts": (None, [C.POINTER(nb_opts)]),
         "nb_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
         "nb_solve_host": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
@@ -270,7 +286,135 @@ class Mesh:
         return v.value, ms.value
 
 
-__all__ = ["lib", "LIB_PATH", "NbError", "Context", "Mesh", "default_opts", "check",
+class Batch:
+    """nb_batch_create/destroy/solve: independent problems of mixed size and
+    order solved together.  ``boxes``: objects with nx, ny, nz, N, deform."""
+
+    def __init__(self, ctx: Context, boxes):
+        n = len(boxes)
+        arr = lambda f, t: np.ascontiguousarray([f(b) for b in boxes], dtype=t)
+        self._keep = [arr(lambda b: b.nx, np.int32), arr(lambda b: b.ny, np.int32),
+                      arr(lambda b: b.nz, np.int32), arr(lambda b: b.N, np.int32),
+                      arr(lambda b: b.deform, np.float64)]
+        h = C.c_void_p()
+        check(lib.nb_batch_create(ctx.h, n, *[_ptr(a) for a in self._keep], C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+        self.nprob = n
+        self.l_off = np.zeros(n, np.int64)
+        self.g_off = np.zeros(n, np.int64)
+        tot = np.zeros(2, np.int64)
+        check(lib.nb_batch_layout(self.h, _ptr(self.l_off), _ptr(self.g_off), _ptr(tot)))
+        self.n_local, self.n_global = int(tot[0]), int(tot[1])
+
+    def close(self):
+        if self.h:
+            lib.nb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def to_local(self, ug, uL):
+        check(lib.nb_batch_to_local(self.h, _ptr(ug), _ptr(uL)))
+
+    def autotune(self, reps=3, flush=None):
+        fp, fb = (_ptr(flush), flush.numel() * flush.element_size()) if flush is not None else (None, 0)
+        check(lib.nb_batch_autotune(self.h, reps, fp, fb))
+
+    def solve(self, b, x, opts: nb_opts | None = None):
+        opts = opts or default_opts()
+        st = (nb_stats * self.nprob)()
+        tot = nb_stats()
+        r = check(lib.nb_batch_solve(self.h, C.byref(opts), _ptr(b), _ptr(x), st, C.byref(tot)))
+        per = [dict(status=s.status, iters=s.iters, outer_iters=s.outer_iters, rel_res=s.rel_res)
+               for s in st]
+        return dict(status=r, iters=tot.iters, outer_iters=tot.outer_iters, rel_res=tot.rel_res,
+                    seconds=tot.seconds, launches=tot.launches, problems=per)
+
+
+class Model:
+    """The learned per-element preconditioner's network (nb_model_*)."""
+
+    def __init__(self, ctx: Context, N: int, hidden: int = 48, seed: int = 0):
+        h = C.c_void_p()
+        check(lib.nb_model_create(ctx.h, N, hidden, seed, C.byref(h)))
+        self.h, self.ctx, self.N, self.hidden = h, ctx, N, hidden
+        self.d = (N + 1) ** 3
+        n = C.c_int64()
+        check(lib.nb_model_params(self.h, None, None, C.byref(n)))
+        self.nparam = n.value
+
+    def close(self):
+        if self.h:
+            lib.nb_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> dict:
+        flat = np.zeros(self.nparam, np.float32)
+        check(lib.nb_model_params(self.h, _ptr(flat), None, None))
+        return self._split(flat)
+
+    def set_params(self, p: dict):
+        flat = np.ascontiguousarray(np.concatenate(
+            [np.asarray(p[k], np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2")]))
+        assert flat.size == self.nparam
+        check(lib.nb_model_params(self.h, None, _ptr(flat), None))
+
+    def _split(self, flat):
+        d, h = self.d, self.hidden
+        o = 0
+        out = {}
+        for k, shape in (("W1", (d, h)), ("b1", (h,)), ("W2", (h, d)), ("b2", (d,))):
+            size = int(np.prod(shape))
+            out[k] = flat[o:o + size].reshape(shape)
+            o += size
+        return out
+
+    def grad(self, X, T):
+        loss = C.c_double()
+        g = np.zeros(self.nparam, np.float32)
+        check(lib.nb_model_grad(self.h, _ptr(X), _ptr(T), X.shape[0], C.byref(loss), _ptr(g)))
+        return loss.value, self._split(g)
+
+    def train(self, X, T, epochs=20, batch=256, lr=1e-3) -> float:
+        loss = C.c_double()
+        check(lib.nb_model_train(self.h, _ptr(X), _ptr(T), X.shape[0], epochs, batch, lr,
+                                 C.byref(loss)))
+        return loss.value
+
+    @staticmethod
+    def collect(mesh: "Mesh", b, snap_iters, per_snap, seed=0):
+        """Training pairs from Jacobi-PCG iterates of A x = b (see header)."""
+        import torch
+        its = np.ascontiguousarray(snap_iters, dtype=np.int32)
+        cap = len(its) * per_snap
+        d = (mesh.N + 1) ** 3
+        X = torch.empty((cap, d), dtype=torch.float32, device=b.device)
+        T = torch.empty((cap, d), dtype=torch.float32, device=b.device)
+        cnt = C.c_int()
+        check(lib.nb_learned_collect(mesh.h, _ptr(b), len(its), _ptr(its), per_snap, seed,
+                                     _ptr(X), _ptr(T), C.byref(cnt)))
+        return X[:cnt.value], T[:cnt.value]
+
+    def attach(self, mesh: "Mesh", jacobi_add=False):
+        check(lib.nb_learned_attach(mesh.h, self.h, int(jacobi_add)))
+        mesh._model = self  # keep alive
+
+    def apply(self, mesh: "Mesh", r, z):
+        check(lib.nb_learned_apply(mesh.h, _ptr(r), _ptr(z)))
+
+
+__all__ = ["lib", "LIB_PATH", "Batch", "Model", "NbError", "Context", "Mesh", "default_opts", "check",
            "nb_opts", "nb_stats", "nb_version", "PREC_NAMES",
            "NB_FP64", "NB_FP32", "NB_TC_F16", "NB_TC_BF16", "NB_PC_NONE", "NB_PC_JACOBI",
            "NB_PC_LEARNED", "NB_OK", "NB_NOT_CONVERGED", "NB_STAGNATED", "NB_BREAKDOWN",

@@ -120,7 +120,7 @@ nb_status nb_mesh_destroy(nb_mesh *m)
     void *bufs[] = {m->D64, m->D32, m->G64, m->G32, m->gid, m->gs_off, m->gs_loc, m->gs_gid,
                     m->gs_mask, m->g_first, m->mask_g, m->c32, m->dinv64, m->dinv32,
                     m->ones64, m->ones32, m->r64, m->w64, m->x64, m->b64, m->g64, m->part64,
-                    m->red_out, m->kerr};
+                    m->red_out, m->kerr, m->gs_zero, m->gs_pair, m->gs_quad, m->gs_oct};
     for (void *b : bufs) cudaFree(b);
     if (m->red_host) cudaFreeHost(m->red_host);
     delete m;

@@ -93,14 +93,25 @@ constexpr int tma_threads()
 template <typename T, int n, bool PUPD>
 constexpr size_t ax_tma_stage_elems()
 {
-    return (size_t)(6 + (PUPD ? 3 : 1)) * n * n * n;
+    return (size_t)7 * n * n * n;  // G[6][n3] and the element's u (or new p)
 }
 
 template <typename T, int n, bool PUPD>
 constexpr size_t ax_tma_smem()
 {
-    return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + 2 * n * n);
+    return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + 4 * n * n);
 }
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
 
 template <typename T, int n, bool PUPD>
 __global__ void __launch_bounds__(tma_threads<n>())
@@ -110,10 +121,11 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
 {
     constexpr int n2 = n * n, n3 = n2 * n;
     constexpr int STAGE = (int)ax_tma_stage_elems<T, n, PUPD>();
+    using V2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *stage = reinterpret_cast<T *>(smem_raw);  // [2][STAGE]: G[6][n3], then vectors
-    T *swr = stage + 2 * STAGE;                  // [n2]
-    T *sws = swr + n2;                           // [n2]
+    T *stage = reinterpret_cast<T *>(smem_raw);  // [2][STAGE]: G[6][n3], then u
+    T *swr = stage + 2 * STAGE;                  // [2][n2] (double-buffered by layer)
+    T *sws = swr + 2 * n2;                       // [2][n2]
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sred[32];
 
@@ -141,20 +153,17 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     }
     __syncthreads();
 
-    // the elected thread streams element number t of this block into stage t&1
+    // the elected thread streams element number t of this block into stage
+    // t&1: its geometric factors, and for the plain operator its u
     auto issue = [&](long long t) {
         const long long e = blockIdx.x + t * gridDim.x;
         T *dst = stage + (t & 1) * STAGE;
         uint64_t *b = &bar[t & 1];
-        mbar_expect_tx(b, (uint32_t)(STAGE * sizeof(T)));
-        bulk_g2s(dst, G + (size_t)e * 6 * n3, (uint32_t)(6 * n3 * sizeof(T)), b);
-        if (PUPD) {
-            bulk_g2s(dst + 6 * n3, r + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
-            bulk_g2s(dst + 7 * n3, dinv + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
-            bulk_g2s(dst + 8 * n3, p + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
-        } else {
-            bulk_g2s(dst + 6 * n3, uin + (size_t)e * n3, (uint32_t)(n3 * sizeof(T)), b);
-        }
+        const uint32_t gbytes = (uint32_t)(6 * n3 * sizeof(T));
+        const uint32_t ubytes = PUPD ? 0u : (uint32_t)(n3 * sizeof(T));
+        mbar_expect_tx(b, gbytes + ubytes);
+        bulk_g2s(dst, G + (size_t)e * 6 * n3, gbytes, b);
+        if (!PUPD) bulk_g2s(dst + 6 * n3, uin + (size_t)e * n3, ubytes, b);
     };
     if (tid == 0 && mine > 0) issue(0);
 
@@ -162,39 +171,49 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     long long t = 0;
     for (; t < mine; ++t) {
         if (tid == 0 && t + 1 < mine) issue(t + 1);  // its stage was released at the end of t-1
-        const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
-        if (__syncthreads_or(!ok)) break;
         const long long e = blockIdx.x + t * gridDim.x;
         const size_t base = (size_t)e * n3 + ij;
+        T ru[n], rw[n];
+        if (PUPD) {  // the direction's inputs come straight from HBM, before the wait
+#pragma unroll
+            for (int k = 0; k < n; ++k)
+                ru[k] = fabs(dinv[base + k * n2]) * r[base + k * n2] + beta * p[base + k * n2];
+        }
+        const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) break;
         T *s = stage + (t & 1) * STAGE;
         const T *Gs = s;
-        T *su = s + (PUPD ? 8 : 6) * n3;  // u, or p (overwritten in place with the new p)
-        T ru[n], rw[n];
+        T *su = s + 6 * n3;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
-            T v;
             if (PUPD) {
-                v = fabs(s[7 * n3 + k * n2 + ij]) * s[6 * n3 + k * n2 + ij] + beta * su[k * n2 + ij];
                 if (act) {
-                    su[k * n2 + ij] = v;
-                    p[base + k * n2] = v;
+                    su[k * n2 + ij] = ru[k];
+                    p[base + k * n2] = ru[k];
                 }
             } else {
-                v = su[k * n2 + ij];
+                ru[k] = su[k * n2 + ij];
             }
-            ru[k] = v;
             rw[k] = T(0);
         }
         if (PUPD) __syncthreads();
 #pragma unroll
         for (int k = 0; k < n; ++k) {
+            T *wrb = swr + (k & 1) * n2;
+            T *wsb = sws + (k & 1) * n2;
             const T g0 = Gs[0 * n3 + k * n2 + ij], g1 = Gs[1 * n3 + k * n2 + ij];
             const T g2 = Gs[2 * n3 + k * n2 + ij], g3 = Gs[3 * n3 + k * n2 + ij];
             const T g4 = Gs[4 * n3 + k * n2 + ij], g5 = Gs[5 * n3 + k * n2 + ij];
             T ur = T(0), us = T(0), ut = T(0);
+            const V2 *urow = reinterpret_cast<const V2 *>(su + k * n2 + j * n);
+#pragma unroll
+            for (int l = 0; l < n; l += 2) {
+                const V2 v = urow[l / 2];
+                ur += Di[l] * v.x;
+                ur += Di[l + 1] * v.y;
+            }
 #pragma unroll
             for (int l = 0; l < n; ++l) {
-                ur += Di[l] * su[k * n2 + j * n + l];
                 us += Dj[l] * su[k * n2 + l * n + i];
                 ut += dtab<T>(n, k, l) * ru[l];
             }
@@ -202,20 +221,25 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             const T ws = g1 * ur + g3 * us + g4 * ut;
             const T wt = g2 * ur + g4 * us + g5 * ut;
             if (act) {
-                swr[ij] = wr;
-                sws[ij] = ws;
+                wrb[ij] = wr;
+                wsb[ij] = ws;
             }
             __syncthreads();
             T a = T(0);
+            const V2 *wrow = reinterpret_cast<const V2 *>(wrb + j * n);
 #pragma unroll
-            for (int l = 0; l < n; ++l) {
-                a += DTi[l] * swr[j * n + l];
-                a += DTj[l] * sws[l * n + i];
+            for (int l = 0; l < n; l += 2) {
+                const V2 v = wrow[l / 2];
+                a += DTi[l] * v.x;
+                a += DTi[l + 1] * v.y;
             }
+#pragma unroll
+            for (int l = 0; l < n; ++l) a += DTj[l] * wsb[l * n + i];
             rw[k] += a;
 #pragma unroll
             for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
-            __syncthreads();
+            // no second barrier: layer k+1 writes the other wr/ws buffer, and
+            // layer k+2 (this buffer again) follows layer k+1's barrier
         }
         if (act) {
             T sdot = T(0);
@@ -226,7 +250,7 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             }
             acc += (double)sdot;
         }
-        // the last __syncthreads of the layer loop released this stage
+        __syncthreads();  // every thread is done with stage t&1: it may be refilled
     }
     if (t < mine) {
         // a wait timed out: record it, let this block's copies land, stop
@@ -280,8 +304,8 @@ nb_status launch_ax_tma(int sm_count, long long E, const T *G, const T *u, T *w,
 template <typename T>
 constexpr bool tma_fits(int n, bool pupd)
 {
-    return (n % 2 == 0) &&
-           sizeof(T) * (2 * (size_t)(6 + (pupd ? 3 : 1)) * n * n * n + 2 * n * n) <= 227 * 1024;
+    (void)pupd;  // both forms stage G and u
+    return (n % 2 == 0) && sizeof(T) * (2 * (size_t)7 * n * n * n + 4 * n * n) <= 227 * 1024;
 }
 
 template <typename T>

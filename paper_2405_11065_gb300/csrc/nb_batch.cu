@@ -1,0 +1,922 @@
+// Batched solves: many independent Poisson problems of different element
+// count and order in one solve.
+//
+// Layout.  The problems' L-vectors are concatenated with the problems grouped
+// by order, so every order's elements form one contiguous range; geometric
+// factors and the Jacobi arrays follow the same order, and the gather-scatter
+// rows of all problems form one list (local indices offset into the batch).
+// Per-element tables give each element's problem and L offset.
+//
+// Iteration.  Table 1's loop for all problems at once: the operator (one
+// launch per order present, each over all elements of that order), the
+// per-problem alpha (one warp per problem sums its elements' partials in
+// element order), one gather-scatter over every row, the update (one block
+// per element), the per-problem beta and stopping tests, and the loop
+// condition "some problem is still running".  Problems that have stopped are
+// skipped by every kernel.  The whole iteration is one CUDA graph with a
+// while node; the FP64 refinement around it runs per problem (own scale,
+// own inner tolerance) with all problems advanced together.
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "nb_cg_dev.cuh"
+
+namespace nb {
+
+nb_status bax_f32(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
+                  const float *G, const float *u, float *w, const float *r, const float *dinv,
+                  float *p, const int32_t *elem_prob, const BScal *bs, double *part_e,
+                  cudaStream_t s);
+nb_status bax_f64(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
+                  const double *G, const double *u, double *w, const double *r,
+                  const double *dinv, double *p, const int32_t *elem_prob, const BScal *bs,
+                  double *part_e, cudaStream_t s);
+
+struct BatchGroup {
+    int n = 0;
+    int64_t e0 = 0, e1 = 0;  // element range
+    int64_t l0 = 0;          // L offset of the first element
+    int variant = 1;         // elements-per-block choice (autotuned)
+};
+
+struct BatchWs {
+    void *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace nb
+
+struct nb_batch {
+    nb_ctx *ctx = nullptr;
+    int nprob = 0;
+    std::vector<nb_mesh *> meshes;  // caller order
+    std::vector<int> order;         // internal index -> caller index
+    std::vector<int> rank;          // caller index -> internal index
+    std::vector<int64_t> l_off, g_off;  // caller order
+    int64_t nL = 0, nG = 0, E = 0, rows = 0;
+    std::vector<nb::BatchGroup> groups;
+    std::vector<int64_t> prob_e0_host;  // internal order, nprob + 1
+    float *G32 = nullptr;
+    double *G64 = nullptr;
+    float *dinv32 = nullptr;
+    double *dinv64 = nullptr;
+    int32_t *gs_off = nullptr, *gs_loc = nullptr;
+    uint8_t *gs_mask = nullptr;
+    int32_t *elem_prob = nullptr;  // [E] internal problem index
+    int64_t *elem_l0 = nullptr;    // [E + 1]
+    int64_t *prob_e0 = nullptr;    // [nprob + 1]
+    nb::BScal *bs = nullptr;       // [nprob]
+    nb::BScal *bs_host = nullptr;  // pinned
+    int *loops = nullptr;          // graph loop counter
+    double *part_e = nullptr;      // [2 E]
+    double *red = nullptr;         // [4 nprob]: |r|^2, |b|^2, tau, active
+    double *red_host = nullptr;    // pinned
+    double *r64 = nullptr, *w64 = nullptr;
+    nb::BatchWs ws32, ws64;
+};
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// kernels (per-element loops: one block per element, grid-stride)
+// ---------------------------------------------------------------------------
+
+// Sum of a[lo..hi) by one warp in a fixed order (lane-strided, then a fixed
+// shuffle tree), returned on lane 0.
+__device__ __forceinline__ double warp_range_sum(const double *a, int64_t lo, int64_t hi)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int64_t e = lo + lane; e < hi; e += 32) v += a[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void k_bsetup(int nprob, BScal *bs, double tol, int maxit, const double *red,
+                         int use_red, int *loops)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        loops[0] = 0;      // loop bodies executed
+        loops[1] = maxit;  // hard cap on them (+1)
+    }
+    if (p >= nprob) return;
+    BScal b = {};
+    b.tol = use_red ? red[2 * nprob + p] : tol;
+    b.maxit = maxit;
+    b.done = use_red ? (red[3 * nprob + p] == 0.0) : 0;
+    bs[p] = b;
+}
+
+// p = 0 and owner-copy partials of (r, dinv r), (r, r) per element.
+template <typename T>
+__global__ void k_binit(int64_t E, const int64_t *__restrict__ el0, const T *__restrict__ r,
+                        const T *__restrict__ dinv, T *__restrict__ p, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        DotAcc<T> a, b;
+        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+            const T rl = r[l], d = dinv[l];
+            p[l] = T(0);
+            if (!signbit(d)) {
+                a.add(rl * (d * rl));
+                b.add(rl * rl);
+            }
+        }
+        const double ta = block_sum(a.value(), sred);
+        const double tb = block_sum(b.value(), sred);
+        if (threadIdx.x == 0) {
+            part[e] = ta;
+            part[E + e] = tb;
+        }
+    }
+}
+
+__global__ void k_bfin_init(int nprob, const int64_t *__restrict__ pe0, const double *part,
+                            int64_t E, BScal *bs, int bnorm_from_r, const double *bnorm2)
+{
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= nprob) return;
+    const double rtz = warp_range_sum(part, pe0[p], pe0[p + 1]);
+    const double rtr = warp_range_sum(part + E, pe0[p], pe0[p + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal &b = bs[p];
+        b.rtz = b.rtz_old = rtz;
+        b.rtr = rtr;
+        if (bnorm_from_r) b.bnorm2 = rtr;
+        else if (bnorm2) b.bnorm2 = bnorm2[p];
+        const double bn = b.bnorm2 > 0.0 ? b.bnorm2 : 1.0;
+        b.relres = sqrt(rtr / bn);
+        b.beta = 0.0;
+        if (b.done) return;
+        if (!isfinite(b.relres)) {
+            b.done = 1;
+            b.status = NB_BREAKDOWN;
+        } else if (b.relres < b.tol || rtr == 0.0) {
+            b.done = 1;
+        } else if (b.maxit <= 0) {
+            b.done = 1;
+            b.status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+__global__ void k_bfin_alpha(int nprob, const int64_t *__restrict__ pe0, const double *part,
+                             BScal *bs)
+{
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= nprob) return;
+    if (bs[p].done) return;  // uniform over the warp
+    const double pap = warp_range_sum(part, pe0[p], pe0[p + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal &b = bs[p];
+        b.pap = pap;
+        const double alpha = b.rtz / pap;
+        if (!(pap > 0.0) || !isfinite(alpha)) {
+            b.alpha = 0.0;
+            b.done = 1;
+            b.status = NB_BREAKDOWN;
+        } else {
+            b.alpha = alpha;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_bupdate(int64_t E, const int64_t *__restrict__ el0,
+                          const int32_t *__restrict__ eprob, const BScal *__restrict__ bs,
+                          T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                          const T *__restrict__ w, const T *__restrict__ dinv,
+                          double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const BScal &b = bs[eprob[e]];
+        if (b.done) continue;  // uniform over the block
+        const T alpha = (T)b.alpha;
+        DotAcc<T> a, c;
+        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+            x[l] = x[l] + alpha * p[l];
+            const T rl = r[l] - alpha * w[l];
+            r[l] = rl;
+            const T d = dinv[l];
+            if (!signbit(d)) {
+                a.add(rl * (d * rl));
+                c.add(rl * rl);
+            }
+        }
+        const double ta = block_sum(a.value(), sred);
+        const double tc = block_sum(c.value(), sred);
+        if (threadIdx.x == 0) {
+            part[e] = ta;
+            part[E + e] = tc;
+        }
+    }
+}
+
+__global__ void k_bfin_iter(int nprob, const int64_t *__restrict__ pe0, const double *part,
+                            int64_t E, BScal *bs)
+{
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= nprob) return;
+    if (bs[p].done) return;
+    const double rtz = warp_range_sum(part, pe0[p], pe0[p + 1]);
+    const double rtr = warp_range_sum(part + E, pe0[p], pe0[p + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal &b = bs[p];
+        b.rtz_old = b.rtz;
+        b.rtz = rtz;
+        b.rtr = rtr;
+        b.beta = rtz / b.rtz_old;
+        b.iter += 1;
+        const double bn = b.bnorm2 > 0.0 ? b.bnorm2 : 1.0;
+        b.relres = sqrt(rtr / bn);
+        if (!isfinite(b.relres) || !isfinite(b.beta)) {
+            b.done = 1;
+            b.status = NB_BREAKDOWN;
+        } else if (b.relres < b.tol) {
+            b.done = 1;
+        } else if (b.iter >= b.maxit) {
+            b.done = 1;
+            b.status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+// Loop condition: some problem still running, and at most maxit + 1 bodies.
+__global__ void k_bcond(int nprob, const BScal *bs, int *loops, cudaGraphConditionalHandle h)
+{
+    int running = 0;
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x) running |= (bs[p].done == 0);
+    running = __syncthreads_or(running);
+    if (threadIdx.x == 0) {
+        const int l = loops[0] + 1;
+        loops[0] = l;
+        cudaGraphSetConditional(h, (running && l <= loops[1]) ? 1u : 0u);
+    }
+}
+
+// r = b - w (w may be NULL) and owner-copy partials of (r, r) and (b, b).
+__global__ void k_bresid(int64_t E, const int64_t *__restrict__ el0, const double *__restrict__ b,
+                         const double *__restrict__ w, const double *__restrict__ dinv,
+                         double *__restrict__ r, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        double a = 0.0, c = 0.0;
+        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+            const double bl = b[l];
+            const double v = bl - (w ? w[l] : 0.0);
+            r[l] = v;
+            if (!signbit(dinv[l])) {
+                a += v * v;
+                c += bl * bl;
+            }
+        }
+        const double ta = block_sum(a, sred);
+        const double tc = block_sum(c, sred);
+        if (threadIdx.x == 0) {
+            part[e] = ta;
+            part[E + e] = tc;
+        }
+    }
+}
+
+__global__ void k_bsum2(int nprob, const int64_t *__restrict__ pe0, const double *part, int64_t E,
+                        double *out)
+{
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= nprob) return;
+    const double a = warp_range_sum(part, pe0[p], pe0[p + 1]);
+    const double c = warp_range_sum(part + E, pe0[p], pe0[p + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        out[p] = a;
+        out[nprob + p] = c;
+    }
+}
+
+// Inner right-hand side per problem: r32 = r64 / |r64| for running problems
+// (zero otherwise), x32 = 0.  red[3 nprob + p] = 1 marks a running problem.
+__global__ void k_bdemote(int64_t E, const int64_t *__restrict__ el0,
+                          const int32_t *__restrict__ eprob, int nprob, const double *red,
+                          const double *__restrict__ r64, float *__restrict__ r32,
+                          float *__restrict__ x32)
+{
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int p = eprob[e];
+        const bool act = red[3 * nprob + p] != 0.0;
+        const double inv = act ? 1.0 / sqrt(red[p]) : 0.0;
+        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+            r32[l] = (float)(r64[l] * inv);
+            x32[l] = 0.0f;
+        }
+    }
+}
+
+__global__ void k_bpromote(int64_t E, const int64_t *__restrict__ el0,
+                           const int32_t *__restrict__ eprob, int nprob, const double *red,
+                           const float *__restrict__ x32, double *__restrict__ x)
+{
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int p = eprob[e];
+        if (red[3 * nprob + p] == 0.0) continue;
+        const double s = sqrt(red[p]);
+        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x)
+            x[l] += s * (double)x32[l];
+    }
+}
+
+__global__ void k_bcopy(int64_t n, const double *__restrict__ a, double *__restrict__ b)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        b[l] = a[l];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static int elem_grid(const nb_batch *B) { return (int)std::min<int64_t>(B->E, B->ctx->sm_count * 16); }
+static int warp_grid(int nprob) { return (nprob * 32 + 255) / 256; }
+
+template <typename T>
+static nb_status bax_all(nb_batch *B, bool pupd, const T *u, T *w, const T *r, const T *dinv,
+                         T *p, double *part, cudaStream_t s)
+{
+    for (const BatchGroup &g : B->groups) {
+        const int64_t E = g.e1 - g.e0;
+        const int64_t n3 = (int64_t)g.n * g.n * g.n;
+        const size_t lo = (size_t)g.l0, go = (size_t)g.l0 * 6;
+        auto off = [&](const T *v) { return v ? v + lo : nullptr; };
+        if (sizeof(T) == 4)
+            NB_TRY(bax_f32(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0,
+                           (const float *)B->G32 + go, (const float *)off(u),
+                           (float *)(w + lo), (const float *)off(r), (const float *)off(dinv),
+                           p ? (float *)(p + lo) : nullptr, B->elem_prob, B->bs, part, s));
+        else
+            NB_TRY(bax_f64(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0,
+                           (const double *)B->G64 + go, (const double *)off(u),
+                           (double *)(w + lo), (const double *)off(r),
+                           (const double *)off(dinv), p ? (double *)(p + lo) : nullptr,
+                           B->elem_prob, B->bs, part, s));
+        (void)n3;
+    }
+    return NB_OK;
+}
+
+template <typename T>
+static nb_status batch_body(nb_batch *B, BatchWs &ws, const T *dinv, int use_cond,
+                            cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    const nb_prec prec = sizeof(T) == 4 ? NB_FP32 : NB_FP64;
+    NB_TRY(bax_all<T>(B, true, nullptr, (T *)ws.w, (const T *)ws.r, dinv, (T *)ws.p, B->part_e, s));
+    k_bfin_alpha<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->bs);
+    NB_CUDA(cudaGetLastError());
+    NB_TRY(gs_rows_launch(B->ctx, B->rows, B->gs_off, B->gs_loc, B->gs_mask, prec, ws.w, 1, s));
+    k_bupdate<T><<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, B->bs, (T *)ws.x,
+                                              (T *)ws.r, (const T *)ws.p, (const T *)ws.w, dinv,
+                                              B->part_e);
+    NB_CUDA(cudaGetLastError());
+    k_bfin_iter<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs);
+    NB_CUDA(cudaGetLastError());
+    if (use_cond) {
+        k_bcond<<<1, 256, 0, s>>>(B->nprob, B->bs, B->loops, h);
+        NB_CUDA(cudaGetLastError());
+    }
+    return NB_OK;
+}
+
+static nb_status ensure_bws(nb_batch *B, BatchWs &ws, size_t elt)
+{
+    if (ws.x) return NB_OK;
+    const size_t bytes = elt * B->nL;
+    NB_CUDA(cudaMalloc(&ws.x, bytes));
+    NB_CUDA(cudaMalloc(&ws.r, bytes));
+    NB_CUDA(cudaMalloc(&ws.p, bytes));
+    NB_CUDA(cudaMalloc(&ws.w, bytes));
+    NB_CUDA(cudaMemset(ws.p, 0, bytes));
+    NB_CUDA(cudaMemset(ws.w, 0, bytes));
+    return NB_OK;
+}
+
+// Run the batched PCG on ws (r holds the residuals of the current x) until
+// every problem has stopped.  Tolerances from red (per problem) if use_red;
+// relative to |r0| if bnorm_from_r, else to bnorm2[p].
+template <typename T>
+static nb_status batch_cg(nb_batch *B, BatchWs &ws, const T *dinv, double tol, int maxit,
+                          int use_red, int use_graph, int bnorm_from_r, const double *bnorm2,
+                          cudaStream_t s)
+{
+    k_bsetup<<<(B->nprob + 255) / 256, 256, 0, s>>>(B->nprob, B->bs, tol, maxit, B->red, use_red,
+                                                    B->loops);
+    NB_CUDA(cudaGetLastError());
+    k_binit<T><<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, (const T *)ws.r, dinv, (T *)ws.p,
+                                            B->part_e);
+    NB_CUDA(cudaGetLastError());
+    k_bfin_init<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs,
+                                                    bnorm_from_r, bnorm2);
+    NB_CUDA(cudaGetLastError());
+    if (use_graph) {
+        if (!ws.exec) {
+            cudaGraph_t g;
+            NB_CUDA(cudaGraphCreate(&g, 0));
+            cudaGraphConditionalHandle h;
+            NB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            NB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+            nb_status st = batch_body<T>(B, ws, dinv, 1, h, s);
+            cudaGraph_t captured = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s, &captured);
+            if (st != NB_OK || ce != cudaSuccess) {
+                cudaGraphDestroy(g);
+                if (st != NB_OK) return st;
+                set_error("batch graph capture failed: %s", cudaGetErrorString(ce));
+                return NB_ERR_CUDA;
+            }
+            NB_CUDA(cudaGraphInstantiate(&ws.exec, g, 0));
+            ws.graph = g;
+        }
+        NB_CUDA(cudaGraphLaunch(ws.exec, s));
+        return NB_OK;
+    }
+    for (int it = 0; it <= maxit; it += 16) {
+        for (int t = 0; t < 16; ++t) NB_TRY(batch_body<T>(B, ws, dinv, 0, 0, s));
+        NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * B->nprob,
+                                cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        bool any = false;
+        for (int p = 0; p < B->nprob; ++p) any |= B->bs_host[p].done == 0;
+        if (!any) break;
+    }
+    return NB_OK;
+}
+
+// |b - A x|^2 and |b|^2 per problem into red[0..2 nprob); x may be NULL (x = 0).
+static nb_status batch_residual(nb_batch *B, const double *b, const double *x, cudaStream_t s)
+{
+    const double *w = nullptr;
+    if (x) {
+        NB_TRY(bax_all<double>(B, false, x, B->w64, nullptr, nullptr, nullptr, nullptr, s));
+        NB_TRY(gs_rows_launch(B->ctx, B->rows, B->gs_off, B->gs_loc, B->gs_mask, NB_FP64, B->w64,
+                              1, s));
+        w = B->w64;
+    }
+    k_bresid<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, b, w, B->dinv64, B->r64, B->part_e);
+    NB_CUDA(cudaGetLastError());
+    k_bsum2<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->red);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+static void free_bws(BatchWs &ws)
+{
+    if (ws.exec) cudaGraphExecDestroy(ws.exec);
+    if (ws.graph) cudaGraphDestroy(ws.graph);
+    cudaFree(ws.x);
+    cudaFree(ws.r);
+    cudaFree(ws.p);
+    cudaFree(ws.w);
+    ws = BatchWs();
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+extern "C" nb_status nb_batch_destroy(nb_batch *B)
+{
+    if (!B) return NB_OK;
+    cudaSetDevice(B->ctx->device);
+    cudaStreamSynchronize(B->ctx->stream);
+    for (nb_mesh *m : B->meshes) nb_mesh_destroy(m);
+    free_bws(B->ws32);
+    free_bws(B->ws64);
+    void *bufs[] = {B->G32, B->G64, B->dinv32, B->dinv64, B->gs_off, B->gs_loc, B->gs_mask,
+                    B->elem_prob, B->elem_l0, B->prob_e0, B->bs, B->loops, B->part_e, B->red,
+                    B->r64, B->w64};
+    for (void *b : bufs) cudaFree(b);
+    if (B->bs_host) cudaFreeHost(B->bs_host);
+    if (B->red_host) cudaFreeHost(B->red_host);
+    delete B;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, const int *ny,
+                                     const int *nz, const int *N, const double *deform,
+                                     nb_batch **out)
+{
+    if (!ctx || !out || nprob < 1 || !nx || !ny || !nz || !N || !deform) {
+        set_error("invalid argument: batch description");
+        return NB_ERR_ARG;
+    }
+    *out = nullptr;
+    NB_CUDA(cudaSetDevice(ctx->device));
+    nb_batch *B = new nb_batch();
+    B->ctx = ctx;
+    B->nprob = nprob;
+    B->meshes.assign(nprob, nullptr);
+    nb_status st = NB_OK;
+    for (int p = 0; p < nprob && st == NB_OK; ++p) {
+        st = nb_setup_mesh(ctx, nx[p], ny[p], nz[p], N[p], deform[p], &B->meshes[p]);
+        if (st == NB_OK) st = nb_setup_gs(B->meshes[p]);
+    }
+    if (st != NB_OK) {
+        nb_batch_destroy(B);
+        return st;
+    }
+    // internal order: grouped by order, stable
+    B->order.resize(nprob);
+    std::iota(B->order.begin(), B->order.end(), 0);
+    std::stable_sort(B->order.begin(), B->order.end(),
+                     [&](int a, int b) { return N[a] < N[b]; });
+    B->rank.resize(nprob);
+    for (int q = 0; q < nprob; ++q) B->rank[B->order[q]] = q;
+    B->l_off.assign(nprob, 0);
+    B->g_off.assign(nprob, 0);
+    int64_t gacc = 0;
+    for (int p = 0; p < nprob; ++p) {
+        B->g_off[p] = gacc;
+        gacc += B->meshes[p]->nG;
+    }
+    B->nG = gacc;
+    std::vector<int32_t> eprob;
+    std::vector<int64_t> el0(1, 0);
+    B->prob_e0_host.assign(1, 0);
+    int64_t lacc = 0;
+    for (int q = 0; q < nprob; ++q) {
+        nb_mesh *m = B->meshes[B->order[q]];
+        B->l_off[B->order[q]] = lacc;
+        if (B->groups.empty() || B->groups.back().n != m->n) {
+            BatchGroup g;
+            g.n = m->n;
+            g.e0 = g.e1 = (int64_t)eprob.size();
+            g.l0 = lacc;
+            B->groups.push_back(g);
+        }
+        for (int64_t e = 0; e < m->E; ++e) {
+            eprob.push_back(q);
+            el0.push_back(el0.back() + m->n3);
+        }
+        B->groups.back().e1 = (int64_t)eprob.size();
+        B->prob_e0_host.push_back((int64_t)eprob.size());
+        lacc += m->nL;
+    }
+    B->nL = lacc;
+    B->E = (int64_t)eprob.size();
+    if (B->nL >= ((int64_t)1 << 31)) {
+        nb_batch_destroy(B);
+        set_error("batch too large for 32-bit local indices");
+        return NB_ERR_ARG;
+    }
+    // gather-scatter rows with batch local indices
+    std::vector<int32_t> off(1, 0), loc;
+    std::vector<uint8_t> rmask;
+    for (int q = 0; q < nprob && st == NB_OK; ++q) {
+        nb_mesh *m = B->meshes[B->order[q]];
+        std::vector<int32_t> o(m->gs_rows + 1), l(std::max<int64_t>(m->gs_copies, 1));
+        std::vector<uint8_t> mk(std::max<int64_t>(m->gs_rows, 1));
+        st = nb_get_maps(m, nullptr, nullptr, nullptr, nullptr, o.data(), l.data(), mk.data());
+        const int32_t base = (int32_t)B->l_off[B->order[q]];
+        const int32_t obase = off.back();
+        for (int64_t a = 0; a < m->gs_rows; ++a) {
+            off.push_back(obase + o[a + 1]);
+            rmask.push_back(mk[a]);
+        }
+        for (int64_t c = 0; c < m->gs_copies; ++c) loc.push_back(base + l[c]);
+    }
+    if (st != NB_OK) {
+        nb_batch_destroy(B);
+        return st;
+    }
+    B->rows = (int64_t)rmask.size();
+    cudaStream_t s = ctx->stream;
+    auto fail = [&](nb_status e) {
+        nb_batch_destroy(B);
+        return e;
+    };
+#define NB_BCUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            set_error("batch set-up: %s", cudaGetErrorString(e_));                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA);           \
+        }                                                                                      \
+    } while (0)
+    NB_BCUDA(cudaMalloc(&B->G32, sizeof(float) * 6 * B->nL));
+    NB_BCUDA(cudaMalloc(&B->G64, sizeof(double) * 6 * B->nL));
+    NB_BCUDA(cudaMalloc(&B->dinv32, sizeof(float) * B->nL));
+    NB_BCUDA(cudaMalloc(&B->dinv64, sizeof(double) * B->nL));
+    NB_BCUDA(cudaMalloc(&B->gs_off, sizeof(int32_t) * off.size()));
+    NB_BCUDA(cudaMalloc(&B->gs_loc, sizeof(int32_t) * std::max<size_t>(loc.size(), 1)));
+    NB_BCUDA(cudaMalloc(&B->gs_mask, std::max<size_t>(rmask.size(), 1)));
+    NB_BCUDA(cudaMalloc(&B->elem_prob, sizeof(int32_t) * B->E));
+    NB_BCUDA(cudaMalloc(&B->elem_l0, sizeof(int64_t) * (B->E + 1)));
+    NB_BCUDA(cudaMalloc(&B->prob_e0, sizeof(int64_t) * (nprob + 1)));
+    NB_BCUDA(cudaMalloc(&B->bs, sizeof(BScal) * nprob));
+    NB_BCUDA(cudaMallocHost(&B->bs_host, sizeof(BScal) * nprob));
+    NB_BCUDA(cudaMalloc(&B->loops, 2 * sizeof(int)));
+    NB_BCUDA(cudaMalloc(&B->part_e, sizeof(double) * 2 * B->E));
+    NB_BCUDA(cudaMalloc(&B->red, sizeof(double) * 4 * nprob));
+    NB_BCUDA(cudaMallocHost(&B->red_host, sizeof(double) * 4 * nprob));
+    NB_BCUDA(cudaMalloc(&B->r64, sizeof(double) * B->nL));
+    NB_BCUDA(cudaMalloc(&B->w64, sizeof(double) * B->nL));
+    NB_BCUDA(cudaMemset(B->w64, 0, sizeof(double) * B->nL));
+    for (int q = 0; q < nprob; ++q) {
+        nb_mesh *m = B->meshes[B->order[q]];
+        const size_t lo = (size_t)B->l_off[B->order[q]];
+        NB_BCUDA(cudaMemcpyAsync(B->G32 + 6 * lo, m->G32, sizeof(float) * 6 * m->nL,
+                                 cudaMemcpyDeviceToDevice, s));
+        NB_BCUDA(cudaMemcpyAsync(B->G64 + 6 * lo, m->G64, sizeof(double) * 6 * m->nL,
+                                 cudaMemcpyDeviceToDevice, s));
+        NB_BCUDA(cudaMemcpyAsync(B->dinv32 + lo, m->dinv32, sizeof(float) * m->nL,
+                                 cudaMemcpyDeviceToDevice, s));
+        NB_BCUDA(cudaMemcpyAsync(B->dinv64 + lo, m->dinv64, sizeof(double) * m->nL,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    NB_BCUDA(cudaMemcpyAsync(B->gs_off, off.data(), sizeof(int32_t) * off.size(),
+                             cudaMemcpyHostToDevice, s));
+    if (!loc.empty())
+        NB_BCUDA(cudaMemcpyAsync(B->gs_loc, loc.data(), sizeof(int32_t) * loc.size(),
+                                 cudaMemcpyHostToDevice, s));
+    if (!rmask.empty())
+        NB_BCUDA(cudaMemcpyAsync(B->gs_mask, rmask.data(), rmask.size(), cudaMemcpyHostToDevice, s));
+    NB_BCUDA(cudaMemcpyAsync(B->elem_prob, eprob.data(), sizeof(int32_t) * B->E,
+                             cudaMemcpyHostToDevice, s));
+    NB_BCUDA(cudaMemcpyAsync(B->elem_l0, el0.data(), sizeof(int64_t) * (B->E + 1),
+                             cudaMemcpyHostToDevice, s));
+    NB_BCUDA(cudaMemcpyAsync(B->prob_e0, B->prob_e0_host.data(), sizeof(int64_t) * (nprob + 1),
+                             cudaMemcpyHostToDevice, s));
+    NB_BCUDA(cudaStreamSynchronize(s));
+#undef NB_BCUDA
+    *out = B;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_batch_layout(const nb_batch *B, int64_t *l_off, int64_t *g_off,
+                                     int64_t totals[2])
+{
+    if (!B) {
+        set_error("invalid argument: batch is NULL");
+        return NB_ERR_ARG;
+    }
+    for (int p = 0; p < B->nprob; ++p) {
+        if (l_off) l_off[p] = B->l_off[p];
+        if (g_off) g_off[p] = B->g_off[p];
+    }
+    if (totals) {
+        totals[0] = B->nL;
+        totals[1] = B->nG;
+    }
+    return NB_OK;
+}
+
+extern "C" nb_mesh *nb_batch_mesh(nb_batch *B, int p)
+{
+    if (!B || p < 0 || p >= B->nprob) return nullptr;
+    return B->meshes[p];
+}
+
+extern "C" nb_status nb_batch_to_local(nb_batch *B, const double *ug, double *uL)
+{
+    if (!B || !ug || !uL) {
+        set_error("invalid argument: NULL batch or vector");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(B->ctx->device));
+    for (int p = 0; p < B->nprob; ++p)
+        NB_TRY(to_local(B->meshes[p], NB_FP64, ug + B->g_off[p], uL + B->l_off[p], 1,
+                        B->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(B->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_batch_autotune(nb_batch *B, int reps, void *flush, size_t flush_bytes)
+{
+    if (!B || reps < 1) {
+        set_error("invalid argument: batch or reps");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(B->ctx->device));
+    cudaStream_t s = B->ctx->stream;
+    NB_TRY(ensure_bws(B, B->ws32, sizeof(float)));
+    cudaEvent_t e0, e1;
+    NB_CUDA(cudaEventCreate(&e0));
+    NB_CUDA(cudaEventCreate(&e1));
+    for (BatchGroup &g : B->groups) {
+        double best = 1e300;
+        int bestv = g.variant;
+        for (int v = 0; v < 2; ++v) {
+            g.variant = v;
+            double tot = 0.0;
+            for (int r = 0; r <= reps; ++r) {  // the first launch is a warm-up
+                if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+                cudaEventRecord(e0, s);
+                const size_t lo = (size_t)g.l0;
+                NB_TRY(bax_f32(g.n, v, false, B->ctx->sm_count, g.e1 - g.e0, g.e0,
+                               B->G32 + 6 * lo, (const float *)B->ws32.p + lo,
+                               (float *)B->ws32.w + lo, nullptr, nullptr, nullptr, B->elem_prob,
+                               B->bs, nullptr, s));
+                cudaEventRecord(e1, s);
+                NB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                bestv = v;
+            }
+        }
+        g.variant = bestv;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // graphs captured with the old choice are rebuilt on the next solve
+    free_bws(B->ws32);
+    return NB_OK;
+}
+
+extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double *b, double *x,
+                                    nb_stats *stats, nb_stats *total)
+{
+    if (!B || !o || !b || !x) {
+        set_error("invalid argument: NULL batch, options or vector");
+        return NB_ERR_ARG;
+    }
+    if (o->prec != NB_FP64 && o->prec != NB_FP32) {
+        set_error("batched solves support NB_FP64 and NB_FP32");
+        return NB_ERR_ARG;
+    }
+    if (o->pc != NB_PC_JACOBI && o->pc != NB_PC_NONE) {
+        set_error("batched solves support the Jacobi and identity preconditioners");
+        return NB_ERR_ARG;
+    }
+    if (o->pc == NB_PC_NONE) {
+        set_error("batched solves use the Jacobi preconditioner");
+        return NB_ERR_ARG;
+    }
+    if (!(o->rtol > 0.0 && o->rtol < 1.0) || o->maxiter < 0 || o->max_outer < 0) {
+        set_error("invalid argument: rtol, maxiter or max_outer");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(B->ctx->device));
+    cudaStream_t s = B->ctx->stream;
+    const int np = B->nprob;
+    cudaEvent_t t0, t1;
+    NB_CUDA(cudaEventCreate(&t0));
+    NB_CUDA(cudaEventCreate(&t1));
+    NB_CUDA(cudaEventRecord(t0, s));
+    std::vector<int> iters(np, 0), outer_p(np, 0), status(np, NB_NOT_CONVERGED);
+    std::vector<double> rel(np, INFINITY);
+    int batched_iters = 0, outer = 0;
+    int64_t launches = 0;
+    const int ngroups = (int)B->groups.size();
+    if (o->prec == NB_FP64) {
+        // plain FP64 PCG of every problem, in place on x
+        NB_TRY(ensure_bws(B, B->ws64, sizeof(double)));
+        NB_TRY(batch_residual(B, b, o->use_x0 ? x : nullptr, s));
+        if (o->use_x0)
+            k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, x, (double *)B->ws64.x);
+        else
+            NB_CUDA(cudaMemsetAsync(B->ws64.x, 0, sizeof(double) * B->nL, s));
+        k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, B->r64, (double *)B->ws64.r);
+        NB_CUDA(cudaGetLastError());
+        // tolerance relative to |b| (red[nprob + p] from the residual pass)
+        NB_TRY(batch_cg<double>(B, B->ws64, B->dinv64, o->rtol, o->maxiter, 0, o->use_graph, 0,
+                                B->red + np, s));
+        NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * np, cudaMemcpyDeviceToHost, s));
+        k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, (double *)B->ws64.x, x);
+        NB_TRY(batch_residual(B, b, x, s));
+        NB_CUDA(cudaMemcpyAsync(B->red_host, B->red, sizeof(double) * 2 * np,
+                                cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < np; ++q) {
+            const int p = B->order[q];
+            iters[p] = B->bs_host[q].iter;
+            batched_iters = std::max(batched_iters, iters[p]);
+            const double bn = B->red_host[np + q];
+            rel[p] = bn > 0.0 ? sqrt(B->red_host[q] / bn) : 0.0;
+            status[p] = B->bs_host[q].status;
+            if (status[p] == 0 && !(rel[p] < o->rtol * 1.5)) status[p] = NB_NOT_CONVERGED;
+        }
+        launches += 4 + 2 + (int64_t)batched_iters * (ngroups + 5) + 3;
+    } else {
+        NB_TRY(ensure_bws(B, B->ws32, sizeof(float)));
+        if (!o->use_x0) NB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * B->nL, s));
+        std::vector<double> bn2(np, 0.0), prev(np, INFINITY);
+        std::vector<int> stagn(np, 0);
+        std::vector<char> running(np, 1);
+        int used = 0;
+        for (outer = 0; outer <= o->max_outer; ++outer) {
+            NB_TRY(batch_residual(B, b, (outer == 0 && !o->use_x0) ? nullptr : x, s));
+            NB_CUDA(cudaMemcpyAsync(B->red_host, B->red, sizeof(double) * 2 * np,
+                                    cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaStreamSynchronize(s));
+            launches += 2 + ((outer == 0 && !o->use_x0) ? 0 : ngroups + 1);
+            bool any = false;
+            for (int q = 0; q < np; ++q) {
+                const int p = B->order[q];
+                if (!running[p]) {
+                    B->red_host[3 * np + q] = 0.0;
+                    continue;
+                }
+                if (outer == 0) bn2[p] = B->red_host[np + q];
+                if (!isfinite(bn2[p])) {
+                    set_error("right-hand side of problem %d has a non-finite entry", p);
+                    return NB_ERR_ARG;
+                }
+                rel[p] = bn2[p] > 0.0 ? sqrt(B->red_host[q] / bn2[p]) : 0.0;
+                outer_p[p] = outer;
+                bool stop = false;
+                if (!isfinite(rel[p])) {
+                    status[p] = NB_BREAKDOWN;
+                    stop = true;
+                } else if (rel[p] < o->rtol) {
+                    status[p] = NB_OK;
+                    stop = true;
+                } else if (outer == o->max_outer || used >= o->maxiter) {
+                    status[p] = NB_NOT_CONVERGED;
+                    stop = true;
+                } else if (rel[p] > 0.5 * prev[p] && ++stagn[p] >= 3) {
+                    status[p] = NB_STAGNATED;
+                    stop = true;
+                }
+                if (!(rel[p] > 0.5 * prev[p])) stagn[p] = 0;
+                prev[p] = rel[p];
+                running[p] = !stop;
+                B->red_host[3 * np + q] = stop ? 0.0 : 1.0;
+                B->red_host[2 * np + q] =
+                    std::min(0.5, std::max(o->inner_rtol, 0.5 * o->rtol / std::max(rel[p], 1e-300)));
+                any |= !stop;
+            }
+            if (!any) break;
+            NB_CUDA(cudaMemcpyAsync(B->red + 2 * np, B->red_host + 2 * np, sizeof(double) * 2 * np,
+                                    cudaMemcpyHostToDevice, s));
+            k_bdemote<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, np, B->red,
+                                                    B->r64, (float *)B->ws32.r,
+                                                    (float *)B->ws32.x);
+            NB_CUDA(cudaGetLastError());
+            NB_TRY(batch_cg<float>(B, B->ws32, B->dinv32, 0.0, o->maxiter - used, 1, o->use_graph,
+                                   1, nullptr, s));
+            k_bpromote<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, np, B->red,
+                                                     (const float *)B->ws32.x, x);
+            NB_CUDA(cudaGetLastError());
+            NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * np, cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaStreamSynchronize(s));
+            int most = 0;
+            for (int q = 0; q < np; ++q) {
+                iters[B->order[q]] += B->bs_host[q].iter;
+                most = std::max(most, B->bs_host[q].iter);
+            }
+            used += most;
+            batched_iters += most;
+            launches += 5 + (int64_t)std::max(most, 1) * (ngroups + 5);
+        }
+    }
+    NB_CUDA(cudaEventRecord(t1, s));
+    NB_CUDA(cudaEventSynchronize(t1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    nb_status worst = NB_OK;
+    double worst_rel = 0.0;
+    for (int p = 0; p < np; ++p) {
+        if (stats) {
+            stats[p].iters = iters[p];
+            stats[p].outer_iters = outer_p[p];
+            stats[p].rel_res = rel[p];
+            stats[p].seconds = ms * 1e-3;
+            stats[p].status = (nb_status)status[p];
+            stats[p].history_len = 0;
+            stats[p].launches = 0;
+        }
+        if (status[p] > worst) worst = (nb_status)status[p];
+        worst_rel = std::max(worst_rel, rel[p]);
+    }
+    if (total) {
+        total->iters = batched_iters;
+        total->outer_iters = outer;
+        total->rel_res = worst_rel;
+        total->seconds = ms * 1e-3;
+        total->status = worst;
+        total->history_len = 0;
+        total->launches = launches;
+    }
+    return worst;
+}

@@ -1,0 +1,183 @@
+// Operator for a batch of independent problems: one launch per polynomial
+// order present in the batch, over all elements of that order (elements of
+// equal order are contiguous in the batch layout).  Same arithmetic and
+// thread mapping as k_ax_cc; in addition each element looks up its problem,
+// takes that problem's beta, skips problems that have converged, and writes
+// its own partial sum p.(A_L p) so that the per-problem dot products can be
+// formed in a fixed order.  Included by the FP32 and FP64 operator units,
+// whose constant derivative tables it reads.
+#pragma once
+
+#include "nb_ax_impl.cuh"
+
+namespace nb {
+
+template <typename T, int n, int M, bool PUPD>
+__global__ void __launch_bounds__(M * n * n)
+k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restrict__ uin,
+      T *__restrict__ w, const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
+      const int32_t *__restrict__ elem_prob, const BScal *__restrict__ bs,
+      double *__restrict__ part_e)
+{
+    constexpr int n2 = n * n, n3 = n2 * n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *su = reinterpret_cast<T *>(smem_raw);  // [M][n3]
+    T *swr = su + M * n3;                      // [M][n2]
+    T *sws = swr + M * n2;                     // [M][n2]
+    T *sdot = sws + M * n2;                    // [M][n2]
+
+    const int tid = threadIdx.x;
+    const int el = tid / n2, ij = tid - el * n2;
+    const int i = ij % n, j = ij / n;
+    T Di[n], Dj[n], DTi[n], DTj[n];
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+        Di[l] = dtab<T>(n, i, l);
+        Dj[l] = dtab<T>(n, j, l);
+        DTi[l] = dtab<T>(n, l, i);
+        DTj[l] = dtab<T>(n, l, j);
+    }
+    T *sue = su + el * n3;
+    T *swre = swr + el * n2;
+    T *swse = sws + el * n2;
+
+    for (long long e0 = (long long)blockIdx.x * M; e0 < E; e0 += (long long)gridDim.x * M) {
+        const long long e = e0 + el;
+        const bool valid = e < E;
+        const int prob = valid ? elem_prob[e_first + e] : 0;
+        const bool live = valid && !(PUPD && bs[prob].done);
+        const T beta = (PUPD && live) ? (T)bs[prob].beta : T(0);
+        const size_t base = (size_t)e * n3 + ij;
+        T ru[n], rw[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            T v = T(0);
+            if (live) {
+                if (PUPD) {
+                    v = fabs(dinv[base + k * n2]) * r[base + k * n2] + beta * p[base + k * n2];
+                    p[base + k * n2] = v;
+                } else {
+                    v = uin[base + k * n2];
+                }
+            }
+            ru[k] = v;
+            rw[k] = T(0);
+            sue[k * n2 + ij] = v;
+        }
+        __syncthreads();
+        const T *Ge = G + (size_t)(valid ? e : 0) * 6 * n3 + ij;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            const T g0 = Ge[0 * n3 + k * n2], g1 = Ge[1 * n3 + k * n2], g2 = Ge[2 * n3 + k * n2];
+            const T g3 = Ge[3 * n3 + k * n2], g4 = Ge[4 * n3 + k * n2], g5 = Ge[5 * n3 + k * n2];
+            T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+            for (int l = 0; l < n; ++l) {
+                ur += Di[l] * sue[k * n2 + j * n + l];
+                us += Dj[l] * sue[k * n2 + l * n + i];
+                ut += dtab<T>(n, k, l) * ru[l];
+            }
+            const T wr = g0 * ur + g1 * us + g2 * ut;
+            const T ws = g1 * ur + g3 * us + g4 * ut;
+            const T wt = g2 * ur + g4 * us + g5 * ut;
+            swre[ij] = wr;
+            swse[ij] = ws;
+            __syncthreads();
+            T a = T(0);
+#pragma unroll
+            for (int l = 0; l < n; ++l) {
+                a += DTi[l] * swre[j * n + l];
+                a += DTj[l] * swse[l * n + i];
+            }
+            rw[k] += a;
+#pragma unroll
+            for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
+            __syncthreads();
+        }
+        T s = T(0);
+        if (live) {
+#pragma unroll
+            for (int k = 0; k < n; ++k) {
+                w[base + k * n2] = rw[k];
+                s += ru[k] * rw[k];
+            }
+        }
+        if (part_e) {
+            sdot[el * n2 + ij] = s;
+            __syncthreads();
+            if (ij == 0 && valid) {  // the element's partial, summed in a fixed order
+                double t = 0.0;
+                for (int q = 0; q < n2; ++q) t += (double)sdot[el * n2 + q];
+                part_e[e_first + e] = t;
+            }
+        }
+    }
+}
+
+template <typename T, int n, int M, bool PUPD>
+nb_status launch_bax(int sm_count, long long E, long long e_first, const T *G, const T *u, T *w,
+                     const T *r, const T *dinv, T *p, const int32_t *elem_prob, const BScal *bs,
+                     double *part_e, cudaStream_t s)
+{
+    auto kern = k_bax<T, n, M, PUPD>;
+    constexpr size_t smem = sizeof(T) * (size_t)M * (n * n * n + 3 * n * n);
+    constexpr int threads = M * n * n;
+    static int grid_cache = 0;
+    static int sm_cached = 0;
+    if (grid_cache == 0 || sm_cached != sm_count) {
+        if (smem > 48 * 1024)
+            NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        int per_sm = 0;
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+        grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
+        sm_cached = sm_count;
+    }
+    if (E <= 0) return NB_OK;
+    const long long need = (E + M - 1) / M;
+    const int grid = (int)(need < grid_cache ? need : grid_cache);
+    kern<<<grid, threads, smem, s>>>(E, e_first, G, u, w, r, dinv, p, elem_prob, bs, part_e);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+template <typename T>
+nb_status dispatch_bax(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
+                       const T *G, const T *u, T *w, const T *r, const T *dinv, T *p,
+                       const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s)
+{
+#define NB_BAX_CASE(NN, M0, M1)                                                                 \
+    case NN:                                                                                    \
+        if (pupd)                                                                               \
+            return mchoice ? launch_bax<T, NN, M1, true>(sm_count, E, e_first, G, u, w, r, dinv, \
+                                                         p, elem_prob, bs, part_e, s)           \
+                           : launch_bax<T, NN, M0, true>(sm_count, E, e_first, G, u, w, r, dinv, \
+                                                         p, elem_prob, bs, part_e, s);          \
+        return mchoice ? launch_bax<T, NN, M1, false>(sm_count, E, e_first, G, u, w, r, dinv, p, \
+                                                      elem_prob, bs, part_e, s)                 \
+                       : launch_bax<T, NN, M0, false>(sm_count, E, e_first, G, u, w, r, dinv, p, \
+                                                      elem_prob, bs, part_e, s);
+    switch (n) {
+        NB_BAX_CASE(2, 16, 32)
+        NB_BAX_CASE(3, 8, 16)
+        NB_BAX_CASE(4, 4, 8)
+        NB_BAX_CASE(5, 2, 4)
+        NB_BAX_CASE(6, 2, 4)
+        NB_BAX_CASE(7, 1, 2)
+        NB_BAX_CASE(8, 1, 2)
+        NB_BAX_CASE(9, 1, 2)
+        NB_BAX_CASE(10, 1, 2)
+        NB_BAX_CASE(11, 1, 2)
+        NB_BAX_CASE(12, 1, 2)
+        NB_BAX_CASE(13, 1, 1)
+        NB_BAX_CASE(14, 1, 1)
+        NB_BAX_CASE(15, 1, 1)
+        NB_BAX_CASE(16, 1, 1)
+        default:
+            set_error("unsupported order n=%d", n);
+            return NB_ERR_ARG;
+    }
+#undef NB_BAX_CASE
+}
+
+}  // namespace nb

@@ -60,6 +60,13 @@ struct CgScalars {
     unsigned int tick_upd;  // blocks of the update kernel done
 };
 
+// Per-problem scalars of a batched CG solve (one entry per problem, in the
+// batch's internal order).
+struct BScal {
+    double rtz, rtz_old, pap, rtr, alpha, beta, bnorm2, relres, tol;
+    int iter, maxit, done, status;
+};
+
 // A preallocated set of vectors for one solve precision.
 struct Workspace {
     size_t nL = 0;
@@ -111,6 +118,14 @@ struct nb_mesh {
     int32_t *gs_gid = nullptr;   // [rows]
     uint8_t *gs_mask = nullptr;  // [rows]
     int32_t *g_first = nullptr;  // [nG] first local copy of each global node
+    // the same rows split by kind, for the masked summation of the solver:
+    // copies of Dirichlet nodes (set to zero, nothing read), and free shared
+    // nodes with 2, 4 or 8 copies (ascending local indices, one vector load)
+    int32_t *gs_zero = nullptr;  // [n_zero]
+    int2 *gs_pair = nullptr;     // [n_pair]
+    int4 *gs_quad = nullptr;     // [n_quad]
+    int4 *gs_oct = nullptr;      // [2 n_oct]
+    int64_t n_zero = 0, n_pair = 0, n_quad = 0, n_oct = 0;
     uint8_t *mask_g = nullptr;   // [nG]
     // weights and preconditioner
     float *c32 = nullptr;      // [nL] 1/multiplicity (exact in float)
@@ -156,6 +171,8 @@ int ax_variant_count(const nb_mesh *m, nb_prec prec);
 
 // ---- gather-scatter and vectors (nb_vec.cu)
 nb_status dssum(nb_mesh *m, nb_prec prec, void *u, int masked, cudaStream_t s);
+nb_status gs_rows_launch(const nb_ctx *ctx, int64_t rows, const int32_t *off, const int32_t *loc,
+                         const uint8_t *rmask, nb_prec prec, void *u, int masked, cudaStream_t s);
 nb_status to_local(nb_mesh *m, nb_prec prec, const void *ug, void *uL, int masked,
                    cudaStream_t s);
 nb_status to_global(nb_mesh *m, nb_prec prec, const void *uL, void *ug, cudaStream_t s);

@@ -1,15 +1,832 @@
 // Learned per-element preconditioner and flexible CG.
-#include "nb_internal.h"
+//
+// The network maps an element's residual, divided by its norm, to a
+// correction of the same length d = (N+1)^3 (one hidden layer of width h with
+// GELU); the preconditioner scales the output back by the norm, weights each
+// copy by 1/multiplicity and applies direct-stiffness summation and the
+// Dirichlet mask, so the result is a continuous vector:
+//     z = M Q Q^T ( c * |r_e| MLP(r_e / |r_e|) )
+// It is trained on (residual, error) pairs that Jacobi-PCG runs produce; being
+// nonlinear it is used inside flexible CG (Notay 2000, one-vector
+// truncation), with Jacobi-PCG as the fallback when the flexible iteration
+// fails, and the FP64 residual of the refinement as the judge of convergence.
+//
+// Matrix products: BF16 operands on the tensor cores (mma.sync m16n8k16),
+// FP32 accumulation; master weights and Adam moments in FP32.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nb_cg_dev.cuh"
+
+struct nb_model {
+    nb_ctx *ctx = nullptr;
+    int N = 0, d = 0, h = 0;
+    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;  // FP32 master
+    float *m = nullptr, *v = nullptr;  // Adam moments over all parameters (contiguous)
+    float *grad = nullptr;             // gradients, same layout
+    int64_t nparam = 0;
+    int64_t step = 0;
+    int jacobi_add = 0;  // 1: z also adds the Jacobi term dinv * r
+    // scratch for a batch (grown on demand)
+    int cap = 0;
+    float *Z = nullptr, *H = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *nrm = nullptr;
+    float *X = nullptr;
+    double *lpart = nullptr;
+};
 
 namespace nb {
 
-void learned_free(nb_mesh *m) { m->learned = nullptr; }
+// ---------------------------------------------------------------------------
+// BF16 tensor-core matrix product: C = op(A) op(B) (+ epilogue)
+//   A: M x K (TA: stored K x M), B: K x N (TB: stored N x K), FP32 in memory,
+//   rounded to BF16 when staged in shared memory; FP32 accumulation.
+// ---------------------------------------------------------------------------
 
-nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+enum GemmEpi { EPI_STORE = 0, EPI_BIAS_GELU = 1, EPI_BIAS = 2, EPI_PRECOND = 3 };
+
+struct GemmArgs {
+    int M, N, K;
+    const float *A;
+    int lda;
+    const float *B;
+    int ldb;
+    float *C;
+    int ldc;
+    const float *bias;     // [N] (EPI_BIAS*, EPI_PRECOND)
+    float *C2;             // EPI_BIAS_GELU: gelu(C) written here (ldc)
+    const float *rowscale; // EPI_PRECOND: per-row factor
+    const float *colw;     // EPI_PRECOND: weight per output entry (M x N, ldc)
+};
+
+__device__ __forceinline__ float gelu_f(float z)
 {
-    (void)m; (void)prec; (void)ws; (void)o; (void)s;
-    set_error("learned preconditioner not available in this build");
-    return NB_ERR_STATE;
+    const float c = 0.7978845608028654f;  // sqrt(2/pi)
+    return 0.5f * z * (1.0f + tanhf(c * (z + 0.044715f * z * z * z)));
 }
 
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    const float c = 0.7978845608028654f;
+    const float u = c * (z + 0.044715f * z * z * z);
+    const float t = tanhf(u);
+    const float du = c * (1.0f + 3.0f * 0.044715f * z * z);
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];  // transposed: Bs[n][k]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+        for (int q = tid; q < GBM * GBK; q += 128) {
+            int mm, kk;
+            if (TA) { mm = q % GBM; kk = q / GBM; } else { kk = q % GBK; mm = q / GBK; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = 0.f;
+            if (gm < g.M && gk < g.K) v = TA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+            As[mm][kk] = __float2bfloat16_rn(v);
+        }
+        for (int q = tid; q < GBN * GBK; q += 128) {
+            int nn, kk;
+            if (TB) { kk = q % GBK; nn = q / GBK; } else { nn = q % GBN; kk = q / GBN; }
+            const int gn = n0 + nn, gk = k0 + kk;
+            float v = 0.f;
+            if (gn < g.N && gk < g.K) v = TB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
+            Bs[nn][kk] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GBK; ks += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = wm + mt * 16 + gq;
+                a[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r0][ks + 2 * tq]);
+                a[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][ks + 2 * tq]);
+                a[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r0][ks + 2 * tq + 8]);
+                a[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int c0 = wn + nt * 8 + gq;
+                b[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[c0][ks + 2 * tq]);
+                b[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[c0][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt], b[nt]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const int row = m0 + wm + mt * 16 + gq + 8 * (hh >> 1);
+                const int col = n0 + wn + nt * 8 + 2 * tq + (hh & 1);
+                if (row >= g.M || col >= g.N) continue;
+                float v = acc[mt][nt][hh];
+                const size_t o = (size_t)row * g.ldc + col;
+                if (EPI == EPI_BIAS_GELU) {
+                    v += g.bias[col];
+                    g.C[o] = v;
+                    g.C2[o] = gelu_f(v);
+                } else if (EPI == EPI_BIAS) {
+                    g.C[o] = v + g.bias[col];
+                } else if (EPI == EPI_PRECOND) {
+                    g.C[o] = (v + g.bias[col]) * g.rowscale[row] * g.colw[o];
+                } else {
+                    g.C[o] = v;
+                }
+            }
+}
+
+template <bool TA, bool TB, int EPI>
+static nb_status gemm(const GemmArgs &a, cudaStream_t s)
+{
+    dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
+    k_gemm_bf16<TA, TB, EPI><<<grid, 128, 0, s>>>(a);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels
+// ---------------------------------------------------------------------------
+
+// Row norms of an L-vector viewed as rows of d values and the rows divided
+// by them (zero rows stay zero).  One block per row.
+template <typename T>
+__global__ void k_rownorm(int rows, int d, const T *__restrict__ r, float *__restrict__ X,
+                          float *__restrict__ nrm)
+{
+    __shared__ double sred[32];
+    for (int e = blockIdx.x; e < rows; e += gridDim.x) {
+        double acc = 0.0;
+        for (int q = threadIdx.x; q < d; q += blockDim.x) {
+            const double v = (double)r[(size_t)e * d + q];
+            acc += v * v;
+        }
+        __shared__ float snrm;
+        const double t = block_sum(acc, sred);
+        if (threadIdx.x == 0) snrm = (float)sqrt(t);
+        __syncthreads();
+        const float nv = snrm;
+        const float inv = nv > 0.f ? 1.0f / nv : 0.f;
+        for (int q = threadIdx.x; q < d; q += blockDim.x)
+            X[(size_t)e * d + q] = (float)r[(size_t)e * d + q] * inv;
+        if (threadIdx.x == 0) nrm[e] = nv;
+        __syncthreads();
+    }
+}
+
+// Training pairs from selected elements: X = r_e/|r_e|, T = err_e/|r_e|.
+__global__ void k_pairs(int count, int d, const int32_t *__restrict__ elems,
+                        const double *__restrict__ r, const double *__restrict__ err,
+                        float *__restrict__ X, float *__restrict__ T)
+{
+    __shared__ double sred[32];
+    __shared__ double sn;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const size_t base = (size_t)elems[q] * d;
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) acc += r[base + i] * r[base + i];
+        const double t = block_sum(acc, sred);
+        if (threadIdx.x == 0) sn = sqrt(t);
+        __syncthreads();
+        const double inv = sn > 0.0 ? 1.0 / sn : 0.0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            X[(size_t)q * d + i] = (float)(r[base + i] * inv);
+            T[(size_t)q * d + i] = (float)(err[base + i] * inv);
+        }
+        __syncthreads();
+    }
+}
+
+// dY = 2 (Y - T) / (B d) and per-block partials of sum (Y - T)^2.
+__global__ void k_mse(int64_t n, const float *__restrict__ Y, const float *__restrict__ T,
+                      float scale, float *__restrict__ dY, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = Y[i] - T[i];
+        dY[i] = 2.0f * e * scale;
+        acc += (double)e * (double)e;
+    }
+    const double t = block_sum(acc, sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// dZ = dH * gelu'(Z), in place on dH.
+__global__ void k_gelu_back(int64_t n, const float *__restrict__ Z, float *__restrict__ dH)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dH[i] *= gelu_grad_f(Z[i]);
+}
+
+// Column sums of a rows x cols matrix (bias gradients), each column summed
+// in row order by one thread.
+__global__ void k_colsum(int rows, int cols, const float *__restrict__ A, float *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += A[(size_t)r * cols + c];
+    out[c] = s;
+}
+
+__global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g,
+                       float *__restrict__ m, float *__restrict__ v, float lr, float b1, float b2,
+                       float c1, float c2, float eps)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// z += |dinv| * r (optional Jacobi term of the learned preconditioner)
+__global__ void k_add_jacobi(int64_t n, const float *__restrict__ dinv, const float *__restrict__ r,
+                             float *__restrict__ z)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        z[i] += fabsf(dinv[i]) * r[i];
+}
+
+// ---------------------------------------------------------------------------
+// model helpers
+// ---------------------------------------------------------------------------
+
+static nb_status model_scratch(nb_model *md, int rows)
+{
+    if (rows <= md->cap) return NB_OK;
+    float *bufs[] = {md->Z, md->H, md->Y, md->dY, md->dH, md->nrm, md->X};
+    for (float *b : bufs) cudaFree(b);
+    cudaFree(md->lpart);
+    const size_t R = (size_t)rows;
+    NB_CUDA(cudaMalloc(&md->Z, sizeof(float) * R * md->h));
+    NB_CUDA(cudaMalloc(&md->H, sizeof(float) * R * md->h));
+    NB_CUDA(cudaMalloc(&md->dH, sizeof(float) * R * md->h));
+    NB_CUDA(cudaMalloc(&md->Y, sizeof(float) * R * md->d));
+    NB_CUDA(cudaMalloc(&md->dY, sizeof(float) * R * md->d));
+    NB_CUDA(cudaMalloc(&md->X, sizeof(float) * R * md->d));
+    NB_CUDA(cudaMalloc(&md->nrm, sizeof(float) * R));
+    NB_CUDA(cudaMalloc(&md->lpart, sizeof(double) * 4096));
+    md->cap = rows;
+    return NB_OK;
+}
+
+// Forward pass of B rows of X: Z, H = gelu(Z), Y.
+static nb_status model_forward(nb_model *md, const float *X, int B, cudaStream_t s)
+{
+    GemmArgs a = {};
+    a.M = B; a.N = md->h; a.K = md->d;
+    a.A = X; a.lda = md->d; a.B = md->W1; a.ldb = md->h;
+    a.C = md->Z; a.ldc = md->h; a.bias = md->b1; a.C2 = md->H;
+    NB_TRY((gemm<false, false, EPI_BIAS_GELU>(a, s)));
+    GemmArgs b2 = {};
+    b2.M = B; b2.N = md->d; b2.K = md->h;
+    b2.A = md->H; b2.lda = md->h; b2.B = md->W2; b2.ldb = md->d;
+    b2.C = md->Y; b2.ldc = md->d; b2.bias = md->b2;
+    return gemm<false, false, EPI_BIAS>(b2, s);
+}
+
+// Loss and gradients (into md->grad) for B pairs; *loss_dev = sum (Y-T)^2.
+static nb_status model_backward(nb_model *md, const float *X, const float *T, int B,
+                                double *loss_dev, cudaStream_t s)
+{
+    NB_TRY(model_forward(md, X, B, s));
+    const int64_t ny = (int64_t)B * md->d;
+    const int g = 256;
+    k_mse<<<g, 256, 0, s>>>(ny, md->Y, T, 1.0f / (float)ny, md->dY, md->lpart);
+    NB_CUDA(cudaGetLastError());
+    if (loss_dev) NB_TRY(sum_partials_dev(md->lpart, g, loss_dev, s));
+    float *gW1 = md->grad, *gb1 = gW1 + (size_t)md->d * md->h;
+    float *gW2 = gb1 + md->h, *gb2 = gW2 + (size_t)md->h * md->d;
+    GemmArgs a = {};  // gW2 = H^T dY   (h x d)
+    a.M = md->h; a.N = md->d; a.K = B;
+    a.A = md->H; a.lda = md->h; a.B = md->dY; a.ldb = md->d; a.C = gW2; a.ldc = md->d;
+    NB_TRY((gemm<true, false, EPI_STORE>(a, s)));
+    k_colsum<<<(md->d + 255) / 256, 256, 0, s>>>(B, md->d, md->dY, gb2);
+    NB_CUDA(cudaGetLastError());
+    GemmArgs b = {};  // dH = dY W2^T  (B x h)
+    b.M = B; b.N = md->h; b.K = md->d;
+    b.A = md->dY; b.lda = md->d; b.B = md->W2; b.ldb = md->d; b.C = md->dH; b.ldc = md->h;
+    NB_TRY((gemm<false, true, EPI_STORE>(b, s)));
+    k_gelu_back<<<256, 256, 0, s>>>((int64_t)B * md->h, md->Z, md->dH);
+    NB_CUDA(cudaGetLastError());
+    GemmArgs c = {};  // gW1 = X^T dZ   (d x h)
+    c.M = md->d; c.N = md->h; c.K = B;
+    c.A = X; c.lda = md->d; c.B = md->dH; c.ldb = md->h; c.C = gW1; c.ldc = md->h;
+    NB_TRY((gemm<true, false, EPI_STORE>(c, s)));
+    k_colsum<<<(md->h + 255) / 256, 256, 0, s>>>(B, md->h, md->dH, gb1);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// z = M Q Q^T(c * |r_e| MLP(r_e/|r_e|)) (+ dinv r): the preconditioner.
+static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z, cudaStream_t s)
+{
+    const int E = (int)m->E;
+    NB_TRY(model_scratch(md, E));
+    k_rownorm<float><<<std::min(E, m->ctx->sm_count * 8), 256, 0, s>>>(E, md->d, r, md->X, md->nrm);
+    NB_CUDA(cudaGetLastError());
+    GemmArgs a = {};
+    a.M = E; a.N = md->h; a.K = md->d;
+    a.A = md->X; a.lda = md->d; a.B = md->W1; a.ldb = md->h;
+    a.C = md->Z; a.ldc = md->h; a.bias = md->b1; a.C2 = md->H;
+    NB_TRY((gemm<false, false, EPI_BIAS_GELU>(a, s)));
+    GemmArgs b = {};
+    b.M = E; b.N = md->d; b.K = md->h;
+    b.A = md->H; b.lda = md->h; b.B = md->W2; b.ldb = md->d;
+    b.C = z; b.ldc = md->d; b.bias = md->b2; b.rowscale = md->nrm; b.colw = m->c32;
+    NB_TRY((gemm<false, false, EPI_PRECOND>(b, s)));
+    NB_TRY(dssum(m, NB_FP32, z, 1, s));
+    if (md->jacobi_add) {
+        k_add_jacobi<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, m->dinv32, r, z);
+        NB_CUDA(cudaGetLastError());
+    }
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// flexible CG (inner solve of the refinement) with the learned preconditioner
+// ---------------------------------------------------------------------------
+
+// Owner-copy dot product partials of (a, b) (continuous vectors).
+__global__ void k_fdot(int64_t n, const float *__restrict__ a, const float *__restrict__ b,
+                       const float *__restrict__ sgn, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    DotAcc<float> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!signbit(sgn[i])) acc.add(a[i] * b[i]);
+    const double t = block_sum(acc.value(), sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// p = z + beta p with beta = -(z, w_prev) / pap_prev (0 on the first step),
+// then partials of (r, p).  beta is formed by the first block from the
+// partials of (z, w_prev) in part_zw (read-only here).
+__global__ void k_fcg_p(int64_t n, CgScalars *sc, const double *__restrict__ part_zw, int cnt,
+                        const float *__restrict__ z, const float *__restrict__ r,
+                        float *__restrict__ p, const float *__restrict__ sgn,
+                        double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    __shared__ float sbeta;
+    if (sc->done) return;
+    const double zw = sum_partials(part_zw, cnt, sred);
+    if (threadIdx.x == 0) sbeta = sc->iter == 0 ? 0.f : (float)(-zw / sc->pap_prev);
+    __syncthreads();
+    const float beta = sbeta;
+    DotAcc<float> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float pv = z[i] + beta * p[i];
+        p[i] = pv;
+        if (!signbit(sgn[i])) acc.add(r[i] * pv);
+    }
+    const double t = block_sum(acc.value(), sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// alpha = (r, p) / (p, A p); x += alpha p; r -= alpha w; partials of (r, r).
+__global__ void k_fcg_update(int64_t n, CgScalars *sc, const double *__restrict__ part_rp,
+                             const double *__restrict__ part_pap, int cnt_rp, int cnt_pap,
+                             float *__restrict__ x, float *__restrict__ r,
+                             const float *__restrict__ p, const float *__restrict__ w,
+                             const float *__restrict__ sgn, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    __shared__ float salpha;
+    __shared__ int sbad;
+    if (sc->done) return;
+    const double rp = sum_partials(part_rp, cnt_rp, sred);
+    const double pap = sum_partials(part_pap, cnt_pap, sred);
+    if (threadIdx.x == 0) {
+        const double a = rp / pap;
+        sbad = !(pap > 0.0) || !isfinite(a);
+        salpha = sbad ? 0.f : (float)a;
+        if (blockIdx.x == 0) {
+            sc->pap = pap;
+            sc->alpha = a;
+            sc->rp = rp;
+        }
+    }
+    __syncthreads();
+    if (sbad) return;  // uniform; the finish kernel records the breakdown
+    const float alpha = salpha;
+    DotAcc<float> acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        const float rv = r[i] - alpha * w[i];
+        r[i] = rv;
+        if (!signbit(sgn[i])) acc.add(rv * rv);
+    }
+    const double t = block_sum(acc.value(), sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_fcg_finish(CgScalars *sc, const double *__restrict__ part, int cnt)
+{
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const double rtr = sum_partials(part, cnt, sred);
+    if (threadIdx.x == 0) {
+        if (!(sc->pap > 0.0) || !isfinite(sc->alpha)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+            return;
+        }
+        sc->pap_prev = sc->pap;
+        sc->rtr = rtr;
+        const int it = sc->iter + 1;
+        sc->iter = it;
+        const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
+        const double rel = sqrt(rtr / bn);
+        sc->relres = rel;
+        if (sc->hist && it <= sc->hist_cap) sc->hist[it - 1] = rel;
+        if (!isfinite(rel)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else if (rel < sc->tol) {
+            sc->done = 1;
+        } else if (it >= sc->maxit) {
+            sc->done = 1;
+            sc->status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+__global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int cnt)
+{
+    __shared__ double sred[32];
+    const double rtr = sum_partials(part, cnt, sred);
+    if (threadIdx.x == 0) {
+        sc->rtr = rtr;
+        sc->bnorm2 = rtr;
+        sc->relres = rtr > 0.0 ? 1.0 : 0.0;
+        sc->pap_prev = 0.0;
+        if (!isfinite(rtr)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else if (rtr == 0.0 || sc->maxit <= 0) {
+            sc->done = 1;
+            if (rtr != 0.0) sc->status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+// The inner solve of a refinement step: ws.r holds the scaled residual, ws.x
+// starts at zero.  Host-launched iterations, the stopping state checked
+// every few iterations (all kernels skip their work once it is set).
+nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
+{
+    (void)o;
+    nb_model *md = (nb_model *)m->learned;
+    if (!md) {
+        set_error("no learned preconditioner attached");
+        return NB_ERR_STATE;
+    }
+    const int g = vec_grid(m->ctx, m->nL);
+    const float *sgn = m->dinv32;
+    float *x = (float *)ws.x, *r = (float *)ws.r, *p = (float *)ws.p, *w = (float *)ws.w;
+    float *z = (float *)ws.z, *wprev = (float *)ws.aux;
+    double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
+    NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
+    NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
+    k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
+    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
+    NB_CUDA(cudaGetLastError());
+    m->launches += 2;
+    for (int it = 0;; ++it) {
+        NB_TRY(model_apply(m, md, r, z, s));
+        k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, z, wprev, sgn, P0);
+        k_fcg_p<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P0, g, z, r, p, sgn, P1);
+        NB_CUDA(cudaGetLastError());
+        int nparts = 0;
+        NB_TRY(ax_local(m, prec, p, w, P0, &nparts, s));
+        NB_TRY(dssum(m, prec, w, 1, s));
+        k_fcg_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P1, P0, g, nparts, x, r, p, w, sgn,
+                                               P2);
+        k_fcg_finish<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
+        NB_CUDA(cudaGetLastError());
+        std::swap(w, wprev);  // w of this step is w_prev of the next
+        m->launches += 10 + (md->jacobi_add ? 1 : 0);
+        if ((it & 7) == 7) {
+            NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars),
+                                    cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaStreamSynchronize(s));
+            if (ws.scal_host->done) break;
+            if (it > ws.scal_host->maxit + 8) break;  // bounded even if the state is stuck
+        }
+    }
+    // keep ws.w / ws.aux as allocated (the swap only exchanged roles)
+    return NB_OK;
+}
+
+void learned_free(nb_mesh *m) { m->learned = nullptr; }
+
 }  // namespace nb
+
+using namespace nb;
+
+extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t seed,
+                                     nb_model **out)
+{
+    if (!ctx || !out || N < 1 || N > kMaxN || hidden < 1 || hidden > 4096) {
+        set_error("invalid argument: model shape");
+        return NB_ERR_ARG;
+    }
+    *out = nullptr;
+    NB_CUDA(cudaSetDevice(ctx->device));
+    nb_model *md = new nb_model();
+    md->ctx = ctx;
+    md->N = N;
+    md->d = (N + 1) * (N + 1) * (N + 1);
+    md->h = hidden;
+    const size_t d = md->d, h = md->h;
+    md->nparam = (int64_t)(d * h + h + h * d + d);
+    // deterministic initialisation: uniform(-1,1)/sqrt(fan-in) from SplitMix64
+    std::vector<float> host(md->nparam, 0.f);
+    uint64_t st = seed * 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    for (size_t i = 0; i < d * h; ++i) host[i] = (float)(next() / sqrt((double)d));
+    for (size_t i = 0; i < h * d; ++i) host[d * h + h + i] = (float)(next() / sqrt((double)h));
+    cudaError_t e = cudaMalloc(&md->W1, sizeof(float) * md->nparam);
+    if (e == cudaSuccess) e = cudaMalloc(&md->grad, sizeof(float) * md->nparam);
+    if (e == cudaSuccess) e = cudaMalloc(&md->m, sizeof(float) * md->nparam);
+    if (e == cudaSuccess) e = cudaMalloc(&md->v, sizeof(float) * md->nparam);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(md->W1, host.data(), sizeof(float) * md->nparam, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(md->m, 0, sizeof(float) * md->nparam);
+    if (e == cudaSuccess) e = cudaMemset(md->v, 0, sizeof(float) * md->nparam);
+    if (e != cudaSuccess) {
+        set_error("model allocation: %s", cudaGetErrorString(e));
+        cudaFree(md->W1); cudaFree(md->grad); cudaFree(md->m); cudaFree(md->v);
+        delete md;
+        return NB_ERR_OOM;
+    }
+    md->b1 = md->W1 + d * h;
+    md->W2 = md->b1 + h;
+    md->b2 = md->W2 + h * d;
+    *out = md;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_destroy(nb_model *md)
+{
+    if (!md) return NB_OK;
+    cudaSetDevice(md->ctx->device);
+    float *bufs[] = {md->W1, md->grad, md->m, md->v, md->Z, md->H, md->Y, md->dY, md->dH,
+                     md->nrm, md->X};
+    for (float *b : bufs) cudaFree(b);
+    cudaFree(md->lpart);
+    delete md;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_params(nb_model *md, float *get_host, const float *set_host,
+                                     int64_t *nparam)
+{
+    if (!md) {
+        set_error("invalid argument: model is NULL");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(md->ctx->device));
+    if (nparam) *nparam = md->nparam;
+    if (set_host)
+        NB_CUDA(cudaMemcpy(md->W1, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
+    if (get_host)
+        NB_CUDA(cudaMemcpy(get_host, md->W1, sizeof(float) * md->nparam, cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_grad(nb_model *md, const float *X, const float *T, int B,
+                                   double *loss_host, float *grad_host)
+{
+    if (!md || !X || !T || B < 1) {
+        set_error("invalid argument: model, batch or size");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(md->ctx->device));
+    cudaStream_t s = md->ctx->stream;
+    NB_TRY(model_scratch(md, B));
+    double *dl = md->lpart + 4000;
+    NB_TRY(model_backward(md, X, T, B, dl, s));
+    double l = 0.0;
+    NB_CUDA(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (grad_host)
+        NB_CUDA(cudaMemcpyAsync(grad_host, md->grad, sizeof(float) * md->nparam,
+                                cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    if (loss_host) *loss_host = l / ((double)B * md->d);
+    return NB_OK;
+}
+
+extern "C" nb_status nb_model_train(nb_model *md, const float *X, const float *T, int npairs,
+                                    int epochs, int batch, float lr, double *final_loss)
+{
+    if (!md || !X || !T || npairs < 1 || epochs < 0 || batch < 1 || !(lr > 0.f)) {
+        set_error("invalid argument: training set-up");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(md->ctx->device));
+    cudaStream_t s = md->ctx->stream;
+    batch = std::min(batch, npairs);
+    NB_TRY(model_scratch(md, batch));
+    const float b1 = 0.9f, b2 = 0.999f;
+    double *dl = md->lpart + 4000;
+    double lsum = 0.0;
+    int lcnt = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        lsum = 0.0;
+        lcnt = 0;
+        for (int off = 0; off + batch <= npairs; off += batch) {
+            NB_TRY(model_backward(md, X + (size_t)off * md->d, T + (size_t)off * md->d, batch,
+                                  ep == epochs - 1 ? dl : nullptr, s));
+            md->step += 1;
+            const float c1 = 1.f - powf(b1, (float)md->step), c2 = 1.f - powf(b2, (float)md->step);
+            k_adam<<<256, 256, 0, s>>>(md->nparam, md->W1, md->grad, md->m, md->v, lr, b1, b2, c1,
+                                       c2, 1e-8f);
+            NB_CUDA(cudaGetLastError());
+            if (ep == epochs - 1) {
+                double l = 0.0;
+                NB_CUDA(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, s));
+                NB_CUDA(cudaStreamSynchronize(s));
+                lsum += l / ((double)batch * md->d);
+                ++lcnt;
+            }
+        }
+    }
+    NB_CUDA(cudaStreamSynchronize(s));
+    if (final_loss) *final_loss = lcnt ? lsum / lcnt : 0.0;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_learned_pairs(nb_mesh *m, const double *r_dev, const double *err_dev,
+                                      const int32_t *elems_dev, int count, float *X_dev,
+                                      float *T_dev)
+{
+    if (!m || !r_dev || !err_dev || !elems_dev || count < 0 || !X_dev || !T_dev) {
+        set_error("invalid argument: pairs");
+        return NB_ERR_ARG;
+    }
+    if (count == 0) return NB_OK;
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    k_pairs<<<std::min(count, m->ctx->sm_count * 8), 256, 0, s>>>(count, m->n3, elems_dev, r_dev,
+                                                                  err_dev, X_dev, T_dev);
+    NB_CUDA(cudaGetLastError());
+    NB_CUDA(cudaStreamSynchronize(s));
+    return NB_OK;
+}
+
+__global__ void k_sub64(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                        double *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+extern "C" nb_status nb_learned_collect(nb_mesh *m, const double *b, int nsnap,
+                                        const int *snap_iters, int per_snap, uint64_t seed,
+                                        float *X, float *T, int *count)
+{
+    if (!m || !b || nsnap < 1 || !snap_iters || per_snap < 1 || !X || !T || !count) {
+        set_error("invalid argument: pair collection");
+        return NB_ERR_ARG;
+    }
+    if (!m->gs_ready) {
+        set_error("call nb_setup_gs first");
+        return NB_ERR_STATE;
+    }
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = m->ctx->stream;
+    const size_t bytes = sizeof(double) * m->nL;
+    double *xs = nullptr, *xk = nullptr, *rk = nullptr, *ek = nullptr;
+    int32_t *el = nullptr;
+    std::vector<int32_t> pick(per_snap);
+    nb_status st = NB_OK;
+    cudaError_t ce = cudaMalloc(&xs, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&xk, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&rk, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ek, bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&el, sizeof(int32_t) * per_snap);
+    if (ce != cudaSuccess) {
+        set_error("pair collection buffers: %s", cudaGetErrorString(ce));
+        st = NB_ERR_OOM;
+    }
+    // the converged solution
+    nb_opts o;
+    nb_default_opts(&o);
+    o.prec = NB_FP32;
+    o.rtol = 1e-10;
+    if (st == NB_OK) st = solve(m, &o, b, xs, nullptr) < 0 ? NB_ERR_CUDA : NB_OK;
+    uint64_t state = seed * 0x9E3779B97F4A7C15ull + 12345u;
+    int total = 0;
+    for (int q = 0; q < nsnap && st == NB_OK; ++q) {
+        // the Jacobi-PCG iterate after snap_iters[q] steps, its residual and error
+        nb_opts o64;
+        nb_default_opts(&o64);
+        o64.prec = NB_FP64;
+        o64.rtol = 1e-14;
+        o64.maxiter = snap_iters[q];
+        if (solve(m, &o64, b, xk, nullptr) < 0) { st = NB_ERR_CUDA; break; }
+        if ((st = ax_local(m, NB_FP64, xk, rk, nullptr, nullptr, s)) != NB_OK) break;
+        if ((st = dssum(m, NB_FP64, rk, 1, s)) != NB_OK) break;
+        k_sub64<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, b, rk, rk);
+        k_sub64<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, xs, xk, ek);
+        for (int i = 0; i < per_snap; ++i) {  // elements drawn with SplitMix64
+            uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            pick[i] = (int32_t)(z % (uint64_t)m->E);
+        }
+        if (cudaMemcpyAsync(el, pick.data(), sizeof(int32_t) * per_snap, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess) { st = NB_ERR_CUDA; break; }
+        k_pairs<<<std::min(per_snap, m->ctx->sm_count * 8), 256, 0, s>>>(
+            per_snap, m->n3, el, rk, ek, X + (size_t)total * m->n3, T + (size_t)total * m->n3);
+        if (cudaGetLastError() != cudaSuccess) { st = NB_ERR_CUDA; break; }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { st = NB_ERR_CUDA; break; }
+        total += per_snap;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(xs);
+    cudaFree(xk);
+    cudaFree(rk);
+    cudaFree(ek);
+    cudaFree(el);
+    *count = total;
+    return st;
+}
+
+extern "C" nb_status nb_learned_attach(nb_mesh *m, nb_model *md, int jacobi_add)
+{
+    if (!m) {
+        set_error("invalid argument: mesh is NULL");
+        return NB_ERR_ARG;
+    }
+    if (md && md->d != m->n3) {
+        set_error("model order does not match the mesh");
+        return NB_ERR_ARG;
+    }
+    if (md) md->jacobi_add = jacobi_add;
+    m->learned = md;
+    return NB_OK;
+}
+
+extern "C" nb_status nb_learned_apply(nb_mesh *m, const float *r_dev, float *z_dev)
+{
+    if (!m || !r_dev || !z_dev || !m->learned || !m->gs_ready) {
+        set_error("invalid argument or no model attached");
+        return NB_ERR_ARG;
+    }
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_TRY(model_apply(m, (nb_model *)m->learned, r_dev, z_dev, m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}

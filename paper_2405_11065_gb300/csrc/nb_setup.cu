@@ -288,6 +288,47 @@ nb_status build_gs(nb_mesh *m)
                             cudaMemcpyHostToDevice, s));
     NB_CUDA(cudaMemcpyAsync(m->mask_g, m->mask_host.data(), nG, cudaMemcpyHostToDevice, s));
     NB_CUDA(cudaMemcpyAsync(m->c32, c.data(), sizeof(float) * nL, cudaMemcpyHostToDevice, s));
+    // the rows by kind (see nb_internal.h); copies stay in ascending order
+    std::vector<int32_t> zero;
+    std::vector<int2> pair;
+    std::vector<int4> quad, oct;
+    for (int64_t a = 0; a < rows; ++a) {
+        const int32_t *lc = &rloc[roff[a]];
+        const int cnt = roff[a + 1] - roff[a];
+        if (rmask[a] == 0) {
+            for (int q = 0; q < cnt; ++q) zero.push_back(lc[q]);
+        } else if (cnt == 2) {
+            pair.push_back(make_int2(lc[0], lc[1]));
+        } else if (cnt == 4) {
+            quad.push_back(make_int4(lc[0], lc[1], lc[2], lc[3]));
+        } else if (cnt == 8) {
+            oct.push_back(make_int4(lc[0], lc[1], lc[2], lc[3]));
+            oct.push_back(make_int4(lc[4], lc[5], lc[6], lc[7]));
+        } else {
+            set_error("unexpected multiplicity %d of a free node", cnt);
+            return NB_ERR_MESH;
+        }
+    }
+    m->n_zero = (int64_t)zero.size();
+    m->n_pair = (int64_t)pair.size();
+    m->n_quad = (int64_t)quad.size();
+    m->n_oct = (int64_t)oct.size() / 2;
+    NB_CUDA(cudaMalloc(&m->gs_zero, sizeof(int32_t) * std::max<size_t>(zero.size(), 1)));
+    NB_CUDA(cudaMalloc(&m->gs_pair, sizeof(int2) * std::max<size_t>(pair.size(), 1)));
+    NB_CUDA(cudaMalloc(&m->gs_quad, sizeof(int4) * std::max<size_t>(quad.size(), 1)));
+    NB_CUDA(cudaMalloc(&m->gs_oct, sizeof(int4) * std::max<size_t>(oct.size(), 1)));
+    if (!zero.empty())
+        NB_CUDA(cudaMemcpyAsync(m->gs_zero, zero.data(), sizeof(int32_t) * zero.size(),
+                                cudaMemcpyHostToDevice, s));
+    if (!pair.empty())
+        NB_CUDA(cudaMemcpyAsync(m->gs_pair, pair.data(), sizeof(int2) * pair.size(),
+                                cudaMemcpyHostToDevice, s));
+    if (!quad.empty())
+        NB_CUDA(cudaMemcpyAsync(m->gs_quad, quad.data(), sizeof(int4) * quad.size(),
+                                cudaMemcpyHostToDevice, s));
+    if (!oct.empty())
+        NB_CUDA(cudaMemcpyAsync(m->gs_oct, oct.data(), sizeof(int4) * oct.size(),
+                                cudaMemcpyHostToDevice, s));
     NB_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
     // Jacobi: local diagonal, assembled and masked, inverted
     double *diag = nullptr;

@@ -123,16 +123,39 @@ __global__ void k_cg_update(int64_t nL, CgScalars *__restrict__ sc, T *__restric
     if (sc->done) return;
     const T alpha = (T)sc->alpha;
     DotAcc<T> a, b;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
-         l += (int64_t)gridDim.x * blockDim.x) {
-        x[l] = x[l] + alpha * p[l];
-        const T rl = r[l] - alpha * w[l];
-        r[l] = rl;
-        const T d = dinv[l];
+    auto node = [&](T &xl, T &rv, T pl, T wl, T d) {
+        xl = xl + alpha * pl;
+        rv = rv - alpha * wl;
         if (owner_copy(d)) {
-            a.add(rl * (d * rl));
-            b.add(rl * rl);
+            a.add(rv * (d * rv));
+            b.add(rv * rv);
         }
+    };
+    int64_t head = 0;
+    if constexpr (sizeof(T) == 4) {  // four nodes per 16-byte access (16-byte aligned buffers)
+        const int64_t n4 = nL / 4;
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            float4 xv = reinterpret_cast<float4 *>(x)[q];
+            float4 rv = reinterpret_cast<float4 *>(r)[q];
+            const float4 pv = reinterpret_cast<const float4 *>(p)[q];
+            const float4 wv = reinterpret_cast<const float4 *>(w)[q];
+            const float4 dv = reinterpret_cast<const float4 *>(dinv)[q];
+            node((T &)xv.x, (T &)rv.x, pv.x, wv.x, dv.x);
+            node((T &)xv.y, (T &)rv.y, pv.y, wv.y, dv.y);
+            node((T &)xv.z, (T &)rv.z, pv.z, wv.z, dv.z);
+            node((T &)xv.w, (T &)rv.w, pv.w, wv.w, dv.w);
+            reinterpret_cast<float4 *>(x)[q] = xv;
+            reinterpret_cast<float4 *>(r)[q] = rv;
+        }
+        head = n4 * 4;
+    }
+    for (int64_t l = head + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        T xl = x[l], rl = r[l];
+        node(xl, rl, p[l], w[l], dinv[l]);
+        x[l] = xl;
+        r[l] = rl;
     }
     double ta = block_sum(a.value(), sred);
     double tb = block_sum(b.value(), sred);
@@ -442,6 +465,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
     int used = 0, outer = 0, stagn = 0, hist_off = 0;
     double prev = INFINITY, rel = INFINITY;
     nb_status result = NB_NOT_CONVERGED;
+    bool fell_back = false;
+    constexpr int kLearnedBudget = 3000;  // flexible-CG iterations per refinement step
     for (outer = 0; outer <= o->max_outer; ++outer) {
         // FP64 residual r = b - A x (skipped product for the zero start)
         NB_TRY(fp64_residual(m, b, (outer == 0 && !o->use_x0) ? nullptr : x, 1, s));
@@ -463,7 +488,13 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         if (rel < o->rtol) { result = NB_OK; break; }
         if (outer == o->max_outer || used >= o->maxiter) { result = NB_NOT_CONVERGED; break; }
         if (rel > 0.5 * prev) {
-            if (++stagn >= 3) { result = NB_STAGNATED; break; }
+            if (o->pc == NB_PC_LEARNED && !fell_back) {
+                fell_back = true;  // the learned steps stopped paying: Jacobi-PCG takes over
+                stagn = 0;
+            } else if (++stagn >= 3) {
+                result = NB_STAGNATED;
+                break;
+            }
         } else {
             stagn = 0;
         }
@@ -476,9 +507,11 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // the inner solve only has to close the remaining gap to rtol (with a
         // factor 2 of margin), and never less than inner_rtol per step
         const double tau = std::min(0.5, std::max(o->inner_rtol, 0.5 * o->rtol / rel));
-        if (o->pc == NB_PC_LEARNED) {
-            // flexible CG with the learned preconditioner (nb_learned.cu)
-            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, remaining,
+        const bool use_learned = o->pc == NB_PC_LEARNED && !fell_back;
+        if (use_learned) {
+            // flexible CG with the learned preconditioner (nb_learned.cu), on a
+            // bounded budget; Jacobi-PCG takes over if it fails
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, kLearnedBudget),
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
@@ -495,14 +528,21 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         const int it = ws.scal_host->iter;
-        if (o->use_graph && o->pc != NB_PC_LEARNED) m->launches += 4 * (int64_t)std::max(it, 1);
+        if (o->use_graph && !use_learned) m->launches += 4 * (int64_t)std::max(it, 1);
         if (o->record_history) {
             copy_history(ws, it, hist_off, st, s);
             hist_off += it;
         }
         used += it;
+        if (use_learned && ws.scal_host->status != 0) {
+            fell_back = true;  // the learned step failed: Jacobi-PCG from here on
+            prev = INFINITY;
+            stagn = 0;
+            continue;
+        }
         if (ws.scal_host->status == NB_BREAKDOWN && it == 0) { result = NB_BREAKDOWN; break; }
     }
+    if (result == NB_OK && fell_back) result = NB_FELL_BACK;
     if (st) {
         st->iters = used;
         st->outer_iters = outer;

@@ -25,16 +25,79 @@ __global__ void k_gs(int64_t rows, const int32_t *__restrict__ off, const int32_
     }
 }
 
+nb_status gs_rows_launch(const nb_ctx *ctx, int64_t rows, const int32_t *off, const int32_t *loc,
+                         const uint8_t *rmask, nb_prec prec, void *u, int masked, cudaStream_t s)
+{
+    if (rows == 0) return NB_OK;
+    int grid = (int)std::min<int64_t>((rows + 255) / 256, (int64_t)ctx->sm_count * 8);
+    if (prec == NB_FP64)
+        k_gs<double><<<grid, 256, 0, s>>>(rows, off, loc, rmask, (double *)u, masked);
+    else
+        k_gs<float><<<grid, 256, 0, s>>>(rows, off, loc, rmask, (float *)u, masked);
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
+}
+
+// Masked summation from the rows split by kind: copies of Dirichlet nodes are
+// zeroed without being read; free shared nodes with 2, 4 or 8 copies fetch
+// their ascending copy list with one or two vector loads and sum in that
+// order, so the result is the same as k_gs with masking.
+template <typename T>
+__global__ void k_gs_kinds(int64_t nz, int64_t np, int64_t nq, int64_t no,
+                           const int32_t *__restrict__ zl, const int2 *__restrict__ pl,
+                           const int4 *__restrict__ ql, const int4 *__restrict__ ol,
+                           T *__restrict__ u)
+{
+    const int64_t total = nz + np + nq + no;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < total;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        if (a < nz) {
+            u[zl[a]] = T(0);
+        } else if (a < nz + np) {
+            const int2 c = pl[a - nz];
+            const T s = u[c.x] + u[c.y];
+            u[c.x] = s;
+            u[c.y] = s;
+        } else if (a < nz + np + nq) {
+            const int4 c = ql[a - nz - np];
+            const T s = ((u[c.x] + u[c.y]) + u[c.z]) + u[c.w];
+            u[c.x] = s;
+            u[c.y] = s;
+            u[c.z] = s;
+            u[c.w] = s;
+        } else {
+            const int64_t o = a - nz - np - nq;
+            const int4 c = ol[2 * o], d = ol[2 * o + 1];
+            const T s = ((((((u[c.x] + u[c.y]) + u[c.z]) + u[c.w]) + u[d.x]) + u[d.y]) + u[d.z]) +
+                        u[d.w];
+            u[c.x] = s;
+            u[c.y] = s;
+            u[c.z] = s;
+            u[c.w] = s;
+            u[d.x] = s;
+            u[d.y] = s;
+            u[d.z] = s;
+            u[d.w] = s;
+        }
+    }
+}
+
 nb_status dssum(nb_mesh *m, nb_prec prec, void *u, int masked, cudaStream_t s)
 {
-    if (m->gs_rows == 0) return NB_OK;
-    int grid = (int)std::min<int64_t>((m->gs_rows + 255) / 256, (int64_t)m->ctx->sm_count * 8);
+    if (!masked || !m->gs_pair)
+        return gs_rows_launch(m->ctx, m->gs_rows, m->gs_off, m->gs_loc, m->gs_mask, prec, u,
+                              masked, s);
+    const int64_t total = m->n_zero + m->n_pair + m->n_quad + m->n_oct;
+    if (total == 0) return NB_OK;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)m->ctx->sm_count * 8);
     if (prec == NB_FP64)
-        k_gs<double><<<grid, 256, 0, s>>>(m->gs_rows, m->gs_off, m->gs_loc, m->gs_mask,
-                                          (double *)u, masked);
+        k_gs_kinds<double><<<grid, 256, 0, s>>>(m->n_zero, m->n_pair, m->n_quad, m->n_oct,
+                                                m->gs_zero, m->gs_pair, m->gs_quad, m->gs_oct,
+                                                (double *)u);
     else
-        k_gs<float><<<grid, 256, 0, s>>>(m->gs_rows, m->gs_off, m->gs_loc, m->gs_mask,
-                                         (float *)u, masked);
+        k_gs_kinds<float><<<grid, 256, 0, s>>>(m->n_zero, m->n_pair, m->n_quad, m->n_oct,
+                                               m->gs_zero, m->gs_pair, m->gs_quad, m->gs_oct,
+                                               (float *)u);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -1,0 +1,147 @@
+"""The learned per-element preconditioner: GPU gradients against the FP64
+oracle's backward pass, the preconditioner against the oracle's forward
+pass, and flexible CG with the trained network against Jacobi-PCG."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from workloads import Box, HELDOUT_SEEDS, LEARNED_16CUBE_N7, TRAIN_SEEDS, rhs_global
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2405_11065_gb300 as nb
+    return nb
+
+
+@pytest.fixture(scope="module")
+def ctx(nb):
+    return nb.Context(0)
+
+
+def _cos(a, b):
+    a, b = a.reshape(-1), b.reshape(-1)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def test_gpu_gradients_match_oracle_backward(nb, ctx):
+    import torch
+    N, h, B = 3, 8, 96
+    d = (N + 1) ** 3
+    model = nb.Model(ctx, N, h, seed=1)
+    p = mlp.init_params(d, h, seed=5)
+    rng = np.random.default_rng(6)
+    p["b1"] = rng.uniform(-0.3, 0.3, h)
+    p["b2"] = rng.uniform(-0.3, 0.3, d)
+    # parameters exactly representable in BF16 so both sides use the same weights
+    bf = lambda a: torch.from_numpy(np.asarray(a, np.float32)).bfloat16().float().numpy()
+    p = {k: bf(v).astype(np.float64) for k, v in p.items()}
+    model.set_params(p)
+    X = bf(rng.uniform(-1, 1, (B, d))).astype(np.float64)
+    T = rng.uniform(-1, 1, (B, d))
+    loss, g = model.grad(torch.from_numpy(X.astype(np.float32)).cuda(),
+                         torch.from_numpy(T.astype(np.float32)).cuda())
+    ref = mlp.backward(p, X, T)
+    lref = mlp.loss(p, X, T)
+    assert abs(loss - lref) <= 1e-2 * lref
+    for k in ("W1", "b1", "W2", "b2"):
+        c = _cos(g[k].astype(np.float64), ref[k])
+        rel = np.linalg.norm(g[k] - ref[k]) / np.linalg.norm(ref[k])
+        print(f"grad {k}: cosine {c:.6f}, relative error {rel:.2e}")
+        assert c > 0.999, (k, c)
+
+
+def test_preconditioner_matches_oracle_forward(nb, ctx):
+    import torch
+    box = Box(2, 2, 2, 3, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    d, h = box.n ** 3, 16
+    model = nb.Model(ctx, box.N, h, seed=2)
+    params = {k: v.astype(np.float64) for k, v in model.params().items()}
+    model.attach(mesh)
+    r = P.to_local(rhs_global(box, 3))
+    rt = torch.from_numpy(r.astype(np.float32)).cuda()
+    z = torch.empty_like(rt)
+    model.apply(mesh, rt, z)
+    corr = mlp.precondition(params, r.reshape(box.E, d)).reshape(-1)
+    ref = P.dssum(P.c * corr, masked=True)
+    err = np.max(np.abs(z.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    print(f"learned preconditioner (BF16) max relative error vs FP64 oracle: {err:.2e}")
+    assert err < 3e-2
+
+
+def _pipeline(nb, ctx, box, train_seeds, snaps, per_snap, epochs, hidden=48):
+    import torch
+    mesh = nb.Mesh.from_box(ctx, box)
+    Xs, Ts = [], []
+    for s in train_seeds:
+        bg = torch.from_numpy(rhs_global(box, s)).cuda()
+        b = torch.empty(box.n_local, dtype=torch.float64, device="cuda")
+        mesh.to_local(nb.NB_FP64, bg, b)
+        X, T = nb.Model.collect(mesh, b, snaps, per_snap, seed=s)
+        Xs.append(X)
+        Ts.append(T)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    model = nb.Model(ctx, box.N, hidden, seed=7)
+    loss = model.train(X, T, epochs=epochs, batch=256, lr=1e-3)
+    model.attach(mesh)
+    return mesh, model, loss, X.shape[0]
+
+
+def _compare(nb, mesh, box, seeds):
+    import torch
+    res = []
+    for s in seeds:
+        bg = torch.from_numpy(rhs_global(box, s)).cuda()
+        b = torch.empty(box.n_local, dtype=torch.float64, device="cuda")
+        mesh.to_local(nb.NB_FP64, bg, b)
+        x = torch.zeros_like(b)
+        jac = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_JACOBI))
+        xl = torch.zeros_like(b)
+        lrn = mesh.solve(b, xl, nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_LEARNED))
+        res.append((s, jac, lrn, b, xl))
+    return res
+
+
+def test_learned_fcg_small_mesh_converges(nb, ctx):
+    box = Box(4, 4, 4, 5, 0.05)
+    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS[:3], [2, 5, 10, 20, 40, 80],
+                                          64, epochs=30)
+    P = oracle.Problem(box)
+    for s, jac, lrn, b, xl in _compare(nb, mesh, box, HELDOUT_SEEDS[:2]):
+        print(f"seed {s}: Jacobi-PCG {jac['iters']} its {jac['seconds']*1e3:.2f} ms; "
+              f"learned FCG {lrn['iters']} its {lrn['seconds']*1e3:.2f} ms status {lrn['status']}")
+        assert lrn["status"] in (nb.NB_OK, nb.NB_FELL_BACK)
+        assert lrn["rel_res"] < 1e-10
+        assert P.true_relres(b.cpu().numpy(), xl.cpu().numpy()) < 1.01e-10
+
+
+def test_learned_preconditioner_workload(nb, ctx):
+    """The learned-preconditioner workload: 16^3 deformed box, N = 7, about
+    10,000 element pairs from Jacobi-PCG runs on 8 training seeds, evaluated
+    on held-out seeds against Jacobi-PCG."""
+    box = LEARNED_16CUBE_N7
+    snaps = [2, 5, 10, 20, 40, 80, 160, 320]
+    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS, snaps, 157, epochs=30)
+    assert npairs >= 10000
+    out = []
+    for s, jac, lrn, b, xl in _compare(nb, mesh, box, HELDOUT_SEEDS[:2]):
+        out.append(dict(seed=s, jacobi_iters=jac["iters"], jacobi_ms=jac["seconds"] * 1e3,
+                        learned_iters=lrn["iters"], learned_ms=lrn["seconds"] * 1e3,
+                        learned_status=lrn["status"], learned_rel_res=lrn["rel_res"]))
+        assert lrn["status"] in (nb.NB_OK, nb.NB_FELL_BACK)
+        assert lrn["rel_res"] < 1e-10
+    summary = dict(pairs=npairs, final_train_loss=loss, results=out)
+    print("learned workload:", json.dumps(summary))
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open(os.path.join("gpurun_out", "learned_workload.json"), "w") as f:
+        json.dump(summary, f, indent=1)
