@@ -282,9 +282,10 @@ nb_status nb_batch_autotune(nb_batch *batch, int reps, void *flush_dev, size_t f
 /* ------------------------------------------------------------------------
  * Learned preconditioner: a per-element network (one hidden layer with GELU,
  * BF16 tensor-core products with FP32 accumulation, FP32 master weights)
- * mapping an element's residual r_e / |r_e| to a correction, used as
- * z = M Q Q^T(c |r_e| MLP(r_e/|r_e|)) inside flexible CG.  Not in the paper;
- * it replaces the paper's multigrid solveM slot with a learned one.
+ * mapping an element's residual r_e / |r_e| to a correction on the element's
+ * interior nodes, used as z = Dinv r + M_int(|r_e| MLP(r_e/|r_e|)) inside
+ * flexible CG (orders N <= 11).  Not in the paper; it takes the slot of the
+ * paper's multigrid solveM with a learned element-interior correction.
  * ------------------------------------------------------------------------ */
 typedef struct nb_model nb_model;
 
@@ -309,24 +310,29 @@ nb_status nb_model_grad(nb_model *model, const float *X_dev, const float *T_dev,
 nb_status nb_model_train(nb_model *model, const float *X_dev, const float *T_dev, int npairs,
                          int epochs, int batch, float lr, double *final_loss);
 
-/* Training pairs from the solver itself: solves A x = b (b: FP64 L-vector,
- * continuous, masked), then for each of nsnap iteration counts runs that many
- * Jacobi-PCG iterations from zero and, for per_snap elements drawn with
- * SplitMix64(seed), writes X = r_k|e / |r_k|e| and T = (x* - x_k)|e / |r_k|e|
- * (device FP32, capacity nsnap * per_snap * d).  *count = pairs written. */
+/* Training pairs from the solver itself, for b (FP64 L-vector, continuous,
+ * masked): for each of nsnap iteration counts k, the solver's iterate x_k
+ * after k steps from zero -- Jacobi-PCG in FP64, or with use_learned != 0 the
+ * refinement's flexible CG with the attached network -- and its residual
+ * r_k = b - A x_k; then for per_snap elements drawn with SplitMix64(seed) the
+ * pair of nb_learned_targets.  X_dev, T_dev: device FP32, capacity
+ * nsnap * per_snap * d.  *count = pairs written.  Errors: NB_ERR_ARG (also
+ * N > 11), NB_ERR_STATE, NB_ERR_OOM, NB_ERR_CUDA. */
 nb_status nb_learned_collect(nb_mesh *mesh, const double *b_dev, int nsnap,
                              const int *snap_iters, int per_snap, uint64_t seed,
-                             float *X_dev, float *T_dev, int *count);
+                             int use_learned, float *X_dev, float *T_dev, int *count);
 
-/* Pairs from given residual and error L-vectors (FP64, device) for the listed
- * elements (device int32). */
-nb_status nb_learned_pairs(nb_mesh *mesh, const double *r_dev, const double *err_dev,
-                           const int32_t *elems_dev, int count, float *X_dev, float *T_dev);
+/* Pairs for given elements (device int32) of a residual L-vector r (FP64,
+ * device): X = r_e/|r_e|, T = (A_ii^-1 r_i - Dinv r_i)/|r_e| on the
+ * element's interior nodes and 0 on its boundary nodes, A_ii the operator's
+ * block on the element interior (solved by conjugate gradients per element
+ * to 1e-9 relative, in FP64). */
+nb_status nb_learned_targets(nb_mesh *mesh, const double *r_dev, const int32_t *elems_dev,
+                             int count, float *X_dev, float *T_dev);
 
-/* Use `model` (NULL detaches) as the mesh's NB_PC_LEARNED preconditioner;
- * jacobi_add != 0 adds the Jacobi term dinv*r to its output.  The model must
- * outlive its use. */
-nb_status nb_learned_attach(nb_mesh *mesh, nb_model *model, int jacobi_add);
+/* Use `model` (NULL detaches) as the mesh's NB_PC_LEARNED preconditioner.
+ * The model must outlive its use. */
+nb_status nb_learned_attach(nb_mesh *mesh, nb_model *model);
 
 /* Apply the attached preconditioner once: z = B(r), FP32 L-vectors. */
 nb_status nb_learned_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);

@@ -99,3 +99,59 @@ def precondition(params, r_elems: np.ndarray):
     safe = np.where(nrm > 0, nrm, 1.0)
     Y, _ = forward(params, r_elems / safe[:, None])
     return Y * nrm[:, None]
+
+
+def interior_mask(N: int) -> np.ndarray:
+    """True on the (N-1)^3 interior nodes of an element, index (k n + j) n + i."""
+    n = N + 1
+    q = np.arange(n ** 3)
+    i, j, k = q % n, (q // n) % n, q // (n * n)
+    return (i > 0) & (i < N) & (j > 0) & (j < N) & (k > 0) & (k < N)
+
+
+def element_interior_block(P, e: int) -> np.ndarray:
+    """Dense block of element e's operator on its interior nodes, built by
+    applying the oracle's local operator to unit vectors."""
+    n3 = P.box.n ** 3
+    mask = interior_mask(P.N)
+    cols = np.nonzero(mask)[0]
+    Ge = P.G[e:e + 1]
+    A = np.zeros((len(cols), len(cols)))
+    for c, q in enumerate(cols):
+        u = np.zeros(n3)
+        u[q] = 1.0
+        A[:, c] = ax_local_element(P, Ge, u)[cols]
+    return A
+
+
+def ax_local_element(P, Ge, u):
+    from . import ax_local
+    return ax_local(P.N, P.D, Ge, u)
+
+
+def interior_targets(P, r: np.ndarray, elems):
+    """The learned preconditioner's training pairs for residual r (L-vector):
+    X = r_e/|r_e| and T = (A_ii^-1 r_i - Dinv r_i)/|r_e| on interior nodes,
+    0 on the element's boundary nodes (dense direct solves)."""
+    n3 = P.box.n ** 3
+    mask = interior_mask(P.N)
+    X = np.zeros((len(elems), n3))
+    T = np.zeros((len(elems), n3))
+    for t, e in enumerate(elems):
+        re = r[e * n3:(e + 1) * n3]
+        nrm = np.linalg.norm(re)
+        if nrm == 0:
+            continue
+        A = element_interior_block(P, e)
+        xi = np.linalg.solve(A, re[mask] / nrm)
+        X[t] = re / nrm
+        T[t, mask] = xi - P.dinv[e * n3:(e + 1) * n3][mask] * re[mask] / nrm
+    return X, T
+
+
+def precondition_interior(params, P, r: np.ndarray) -> np.ndarray:
+    """z = Dinv r + M_int (|r_e| MLP(r_e/|r_e|)) for an L-vector r."""
+    n3 = P.box.n ** 3
+    corr = precondition(params, r.reshape(-1, n3))
+    corr = corr * interior_mask(P.N)[None, :]
+    return P.dinv * r + corr.reshape(-1)

@@ -83,9 +83,10 @@ def _load():
         "nb_model_params": (i32, [vp, vp, vp, C.POINTER(i64)]),
         "nb_model_grad": (i32, [vp, vp, vp, i32, C.POINTER(dbl), vp]),
         "nb_model_train": (i32, [vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(dbl)]),
-        "nb_learned_collect": (i32, [vp, vp, i32, vp, i32, C.c_uint64, vp, vp, C.POINTER(i32)]),
-        "nb_learned_pairs": (i32, [vp, vp, vp, vp, i32, vp, vp]),
-        "nb_learned_attach": (i32, [vp, vp, i32]),
+        "nb_learned_collect": (i32, [vp, vp, i32, vp, i32, C.c_uint64, i32, vp, vp,
+                                     C.POINTER(i32)]),
+        "nb_learned_targets": (i32, [vp, vp, vp, i32, vp, vp]),
+        "nb_learned_attach": (i32, [vp, vp]),
         "nb_learned_apply": (i32, [vp, vp, vp]),
         "nb_default_opts": (None, [C.POINTER(nb_opts)]),
         "nb_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
@@ -393,8 +394,9 @@ class Model:
         return loss.value
 
     @staticmethod
-    def collect(mesh: "Mesh", b, snap_iters, per_snap, seed=0):
-        """Training pairs from Jacobi-PCG iterates of A x = b (see header)."""
+    def collect(mesh: "Mesh", b, snap_iters, per_snap, seed=0, use_learned=False):
+        """Training pairs from the solver's own iterates of A x = b: Jacobi-PCG,
+        or flexible CG with the attached network (see the C header)."""
         import torch
         its = np.ascontiguousarray(snap_iters, dtype=np.int32)
         cap = len(its) * per_snap
@@ -403,11 +405,22 @@ class Model:
         T = torch.empty((cap, d), dtype=torch.float32, device=b.device)
         cnt = C.c_int()
         check(lib.nb_learned_collect(mesh.h, _ptr(b), len(its), _ptr(its), per_snap, seed,
-                                     _ptr(X), _ptr(T), C.byref(cnt)))
+                                     int(use_learned), _ptr(X), _ptr(T), C.byref(cnt)))
         return X[:cnt.value], T[:cnt.value]
 
-    def attach(self, mesh: "Mesh", jacobi_add=False):
-        check(lib.nb_learned_attach(mesh.h, self.h, int(jacobi_add)))
+    @staticmethod
+    def targets(mesh: "Mesh", r, elems):
+        """X, T of nb_learned_targets for a residual L-vector (FP64 CUDA)."""
+        import torch
+        el = torch.as_tensor(np.ascontiguousarray(elems, dtype=np.int32)).to(r.device)
+        d = (mesh.N + 1) ** 3
+        X = torch.empty((len(el), d), dtype=torch.float32, device=r.device)
+        T = torch.empty_like(X)
+        check(lib.nb_learned_targets(mesh.h, _ptr(r), _ptr(el), len(el), _ptr(X), _ptr(T)))
+        return X, T
+
+    def attach(self, mesh: "Mesh"):
+        check(lib.nb_learned_attach(mesh.h, self.h))
         mesh._model = self  # keep alive
 
     def apply(self, mesh: "Mesh", r, z):

@@ -93,13 +93,15 @@ constexpr int tma_threads()
 template <typename T, int n, bool PUPD>
 constexpr size_t ax_tma_stage_elems()
 {
-    return (size_t)7 * n * n * n;  // G[6][n3] and the element's u (or new p)
+    // G[6][n3] per stage, plus the element's u for the plain operator (the
+    // fused CG step forms p itself into one buffer shared by both stages)
+    return (size_t)(PUPD ? 6 : 7) * n * n * n;
 }
 
 template <typename T, int n, bool PUPD>
 constexpr size_t ax_tma_smem()
 {
-    return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + 4 * n * n);
+    return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + (PUPD ? n * n * n : 0) + 4 * n * n);
 }
 
 template <typename T>
@@ -124,7 +126,8 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     using V2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *stage = reinterpret_cast<T *>(smem_raw);  // [2][STAGE]: G[6][n3], then u
-    T *swr = stage + 2 * STAGE;                  // [2][n2] (double-buffered by layer)
+    T *pbuf = stage + 2 * STAGE;                 // [n3] the fused step's p (PUPD only)
+    T *swr = pbuf + (PUPD ? n3 : 0);             // [2][n2] (double-buffered by layer)
     T *sws = swr + 2 * n2;                       // [2][n2]
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sred[32];
@@ -183,7 +186,7 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
         if (__syncthreads_or(!ok)) break;
         T *s = stage + (t & 1) * STAGE;
         const T *Gs = s;
-        T *su = s + 6 * n3;
+        T *su = PUPD ? pbuf : s + 6 * n3;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
             if (PUPD) {
@@ -305,6 +308,7 @@ template <typename T>
 constexpr bool tma_fits(int n, bool pupd)
 {
     (void)pupd;  // both forms stage G and u
+    // the plain form's stages (2 x 7 n^3) are the larger of the two
     return (n % 2 == 0) && sizeof(T) * (2 * (size_t)7 * n * n * n + 4 * n * n) <= 227 * 1024;
 }
 

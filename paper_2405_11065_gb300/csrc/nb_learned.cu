@@ -2,14 +2,18 @@
 //
 // The network maps an element's residual, divided by its norm, to a
 // correction of the same length d = (N+1)^3 (one hidden layer of width h with
-// GELU); the preconditioner scales the output back by the norm, weights each
-// copy by 1/multiplicity and applies direct-stiffness summation and the
-// Dirichlet mask, so the result is a continuous vector:
-//     z = M Q Q^T ( c * |r_e| MLP(r_e / |r_e|) )
-// It is trained on (residual, error) pairs that Jacobi-PCG runs produce; being
-// nonlinear it is used inside flexible CG (Notay 2000, one-vector
-// truncation), with Jacobi-PCG as the fallback when the flexible iteration
-// fails, and the FP64 residual of the refinement as the judge of convergence.
+// GELU).  The preconditioner is Jacobi plus the scaled network output on the
+// element's interior nodes:
+//     z = Dinv r + M_int ( |r_e| MLP(r_e / |r_e|) )
+// Interior nodes belong to one element only, so z is continuous without a
+// summation.  The network is trained to supply what Jacobi misses inside an
+// element: its targets are (A_ii^-1 r_i - Dinv r_i) / |r_e|, the
+// element-interior solve minus the Jacobi step, for residuals that the
+// solver itself produces (Jacobi-PCG iterates first, then flexible-CG
+// iterates with the network being trained).  Being nonlinear, it is used
+// inside flexible CG (Notay 2000, one-vector truncation), with Jacobi-PCG as
+// the fallback when the flexible iteration fails and the FP64 residual of the
+// refinement as the judge of convergence.
 //
 // Matrix products: BF16 operands on the tensor cores (mma.sync m16n8k16),
 // FP32 accumulation; master weights and Adam moments in FP32.
@@ -29,7 +33,6 @@ struct nb_model {
     float *grad = nullptr;             // gradients, same layout
     int64_t nparam = 0;
     int64_t step = 0;
-    int jacobi_add = 0;  // 1: z also adds the Jacobi term dinv * r
     // scratch for a batch (grown on demand)
     int cap = 0;
     float *Z = nullptr, *H = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *nrm = nullptr;
@@ -59,8 +62,10 @@ struct GemmArgs {
     int ldc;
     const float *bias;     // [N] (EPI_BIAS*, EPI_PRECOND)
     float *C2;             // EPI_BIAS_GELU: gelu(C) written here (ldc)
-    const float *rowscale; // EPI_PRECOND: per-row factor
-    const float *colw;     // EPI_PRECOND: weight per output entry (M x N, ldc)
+    const float *rowscale; // EPI_PRECOND: per-row factor |r_e|
+    const float *rvec;     // EPI_PRECOND: the residual (M x N, ldc)
+    const float *dinv;     // EPI_PRECOND: signed Jacobi inverse diagonal (M x N, ldc)
+    int n;                 // EPI_PRECOND: points per direction (N = n^3 columns)
 };
 
 __device__ __forceinline__ float gelu_f(float z)
@@ -157,7 +162,14 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                 } else if (EPI == EPI_BIAS) {
                     g.C[o] = v + g.bias[col];
                 } else if (EPI == EPI_PRECOND) {
-                    g.C[o] = (v + g.bias[col]) * g.rowscale[row] * g.colw[o];
+                    // Jacobi everywhere, plus the learned correction on the
+                    // element's interior nodes (which have a single copy)
+                    const int ci = col % g.n, cj = (col / g.n) % g.n, ck = col / (g.n * g.n);
+                    const bool inner = ci > 0 && ci < g.n - 1 && cj > 0 && cj < g.n - 1 &&
+                                       ck > 0 && ck < g.n - 1;
+                    float z = fabsf(g.dinv[o]) * g.rvec[o];
+                    if (inner) z += (v + g.bias[col]) * g.rowscale[row];
+                    g.C[o] = z;
                 } else {
                     g.C[o] = v;
                 }
@@ -203,24 +215,114 @@ __global__ void k_rownorm(int rows, int d, const T *__restrict__ r, float *__res
     }
 }
 
-// Training pairs from selected elements: X = r_e/|r_e|, T = err_e/|r_e|.
-__global__ void k_pairs(int count, int d, const int32_t *__restrict__ elems,
-                        const double *__restrict__ r, const double *__restrict__ err,
-                        float *__restrict__ X, float *__restrict__ T)
+// Training pairs for the element-interior correction.  For each listed
+// element: X = r_e / |r_e|, and T = (A_ii^-1 r_i - Dinv r_i) / |r_e| on the
+// element's interior nodes (0 on its boundary nodes), where A_ii is the block
+// of the operator on the element's interior nodes (they belong to this
+// element only) and Dinv the Jacobi inverse diagonal.  A_ii^-1 r_i is computed
+// by conjugate gradients on the element, one block per element, with the
+// element operator applied node by node in FP64 (training data, not the hot
+// path).  Shared memory: p, w, wr, ws, wt, x, res (7 n^3 doubles) and D.
+__device__ __forceinline__ bool interior_node(int q, int n)
 {
+    const int i = q % n, j = (q / n) % n, k = q / (n * n);
+    return i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1;
+}
+
+// Block-wide sum returned to every thread (block_sum gives it to thread 0).
+__device__ __forceinline__ double block_sum_all(double v, double *sred, double *slot)
+{
+    const double t = block_sum(v, sred);
+    if (threadIdx.x == 0) *slot = t;
+    __syncthreads();
+    const double r = *slot;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_interior_pairs(int count, int n, const int32_t *__restrict__ elems,
+                                 const double *__restrict__ r, const double *__restrict__ G,
+                                 const double *__restrict__ Dg, const double *__restrict__ dinv,
+                                 double tol, int maxit, float *__restrict__ X,
+                                 float *__restrict__ T)
+{
+    extern __shared__ double shd[];
+    const int n3 = n * n * n;
+    double *sp = shd, *sw = sp + n3, *swr = sw + n3, *sws = swr + n3, *swt = sws + n3;
+    double *sx = swt + n3, *sres = sx + n3, *sD = sres + n3;  // sD: n*n
     __shared__ double sred[32];
-    __shared__ double sn;
+    __shared__ double slot;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = Dg[t];
+    __syncthreads();
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
-        const size_t base = (size_t)elems[q] * d;
+        const int64_t e = elems[q];
+        const double *re = r + e * n3;
+        const double *Ge = G + e * 6 * n3;
         double acc = 0.0;
-        for (int i = threadIdx.x; i < d; i += blockDim.x) acc += r[base + i] * r[base + i];
-        const double t = block_sum(acc, sred);
-        if (threadIdx.x == 0) sn = sqrt(t);
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) acc += re[t] * re[t];
+        const double rn = sqrt(block_sum_all(acc, sred, &slot));
+        const double inv = rn > 0.0 ? 1.0 / rn : 0.0;
+        acc = 0.0;
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+            X[(size_t)q * n3 + t] = (float)(re[t] * inv);
+            const double bi = interior_node(t, n) ? re[t] * inv : 0.0;  // the scaled system
+            sx[t] = 0.0;
+            sres[t] = bi;
+            sp[t] = bi;
+            acc += bi * bi;
+        }
+        // every thread holds the same rr, so the loop below is uniform
+        double rr = block_sum_all(acc, sred, &slot);
+        const double rr0 = rr;
+        for (int it = 0; it < maxit && rr > tol * tol * rr0; ++it) {
+            // w = M_int A_e M_int p (p is zero off the interior)
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+                const int i = t % n, j = (t / n) % n, k = t / (n * n);
+                double ur = 0.0, us = 0.0, ut = 0.0;
+                for (int l = 0; l < n; ++l) {
+                    ur += sD[i * n + l] * sp[(k * n + j) * n + l];
+                    us += sD[j * n + l] * sp[(k * n + l) * n + i];
+                    ut += sD[k * n + l] * sp[(l * n + j) * n + i];
+                }
+                const double g0 = Ge[t], g1 = Ge[n3 + t], g2 = Ge[2 * n3 + t];
+                const double g3 = Ge[3 * n3 + t], g4 = Ge[4 * n3 + t], g5 = Ge[5 * n3 + t];
+                swr[t] = g0 * ur + g1 * us + g2 * ut;
+                sws[t] = g1 * ur + g3 * us + g4 * ut;
+                swt[t] = g2 * ur + g4 * us + g5 * ut;
+            }
+            __syncthreads();
+            acc = 0.0;
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+                const int i = t % n, j = (t / n) % n, k = t / (n * n);
+                double s = 0.0;
+                if (interior_node(t, n)) {
+                    for (int l = 0; l < n; ++l) s += sD[l * n + i] * swr[(k * n + j) * n + l];
+                    for (int l = 0; l < n; ++l) s += sD[l * n + j] * sws[(k * n + l) * n + i];
+                    for (int l = 0; l < n; ++l) s += sD[l * n + k] * swt[(l * n + j) * n + i];
+                }
+                sw[t] = s;
+                acc += s * sp[t];
+            }
+            const double pap = block_sum_all(acc, sred, &slot);
+            if (!(pap > 0.0)) break;  // uniform
+            const double alpha = rr / pap;
+            acc = 0.0;
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+                sx[t] += alpha * sp[t];
+                sres[t] -= alpha * sw[t];
+                acc += sres[t] * sres[t];
+            }
+            const double rr1 = block_sum_all(acc, sred, &slot);
+            const double beta = rr1 / rr;
+            for (int t = threadIdx.x; t < n3; t += blockDim.x) sp[t] = sres[t] + beta * sp[t];
+            __syncthreads();
+            rr = rr1;
+        }
         __syncthreads();
-        const double inv = sn > 0.0 ? 1.0 / sn : 0.0;
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            X[(size_t)q * d + i] = (float)(r[base + i] * inv);
-            T[(size_t)q * d + i] = (float)(err[base + i] * inv);
+        for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+            const double v =
+                interior_node(t, n) ? sx[t] - fabs(dinv[e * n3 + t]) * re[t] * inv : 0.0;
+            T[(size_t)q * n3 + t] = (float)v;
         }
         __syncthreads();
     }
@@ -277,14 +379,6 @@ __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict
 }
 
 // z += |dinv| * r (optional Jacobi term of the learned preconditioner)
-__global__ void k_add_jacobi(int64_t n, const float *__restrict__ dinv, const float *__restrict__ r,
-                             float *__restrict__ z)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        z[i] += fabsf(dinv[i]) * r[i];
-}
-
 // ---------------------------------------------------------------------------
 // model helpers
 // ---------------------------------------------------------------------------
@@ -371,14 +465,10 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
     GemmArgs b = {};
     b.M = E; b.N = md->d; b.K = md->h;
     b.A = md->H; b.lda = md->h; b.B = md->W2; b.ldb = md->d;
-    b.C = z; b.ldc = md->d; b.bias = md->b2; b.rowscale = md->nrm; b.colw = m->c32;
-    NB_TRY((gemm<false, false, EPI_PRECOND>(b, s)));
-    NB_TRY(dssum(m, NB_FP32, z, 1, s));
-    if (md->jacobi_add) {
-        k_add_jacobi<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, m->dinv32, r, z);
-        NB_CUDA(cudaGetLastError());
-    }
-    return NB_OK;
+    b.C = z; b.ldc = md->d; b.bias = md->b2; b.rowscale = md->nrm;
+    b.rvec = r; b.dinv = m->dinv32; b.n = m->n;
+    // interior nodes have one copy and Jacobi is continuous: no summation needed
+    return gemm<false, false, EPI_PRECOND>(b, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,7 +637,7 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         k_fcg_finish<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
         NB_CUDA(cudaGetLastError());
         std::swap(w, wprev);  // w of this step is w_prev of the next
-        m->launches += 10 + (md->jacobi_add ? 1 : 0);
+        m->launches += 9;  // row norms, 2 products, 2 dots, operator, summation, update, finish
         if ((it & 7) == 7) {
             NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars),
                                     cudaMemcpyDeviceToHost, s));
@@ -705,24 +795,6 @@ extern "C" nb_status nb_model_train(nb_model *md, const float *X, const float *T
     return NB_OK;
 }
 
-extern "C" nb_status nb_learned_pairs(nb_mesh *m, const double *r_dev, const double *err_dev,
-                                      const int32_t *elems_dev, int count, float *X_dev,
-                                      float *T_dev)
-{
-    if (!m || !r_dev || !err_dev || !elems_dev || count < 0 || !X_dev || !T_dev) {
-        set_error("invalid argument: pairs");
-        return NB_ERR_ARG;
-    }
-    if (count == 0) return NB_OK;
-    NB_CUDA(cudaSetDevice(m->ctx->device));
-    cudaStream_t s = m->ctx->stream;
-    k_pairs<<<std::min(count, m->ctx->sm_count * 8), 256, 0, s>>>(count, m->n3, elems_dev, r_dev,
-                                                                  err_dev, X_dev, T_dev);
-    NB_CUDA(cudaGetLastError());
-    NB_CUDA(cudaStreamSynchronize(s));
-    return NB_OK;
-}
-
 __global__ void k_sub64(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
                         double *__restrict__ out)
 {
@@ -733,7 +805,7 @@ __global__ void k_sub64(int64_t n, const double *__restrict__ a, const double *_
 
 extern "C" nb_status nb_learned_collect(nb_mesh *m, const double *b, int nsnap,
                                         const int *snap_iters, int per_snap, uint64_t seed,
-                                        float *X, float *T, int *count)
+                                        int use_learned, float *X, float *T, int *count)
 {
     if (!m || !b || nsnap < 1 || !snap_iters || per_snap < 1 || !X || !T || !count) {
         set_error("invalid argument: pair collection");
@@ -743,42 +815,53 @@ extern "C" nb_status nb_learned_collect(nb_mesh *m, const double *b, int nsnap,
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
+    if (m->n > 12) {
+        set_error("the learned preconditioner supports orders N <= 11");
+        return NB_ERR_ARG;
+    }
+    if (use_learned && !m->learned) {
+        set_error("use_learned needs an attached model");
+        return NB_ERR_STATE;
+    }
     NB_CUDA(cudaSetDevice(m->ctx->device));
     cudaStream_t s = m->ctx->stream;
     const size_t bytes = sizeof(double) * m->nL;
-    double *xs = nullptr, *xk = nullptr, *rk = nullptr, *ek = nullptr;
+    const size_t smem = sizeof(double) * (7 * (size_t)m->n3 + (size_t)m->n * m->n);
+    NB_CUDA(cudaFuncSetAttribute(k_interior_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    double *xk = nullptr, *rk = nullptr;
     int32_t *el = nullptr;
     std::vector<int32_t> pick(per_snap);
     nb_status st = NB_OK;
-    cudaError_t ce = cudaMalloc(&xs, bytes);
-    if (ce == cudaSuccess) ce = cudaMalloc(&xk, bytes);
+    cudaError_t ce = cudaMalloc(&xk, bytes);
     if (ce == cudaSuccess) ce = cudaMalloc(&rk, bytes);
-    if (ce == cudaSuccess) ce = cudaMalloc(&ek, bytes);
     if (ce == cudaSuccess) ce = cudaMalloc(&el, sizeof(int32_t) * per_snap);
     if (ce != cudaSuccess) {
         set_error("pair collection buffers: %s", cudaGetErrorString(ce));
         st = NB_ERR_OOM;
     }
-    // the converged solution
-    nb_opts o;
-    nb_default_opts(&o);
-    o.prec = NB_FP32;
-    o.rtol = 1e-10;
-    if (st == NB_OK) st = solve(m, &o, b, xs, nullptr) < 0 ? NB_ERR_CUDA : NB_OK;
     uint64_t state = seed * 0x9E3779B97F4A7C15ull + 12345u;
     int total = 0;
     for (int q = 0; q < nsnap && st == NB_OK; ++q) {
-        // the Jacobi-PCG iterate after snap_iters[q] steps, its residual and error
-        nb_opts o64;
-        nb_default_opts(&o64);
-        o64.prec = NB_FP64;
-        o64.rtol = 1e-14;
-        o64.maxiter = snap_iters[q];
-        if (solve(m, &o64, b, xk, nullptr) < 0) { st = NB_ERR_CUDA; break; }
+        // the solver's iterate after snap_iters[q] steps from zero: Jacobi-PCG
+        // in FP64, or the refinement's flexible CG with the attached network
+        nb_opts o;
+        nb_default_opts(&o);
+        if (use_learned) {
+            o.prec = NB_FP32;
+            o.pc = NB_PC_LEARNED;
+            o.max_outer = 1;
+            o.inner_rtol = 1e-12;
+        } else {
+            o.prec = NB_FP64;
+        }
+        o.rtol = 1e-14;
+        o.maxiter = snap_iters[q];
+        if (solve(m, &o, b, xk, nullptr) < 0) { st = NB_ERR_CUDA; break; }
+        // its residual r_k = b - A x_k
         if ((st = ax_local(m, NB_FP64, xk, rk, nullptr, nullptr, s)) != NB_OK) break;
         if ((st = dssum(m, NB_FP64, rk, 1, s)) != NB_OK) break;
         k_sub64<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, b, rk, rk);
-        k_sub64<<<m->ctx->sm_count * 4, 256, 0, s>>>(m->nL, xs, xk, ek);
         for (int i = 0; i < per_snap; ++i) {  // elements drawn with SplitMix64
             uint64_t z = (state += 0x9E3779B97F4A7C15ull);
             z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -788,23 +871,45 @@ extern "C" nb_status nb_learned_collect(nb_mesh *m, const double *b, int nsnap,
         }
         if (cudaMemcpyAsync(el, pick.data(), sizeof(int32_t) * per_snap, cudaMemcpyHostToDevice,
                             s) != cudaSuccess) { st = NB_ERR_CUDA; break; }
-        k_pairs<<<std::min(per_snap, m->ctx->sm_count * 8), 256, 0, s>>>(
-            per_snap, m->n3, el, rk, ek, X + (size_t)total * m->n3, T + (size_t)total * m->n3);
+        k_interior_pairs<<<std::min(per_snap, m->ctx->sm_count * 8), 256, smem, s>>>(
+            per_snap, m->n, el, rk, m->G64, m->D64, m->dinv64, 1e-9, 1000,
+            X + (size_t)total * m->n3, T + (size_t)total * m->n3);
         if (cudaGetLastError() != cudaSuccess) { st = NB_ERR_CUDA; break; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { st = NB_ERR_CUDA; break; }
         total += per_snap;
     }
     cudaStreamSynchronize(s);
-    cudaFree(xs);
     cudaFree(xk);
     cudaFree(rk);
-    cudaFree(ek);
     cudaFree(el);
     *count = total;
     return st;
 }
 
-extern "C" nb_status nb_learned_attach(nb_mesh *m, nb_model *md, int jacobi_add)
+extern "C" nb_status nb_learned_targets(nb_mesh *m, const double *r_dev, const int32_t *elems_dev,
+                                        int count, float *X_dev, float *T_dev)
+{
+    if (!m || !r_dev || !elems_dev || count < 0 || !X_dev || !T_dev) {
+        set_error("invalid argument: targets");
+        return NB_ERR_ARG;
+    }
+    if (!m->gs_ready || m->n > 12) {
+        set_error("needs nb_setup_gs and N <= 11");
+        return NB_ERR_STATE;
+    }
+    if (count == 0) return NB_OK;
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    const size_t smem = sizeof(double) * (7 * (size_t)m->n3 + (size_t)m->n * m->n);
+    NB_CUDA(cudaFuncSetAttribute(k_interior_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    k_interior_pairs<<<std::min(count, m->ctx->sm_count * 8), 256, smem, m->ctx->stream>>>(
+        count, m->n, elems_dev, r_dev, m->G64, m->D64, m->dinv64, 1e-9, 1000, X_dev, T_dev);
+    NB_CUDA(cudaGetLastError());
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_learned_attach(nb_mesh *m, nb_model *md)
 {
     if (!m) {
         set_error("invalid argument: mesh is NULL");
@@ -814,7 +919,6 @@ extern "C" nb_status nb_learned_attach(nb_mesh *m, nb_model *md, int jacobi_add)
         set_error("model order does not match the mesh");
         return NB_ERR_ARG;
     }
-    if (md) md->jacobi_add = jacobi_add;
     m->learned = md;
     return NB_OK;
 }

@@ -102,7 +102,9 @@ def test_batch_mixed_refinement(nb, ctx):
 
 def test_batch_from_the_batched_workload(nb, ctx):
     """Problems drawn like the 256-problem batched workload (E in 8..512,
-    N in {5,7,9,11}), checked by the oracle's FP64 residual."""
+    N in {5,7,9,11}), checked by the oracle's FP64 residual.  A prime E gives
+    a 1 x 1 x E chain of elements whose condition number needs tens of
+    thousands of Jacobi-PCG iterations, hence the iteration limit."""
     import torch
     probs = batched_problems(12)
     boxes = [bx for bx, _ in probs]
@@ -110,7 +112,7 @@ def test_batch_from_the_batched_workload(nb, ctx):
     batch.autotune(reps=2)
     b = _batch_rhs(batch, boxes, [s for _, s in probs])
     x = torch.zeros_like(b)
-    out = batch.solve(b, x, nb.default_opts(prec=nb.NB_FP32, rtol=1e-10))
+    out = batch.solve(b, x, nb.default_opts(prec=nb.NB_FP32, rtol=1e-10, maxiter=200000))
     assert out["status"] == 0, out
     xs, bs = x.cpu().numpy(), b.cpu().numpy()
     for p, bx in enumerate(boxes):

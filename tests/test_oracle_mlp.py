@@ -66,3 +66,31 @@ def test_training_reduces_loss_on_a_linear_map():
     for _ in range(300):
         mlp.adam_step(p, mlp.backward(p, X, T), st, lr=3e-3)
     assert mlp.loss(p, X, T) < 0.5 * l0
+
+
+def test_interior_targets_solve_the_interior_block():
+    """The learned preconditioner's targets: the dense interior block equals
+    the independently assembled element matrix restricted to the interior,
+    and T + Dinv r solves it."""
+    import oracle
+    from test_oracle_operator import _dense_element_matrix
+    from workloads import Box, rhs_global
+    box = Box(2, 2, 1, 4, 0.05)
+    P = oracle.Problem(box)
+    mask = mlp.interior_mask(box.N)
+    assert mask.sum() == (box.N - 1) ** 3
+    for e in (0, 3):
+        A = mlp.element_interior_block(P, e)
+        ref = _dense_element_matrix(P.D, P.G[e])[np.ix_(mask, mask)]
+        np.testing.assert_allclose(A, ref, atol=1e-13 * np.abs(ref).max())
+    r = P.to_local(rhs_global(box, 5))
+    X, T = mlp.interior_targets(P, r, [0, 3])
+    n3 = box.n ** 3
+    for t, e in enumerate((0, 3)):
+        re = r[e * n3:(e + 1) * n3]
+        nrm = np.linalg.norm(re)
+        np.testing.assert_allclose(X[t], re / nrm, rtol=1e-15)
+        A = mlp.element_interior_block(P, e)
+        xi = T[t][mask] + P.dinv[e * n3:(e + 1) * n3][mask] * re[mask] / nrm
+        np.testing.assert_allclose(A @ xi, re[mask] / nrm, atol=1e-12)
+        assert np.all(T[t][~mask] == 0)
