@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
-    ap.add_argument("--mode", choices=["full", "solve", "ax"], default="full",
+    ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned"],
+                    default="full",
                     help="solve: only the timed solves (for a kernel launch list); "
-                         "ax: only a few launches of the operators (for a profiler capture)")
+                         "ax: only a few launches of the operators (for a profiler capture); "
+                         "sweep / batched / learned: the other workloads, one JSON line each")
     ap.add_argument("--prec", default="fp32", help="precision of --mode ax")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default operator variants (profiler runs: timing under a "
@@ -68,6 +70,23 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
     return rank, world, local
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over the ranks of the process group (x itself alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, n_global: int, steps: int, max_ms: float) -> float:
+    """Unique DOFs solved by all ranks per second (each rank solves its own
+    replica), in GDOF/s, over the slowest rank's time."""
+    return world * n_global * steps / (max_ms * 1e-3) / 1e9
 
 
 def oracle_iterations():
@@ -234,10 +253,145 @@ def run_reference(args):
     return 0
 
 
+def _rhs_local(nb, mesh, box, seed, dev):
+    import torch
+    bg = torch.from_numpy(W.rhs_global(box, seed)).to(dev)
+    b = torch.empty(box.n_local, dtype=torch.float64, device=dev)
+    mesh.to_local(nb.NB_FP64, bg, b, masked=True)
+    return b
+
+
+def run_sweep(args):
+    """Operator throughput and CG time to 1e-10 on deformed cubes E = 8^3 ..
+    32^3 at N in {5, 7, 9, 11, 15}: FP64, FP32 and tensor-core operators."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
+    peak, _ = measured_peaks()
+    for box in W.sweep_boxes():
+        mesh = nb.Mesh.from_box(ctx, box)
+        nL = box.n_local
+        line = {"mode": "sweep", "E": box.E, "N": box.N, "n_local": nL, "n_global": box.n_global}
+        for pname, elt in (("fp64", 8), ("fp32", 4), ("tc_f16", 4), ("tc_bf16", 4)):
+            prec = nb.PREC_NAMES[pname]
+            if pname in ("fp64", "fp32"):
+                mesh.autotune(prec, reps=2, flush=flush)
+            ms = mesh.time_ax(prec, cg_step=False, reps=5, flush=flush)
+            gbs = 8 * elt * nL / (ms * 1e-3) / 1e9
+            line[pname] = {"ax_ms": ms, "ax_gdofs_local": nL / (ms * 1e-3) / 1e9,
+                           "ax_gbs_algorithmic": gbs, "hbm_frac": gbs / peak}
+        b = _rhs_local(nb, mesh, box, 0, dev)
+        x = torch.zeros_like(b)
+        mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32))
+        x.zero_()
+        out = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32))
+        line["cg_fp32_refined"] = {"ms": out["seconds"] * 1e3, "iters": out["iters"],
+                                   "outer": out["outer_iters"], "rel_res": out["rel_res"],
+                                   "status": out["status"]}
+        if nL <= 20_000_000:
+            x.zero_()
+            o64 = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64))
+            line["cg_fp64"] = {"ms": o64["seconds"] * 1e3, "iters": o64["iters"],
+                               "rel_res": o64["rel_res"], "status": o64["status"]}
+        print(json.dumps(line), flush=True)
+        mesh.close()
+        del b, x
+        torch.cuda.empty_cache()
+    return 0
+
+
+def run_batched(args):
+    """256 independent problems, E ~ U{8..512} (most cubic box), N in
+    {5,7,9,11}, mixed precision with FP64 refinement, one graph per solve."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    probs = W.batched_problems(256)
+    boxes = [bx for bx, _ in probs]
+    t0 = time.perf_counter()
+    batch = nb.Batch(ctx, boxes)
+    setup_s = time.perf_counter() - t0
+    flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
+    batch.autotune(reps=3, flush=flush)
+    ug = torch.from_numpy(np.concatenate([W.rhs_global(bx, s) for bx, s in probs])).to(dev)
+    b = torch.empty(batch.n_local, dtype=torch.float64, device=dev)
+    batch.to_local(ug, b)
+    x = torch.zeros_like(b)
+    opts = nb.default_opts(prec=nb.NB_FP32, maxiter=400000)
+    batch.solve(b, x, opts)
+    times = []
+    for _ in range(max(args.steps, 1)):
+        x.zero_()
+        out = batch.solve(b, x, opts)
+        times.append(out["seconds"])
+    iters = [p["iters"] for p in out["problems"]]
+    t = statistics.median(times)
+    line = {"mode": "batched", "problems": len(boxes), "n_local": batch.n_local,
+            "n_global": batch.n_global, "orders": sorted(set(bx.N for bx in boxes)),
+            "setup_s": setup_s, "solve_ms": t * 1e3,
+            "gdofs_solved_per_s": batch.n_global / t / 1e9,
+            "batched_iterations": out["iters"], "max_problem_iters": max(iters),
+            "median_problem_iters": float(np.median(iters)), "status": out["status"],
+            "worst_rel_res": out["rel_res"], "launches": out["launches"],
+            "all_ok": all(p["status"] == 0 for p in out["problems"])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_learned(args):
+    """The learned-preconditioner workload (16^3 deformed box, N = 7)."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    box = W.LEARNED_16CUBE_N7
+    mesh = nb.Mesh.from_box(ctx, box)
+    model = nb.Model(ctx, box.N, 48, seed=7)
+    snaps = [1, 4, 16, 64, 128, 256, 512, 800]  # across the whole ~900-iteration solve
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    for s in W.TRAIN_SEEDS:
+        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, s, dev), snaps, 80, seed=s)
+        Xs.append(X)
+        Ts.append(T)
+    loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=30, batch=256, lr=1e-3)
+    model.attach(mesh)
+    for s in W.TRAIN_SEEDS:
+        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, s, dev), snaps, 80, seed=s + 100,
+                                use_learned=True)
+        Xs.append(X)
+        Ts.append(T)
+    loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=15, batch=256, lr=5e-4)
+    train_s = time.perf_counter() - t0
+    res = []
+    for s in W.HELDOUT_SEEDS:
+        b = _rhs_local(nb, mesh, box, s, dev)
+        row = {"seed": s}
+        for name, pc in (("jacobi", nb.NB_PC_JACOBI), ("learned", nb.NB_PC_LEARNED)):
+            x = torch.zeros_like(b)
+            o = nb.default_opts(prec=nb.NB_FP32, pc=pc, rtol=1e-8)
+            mesh.solve(b, x, o)
+            x.zero_()
+            out = mesh.solve(b, x, o)
+            row[name] = {"iters": out["iters"], "ms": out["seconds"] * 1e3,
+                         "status": out["status"], "rel_res": out["rel_res"]}
+        res.append(row)
+    line = {"mode": "learned", "E": box.E, "N": box.N, "pairs": int(sum(x.shape[0] for x in Xs)),
+            "params": model.nparam, "train_s": train_s, "final_loss": loss, "rtol": 1e-8,
+            "results": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode in ("sweep", "batched", "learned"):
+        return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned}[args.mode](args)
     rank, world, local = dist_env()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -312,11 +466,7 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(c) for a, c in evs]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(total_ms, dev)
     ok = all(s["status"] == 0 and s["rel_res"] < RTOL for s in stats)
     if args.mode == "solve":
         if rank == 0:
@@ -350,6 +500,22 @@ def main():
     t64 = statistics.median(fp64_ms)
     tm = statistics.median(step_ms)
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+
+    # the paper's accuracy metric: AE_k = |r_m,k - r_d,k| between the residual
+    # histories of an all-FP32 CG loop (the paper's mixed version, no
+    # refinement) and the FP64 loop, and their mean MAE
+    cap = 4000
+    h64 = mesh.solve(b, torch.zeros_like(b), nb.default_opts(prec=nb.NB_FP64, rtol=RTOL),
+                     history_cap=cap)["history"]
+    h32 = mesh.solve(b, torch.zeros_like(b),
+                     nb.default_opts(prec=nb.NB_FP32, rtol=RTOL, inner_rtol=RTOL, max_outer=1),
+                     history_cap=cap)["history"]
+    kk = min(len(h64), len(h32))
+    ae = np.abs(np.asarray(h32[:kk]) - np.asarray(h64[:kk]))
+    accuracy = {"metric": "relative residual histories, FP32 CG loop vs FP64 CG loop",
+                "fp64_iters": int(len(h64)), "fp32_loop_iters": int(len(h32)),
+                "ae_at_fp64_convergence": float(ae[-1]) if kk else None,
+                "mae": float(ae.mean()) if kk else None}
 
     # operator throughput and roofline of the dominant kernel
     hbm_peak, peak_kind = measured_peaks()
@@ -398,7 +564,7 @@ def main():
                "ms_per_step": te, "status": outh["status"]}
 
     launches = int(sum(s["launches"] for s in stats))
-    value = world * BOX.n_global * args.steps / (max_ms * 1e-3) / 1e9
+    value = whole_job_value(world, BOX.n_global, args.steps, max_ms)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,6 +588,7 @@ def main():
             "rel_res": {"mixed": stats[-1]["rel_res"], "fp64": fp64_stats["rel_res"],
                         "mixed_recomputed": true_rel},
             "mixed_vs_fp64_solution_rel_diff": sol_diff,
+            "accuracy_ae_mae": accuracy,
             "all_steps_converged": ok,
             "ax": ax,
             "wall_s_timed_region": wall,

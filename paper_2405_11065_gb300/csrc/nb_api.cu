@@ -34,6 +34,8 @@ static void free_ws(Workspace &ws)
 {
     if (ws.exec) cudaGraphExecDestroy(ws.exec);
     if (ws.graph) cudaGraphDestroy(ws.graph);
+    if (ws.exec2) cudaGraphExecDestroy(ws.exec2);
+    if (ws.graph2) cudaGraphDestroy(ws.graph2);
     cudaFree(ws.x);
     cudaFree(ws.r);
     cudaFree(ws.p);

@@ -81,6 +81,9 @@ struct Workspace {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_key = -1;           // which configuration the graph holds
+    cudaGraph_t graph2 = nullptr;       // flexible-CG iteration graph
+    cudaGraphExec_t exec2 = nullptr;
+    intptr_t graph2_key = 0;            // the model it was captured with
 };
 
 // Launch shape of the ax kernel for one (precision, order).

@@ -583,6 +583,16 @@ __global__ void k_fcg_finish(CgScalars *sc, const double *__restrict__ part, int
     }
 }
 
+// While-node condition of the captured flexible CG (two steps per body): stop
+// when the scalars say so, and in any case after maxit / 2 + 1 bodies.
+__global__ void k_fcg_cond(CgScalars *sc, cudaGraphConditionalHandle h)
+{
+    const int loops = sc->loops + 1;
+    sc->loops = loops;
+    const bool stop = sc->done != 0 || 2 * loops > sc->maxit + 2;
+    cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
 __global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int cnt)
 {
     __shared__ double sred[32];
@@ -618,24 +628,77 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     float *x = (float *)ws.x, *r = (float *)ws.r, *p = (float *)ws.p, *w = (float *)ws.w;
     float *z = (float *)ws.z, *wprev = (float *)ws.aux;
     double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
+    NB_TRY(model_scratch(md, (int)m->E));  // before any capture: it may allocate
     NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
     NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
     k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
     k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
     NB_CUDA(cudaGetLastError());
     m->launches += 2;
-    for (int it = 0;; ++it) {
+    // one flexible-CG step; w receives A p, wprev holds the previous A p
+    auto step = [&](float *wcur, float *wold) -> nb_status {
         NB_TRY(model_apply(m, md, r, z, s));
-        k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, z, wprev, sgn, P0);
+        k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, z, wold, sgn, P0);
         k_fcg_p<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P0, g, z, r, p, sgn, P1);
         NB_CUDA(cudaGetLastError());
         int nparts = 0;
-        NB_TRY(ax_local(m, prec, p, w, P0, &nparts, s));
-        NB_TRY(dssum(m, prec, w, 1, s));
-        k_fcg_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P1, P0, g, nparts, x, r, p, w, sgn,
-                                               P2);
+        NB_TRY(ax_local(m, prec, p, wcur, P0, &nparts, s));
+        NB_TRY(dssum(m, prec, wcur, 1, s));
+        k_fcg_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P1, P0, g, nparts, x, r, p, wcur,
+                                               sgn, P2);
         k_fcg_finish<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
         NB_CUDA(cudaGetLastError());
+        return NB_OK;
+    };
+    if (o->use_graph) {
+        // the loop body is two steps (the roles of w and wprev swap between
+        // them), repeated by a while node until the scalars say stop
+        const intptr_t key = (intptr_t)md;
+        if (!ws.exec2 || ws.graph2_key != key) {
+            if (ws.exec2) NB_CUDA(cudaGraphExecDestroy(ws.exec2));
+            if (ws.graph2) NB_CUDA(cudaGraphDestroy(ws.graph2));
+            ws.exec2 = nullptr;
+            ws.graph2 = nullptr;
+            cudaGraph_t gr;
+            NB_CUDA(cudaGraphCreate(&gr, 0));
+            cudaGraphConditionalHandle h;
+            NB_CUDA(cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            NB_CUDA(cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+            nb_status st = step(w, wprev);
+            if (st == NB_OK) st = step(wprev, w);
+            if (st == NB_OK) {
+                k_fcg_cond<<<1, 1, 0, s>>>(ws.scal, h);
+                if (cudaGetLastError() != cudaSuccess) st = NB_ERR_CUDA;
+            }
+            cudaGraph_t captured = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s, &captured);
+            if (st != NB_OK || ce != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                if (st != NB_OK) return st;
+                set_error("flexible-CG graph capture failed: %s", cudaGetErrorString(ce));
+                return NB_ERR_CUDA;
+            }
+            NB_CUDA(cudaGraphInstantiate(&ws.exec2, gr, 0));
+            ws.graph2 = gr;
+            ws.graph2_key = key;
+        }
+        NB_CUDA(cudaGraphLaunch(ws.exec2, s));
+        NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        m->launches += 19 * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
+        return NB_OK;
+    }
+    for (int it = 0;; ++it) {
+        NB_TRY(step(w, wprev));
         std::swap(w, wprev);  // w of this step is w_prev of the next
         m->launches += 9;  // row norms, 2 products, 2 dots, operator, summation, update, finish
         if ((it & 7) == 7) {
