@@ -196,12 +196,13 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_impl.cuh", "paper_2405_11065_gb300/csrc/nb_ax_f32.cu"]
+AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_tma.cuh", "paper_2405_11065_gb300/csrc/nb_ax_impl.cuh",
+              "paper_2405_11065_gb300/csrc/nb_ax.cu"]
 
 
-def profiled_traffic(sha):
+def profiled_traffic(sha, kernel):
     """DRAM bytes per launch of the FP32 CG-step operator from the committed
-    ncu summary, if it was taken on the current kernel source."""
+    ncu summary, if it was taken on the current source of the same kernel."""
     p = os.path.join(ROOT, "profiles", "ax_fp32_cg_step_E4096_N9.md")
     if not os.path.exists(p):
         return None
@@ -210,7 +211,7 @@ def profiled_traffic(sha):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != sha:
+    if vals.get("kernel_source_sha") != sha or vals.get("kernel") != kernel:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -535,8 +536,10 @@ def main():
     sha = source_sha(AX_SOURCES)
     bytes_cg = 11 * 4 * nL
     achieved = bytes_cg / (ax["fp32"]["cg_step_ms"] * 1e-3) / 1e9
-    traffic = profiled_traffic(sha)
-    roofline = {"kernel": "k_ax_cc<float,10,*,PUPD> (fused p-update + operator, FP32)",
+    kname = ("k_ax_cc<float,%d,M,PUPD>" % n) if tune["fp32"]["variant"] in (0, 1) else \
+        ("k_ax_tma<float,%d,PUPD>" % n)
+    traffic = profiled_traffic(sha, kname)
+    roofline = {"kernel": kname + " (fused p-update + operator + pap, FP32)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": f"{peak_kind} (STREAM copy)",
                 "traffic": traffic, "algorithmic_bytes_per_launch": bytes_cg,

@@ -42,11 +42,12 @@ nb_status ax_tma_f32(int n, bool pupd, int sm_count, long long E, const float *G
 bool ax_tma_available_f32(int n, bool pupd) { return tma_fits<float>(n, pupd); }
 
 nb_status bax_f32(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
-                   const float *G, const float *u, float *w, const float *r, const float *dinv, float *p,
-                   const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s)
+                  const int32_t *list, const int *cnt, const float *G, const float *u, float *w,
+                  const float *r, const float *dinv, float *p, const int32_t *elem_prob, const BScal *bs,
+                  double *part_e, cudaStream_t s)
 {
-    return dispatch_bax<float>(n, mchoice, pupd, sm_count, E, e_first, G, u, w, r, dinv, p,
-                             elem_prob, bs, part_e, s);
+    return dispatch_bax<float>(n, mchoice, pupd, sm_count, E, e_first, list, cnt, G, u, w, r, dinv,
+                             p, elem_prob, bs, part_e, s);
 }
 
 }  // namespace nb

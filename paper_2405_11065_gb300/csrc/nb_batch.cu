@@ -8,14 +8,21 @@
 // Per-element tables give each element's problem and L offset.
 //
 // Iteration.  Table 1's loop for all problems at once: the operator (one
-// launch per order present, each over all elements of that order), the
-// per-problem alpha (one warp per problem sums its elements' partials in
-// element order), one gather-scatter over every row, the update (one block
-// per element), the per-problem beta and stopping tests, and the loop
-// condition "some problem is still running".  Problems that have stopped are
-// skipped by every kernel.  The whole iteration is one CUDA graph with a
-// while node; the FP64 refinement around it runs per problem (own scale,
-// own inner tolerance) with all problems advanced together.
+// launch per order present), the per-problem alpha (one warp per problem sums
+// its elements' partials in element order), the gather-scatter, the update
+// (one block per element), the per-problem beta and stopping tests, and the
+// loop condition "some problem is still running".  The iteration is one CUDA
+// graph with a while node, launched for K iterations at a time.
+//
+// Active lists.  Every kernel walks device lists of the elements (per order,
+// and over all orders) and of the gather-scatter row chunks of the problems
+// still running; between graph launches the host reads the problems' flags
+// and rebuilds the lists once a quarter of the listed elements belong to
+// problems that have stopped, so a batch whose stragglers run for thousands
+// of iterations pays for the stragglers only.  Problems that stopped within
+// a launch are skipped by every kernel.  The FP64 refinement around the loop
+// runs per problem (own scale, own inner tolerance) with the running problems
+// advanced together.
 #include <math.h>
 
 #include <algorithm>
@@ -27,13 +34,15 @@
 namespace nb {
 
 nb_status bax_f32(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
-                  const float *G, const float *u, float *w, const float *r, const float *dinv,
-                  float *p, const int32_t *elem_prob, const BScal *bs, double *part_e,
-                  cudaStream_t s);
+                  const int32_t *list, const int *cnt, const float *G, const float *u, float *w,
+                  const float *r, const float *dinv, float *p, const int32_t *elem_prob,
+                  const BScal *bs, double *part_e, cudaStream_t s);
 nb_status bax_f64(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
-                  const double *G, const double *u, double *w, const double *r,
-                  const double *dinv, double *p, const int32_t *elem_prob, const BScal *bs,
-                  double *part_e, cudaStream_t s);
+                  const int32_t *list, const int *cnt, const double *G, const double *u,
+                  double *w, const double *r, const double *dinv, double *p,
+                  const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s);
+
+constexpr int kRowChunk = 2048;  // gather-scatter rows per list entry
 
 struct BatchGroup {
     int n = 0;
@@ -60,6 +69,8 @@ struct nb_batch {
     int64_t nL = 0, nG = 0, E = 0, rows = 0;
     std::vector<nb::BatchGroup> groups;
     std::vector<int64_t> prob_e0_host;  // internal order, nprob + 1
+    std::vector<int64_t> prob_row0_host;  // internal order, nprob + 1: gather-scatter rows
+    std::vector<int> prob_group;        // internal order: index into groups
     float *G32 = nullptr;
     double *G64 = nullptr;
     float *dinv32 = nullptr;
@@ -72,11 +83,21 @@ struct nb_batch {
     nb::BScal *bs = nullptr;       // [nprob]
     nb::BScal *bs_host = nullptr;  // pinned
     int *loops = nullptr;          // graph loop counter
+    int *loops_host = nullptr;     // pinned mirror
     double *part_e = nullptr;      // [2 E]
     double *red = nullptr;         // [4 nprob]: |r|^2, |b|^2, tau, active
     double *red_host = nullptr;    // pinned
     double *r64 = nullptr, *w64 = nullptr;
     nb::BatchWs ws32, ws64;
+    // active lists (device, one allocation; pinned mirror): counts
+    // [groups: elements per order, all elements, row chunks], then per order
+    // the element list in the order's slot [e0, e1), the list over all
+    // orders, and the row chunks (first row, end row, problem, 0)
+    int *act = nullptr;
+    int *act_host = nullptr;
+    int64_t act_words = 0, act_e_off = 0, act_all_off = 0, act_ch_off = 0, max_chunks = 0;
+    std::vector<char> act_run;  // problems the lists currently hold
+    int64_t act_elems = 0;
 };
 
 namespace nb {
@@ -97,14 +118,21 @@ __device__ __forceinline__ double warp_range_sum(const double *a, int64_t lo, in
     return v;
 }
 
+// Element lists: batch element indices with their count on the device; a
+// null list stands for every element.
+__device__ __forceinline__ int64_t list_len(const int *cnt, int64_t E)
+{
+    return cnt ? (int64_t)*cnt : E;
+}
+__device__ __forceinline__ int64_t list_at(const int32_t *list, int64_t i)
+{
+    return list ? (int64_t)list[i] : i;
+}
+
 __global__ void k_bsetup(int nprob, BScal *bs, double tol, int maxit, const double *red,
-                         int use_red, int *loops)
+                         int use_red)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) {
-        loops[0] = 0;      // loop bodies executed
-        loops[1] = maxit;  // hard cap on them (+1)
-    }
     if (p >= nprob) return;
     BScal b = {};
     b.tol = use_red ? red[2 * nprob + p] : tol;
@@ -113,13 +141,23 @@ __global__ void k_bsetup(int nprob, BScal *bs, double tol, int maxit, const doub
     bs[p] = b;
 }
 
-// p = 0 and owner-copy partials of (r, dinv r), (r, r) per element.
+// Bodies of one graph launch: loops[0] counts them, loops[1] + 1 is the cap.
+__global__ void k_bchunk(int *loops, int cap)
+{
+    loops[0] = 0;
+    loops[1] = cap;
+}
+
+// p = 0 and owner-copy partials of (r, dinv r), (r, r) per listed element.
 template <typename T>
-__global__ void k_binit(int64_t E, const int64_t *__restrict__ el0, const T *__restrict__ r,
+__global__ void k_binit(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+                        const int64_t *__restrict__ el0, const T *__restrict__ r,
                         const T *__restrict__ dinv, T *__restrict__ p, double *__restrict__ part)
 {
     __shared__ double sred[32];
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const int64_t e = list_at(list, i);
         DotAcc<T> a, b;
         for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
             const T rl = r[l], d = dinv[l];
@@ -188,15 +226,41 @@ __global__ void k_bfin_alpha(int nprob, const int64_t *__restrict__ pe0, const d
     }
 }
 
+// Masked direct-stiffness summation over the listed row chunks, copies
+// summed in ascending local order (as k_gs); chunks of problems that have
+// stopped are skipped when bs is given.
 template <typename T>
-__global__ void k_bupdate(int64_t E, const int64_t *__restrict__ el0,
+__global__ void k_bgs(const int4 *__restrict__ ch, const int *__restrict__ cnt,
+                      const int32_t *__restrict__ off, const int32_t *__restrict__ loc,
+                      const uint8_t *__restrict__ rmask, const BScal *__restrict__ bs,
+                      T *__restrict__ u)
+{
+    const int nc = *cnt;
+    for (int c = blockIdx.x; c < nc; c += gridDim.x) {
+        const int4 q = ch[c];
+        if (bs && bs[q.z].done) continue;  // uniform over the block
+        for (int a = q.x + threadIdx.x; a < q.y; a += blockDim.x) {
+            const int o0 = off[a], o1 = off[a + 1];
+            T s = T(0);
+            for (int o = o0; o < o1; ++o) s += u[loc[o]];
+            if (rmask[a] == 0) s = T(0);
+            for (int o = o0; o < o1; ++o) u[loc[o]] = s;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_bupdate(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+                          const int64_t *__restrict__ el0,
                           const int32_t *__restrict__ eprob, const BScal *__restrict__ bs,
                           T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                           const T *__restrict__ w, const T *__restrict__ dinv,
                           double *__restrict__ part)
 {
     __shared__ double sred[32];
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const int64_t e = list_at(list, i);
         const BScal &b = bs[eprob[e]];
         if (b.done) continue;  // uniform over the block
         const T alpha = (T)b.alpha;
@@ -262,13 +326,17 @@ __global__ void k_bcond(int nprob, const BScal *bs, int *loops, cudaGraphConditi
     }
 }
 
-// r = b - w (w may be NULL) and owner-copy partials of (r, r) and (b, b).
-__global__ void k_bresid(int64_t E, const int64_t *__restrict__ el0, const double *__restrict__ b,
+// r = b - w (w may be NULL) and owner-copy partials of (r, r) and (b, b)
+// per listed element.
+__global__ void k_bresid(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+                         const int64_t *__restrict__ el0, const double *__restrict__ b,
                          const double *__restrict__ w, const double *__restrict__ dinv,
                          double *__restrict__ r, double *__restrict__ part)
 {
     __shared__ double sred[32];
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const int64_t e = list_at(list, i);
         double a = 0.0, c = 0.0;
         for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
             const double bl = b[l];
@@ -303,12 +371,15 @@ __global__ void k_bsum2(int nprob, const int64_t *__restrict__ pe0, const double
 
 // Inner right-hand side per problem: r32 = r64 / |r64| for running problems
 // (zero otherwise), x32 = 0.  red[3 nprob + p] = 1 marks a running problem.
-__global__ void k_bdemote(int64_t E, const int64_t *__restrict__ el0,
+__global__ void k_bdemote(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+                          const int64_t *__restrict__ el0,
                           const int32_t *__restrict__ eprob, int nprob, const double *red,
                           const double *__restrict__ r64, float *__restrict__ r32,
                           float *__restrict__ x32)
 {
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const int64_t e = list_at(list, i);
         const int p = eprob[e];
         const bool act = red[3 * nprob + p] != 0.0;
         const double inv = act ? 1.0 / sqrt(red[p]) : 0.0;
@@ -319,11 +390,14 @@ __global__ void k_bdemote(int64_t E, const int64_t *__restrict__ el0,
     }
 }
 
-__global__ void k_bpromote(int64_t E, const int64_t *__restrict__ el0,
+__global__ void k_bpromote(int64_t E, const int32_t *__restrict__ list,
+                           const int *__restrict__ cnt, const int64_t *__restrict__ el0,
                            const int32_t *__restrict__ eprob, int nprob, const double *red,
                            const float *__restrict__ x32, double *__restrict__ x)
 {
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+        const int64_t e = list_at(list, i);
         const int p = eprob[e];
         if (red[3 * nprob + p] == 0.0) continue;
         const double s = sqrt(red[p]);
@@ -345,28 +419,77 @@ __global__ void k_bcopy(int64_t n, const double *__restrict__ a, double *__restr
 
 static int elem_grid(const nb_batch *B) { return (int)std::min<int64_t>(B->E, B->ctx->sm_count * 16); }
 static int warp_grid(int nprob) { return (nprob * 32 + 255) / 256; }
+static int chunk_grid(const nb_batch *B)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(B->max_chunks, B->ctx->sm_count * 8));
+}
+
+// device views of the active lists
+static const int *cnt_group(const nb_batch *B, int g) { return B->act + g; }
+static const int32_t *list_group(const nb_batch *B, int g)
+{
+    return B->act + B->act_e_off + B->groups[g].e0;
+}
+static const int *cnt_all(const nb_batch *B) { return B->act + B->groups.size(); }
+static const int32_t *list_all(const nb_batch *B) { return B->act + B->act_all_off; }
+static const int *cnt_chunks(const nb_batch *B) { return B->act + B->groups.size() + 1; }
+static const int4 *list_chunks(const nb_batch *B)
+{
+    return reinterpret_cast<const int4 *>(B->act + B->act_ch_off);
+}
+
+// Make the lists hold the elements and row chunks of the problems marked in
+// run (internal order).  One host-to-device copy; nothing is done if the
+// lists already hold that set.
+static nb_status set_active(nb_batch *B, const std::vector<char> &run, cudaStream_t s)
+{
+    if (run == B->act_run) return NB_OK;
+    NB_CUDA(cudaStreamSynchronize(s));  // the pinned mirror of the last upload is free again
+    int *h = B->act_host;
+    const int ng = (int)B->groups.size();
+    int32_t *le = h + B->act_e_off, *la = h + B->act_all_off;
+    int4 *ch = reinterpret_cast<int4 *>(h + B->act_ch_off);
+    std::fill(h, h + ng + 2, 0);
+    int nall = 0, nch = 0;
+    for (int q = 0; q < B->nprob; ++q) {
+        if (!run[q]) continue;
+        const int g = B->prob_group[q];
+        for (int64_t e = B->prob_e0_host[q]; e < B->prob_e0_host[q + 1]; ++e) {
+            le[B->groups[g].e0 + h[g]++] = (int32_t)e;
+            la[nall++] = (int32_t)e;
+        }
+        const int64_t r1 = B->prob_row0_host[q + 1];
+        for (int64_t r = B->prob_row0_host[q]; r < r1; r += kRowChunk)
+            ch[nch++] = make_int4((int)r, (int)std::min<int64_t>(r + kRowChunk, r1), q, 0);
+    }
+    h[ng] = nall;
+    h[ng + 1] = nch;
+    NB_CUDA(cudaMemcpyAsync(B->act, h, sizeof(int) * B->act_words, cudaMemcpyHostToDevice, s));
+    B->act_run = run;
+    B->act_elems = nall;
+    return NB_OK;
+}
 
 template <typename T>
 static nb_status bax_all(nb_batch *B, bool pupd, const T *u, T *w, const T *r, const T *dinv,
                          T *p, double *part, cudaStream_t s)
 {
-    for (const BatchGroup &g : B->groups) {
+    for (int gi = 0; gi < (int)B->groups.size(); ++gi) {
+        const BatchGroup &g = B->groups[gi];
         const int64_t E = g.e1 - g.e0;
-        const int64_t n3 = (int64_t)g.n * g.n * g.n;
         const size_t lo = (size_t)g.l0, go = (size_t)g.l0 * 6;
         auto off = [&](const T *v) { return v ? v + lo : nullptr; };
         if (sizeof(T) == 4)
-            NB_TRY(bax_f32(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0,
-                           (const float *)B->G32 + go, (const float *)off(u),
+            NB_TRY(bax_f32(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
+                           cnt_group(B, gi), (const float *)B->G32 + go, (const float *)off(u),
                            (float *)(w + lo), (const float *)off(r), (const float *)off(dinv),
                            p ? (float *)(p + lo) : nullptr, B->elem_prob, B->bs, part, s));
         else
-            NB_TRY(bax_f64(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0,
-                           (const double *)B->G64 + go, (const double *)off(u),
+            NB_TRY(bax_f64(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
+                           cnt_group(B, gi), (const double *)B->G64 + go, (const double *)off(u),
                            (double *)(w + lo), (const double *)off(r),
                            (const double *)off(dinv), p ? (double *)(p + lo) : nullptr,
                            B->elem_prob, B->bs, part, s));
-        (void)n3;
     }
     return NB_OK;
 }
@@ -375,14 +498,15 @@ template <typename T>
 static nb_status batch_body(nb_batch *B, BatchWs &ws, const T *dinv, int use_cond,
                             cudaGraphConditionalHandle h, cudaStream_t s)
 {
-    const nb_prec prec = sizeof(T) == 4 ? NB_FP32 : NB_FP64;
     NB_TRY(bax_all<T>(B, true, nullptr, (T *)ws.w, (const T *)ws.r, dinv, (T *)ws.p, B->part_e, s));
     k_bfin_alpha<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->bs);
     NB_CUDA(cudaGetLastError());
-    NB_TRY(gs_rows_launch(B->ctx, B->rows, B->gs_off, B->gs_loc, B->gs_mask, prec, ws.w, 1, s));
-    k_bupdate<T><<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, B->bs, (T *)ws.x,
-                                              (T *)ws.r, (const T *)ws.p, (const T *)ws.w, dinv,
-                                              B->part_e);
+    k_bgs<T><<<chunk_grid(B), 256, 0, s>>>(list_chunks(B), cnt_chunks(B), B->gs_off, B->gs_loc,
+                                           B->gs_mask, B->bs, (T *)ws.w);
+    NB_CUDA(cudaGetLastError());
+    k_bupdate<T><<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+                                              B->elem_prob, B->bs, (T *)ws.x, (T *)ws.r,
+                                              (const T *)ws.p, (const T *)ws.w, dinv, B->part_e);
     NB_CUDA(cudaGetLastError());
     k_bfin_iter<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs);
     NB_CUDA(cudaGetLastError());
@@ -406,77 +530,103 @@ static nb_status ensure_bws(nb_batch *B, BatchWs &ws, size_t elt)
     return NB_OK;
 }
 
-// Run the batched PCG on ws (r holds the residuals of the current x) until
-// every problem has stopped.  Tolerances from red (per problem) if use_red;
-// relative to |r0| if bnorm_from_r, else to bnorm2[p].
+// Run the batched PCG on ws (r holds the residuals of the current x) for the
+// problems in the active lists until every one has stopped.  Tolerances from
+// red (per problem) if use_red; relative to |r0| if bnorm_from_r, else to
+// bnorm2[p].  The loop runs up to K iterations per graph launch (K doubling
+// up to 512 while no list is rebuilt); the kernels launched are added to
+// *launches.
 template <typename T>
 static nb_status batch_cg(nb_batch *B, BatchWs &ws, const T *dinv, double tol, int maxit,
                           int use_red, int use_graph, int bnorm_from_r, const double *bnorm2,
-                          cudaStream_t s)
+                          cudaStream_t s, int64_t *launches)
 {
-    k_bsetup<<<(B->nprob + 255) / 256, 256, 0, s>>>(B->nprob, B->bs, tol, maxit, B->red, use_red,
-                                                    B->loops);
+    const int64_t per_body = (int64_t)B->groups.size() + 4 + (use_graph ? 1 : 0);
+    *launches += 3;
+    k_bsetup<<<(B->nprob + 255) / 256, 256, 0, s>>>(B->nprob, B->bs, tol, maxit, B->red, use_red);
     NB_CUDA(cudaGetLastError());
-    k_binit<T><<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, (const T *)ws.r, dinv, (T *)ws.p,
-                                            B->part_e);
+    k_binit<T><<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+                                            (const T *)ws.r, dinv, (T *)ws.p, B->part_e);
     NB_CUDA(cudaGetLastError());
     k_bfin_init<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs,
                                                     bnorm_from_r, bnorm2);
     NB_CUDA(cudaGetLastError());
-    if (use_graph) {
-        if (!ws.exec) {
-            cudaGraph_t g;
-            NB_CUDA(cudaGraphCreate(&g, 0));
-            cudaGraphConditionalHandle h;
-            NB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = h;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t node;
-            NB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                                  cudaStreamCaptureModeRelaxed));
-            nb_status st = batch_body<T>(B, ws, dinv, 1, h, s);
-            cudaGraph_t captured = nullptr;
-            cudaError_t ce = cudaStreamEndCapture(s, &captured);
-            if (st != NB_OK || ce != cudaSuccess) {
-                cudaGraphDestroy(g);
-                if (st != NB_OK) return st;
-                set_error("batch graph capture failed: %s", cudaGetErrorString(ce));
-                return NB_ERR_CUDA;
-            }
-            NB_CUDA(cudaGraphInstantiate(&ws.exec, g, 0));
-            ws.graph = g;
+    if (use_graph && !ws.exec) {
+        cudaGraph_t g;
+        NB_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        NB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        NB_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed));
+        nb_status st = batch_body<T>(B, ws, dinv, 1, h, s);
+        cudaGraph_t captured = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &captured);
+        if (st != NB_OK || ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            if (st != NB_OK) return st;
+            set_error("batch graph capture failed: %s", cudaGetErrorString(ce));
+            return NB_ERR_CUDA;
         }
-        NB_CUDA(cudaGraphLaunch(ws.exec, s));
-        return NB_OK;
+        NB_CUDA(cudaGraphInstantiate(&ws.exec, g, 0));
+        ws.graph = g;
     }
-    for (int it = 0; it <= maxit; it += 16) {
-        for (int t = 0; t < 16; ++t) NB_TRY(batch_body<T>(B, ws, dinv, 0, 0, s));
+    std::vector<char> run(B->nprob);
+    int K = 32;
+    int64_t done_bodies = 0;
+    for (;;) {
+        if (use_graph) {
+            k_bchunk<<<1, 1, 0, s>>>(B->loops, K - 1);  // the first body runs unconditionally
+            NB_CUDA(cudaGetLastError());
+            NB_CUDA(cudaGraphLaunch(ws.exec, s));
+            NB_CUDA(cudaMemcpyAsync(B->loops_host, B->loops, sizeof(int), cudaMemcpyDeviceToHost,
+                                    s));
+        } else {
+            for (int t = 0; t < K; ++t) NB_TRY(batch_body<T>(B, ws, dinv, 0, 0, s));
+        }
         NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * B->nprob,
                                 cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
-        bool any = false;
-        for (int p = 0; p < B->nprob; ++p) any |= B->bs_host[p].done == 0;
-        if (!any) break;
+        const int ran = use_graph ? B->loops_host[0] : K;
+        done_bodies += ran;
+        *launches += (use_graph ? 1 : 0) + ran * per_body;
+        int64_t live = 0;
+        for (int q = 0; q < B->nprob; ++q) {
+            run[q] = B->bs_host[q].done == 0 && B->act_run[q];
+            if (run[q]) live += B->prob_e0_host[q + 1] - B->prob_e0_host[q];
+        }
+        if (live == 0 || done_bodies > (int64_t)maxit) break;
+        if (4 * live < 3 * B->act_elems) {
+            NB_TRY(set_active(B, run, s));
+            K = 32;
+        } else {
+            K = std::min(2 * K, 512);
+        }
     }
     return NB_OK;
 }
 
-// |b - A x|^2 and |b|^2 per problem into red[0..2 nprob); x may be NULL (x = 0).
+// |b - A x|^2 and |b|^2 per listed problem into red[0..2 nprob); x may be
+// NULL (x = 0).
 static nb_status batch_residual(nb_batch *B, const double *b, const double *x, cudaStream_t s)
 {
     const double *w = nullptr;
     if (x) {
         NB_TRY(bax_all<double>(B, false, x, B->w64, nullptr, nullptr, nullptr, nullptr, s));
-        NB_TRY(gs_rows_launch(B->ctx, B->rows, B->gs_off, B->gs_loc, B->gs_mask, NB_FP64, B->w64,
-                              1, s));
+        k_bgs<double><<<chunk_grid(B), 256, 0, s>>>(list_chunks(B), cnt_chunks(B), B->gs_off,
+                                                    B->gs_loc, B->gs_mask, nullptr, B->w64);
+        NB_CUDA(cudaGetLastError());
         w = B->w64;
     }
-    k_bresid<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, b, w, B->dinv64, B->r64, B->part_e);
+    k_bresid<<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0, b, w,
+                                          B->dinv64, B->r64, B->part_e);
     NB_CUDA(cudaGetLastError());
     k_bsum2<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->red);
     NB_CUDA(cudaGetLastError());
@@ -508,10 +658,12 @@ extern "C" nb_status nb_batch_destroy(nb_batch *B)
     free_bws(B->ws64);
     void *bufs[] = {B->G32, B->G64, B->dinv32, B->dinv64, B->gs_off, B->gs_loc, B->gs_mask,
                     B->elem_prob, B->elem_l0, B->prob_e0, B->bs, B->loops, B->part_e, B->red,
-                    B->r64, B->w64};
+                    B->r64, B->w64, B->act};
     for (void *b : bufs) cudaFree(b);
     if (B->bs_host) cudaFreeHost(B->bs_host);
     if (B->red_host) cudaFreeHost(B->red_host);
+    if (B->act_host) cudaFreeHost(B->act_host);
+    if (B->loops_host) cudaFreeHost(B->loops_host);
     delete B;
     return NB_OK;
 }
@@ -568,6 +720,7 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
             g.l0 = lacc;
             B->groups.push_back(g);
         }
+        B->prob_group.push_back((int)B->groups.size() - 1);
         for (int64_t e = 0; e < m->E; ++e) {
             eprob.push_back(q);
             el0.push_back(el0.back() + m->n3);
@@ -586,6 +739,7 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     // gather-scatter rows with batch local indices
     std::vector<int32_t> off(1, 0), loc;
     std::vector<uint8_t> rmask;
+    B->prob_row0_host.assign(1, 0);
     for (int q = 0; q < nprob && st == NB_OK; ++q) {
         nb_mesh *m = B->meshes[B->order[q]];
         std::vector<int32_t> o(m->gs_rows + 1), l(std::max<int64_t>(m->gs_copies, 1));
@@ -598,6 +752,8 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
             rmask.push_back(mk[a]);
         }
         for (int64_t c = 0; c < m->gs_copies; ++c) loc.push_back(base + l[c]);
+        B->prob_row0_host.push_back((int64_t)rmask.size());
+        B->max_chunks += (m->gs_rows + kRowChunk - 1) / kRowChunk;
     }
     if (st != NB_OK) {
         nb_batch_destroy(B);
@@ -630,9 +786,20 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     NB_BCUDA(cudaMalloc(&B->bs, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMallocHost(&B->bs_host, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMalloc(&B->loops, 2 * sizeof(int)));
+    NB_BCUDA(cudaMallocHost(&B->loops_host, 2 * sizeof(int)));
     NB_BCUDA(cudaMalloc(&B->part_e, sizeof(double) * 2 * B->E));
     NB_BCUDA(cudaMalloc(&B->red, sizeof(double) * 4 * nprob));
     NB_BCUDA(cudaMallocHost(&B->red_host, sizeof(double) * 4 * nprob));
+    {
+        const int64_t nc = ((int64_t)B->groups.size() + 2 + 3) / 4 * 4;
+        B->act_e_off = nc;
+        B->act_all_off = nc + B->E;
+        B->act_ch_off = (nc + 2 * B->E + 3) / 4 * 4;  // int4 chunks on a 16-byte boundary
+        B->act_words = B->act_ch_off + 4 * std::max<int64_t>(B->max_chunks, 1);
+        NB_BCUDA(cudaMalloc(&B->act, sizeof(int) * B->act_words));
+        NB_BCUDA(cudaMallocHost(&B->act_host, sizeof(int) * B->act_words));
+        NB_BCUDA(cudaMemset(B->act, 0, sizeof(int) * B->act_words));
+    }
     NB_BCUDA(cudaMalloc(&B->r64, sizeof(double) * B->nL));
     NB_BCUDA(cudaMalloc(&B->w64, sizeof(double) * B->nL));
     NB_BCUDA(cudaMemset(B->w64, 0, sizeof(double) * B->nL));
@@ -727,8 +894,8 @@ extern "C" nb_status nb_batch_autotune(nb_batch *B, int reps, void *flush, size_
                 if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
                 cudaEventRecord(e0, s);
                 const size_t lo = (size_t)g.l0;
-                NB_TRY(bax_f32(g.n, v, false, B->ctx->sm_count, g.e1 - g.e0, g.e0,
-                               B->G32 + 6 * lo, (const float *)B->ws32.p + lo,
+                NB_TRY(bax_f32(g.n, v, false, B->ctx->sm_count, g.e1 - g.e0, g.e0, nullptr,
+                               nullptr, B->G32 + 6 * lo, (const float *)B->ws32.p + lo,
                                (float *)B->ws32.w + lo, nullptr, nullptr, nullptr, B->elem_prob,
                                B->bs, nullptr, s));
                 cudaEventRecord(e1, s);
@@ -786,22 +953,30 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
     int batched_iters = 0, outer = 0;
     int64_t launches = 0;
     const int ngroups = (int)B->groups.size();
+    const std::vector<char> all(np, 1);
     if (o->prec == NB_FP64) {
         // plain FP64 PCG of every problem, in place on x
         NB_TRY(ensure_bws(B, B->ws64, sizeof(double)));
+        NB_TRY(set_active(B, all, s));
         NB_TRY(batch_residual(B, b, o->use_x0 ? x : nullptr, s));
-        if (o->use_x0)
+        launches += 2 + (o->use_x0 ? ngroups + 1 : 0);
+        if (o->use_x0) {
             k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, x, (double *)B->ws64.x);
-        else
+            ++launches;
+        } else {
             NB_CUDA(cudaMemsetAsync(B->ws64.x, 0, sizeof(double) * B->nL, s));
+        }
         k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, B->r64, (double *)B->ws64.r);
         NB_CUDA(cudaGetLastError());
+        ++launches;
         // tolerance relative to |b| (red[nprob + p] from the residual pass)
         NB_TRY(batch_cg<double>(B, B->ws64, B->dinv64, o->rtol, o->maxiter, 0, o->use_graph, 0,
-                                B->red + np, s));
+                                B->red + np, s, &launches));
         NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * np, cudaMemcpyDeviceToHost, s));
         k_bcopy<<<B->ctx->sm_count * 4, 256, 0, s>>>(B->nL, (double *)B->ws64.x, x);
+        NB_TRY(set_active(B, all, s));  // the final residual of every problem
         NB_TRY(batch_residual(B, b, x, s));
+        launches += 1 + ngroups + 3;
         NB_CUDA(cudaMemcpyAsync(B->red_host, B->red, sizeof(double) * 2 * np,
                                 cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
@@ -814,7 +989,6 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
             status[p] = B->bs_host[q].status;
             if (status[p] == 0 && !(rel[p] < o->rtol * 1.5)) status[p] = NB_NOT_CONVERGED;
         }
-        launches += 4 + 2 + (int64_t)batched_iters * (ngroups + 5) + 3;
     } else {
         NB_TRY(ensure_bws(B, B->ws32, sizeof(float)));
         if (!o->use_x0) NB_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * B->nL, s));
@@ -822,7 +996,10 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
         std::vector<int> stagn(np, 0);
         std::vector<char> running(np, 1);
         int used = 0;
+        std::vector<char> run_q(np, 1);  // running problems, internal order
         for (outer = 0; outer <= o->max_outer; ++outer) {
+            for (int q = 0; q < np; ++q) run_q[q] = running[B->order[q]];
+            NB_TRY(set_active(B, run_q, s));
             NB_TRY(batch_residual(B, b, (outer == 0 && !o->use_x0) ? nullptr : x, s));
             NB_CUDA(cudaMemcpyAsync(B->red_host, B->red, sizeof(double) * 2 * np,
                                     cudaMemcpyDeviceToHost, s));
@@ -865,15 +1042,19 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
                 any |= !stop;
             }
             if (!any) break;
+            for (int q = 0; q < np; ++q) run_q[q] = running[B->order[q]];
+            NB_TRY(set_active(B, run_q, s));
             NB_CUDA(cudaMemcpyAsync(B->red + 2 * np, B->red_host + 2 * np, sizeof(double) * 2 * np,
                                     cudaMemcpyHostToDevice, s));
-            k_bdemote<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, np, B->red,
-                                                    B->r64, (float *)B->ws32.r,
-                                                    (float *)B->ws32.x);
+            k_bdemote<<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+                                                    B->elem_prob, np, B->red, B->r64,
+                                                    (float *)B->ws32.r, (float *)B->ws32.x);
             NB_CUDA(cudaGetLastError());
             NB_TRY(batch_cg<float>(B, B->ws32, B->dinv32, 0.0, o->maxiter - used, 1, o->use_graph,
-                                   1, nullptr, s));
-            k_bpromote<<<elem_grid(B), 256, 0, s>>>(B->E, B->elem_l0, B->elem_prob, np, B->red,
+                                   1, nullptr, s, &launches));
+            NB_TRY(set_active(B, run_q, s));  // every problem of this step is promoted
+            k_bpromote<<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+                                                     B->elem_prob, np, B->red,
                                                      (const float *)B->ws32.x, x);
             NB_CUDA(cudaGetLastError());
             NB_CUDA(cudaMemcpyAsync(B->bs_host, B->bs, sizeof(BScal) * np, cudaMemcpyDeviceToHost, s));
@@ -885,7 +1066,7 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
             }
             used += most;
             batched_iters += most;
-            launches += 5 + (int64_t)std::max(most, 1) * (ngroups + 5);
+            launches += 2;  // demote and promote
         }
     }
     NB_CUDA(cudaEventRecord(t1, s));

@@ -1,9 +1,10 @@
 // Operator for a batch of independent problems: one launch per polynomial
-// order present in the batch, over all elements of that order (elements of
-// equal order are contiguous in the batch layout).  Same arithmetic and
-// thread mapping as k_ax_cc; in addition each element looks up its problem,
-// takes that problem's beta, skips problems that have converged, and writes
-// its own partial sum p.(A_L p) so that the per-problem dot products can be
+// order present in the batch, over the listed elements of that order (the
+// elements of the problems still running; all of the order's elements when
+// no list is given).  Same arithmetic and thread mapping as k_ax_cc; in
+// addition each element looks up its problem, takes that problem's beta,
+// skips problems that have converged (no loads, no stores), and writes its
+// own partial sum p.(A_L p) so that the per-problem dot products can be
 // formed in a fixed order.  Included by the FP32 and FP64 operator units,
 // whose constant derivative tables it reads.
 #pragma once
@@ -14,7 +15,8 @@ namespace nb {
 
 template <typename T, int n, int M, bool PUPD>
 __global__ void __launch_bounds__(M * n * n)
-k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restrict__ uin,
+k_bax(long long E, long long e_first, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+      const T *__restrict__ G, const T *__restrict__ uin,
       T *__restrict__ w, const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
       const int32_t *__restrict__ elem_prob, const BScal *__restrict__ bs,
       double *__restrict__ part_e)
@@ -41,11 +43,15 @@ k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restri
     T *swre = swr + el * n2;
     T *swse = sws + el * n2;
 
-    for (long long e0 = (long long)blockIdx.x * M; e0 < E; e0 += (long long)gridDim.x * M) {
-        const long long e = e0 + el;
-        const bool valid = e < E;
+    // list entries are batch element indices; e is the index within the order
+    const long long ne = list ? (long long)*cnt : E;
+    for (long long i0 = (long long)blockIdx.x * M; i0 < ne; i0 += (long long)gridDim.x * M) {
+        const long long idx = i0 + el;
+        const bool valid = idx < ne && el < M;
+        const long long e = valid ? (list ? (long long)list[idx] - e_first : idx) : 0;
         const int prob = valid ? elem_prob[e_first + e] : 0;
         const bool live = valid && !(PUPD && bs[prob].done);
+        if (!__syncthreads_or(live)) continue;  // block-uniform
         const T beta = (PUPD && live) ? (T)bs[prob].beta : T(0);
         const size_t base = (size_t)e * n3 + ij;
         T ru[n], rw[n];
@@ -65,11 +71,18 @@ k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restri
             sue[k * n2 + ij] = v;
         }
         __syncthreads();
-        const T *Ge = G + (size_t)(valid ? e : 0) * 6 * n3 + ij;
+        const T *Ge = G + (size_t)e * 6 * n3 + ij;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
-            const T g0 = Ge[0 * n3 + k * n2], g1 = Ge[1 * n3 + k * n2], g2 = Ge[2 * n3 + k * n2];
-            const T g3 = Ge[3 * n3 + k * n2], g4 = Ge[4 * n3 + k * n2], g5 = Ge[5 * n3 + k * n2];
+            T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
+            if (live) {
+                g0 = Ge[0 * n3 + k * n2];
+                g1 = Ge[1 * n3 + k * n2];
+                g2 = Ge[2 * n3 + k * n2];
+                g3 = Ge[3 * n3 + k * n2];
+                g4 = Ge[4 * n3 + k * n2];
+                g5 = Ge[5 * n3 + k * n2];
+            }
             T ur = T(0), us = T(0), ut = T(0);
 #pragma unroll
             for (int l = 0; l < n; ++l) {
@@ -105,7 +118,7 @@ k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restri
         if (part_e) {
             sdot[el * n2 + ij] = s;
             __syncthreads();
-            if (ij == 0 && valid) {  // the element's partial, summed in a fixed order
+            if (ij == 0 && live) {  // the element's partial, summed in a fixed order
                 double t = 0.0;
                 for (int q = 0; q < n2; ++q) t += (double)sdot[el * n2 + q];
                 part_e[e_first + e] = t;
@@ -115,9 +128,9 @@ k_bax(long long E, long long e_first, const T *__restrict__ G, const T *__restri
 }
 
 template <typename T, int n, int M, bool PUPD>
-nb_status launch_bax(int sm_count, long long E, long long e_first, const T *G, const T *u, T *w,
-                     const T *r, const T *dinv, T *p, const int32_t *elem_prob, const BScal *bs,
-                     double *part_e, cudaStream_t s)
+nb_status launch_bax(int sm_count, long long E, long long e_first, const int32_t *list,
+                     const int *cnt, const T *G, const T *u, T *w, const T *r, const T *dinv, T *p,
+                     const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s)
 {
     auto kern = k_bax<T, n, M, PUPD>;
     constexpr size_t smem = sizeof(T) * (size_t)M * (n * n * n + 3 * n * n);
@@ -136,27 +149,26 @@ nb_status launch_bax(int sm_count, long long E, long long e_first, const T *G, c
     if (E <= 0) return NB_OK;
     const long long need = (E + M - 1) / M;
     const int grid = (int)(need < grid_cache ? need : grid_cache);
-    kern<<<grid, threads, smem, s>>>(E, e_first, G, u, w, r, dinv, p, elem_prob, bs, part_e);
+    kern<<<grid, threads, smem, s>>>(E, e_first, list, cnt, G, u, w, r, dinv, p, elem_prob, bs,
+                                     part_e);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
 
 template <typename T>
 nb_status dispatch_bax(int n, int mchoice, bool pupd, int sm_count, long long E, long long e_first,
-                       const T *G, const T *u, T *w, const T *r, const T *dinv, T *p,
-                       const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s)
+                       const int32_t *list, const int *cnt, const T *G, const T *u, T *w,
+                       const T *r, const T *dinv, T *p, const int32_t *elem_prob, const BScal *bs,
+                       double *part_e, cudaStream_t s)
 {
-#define NB_BAX_CASE(NN, M0, M1)                                                                 \
-    case NN:                                                                                    \
-        if (pupd)                                                                               \
-            return mchoice ? launch_bax<T, NN, M1, true>(sm_count, E, e_first, G, u, w, r, dinv, \
-                                                         p, elem_prob, bs, part_e, s)           \
-                           : launch_bax<T, NN, M0, true>(sm_count, E, e_first, G, u, w, r, dinv, \
-                                                         p, elem_prob, bs, part_e, s);          \
-        return mchoice ? launch_bax<T, NN, M1, false>(sm_count, E, e_first, G, u, w, r, dinv, p, \
-                                                      elem_prob, bs, part_e, s)                 \
-                       : launch_bax<T, NN, M0, false>(sm_count, E, e_first, G, u, w, r, dinv, p, \
-                                                      elem_prob, bs, part_e, s);
+#define NB_BAX_ARGS sm_count, E, e_first, list, cnt, G, u, w, r, dinv, p, elem_prob, bs, part_e, s
+#define NB_BAX_CASE(NN, M0, M1)                                                     \
+    case NN:                                                                        \
+        if (pupd)                                                                   \
+            return mchoice ? launch_bax<T, NN, M1, true>(NB_BAX_ARGS)               \
+                           : launch_bax<T, NN, M0, true>(NB_BAX_ARGS);              \
+        return mchoice ? launch_bax<T, NN, M1, false>(NB_BAX_ARGS)                  \
+                       : launch_bax<T, NN, M0, false>(NB_BAX_ARGS);
     switch (n) {
         NB_BAX_CASE(2, 16, 32)
         NB_BAX_CASE(3, 8, 16)
@@ -178,6 +190,7 @@ nb_status dispatch_bax(int n, int mchoice, bool pupd, int sm_count, long long E,
             return NB_ERR_ARG;
     }
 #undef NB_BAX_CASE
+#undef NB_BAX_ARGS
 }
 
 }  // namespace nb
