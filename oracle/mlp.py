@@ -4,11 +4,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 The network maps an element's residual, divided by its Euclidean norm, to a
 correction of the same length d = (N+1)^3, which the preconditioner scales
-back by that norm:
+back by that norm.  One hidden layer of width h whose output layer reuses the
+input layer's weights (tied weights), with per-unit output gains a:
 
-    Z = X W1 + b1,  H = gelu(Z),  Y = H W2 + b2
+    Z = X W,  H = gelu(Z),  Y = (H * a) W^T          (W: d x h, a: h)
 
 with the tanh form of GELU, gelu(z) = z/2 (1 + tanh(sqrt(2/pi)(z + 0.044715 z^3))).
+Each row is y(x) = W (a * gelu(W^T x)), the gradient of the scalar potential
+sum_j a_j G(w_j . x) with G' = gelu, so its Jacobian W diag(a gelu'(W^T x)) W^T
+is symmetric at every input and y(0) = 0.  A preconditioner built from it is
+therefore symmetric to first order, which the short-recurrence flexible CG
+needs (an untied network with the same training error lost that property
+and converged more slowly than plain Jacobi).
 Training minimises the mean squared error L = sum((Y - T)^2) / (B d) over a
 batch of B pairs with Adam (Kingma and Ba, 2015).  The backward pass below is
 the chain rule written out; it is pinned against central finite differences
@@ -35,20 +42,15 @@ def gelu_grad(z):
 
 
 def init_params(d: int, h: int, seed: int):
-    """Deterministic initialisation (uniform, scaled by 1/sqrt(fan-in))."""
+    """Deterministic initialisation: W uniform(-1, 1)/sqrt(d), gains a = 1."""
     rng = np.random.default_rng(seed)
-    return {
-        "W1": rng.uniform(-1, 1, (d, h)) / math.sqrt(d),
-        "b1": np.zeros(h),
-        "W2": rng.uniform(-1, 1, (h, d)) / math.sqrt(h),
-        "b2": np.zeros(d),
-    }
+    return {"W": rng.uniform(-1, 1, (d, h)) / math.sqrt(d), "a": np.ones(h)}
 
 
 def forward(params, X):
-    Z = X @ params["W1"] + params["b1"]
+    Z = X @ params["W"]
     H = gelu(Z)
-    Y = H @ params["W2"] + params["b2"]
+    Y = (H * params["a"]) @ params["W"].T
     return Y, (X, Z, H)
 
 
@@ -58,16 +60,15 @@ def loss(params, X, T):
 
 
 def backward(params, X, T):
-    """Gradients of ``loss`` with respect to every parameter."""
+    """Gradients of ``loss`` with respect to W (both of its uses) and a."""
     Y, (X, Z, H) = forward(params, X)
+    W, a = params["W"], params["a"]
     dY = 2.0 * (Y - T) / Y.size
-    gW2 = H.T @ dY
-    gb2 = dY.sum(axis=0)
-    dH = dY @ params["W2"].T
-    dZ = dH * gelu_grad(Z)
-    gW1 = X.T @ dZ
-    gb1 = dZ.sum(axis=0)
-    return {"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2}
+    G = dY @ W                      # d loss / d (H * a)
+    ga = np.sum(G * H, axis=0)
+    dZ = G * a * gelu_grad(Z)
+    gW = X.T @ dZ + dY.T @ (H * a)  # input use + output use of W
+    return {"W": gW, "a": ga}
 
 
 def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
@@ -83,14 +84,6 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         vhat = v / (1 - b2 ** t)
         params[k] = params[k] - lr * mhat / (np.sqrt(vhat) + eps)
     return params
-
-
-def make_pairs(r_elems: np.ndarray, e_elems: np.ndarray):
-    """Training pairs from element slices of residuals and errors (rows):
-    input r/|r|, target e/|r| (rows with |r| = 0 are dropped)."""
-    nrm = np.linalg.norm(r_elems, axis=1)
-    keep = nrm > 0
-    return r_elems[keep] / nrm[keep, None], e_elems[keep] / nrm[keep, None]
 
 
 def precondition(params, r_elems: np.ndarray):

@@ -1,6 +1,7 @@
 """Pins of the network oracle: backward pass against central finite
-differences of the loss, GELU against its closed form, Adam against a
-hand-computed first step."""
+differences of the loss, GELU against its closed form, the symmetric
+Jacobian of the tied network against finite differences of the forward
+pass, Adam against a hand-computed first step."""
 import math
 
 import numpy as np
@@ -25,8 +26,8 @@ def test_backward_matches_finite_differences(shape):
     d, h, B = shape
     p = mlp.init_params(d, h, seed=3)
     rng = np.random.default_rng(4)
-    p["b1"] = rng.uniform(-0.5, 0.5, h)
-    p["b2"] = rng.uniform(-0.5, 0.5, d)
+    p["W"] = p["W"] * 3.0  # pre-activations of order one: GELU far from linear
+    p["a"] = rng.uniform(-1.5, 1.5, h)
     X = rng.uniform(-1, 1, (B, d))
     T = rng.uniform(-1, 1, (B, d))
     g = mlp.backward(p, X, T)
@@ -45,6 +46,32 @@ def test_backward_matches_finite_differences(shape):
             assert abs(got - fd) <= 1e-7 * max(1.0, abs(fd)) + 1e-10, (k, idx, got, fd)
 
 
+def test_tied_network_jacobian_is_symmetric_and_zero_maps_to_zero():
+    """y(x) = W (a * gelu(W^T x)): central differences of the forward pass
+    give a symmetric Jacobian at random points, equal to
+    W diag(a gelu'(W^T x)) W^T; an untied network fails the same check."""
+    d, h = 12, 5
+    rng = np.random.default_rng(7)
+    p = {"W": rng.normal(size=(d, h)), "a": rng.uniform(-2, 2, h)}
+    assert np.all(mlp.forward(p, np.zeros((1, d)))[0] == 0.0)
+    eps = 1e-6
+    for _ in range(3):
+        x = rng.uniform(-1, 1, d)
+        J = np.zeros((d, d))
+        for q in range(d):
+            e = np.zeros(d)
+            e[q] = eps
+            J[:, q] = (mlp.forward(p, (x + e)[None])[0][0] - mlp.forward(p, (x - e)[None])[0][0]) / (2 * eps)
+        np.testing.assert_allclose(J, J.T, atol=1e-7 * np.abs(J).max())
+        ref = p["W"] @ np.diag(p["a"] * mlp.gelu_grad(p["W"].T @ x)) @ p["W"].T
+        np.testing.assert_allclose(J, ref, atol=1e-7 * np.abs(J).max())
+    # the check has teeth: with separate output weights the Jacobian is not symmetric
+    W2 = rng.normal(size=(h, d))
+    x = rng.uniform(-1, 1, d)
+    Ju = W2.T @ np.diag(mlp.gelu_grad(p["W"].T @ x)) @ p["W"].T
+    assert np.abs(Ju - Ju.T).max() > 1e-2 * np.abs(Ju).max()
+
+
 def test_adam_first_step_is_lr_times_sign():
     p = {"w": np.array([1.0, -2.0, 3.0])}
     g = {"w": np.array([0.5, -0.25, 0.0])}
@@ -55,15 +82,17 @@ def test_adam_first_step_is_lr_times_sign():
 
 
 def test_training_reduces_loss_on_a_linear_map():
+    """The tied network fits a symmetric linear map (the form its Jacobian has)."""
     rng = np.random.default_rng(0)
-    d, h = 16, 8
+    d, h = 16, 16
     A = rng.normal(size=(d, d)) / 4
+    A = 0.5 * (A + A.T)
     X = rng.normal(size=(256, d))
     T = X @ A
     p = mlp.init_params(d, h, seed=1)
     st = {}
     l0 = mlp.loss(p, X, T)
-    for _ in range(300):
+    for _ in range(1000):
         mlp.adam_step(p, mlp.backward(p, X, T), st, lr=3e-3)
     assert mlp.loss(p, X, T) < 0.5 * l0
 
