@@ -350,22 +350,18 @@ def run_learned(args):
     ctx = nb.Context(0)
     box = W.LEARNED_16CUBE_N7
     mesh = nb.Mesh.from_box(ctx, box)
-    model = nb.Model(ctx, box.N, 48, seed=7)
-    snaps = [1, 4, 16, 64, 128, 256, 512, 800]  # across the whole ~900-iteration solve
+    model = nb.Model(ctx, box.N, 96, seed=7)
+    snaps = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 800]  # across the ~900-iteration solve
     t0 = time.perf_counter()
     Xs, Ts = [], []
     for s in W.TRAIN_SEEDS:
-        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, s, dev), snaps, 80, seed=s)
+        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, s, dev), snaps, 120, seed=s)
         Xs.append(X)
         Ts.append(T)
-    loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=30, batch=256, lr=1e-3)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    model.train(X, T, epochs=40, batch=256, lr=1e-3)
+    loss = model.train(X, T, epochs=20, batch=256, lr=3e-4)
     model.attach(mesh)
-    for s in W.TRAIN_SEEDS:
-        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, s, dev), snaps, 80, seed=s + 100,
-                                use_learned=True)
-        Xs.append(X)
-        Ts.append(T)
-    loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=15, batch=256, lr=5e-4)
     train_s = time.perf_counter() - t0
     res = []
     for s in W.HELDOUT_SEEDS:

@@ -280,23 +280,25 @@ nb_status nb_batch_solve(nb_batch *batch, const nb_opts *opts, const double *b_d
 nb_status nb_batch_autotune(nb_batch *batch, int reps, void *flush_dev, size_t flush_bytes);
 
 /* ------------------------------------------------------------------------
- * Learned preconditioner: a per-element network (one hidden layer with GELU,
- * BF16 tensor-core products with FP32 accumulation, FP32 master weights)
- * mapping an element's residual r_e / |r_e| to a correction on the element's
- * interior nodes, used as z = Dinv r + M_int(|r_e| MLP(r_e/|r_e|)) inside
- * flexible CG (orders N <= 11).  Not in the paper; it takes the slot of the
- * paper's multigrid solveM with a learned element-interior correction.
+ * Learned preconditioner: a per-element network mapping an element's
+ * residual x = r_e / |r_e| to a correction on the element's interior nodes,
+ * y(x) = W (a * gelu(W^T x)) -- one hidden layer of h units whose output
+ * layer reuses the input weights W (d x h) with per-unit gains a, so that
+ * its Jacobian is symmetric -- used as z = Dinv r + M_int(|r_e| y(x)) inside
+ * flexible CG (orders N <= 11).  BF16 tensor-core products with FP32
+ * accumulation, FP32 master weights.  Not in the paper; it takes the slot of
+ * the paper's multigrid solveM with a learned element-interior correction.
  * ------------------------------------------------------------------------ */
 typedef struct nb_model nb_model;
 
 /* A network for order N: d = (N+1)^3 inputs and outputs, `hidden` units,
- * weights uniform(-1,1)/sqrt(fan-in) drawn from SplitMix64(seed), biases 0. */
+ * W uniform(-1,1)/sqrt(d) drawn from SplitMix64(seed), gains a = 1. */
 nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t seed, nb_model **out);
 nb_status nb_model_destroy(nb_model *model);
 
-/* Parameters as one FP32 host array [W1 (d x h, row-major), b1 (h),
- * W2 (h x d), b2 (d)]: copied out to get_host and/or in from set_host (either
- * may be NULL); *nparam (may be NULL) receives the count. */
+/* Parameters as one FP32 host array [W (d x h, row-major), a (h)]: copied
+ * out to get_host and/or in from set_host (either may be NULL); *nparam (may
+ * be NULL) receives the count d h + h. */
 nb_status nb_model_params(nb_model *model, float *get_host, const float *set_host,
                           int64_t *nparam);
 

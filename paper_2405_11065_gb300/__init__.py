@@ -367,7 +367,7 @@ class Model:
 
     def set_params(self, p: dict):
         flat = np.ascontiguousarray(np.concatenate(
-            [np.asarray(p[k], np.float32).reshape(-1) for k in ("W1", "b1", "W2", "b2")]))
+            [np.asarray(p[k], np.float32).reshape(-1) for k in ("W", "a")]))
         assert flat.size == self.nparam
         check(lib.nb_model_params(self.h, None, _ptr(flat), None))
 
@@ -375,7 +375,7 @@ class Model:
         d, h = self.d, self.hidden
         o = 0
         out = {}
-        for k, shape in (("W1", (d, h)), ("b1", (h,)), ("W2", (h, d)), ("b2", (d,))):
+        for k, shape in (("W", (d, h)), ("a", (h,))):
             size = int(np.prod(shape))
             out[k] = flat[o:o + size].reshape(shape)
             o += size

@@ -50,4 +50,15 @@ nb_status bax_f32(int n, int mchoice, bool pupd, int sm_count, long long E, long
                              p, elem_prob, bs, part_e, s);
 }
 
+nb_status bax_tma_f32(int n, int sm_count, long long E, long long e_first, const int32_t *list,
+                      const int *cnt, const float *G, float *w, const float *r, const float *dinv,
+                      float *p, const int32_t *elem_prob, BScal *bs, double *part_e, int *err,
+                      cudaStream_t s)
+{
+    return dispatch_bax_tma<float>(n, sm_count, E, e_first, list, cnt, G, w, r, dinv, p,
+                                   elem_prob, bs, part_e, err, s);
+}
+
+bool bax_tma_available_f32(int n) { return bax_tma_fits<float>(n); }
+
 }  // namespace nb

@@ -38,7 +38,7 @@ k_ax_cc(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__re
         CgScalars *__restrict__ scal, double *__restrict__ part)
 {
     constexpr int n2 = n * n, n3 = n2 * n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *su = reinterpret_cast<T *>(smem_raw);        // [M][n3]
     T *swr = su + M * n3;                            // [M][n2]
     T *sws = swr + M * n2;                           // [M][n2]

@@ -44,6 +44,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// Plain arrival: completes the phase of a barrier that expects no bytes.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Global -> shared bulk copy completing on bar (bytes: multiple of 16, both
 // addresses 16-byte aligned).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
@@ -115,6 +121,65 @@ struct Vec2<double> {
     using type = double2;
 };
 
+// One element's operator from shared memory: Gs = G[6][n3] and su = u (n3)
+// of the element; ru holds the thread's (i,j) column of u, rw receives that
+// column of A_e u.  wr/ws of layer k go through buffer k&1 of swr/sws, with one
+// barrier per layer: layer k+1 writes the other buffer, and layer k+2 (this
+// buffer again) follows layer k+1's barrier.
+template <typename T, int n>
+__device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&ru)[n], T (&rw)[n],
+                                            T *swr, T *sws, const T (&Di)[n], const T (&Dj)[n],
+                                            const T (&DTi)[n], const T (&DTj)[n], int i, int j,
+                                            int ij, bool act)
+{
+    constexpr int n2 = n * n, n3 = n2 * n;
+    using V2 = typename Vec2<T>::type;
+#pragma unroll
+    for (int k = 0; k < n; ++k) rw[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+        T *wrb = swr + (k & 1) * n2;
+        T *wsb = sws + (k & 1) * n2;
+        const T g0 = Gs[0 * n3 + k * n2 + ij], g1 = Gs[1 * n3 + k * n2 + ij];
+        const T g2 = Gs[2 * n3 + k * n2 + ij], g3 = Gs[3 * n3 + k * n2 + ij];
+        const T g4 = Gs[4 * n3 + k * n2 + ij], g5 = Gs[5 * n3 + k * n2 + ij];
+        T ur = T(0), us = T(0), ut = T(0);
+        const V2 *urow = reinterpret_cast<const V2 *>(su + k * n2 + j * n);
+#pragma unroll
+        for (int l = 0; l < n; l += 2) {
+            const V2 v = urow[l / 2];
+            ur += Di[l] * v.x;
+            ur += Di[l + 1] * v.y;
+        }
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+            us += Dj[l] * su[k * n2 + l * n + i];
+            ut += dtab<T>(n, k, l) * ru[l];
+        }
+        const T wr = g0 * ur + g1 * us + g2 * ut;
+        const T ws = g1 * ur + g3 * us + g4 * ut;
+        const T wt = g2 * ur + g4 * us + g5 * ut;
+        if (act) {
+            wrb[ij] = wr;
+            wsb[ij] = ws;
+        }
+        __syncthreads();
+        T a = T(0);
+        const V2 *wrow = reinterpret_cast<const V2 *>(wrb + j * n);
+#pragma unroll
+        for (int l = 0; l < n; l += 2) {
+            const V2 v = wrow[l / 2];
+            a += DTi[l] * v.x;
+            a += DTi[l + 1] * v.y;
+        }
+#pragma unroll
+        for (int l = 0; l < n; ++l) a += DTj[l] * wsb[l * n + i];
+        rw[k] += a;
+#pragma unroll
+        for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
+    }
+}
+
 template <typename T, int n, bool PUPD>
 __global__ void __launch_bounds__(tma_threads<n>())
 k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__restrict__ w,
@@ -123,7 +188,6 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
 {
     constexpr int n2 = n * n, n3 = n2 * n;
     constexpr int STAGE = (int)ax_tma_stage_elems<T, n, PUPD>();
-    using V2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *stage = reinterpret_cast<T *>(smem_raw);  // [2][STAGE]: G[6][n3], then u
     T *pbuf = stage + 2 * STAGE;                 // [n3] the fused step's p (PUPD only)
@@ -197,53 +261,9 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             } else {
                 ru[k] = su[k * n2 + ij];
             }
-            rw[k] = T(0);
         }
         if (PUPD) __syncthreads();
-#pragma unroll
-        for (int k = 0; k < n; ++k) {
-            T *wrb = swr + (k & 1) * n2;
-            T *wsb = sws + (k & 1) * n2;
-            const T g0 = Gs[0 * n3 + k * n2 + ij], g1 = Gs[1 * n3 + k * n2 + ij];
-            const T g2 = Gs[2 * n3 + k * n2 + ij], g3 = Gs[3 * n3 + k * n2 + ij];
-            const T g4 = Gs[4 * n3 + k * n2 + ij], g5 = Gs[5 * n3 + k * n2 + ij];
-            T ur = T(0), us = T(0), ut = T(0);
-            const V2 *urow = reinterpret_cast<const V2 *>(su + k * n2 + j * n);
-#pragma unroll
-            for (int l = 0; l < n; l += 2) {
-                const V2 v = urow[l / 2];
-                ur += Di[l] * v.x;
-                ur += Di[l + 1] * v.y;
-            }
-#pragma unroll
-            for (int l = 0; l < n; ++l) {
-                us += Dj[l] * su[k * n2 + l * n + i];
-                ut += dtab<T>(n, k, l) * ru[l];
-            }
-            const T wr = g0 * ur + g1 * us + g2 * ut;
-            const T ws = g1 * ur + g3 * us + g4 * ut;
-            const T wt = g2 * ur + g4 * us + g5 * ut;
-            if (act) {
-                wrb[ij] = wr;
-                wsb[ij] = ws;
-            }
-            __syncthreads();
-            T a = T(0);
-            const V2 *wrow = reinterpret_cast<const V2 *>(wrb + j * n);
-#pragma unroll
-            for (int l = 0; l < n; l += 2) {
-                const V2 v = wrow[l / 2];
-                a += DTi[l] * v.x;
-                a += DTi[l + 1] * v.y;
-            }
-#pragma unroll
-            for (int l = 0; l < n; ++l) a += DTj[l] * wsb[l * n + i];
-            rw[k] += a;
-#pragma unroll
-            for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
-            // no second barrier: layer k+1 writes the other wr/ws buffer, and
-            // layer k+2 (this buffer again) follows layer k+1's barrier
-        }
+        tma_element<T, n>(Gs, su, ru, rw, swr, sws, Di, Dj, DTi, DTj, i, j, ij, act);
         if (act) {
             T sdot = T(0);
 #pragma unroll

@@ -42,13 +42,19 @@ nb_status bax_f64(int n, int mchoice, bool pupd, int sm_count, long long E, long
                   double *w, const double *r, const double *dinv, double *p,
                   const int32_t *elem_prob, const BScal *bs, double *part_e, cudaStream_t s);
 
+nb_status bax_tma_f32(int n, int sm_count, long long E, long long e_first, const int32_t *list,
+                      const int *cnt, const float *G, float *w, const float *r, const float *dinv,
+                      float *p, const int32_t *elem_prob, BScal *bs, double *part_e, int *err,
+                      cudaStream_t s);
+bool bax_tma_available_f32(int n);
+
 constexpr int kRowChunk = 2048;  // gather-scatter rows per list entry
 
 struct BatchGroup {
     int n = 0;
     int64_t e0 = 0, e1 = 0;  // element range
     int64_t l0 = 0;          // L offset of the first element
-    int variant = 1;         // elements-per-block choice (autotuned)
+    int variant = 1;         // FP32 step: 0, 1 elements-per-block choices, 2 bulk copy (autotuned)
 };
 
 struct BatchWs {
@@ -84,6 +90,7 @@ struct nb_batch {
     nb::BScal *bs_host = nullptr;  // pinned
     int *loops = nullptr;          // graph loop counter
     int *loops_host = nullptr;     // pinned mirror
+    int *kerr = nullptr;           // device flag: a bulk-copy wait timed out
     double *part_e = nullptr;      // [2 E]
     double *red = nullptr;         // [4 nprob]: |r|^2, |b|^2, tau, active
     double *red_host = nullptr;    // pinned
@@ -113,6 +120,14 @@ __device__ __forceinline__ double warp_range_sum(const double *a, int64_t lo, in
     const int lane = threadIdx.x & 31;
     double v = 0.0;
     for (int64_t e = lo + lane; e < hi; e += 32) v += a[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over a warp by a fixed shuffle tree, on lane 0.
+__device__ __forceinline__ double warp_sum(double v)
+{
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
@@ -148,18 +163,21 @@ __global__ void k_bchunk(int *loops, int cap)
     loops[1] = cap;
 }
 
-// p = 0 and owner-copy partials of (r, dinv r), (r, r) per listed element.
+// p = 0 and owner-copy partials of (r, dinv r), (r, r) per listed element
+// (one warp per element).
 template <typename T>
 __global__ void k_binit(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
                         const int64_t *__restrict__ el0, const T *__restrict__ r,
                         const T *__restrict__ dinv, T *__restrict__ p, double *__restrict__ part)
 {
-    __shared__ double sred[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ne = list_len(cnt, E);
-    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < ne;
+         i += nwarps) {
         const int64_t e = list_at(list, i);
         DotAcc<T> a, b;
-        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+        for (int64_t l = el0[e] + lane; l < el0[e + 1]; l += 32) {
             const T rl = r[l], d = dinv[l];
             p[l] = T(0);
             if (!signbit(d)) {
@@ -167,9 +185,9 @@ __global__ void k_binit(int64_t E, const int32_t *__restrict__ list, const int *
                 b.add(rl * rl);
             }
         }
-        const double ta = block_sum(a.value(), sred);
-        const double tb = block_sum(b.value(), sred);
-        if (threadIdx.x == 0) {
+        const double ta = warp_sum(a.value());
+        const double tb = warp_sum(b.value());
+        if (lane == 0) {
             part[e] = ta;
             part[E + e] = tb;
         }
@@ -249,6 +267,9 @@ __global__ void k_bgs(const int4 *__restrict__ ch, const int *__restrict__ cnt,
     }
 }
 
+// x += alpha_q p, r -= alpha_q w and the owner-copy partials of (r, dinv r),
+// (r, r) per listed element: one warp per element (lane-strided, coalesced),
+// the partials summed by a fixed shuffle tree.
 template <typename T>
 __global__ void k_bupdate(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
                           const int64_t *__restrict__ el0,
@@ -257,15 +278,17 @@ __global__ void k_bupdate(int64_t E, const int32_t *__restrict__ list, const int
                           const T *__restrict__ w, const T *__restrict__ dinv,
                           double *__restrict__ part)
 {
-    __shared__ double sred[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t ne = list_len(cnt, E);
-    for (int64_t i = blockIdx.x; i < ne; i += gridDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < ne;
+         i += nwarps) {
         const int64_t e = list_at(list, i);
         const BScal &b = bs[eprob[e]];
-        if (b.done) continue;  // uniform over the block
+        if (b.done) continue;  // uniform over the warp
         const T alpha = (T)b.alpha;
         DotAcc<T> a, c;
-        for (int64_t l = el0[e] + threadIdx.x; l < el0[e + 1]; l += blockDim.x) {
+        for (int64_t l = el0[e] + lane; l < el0[e + 1]; l += 32) {
             x[l] = x[l] + alpha * p[l];
             const T rl = r[l] - alpha * w[l];
             r[l] = rl;
@@ -275,9 +298,9 @@ __global__ void k_bupdate(int64_t E, const int32_t *__restrict__ list, const int
                 c.add(rl * rl);
             }
         }
-        const double ta = block_sum(a.value(), sred);
-        const double tc = block_sum(c.value(), sred);
-        if (threadIdx.x == 0) {
+        const double ta = warp_sum(a.value());
+        const double tc = warp_sum(c.value());
+        if (lane == 0) {
             part[e] = ta;
             part[E + e] = tc;
         }
@@ -418,6 +441,11 @@ __global__ void k_bcopy(int64_t n, const double *__restrict__ a, double *__restr
 // ---------------------------------------------------------------------------
 
 static int elem_grid(const nb_batch *B) { return (int)std::min<int64_t>(B->E, B->ctx->sm_count * 16); }
+// one warp per element, 8 per block of 256 threads
+static int warp_elem_grid(const nb_batch *B)
+{
+    return (int)std::min<int64_t>((B->E + 7) / 8, B->ctx->sm_count * 16);
+}
 static int warp_grid(int nprob) { return (nprob * 32 + 255) / 256; }
 static int chunk_grid(const nb_batch *B)
 {
@@ -470,27 +498,38 @@ static nb_status set_active(nb_batch *B, const std::vector<char> &run, cudaStrea
     return NB_OK;
 }
 
+// The operator on one order's listed elements (variant: see BatchGroup).
+template <typename T>
+static nb_status bax_group(nb_batch *B, int gi, int variant, bool pupd, const T *u, T *w,
+                           const T *r, const T *dinv, T *p, double *part, cudaStream_t s)
+{
+    const BatchGroup &g = B->groups[gi];
+    const int64_t E = g.e1 - g.e0;
+    const size_t lo = (size_t)g.l0, go = (size_t)g.l0 * 6;
+    auto off = [&](const T *v) { return v ? v + lo : nullptr; };
+    if (sizeof(T) == 4 && pupd && variant == 2)
+        return bax_tma_f32(g.n, B->ctx->sm_count, E, g.e0, list_group(B, gi), cnt_group(B, gi),
+                           (const float *)B->G32 + go, (float *)(w + lo), (const float *)off(r),
+                           (const float *)off(dinv), (float *)(p + lo), B->elem_prob, B->bs,
+                           part, B->kerr, s);
+    const int mchoice = variant == 0 ? 0 : 1;
+    if (sizeof(T) == 4)
+        return bax_f32(g.n, mchoice, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
+                       cnt_group(B, gi), (const float *)B->G32 + go, (const float *)off(u),
+                       (float *)(w + lo), (const float *)off(r), (const float *)off(dinv),
+                       p ? (float *)(p + lo) : nullptr, B->elem_prob, B->bs, part, s);
+    return bax_f64(g.n, mchoice, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
+                   cnt_group(B, gi), (const double *)B->G64 + go, (const double *)off(u),
+                   (double *)(w + lo), (const double *)off(r), (const double *)off(dinv),
+                   p ? (double *)(p + lo) : nullptr, B->elem_prob, B->bs, part, s);
+}
+
 template <typename T>
 static nb_status bax_all(nb_batch *B, bool pupd, const T *u, T *w, const T *r, const T *dinv,
                          T *p, double *part, cudaStream_t s)
 {
-    for (int gi = 0; gi < (int)B->groups.size(); ++gi) {
-        const BatchGroup &g = B->groups[gi];
-        const int64_t E = g.e1 - g.e0;
-        const size_t lo = (size_t)g.l0, go = (size_t)g.l0 * 6;
-        auto off = [&](const T *v) { return v ? v + lo : nullptr; };
-        if (sizeof(T) == 4)
-            NB_TRY(bax_f32(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
-                           cnt_group(B, gi), (const float *)B->G32 + go, (const float *)off(u),
-                           (float *)(w + lo), (const float *)off(r), (const float *)off(dinv),
-                           p ? (float *)(p + lo) : nullptr, B->elem_prob, B->bs, part, s));
-        else
-            NB_TRY(bax_f64(g.n, g.variant, pupd, B->ctx->sm_count, E, g.e0, list_group(B, gi),
-                           cnt_group(B, gi), (const double *)B->G64 + go, (const double *)off(u),
-                           (double *)(w + lo), (const double *)off(r),
-                           (const double *)off(dinv), p ? (double *)(p + lo) : nullptr,
-                           B->elem_prob, B->bs, part, s));
-    }
+    for (int gi = 0; gi < (int)B->groups.size(); ++gi)
+        NB_TRY(bax_group<T>(B, gi, B->groups[gi].variant, pupd, u, w, r, dinv, p, part, s));
     return NB_OK;
 }
 
@@ -504,7 +543,7 @@ static nb_status batch_body(nb_batch *B, BatchWs &ws, const T *dinv, int use_con
     k_bgs<T><<<chunk_grid(B), 256, 0, s>>>(list_chunks(B), cnt_chunks(B), B->gs_off, B->gs_loc,
                                            B->gs_mask, B->bs, (T *)ws.w);
     NB_CUDA(cudaGetLastError());
-    k_bupdate<T><<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+    k_bupdate<T><<<warp_elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
                                               B->elem_prob, B->bs, (T *)ws.x, (T *)ws.r,
                                               (const T *)ws.p, (const T *)ws.w, dinv, B->part_e);
     NB_CUDA(cudaGetLastError());
@@ -545,7 +584,7 @@ static nb_status batch_cg(nb_batch *B, BatchWs &ws, const T *dinv, double tol, i
     *launches += 3;
     k_bsetup<<<(B->nprob + 255) / 256, 256, 0, s>>>(B->nprob, B->bs, tol, maxit, B->red, use_red);
     NB_CUDA(cudaGetLastError());
-    k_binit<T><<<elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
+    k_binit<T><<<warp_elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
                                             (const T *)ws.r, dinv, (T *)ws.p, B->part_e);
     NB_CUDA(cudaGetLastError());
     k_bfin_init<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs,
@@ -658,7 +697,7 @@ extern "C" nb_status nb_batch_destroy(nb_batch *B)
     free_bws(B->ws64);
     void *bufs[] = {B->G32, B->G64, B->dinv32, B->dinv64, B->gs_off, B->gs_loc, B->gs_mask,
                     B->elem_prob, B->elem_l0, B->prob_e0, B->bs, B->loops, B->part_e, B->red,
-                    B->r64, B->w64, B->act};
+                    B->r64, B->w64, B->act, B->kerr};
     for (void *b : bufs) cudaFree(b);
     if (B->bs_host) cudaFreeHost(B->bs_host);
     if (B->red_host) cudaFreeHost(B->red_host);
@@ -784,9 +823,13 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     NB_BCUDA(cudaMalloc(&B->elem_l0, sizeof(int64_t) * (B->E + 1)));
     NB_BCUDA(cudaMalloc(&B->prob_e0, sizeof(int64_t) * (nprob + 1)));
     NB_BCUDA(cudaMalloc(&B->bs, sizeof(BScal) * nprob));
+    NB_BCUDA(cudaMemset(B->bs, 0, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMallocHost(&B->bs_host, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMalloc(&B->loops, 2 * sizeof(int)));
     NB_BCUDA(cudaMallocHost(&B->loops_host, 2 * sizeof(int)));
+    NB_BCUDA(cudaMalloc(&B->kerr, sizeof(int)));
+    NB_BCUDA(cudaMemset(B->kerr, 0, sizeof(int)));
+    for (BatchGroup &g : B->groups) g.variant = bax_tma_available_f32(g.n) ? 2 : 1;
     NB_BCUDA(cudaMalloc(&B->part_e, sizeof(double) * 2 * B->E));
     NB_BCUDA(cudaMalloc(&B->red, sizeof(double) * 4 * nprob));
     NB_BCUDA(cudaMallocHost(&B->red_host, sizeof(double) * 4 * nprob));
@@ -881,23 +924,25 @@ extern "C" nb_status nb_batch_autotune(nb_batch *B, int reps, void *flush, size_
     NB_CUDA(cudaSetDevice(B->ctx->device));
     cudaStream_t s = B->ctx->stream;
     NB_TRY(ensure_bws(B, B->ws32, sizeof(float)));
+    NB_TRY(set_active(B, std::vector<char>(B->nprob, 1), s));
+    // every problem running with beta = 0: the step the solver launches
+    NB_CUDA(cudaMemsetAsync(B->bs, 0, sizeof(BScal) * B->nprob, s));
     cudaEvent_t e0, e1;
     NB_CUDA(cudaEventCreate(&e0));
     NB_CUDA(cudaEventCreate(&e1));
-    for (BatchGroup &g : B->groups) {
+    for (int gi = 0; gi < (int)B->groups.size(); ++gi) {
+        BatchGroup &g = B->groups[gi];
         double best = 1e300;
         int bestv = g.variant;
-        for (int v = 0; v < 2; ++v) {
-            g.variant = v;
+        const int nv = bax_tma_available_f32(g.n) ? 3 : 2;
+        for (int v = 0; v < nv; ++v) {
             double tot = 0.0;
             for (int r = 0; r <= reps; ++r) {  // the first launch is a warm-up
                 if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
                 cudaEventRecord(e0, s);
-                const size_t lo = (size_t)g.l0;
-                NB_TRY(bax_f32(g.n, v, false, B->ctx->sm_count, g.e1 - g.e0, g.e0, nullptr,
-                               nullptr, B->G32 + 6 * lo, (const float *)B->ws32.p + lo,
-                               (float *)B->ws32.w + lo, nullptr, nullptr, nullptr, B->elem_prob,
-                               B->bs, nullptr, s));
+                NB_TRY(bax_group<float>(B, gi, v, true, nullptr, (float *)B->ws32.w,
+                                        (const float *)B->ws32.r, B->dinv32, (float *)B->ws32.p,
+                                        B->part_e, s));
                 cudaEventRecord(e1, s);
                 NB_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -1075,6 +1120,13 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
     cudaEventElapsedTime(&ms, t0, t1);
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    int kerr = 0;
+    NB_CUDA(cudaMemcpy(&kerr, B->kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kerr) {
+        cudaMemset(B->kerr, 0, sizeof(int));
+        set_error("a bulk copy of the batched operator did not complete within one second");
+        return NB_ERR_CUDA;
+    }
     nb_status worst = NB_OK;
     double worst_rel = 0.0;
     for (int p = 0; p < np; ++p) {

@@ -1,10 +1,13 @@
 // Learned per-element preconditioner and flexible CG.
 //
 // The network maps an element's residual, divided by its norm, to a
-// correction of the same length d = (N+1)^3 (one hidden layer of width h with
-// GELU).  The preconditioner is Jacobi plus the scaled network output on the
-// element's interior nodes:
-//     z = Dinv r + M_int ( |r_e| MLP(r_e / |r_e|) )
+// correction of the same length d = (N+1)^3: one hidden layer of width h with
+// GELU whose output layer reuses the input weights (tied), with per-unit
+// gains a:  y(x) = W (a * gelu(W^T x)).  Its Jacobian
+// W diag(a gelu'(W^T x)) W^T is symmetric at every input, which the
+// short-recurrence flexible CG needs.  The preconditioner is Jacobi plus the
+// scaled network output on the element's interior nodes:
+//     z = Dinv r + M_int ( |r_e| y(r_e / |r_e|) )
 // Interior nodes belong to one element only, so z is continuous without a
 // summation.  The network is trained to supply what Jacobi misses inside an
 // element: its targets are (A_ii^-1 r_i - Dinv r_i) / |r_e|, the
@@ -28,7 +31,7 @@
 struct nb_model {
     nb_ctx *ctx = nullptr;
     int N = 0, d = 0, h = 0;
-    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;  // FP32 master
+    float *W = nullptr, *a = nullptr;  // FP32 master: W (d x h, row-major), gains a (h)
     float *m = nullptr, *v = nullptr;  // Adam moments over all parameters (contiguous)
     float *grad = nullptr;             // gradients, same layout
     int64_t nparam = 0;
@@ -36,6 +39,7 @@ struct nb_model {
     // scratch for a batch (grown on demand)
     int cap = 0;
     float *Z = nullptr, *H = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *nrm = nullptr;
+    float *gpart = nullptr;  // per-block partials of the gain gradient
     float *X = nullptr;
     double *lpart = nullptr;
 };
@@ -50,7 +54,7 @@ namespace nb {
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
 
-enum GemmEpi { EPI_STORE = 0, EPI_BIAS_GELU = 1, EPI_BIAS = 2, EPI_PRECOND = 3 };
+enum GemmEpi { EPI_STORE = 0, EPI_GELU_GAIN = 1, EPI_ADD = 2, EPI_PRECOND = 3 };
 
 struct GemmArgs {
     int M, N, K;
@@ -60,8 +64,8 @@ struct GemmArgs {
     int ldb;
     float *C;
     int ldc;
-    const float *bias;     // [N] (EPI_BIAS*, EPI_PRECOND)
-    float *C2;             // EPI_BIAS_GELU: gelu(C) written here (ldc)
+    const float *gain;     // [N] (EPI_GELU_GAIN)
+    float *C2;             // EPI_GELU_GAIN: gain * gelu(C) written here (ldc)
     const float *rowscale; // EPI_PRECOND: per-row factor |r_e|
     const float *rvec;     // EPI_PRECOND: the residual (M x N, ldc)
     const float *dinv;     // EPI_PRECOND: signed Jacobi inverse diagonal (M x N, ldc)
@@ -155,12 +159,11 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                 if (row >= g.M || col >= g.N) continue;
                 float v = acc[mt][nt][hh];
                 const size_t o = (size_t)row * g.ldc + col;
-                if (EPI == EPI_BIAS_GELU) {
-                    v += g.bias[col];
-                    g.C[o] = v;
-                    g.C2[o] = gelu_f(v);
-                } else if (EPI == EPI_BIAS) {
-                    g.C[o] = v + g.bias[col];
+                if (EPI == EPI_GELU_GAIN) {
+                    if (g.C) g.C[o] = v;
+                    g.C2[o] = g.gain[col] * gelu_f(v);
+                } else if (EPI == EPI_ADD) {
+                    g.C[o] += v;
                 } else if (EPI == EPI_PRECOND) {
                     // Jacobi everywhere, plus the learned correction on the
                     // element's interior nodes (which have a single copy)
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                     const bool inner = ci > 0 && ci < g.n - 1 && cj > 0 && cj < g.n - 1 &&
                                        ck > 0 && ck < g.n - 1;
                     float z = fabsf(g.dinv[o]) * g.rvec[o];
-                    if (inner) z += (v + g.bias[col]) * g.rowscale[row];
+                    if (inner) z += v * g.rowscale[row];
                     g.C[o] = z;
                 } else {
                     g.C[o] = v;
@@ -344,16 +347,30 @@ __global__ void k_mse(int64_t n, const float *__restrict__ Y, const float *__res
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// dZ = dH * gelu'(Z), in place on dH.
-__global__ void k_gelu_back(int64_t n, const float *__restrict__ Z, float *__restrict__ dH)
+// Backward through the hidden layer of the tied network.  G = dY W holds the
+// gradient with respect to the scaled activations a * gelu(Z); in place it
+// becomes dZ = G * a * gelu'(Z), and each block leaves its partial of the
+// gain gradient sum_b G * gelu(Z) per unit in gpart[block][h] (rows in a
+// fixed order: block-strided, then summed by k_colsum in block order).
+__global__ void k_tied_back(int rows, int h, const float *__restrict__ Z,
+                            const float *__restrict__ gain, float *__restrict__ G,
+                            float *__restrict__ gpart)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        dH[i] *= gelu_grad_f(Z[i]);
+    for (int c = threadIdx.x; c < h; c += blockDim.x) {
+        const float ac = gain[c];
+        float s = 0.f;
+        for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+            const size_t o = (size_t)r * h + c;
+            const float z = Z[o], gv = G[o];
+            s += gv * gelu_f(z);
+            G[o] = gv * ac * gelu_grad_f(z);
+        }
+        gpart[(size_t)blockIdx.x * h + c] = s;
+    }
 }
 
-// Column sums of a rows x cols matrix (bias gradients), each column summed
-// in row order by one thread.
+// Column sums of a rows x cols matrix, each column summed in row order by
+// one thread.
 __global__ void k_colsum(int rows, int cols, const float *__restrict__ A, float *__restrict__ out)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,10 +400,12 @@ __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict
 // model helpers
 // ---------------------------------------------------------------------------
 
+constexpr int kBackBlocks = 64;  // blocks of k_tied_back (partials of the gain gradient)
+
 static nb_status model_scratch(nb_model *md, int rows)
 {
     if (rows <= md->cap) return NB_OK;
-    float *bufs[] = {md->Z, md->H, md->Y, md->dY, md->dH, md->nrm, md->X};
+    float *bufs[] = {md->Z, md->H, md->Y, md->dY, md->dH, md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
     cudaFree(md->lpart);
     const size_t R = (size_t)rows;
@@ -398,23 +417,24 @@ static nb_status model_scratch(nb_model *md, int rows)
     NB_CUDA(cudaMalloc(&md->X, sizeof(float) * R * md->d));
     NB_CUDA(cudaMalloc(&md->nrm, sizeof(float) * R));
     NB_CUDA(cudaMalloc(&md->lpart, sizeof(double) * 4096));
+    NB_CUDA(cudaMalloc(&md->gpart, sizeof(float) * kBackBlocks * md->h));
     md->cap = rows;
     return NB_OK;
 }
 
-// Forward pass of B rows of X: Z, H = gelu(Z), Y.
+// Forward pass of B rows of X: Z = X W, H = a * gelu(Z), Y = H W^T.
 static nb_status model_forward(nb_model *md, const float *X, int B, cudaStream_t s)
 {
     GemmArgs a = {};
     a.M = B; a.N = md->h; a.K = md->d;
-    a.A = X; a.lda = md->d; a.B = md->W1; a.ldb = md->h;
-    a.C = md->Z; a.ldc = md->h; a.bias = md->b1; a.C2 = md->H;
-    NB_TRY((gemm<false, false, EPI_BIAS_GELU>(a, s)));
-    GemmArgs b2 = {};
-    b2.M = B; b2.N = md->d; b2.K = md->h;
-    b2.A = md->H; b2.lda = md->h; b2.B = md->W2; b2.ldb = md->d;
-    b2.C = md->Y; b2.ldc = md->d; b2.bias = md->b2;
-    return gemm<false, false, EPI_BIAS>(b2, s);
+    a.A = X; a.lda = md->d; a.B = md->W; a.ldb = md->h;
+    a.C = md->Z; a.ldc = md->h; a.gain = md->a; a.C2 = md->H;
+    NB_TRY((gemm<false, false, EPI_GELU_GAIN>(a, s)));
+    GemmArgs b = {};  // op(B) = W^T: B stored d x h
+    b.M = B; b.N = md->d; b.K = md->h;
+    b.A = md->H; b.lda = md->h; b.B = md->W; b.ldb = md->h;
+    b.C = md->Y; b.ldc = md->d;
+    return gemm<false, true, EPI_STORE>(b, s);
 }
 
 // Loss and gradients (into md->grad) for B pairs; *loss_dev = sum (Y-T)^2.
@@ -427,30 +447,26 @@ static nb_status model_backward(nb_model *md, const float *X, const float *T, in
     k_mse<<<g, 256, 0, s>>>(ny, md->Y, T, 1.0f / (float)ny, md->dY, md->lpart);
     NB_CUDA(cudaGetLastError());
     if (loss_dev) NB_TRY(sum_partials_dev(md->lpart, g, loss_dev, s));
-    float *gW1 = md->grad, *gb1 = gW1 + (size_t)md->d * md->h;
-    float *gW2 = gb1 + md->h, *gb2 = gW2 + (size_t)md->h * md->d;
-    GemmArgs a = {};  // gW2 = H^T dY   (h x d)
-    a.M = md->h; a.N = md->d; a.K = B;
-    a.A = md->H; a.lda = md->h; a.B = md->dY; a.ldb = md->d; a.C = gW2; a.ldc = md->d;
-    NB_TRY((gemm<true, false, EPI_STORE>(a, s)));
-    k_colsum<<<(md->d + 255) / 256, 256, 0, s>>>(B, md->d, md->dY, gb2);
+    float *gW = md->grad, *ga = gW + (size_t)md->d * md->h;
+    GemmArgs a = {};  // G = dY W   (B x h)
+    a.M = B; a.N = md->h; a.K = md->d;
+    a.A = md->dY; a.lda = md->d; a.B = md->W; a.ldb = md->h; a.C = md->dH; a.ldc = md->h;
+    NB_TRY((gemm<false, false, EPI_STORE>(a, s)));
+    const int nb_ = std::min(kBackBlocks, B);
+    k_tied_back<<<nb_, 128, 0, s>>>(B, md->h, md->Z, md->a, md->dH, md->gpart);
+    k_colsum<<<(md->h + 127) / 128, 128, 0, s>>>(nb_, md->h, md->gpart, ga);
     NB_CUDA(cudaGetLastError());
-    GemmArgs b = {};  // dH = dY W2^T  (B x h)
-    b.M = B; b.N = md->h; b.K = md->d;
-    b.A = md->dY; b.lda = md->d; b.B = md->W2; b.ldb = md->d; b.C = md->dH; b.ldc = md->h;
-    NB_TRY((gemm<false, true, EPI_STORE>(b, s)));
-    k_gelu_back<<<256, 256, 0, s>>>((int64_t)B * md->h, md->Z, md->dH);
-    NB_CUDA(cudaGetLastError());
-    GemmArgs c = {};  // gW1 = X^T dZ   (d x h)
+    GemmArgs c = {};  // gW = X^T dZ   (d x h): the input use of W
     c.M = md->d; c.N = md->h; c.K = B;
-    c.A = X; c.lda = md->d; c.B = md->dH; c.ldb = md->h; c.C = gW1; c.ldc = md->h;
+    c.A = X; c.lda = md->d; c.B = md->dH; c.ldb = md->h; c.C = gW; c.ldc = md->h;
     NB_TRY((gemm<true, false, EPI_STORE>(c, s)));
-    k_colsum<<<(md->h + 255) / 256, 256, 0, s>>>(B, md->h, md->dH, gb1);
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
+    GemmArgs e = {};  // gW += dY^T H  (d x h): the output use of W
+    e.M = md->d; e.N = md->h; e.K = B;
+    e.A = md->dY; e.lda = md->d; e.B = md->H; e.ldb = md->h; e.C = gW; e.ldc = md->h;
+    return gemm<true, false, EPI_ADD>(e, s);
 }
 
-// z = M Q Q^T(c * |r_e| MLP(r_e/|r_e|)) (+ dinv r): the preconditioner.
+// z = |dinv| r + M_int(|r_e| y(r_e/|r_e|)): the preconditioner.
 static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z, cudaStream_t s)
 {
     const int E = (int)m->E;
@@ -459,16 +475,16 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
     NB_CUDA(cudaGetLastError());
     GemmArgs a = {};
     a.M = E; a.N = md->h; a.K = md->d;
-    a.A = md->X; a.lda = md->d; a.B = md->W1; a.ldb = md->h;
-    a.C = md->Z; a.ldc = md->h; a.bias = md->b1; a.C2 = md->H;
-    NB_TRY((gemm<false, false, EPI_BIAS_GELU>(a, s)));
+    a.A = md->X; a.lda = md->d; a.B = md->W; a.ldb = md->h;
+    a.C = nullptr; a.ldc = md->h; a.gain = md->a; a.C2 = md->H;
+    NB_TRY((gemm<false, false, EPI_GELU_GAIN>(a, s)));
     GemmArgs b = {};
     b.M = E; b.N = md->d; b.K = md->h;
-    b.A = md->H; b.lda = md->h; b.B = md->W2; b.ldb = md->d;
-    b.C = z; b.ldc = md->d; b.bias = md->b2; b.rowscale = md->nrm;
+    b.A = md->H; b.lda = md->h; b.B = md->W; b.ldb = md->h;
+    b.C = z; b.ldc = md->d; b.rowscale = md->nrm;
     b.rvec = r; b.dinv = m->dinv32; b.n = m->n;
     // interior nodes have one copy and Jacobi is continuous: no summation needed
-    return gemm<false, false, EPI_PRECOND>(b, s);
+    return gemm<false, true, EPI_PRECOND>(b, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -734,9 +750,9 @@ extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t se
     md->d = (N + 1) * (N + 1) * (N + 1);
     md->h = hidden;
     const size_t d = md->d, h = md->h;
-    md->nparam = (int64_t)(d * h + h + h * d + d);
-    // deterministic initialisation: uniform(-1,1)/sqrt(fan-in) from SplitMix64
-    std::vector<float> host(md->nparam, 0.f);
+    md->nparam = (int64_t)(d * h + h);
+    // deterministic initialisation: W uniform(-1,1)/sqrt(d) from SplitMix64, a = 1
+    std::vector<float> host(md->nparam, 1.f);
     uint64_t st = seed * 0x9E3779B97F4A7C15ull;
     auto next = [&]() {
         uint64_t z = (st += 0x9E3779B97F4A7C15ull);
@@ -746,24 +762,21 @@ extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t se
         return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
     };
     for (size_t i = 0; i < d * h; ++i) host[i] = (float)(next() / sqrt((double)d));
-    for (size_t i = 0; i < h * d; ++i) host[d * h + h + i] = (float)(next() / sqrt((double)h));
-    cudaError_t e = cudaMalloc(&md->W1, sizeof(float) * md->nparam);
+    cudaError_t e = cudaMalloc(&md->W, sizeof(float) * md->nparam);
     if (e == cudaSuccess) e = cudaMalloc(&md->grad, sizeof(float) * md->nparam);
     if (e == cudaSuccess) e = cudaMalloc(&md->m, sizeof(float) * md->nparam);
     if (e == cudaSuccess) e = cudaMalloc(&md->v, sizeof(float) * md->nparam);
     if (e == cudaSuccess)
-        e = cudaMemcpy(md->W1, host.data(), sizeof(float) * md->nparam, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(md->W, host.data(), sizeof(float) * md->nparam, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(md->m, 0, sizeof(float) * md->nparam);
     if (e == cudaSuccess) e = cudaMemset(md->v, 0, sizeof(float) * md->nparam);
     if (e != cudaSuccess) {
         set_error("model allocation: %s", cudaGetErrorString(e));
-        cudaFree(md->W1); cudaFree(md->grad); cudaFree(md->m); cudaFree(md->v);
+        cudaFree(md->W); cudaFree(md->grad); cudaFree(md->m); cudaFree(md->v);
         delete md;
         return NB_ERR_OOM;
     }
-    md->b1 = md->W1 + d * h;
-    md->W2 = md->b1 + h;
-    md->b2 = md->W2 + h * d;
+    md->a = md->W + d * h;
     *out = md;
     return NB_OK;
 }
@@ -772,8 +785,8 @@ extern "C" nb_status nb_model_destroy(nb_model *md)
 {
     if (!md) return NB_OK;
     cudaSetDevice(md->ctx->device);
-    float *bufs[] = {md->W1, md->grad, md->m, md->v, md->Z, md->H, md->Y, md->dY, md->dH,
-                     md->nrm, md->X};
+    float *bufs[] = {md->W, md->grad, md->m, md->v, md->Z, md->H, md->Y, md->dY, md->dH,
+                     md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
     cudaFree(md->lpart);
     delete md;
@@ -790,9 +803,9 @@ extern "C" nb_status nb_model_params(nb_model *md, float *get_host, const float 
     NB_CUDA(cudaSetDevice(md->ctx->device));
     if (nparam) *nparam = md->nparam;
     if (set_host)
-        NB_CUDA(cudaMemcpy(md->W1, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
+        NB_CUDA(cudaMemcpy(md->W, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
     if (get_host)
-        NB_CUDA(cudaMemcpy(get_host, md->W1, sizeof(float) * md->nparam, cudaMemcpyDeviceToHost));
+        NB_CUDA(cudaMemcpy(get_host, md->W, sizeof(float) * md->nparam, cudaMemcpyDeviceToHost));
     return NB_OK;
 }
 
@@ -841,7 +854,7 @@ extern "C" nb_status nb_model_train(nb_model *md, const float *X, const float *T
                                   ep == epochs - 1 ? dl : nullptr, s));
             md->step += 1;
             const float c1 = 1.f - powf(b1, (float)md->step), c2 = 1.f - powf(b2, (float)md->step);
-            k_adam<<<256, 256, 0, s>>>(md->nparam, md->W1, md->grad, md->m, md->v, lr, b1, b2, c1,
+            k_adam<<<256, 256, 0, s>>>(md->nparam, md->W, md->grad, md->m, md->v, lr, b1, b2, c1,
                                        c2, 1e-8f);
             NB_CUDA(cudaGetLastError());
             if (ep == epochs - 1) {

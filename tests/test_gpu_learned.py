@@ -40,8 +40,8 @@ def test_gpu_gradients_match_oracle_backward(nb, ctx):
     model = nb.Model(ctx, N, h, seed=1)
     p = mlp.init_params(d, h, seed=5)
     rng = np.random.default_rng(6)
-    p["b1"] = rng.uniform(-0.3, 0.3, h)
-    p["b2"] = rng.uniform(-0.3, 0.3, d)
+    p["W"] = p["W"] * 3.0  # pre-activations of order one
+    p["a"] = rng.uniform(-1.5, 1.5, h)
     # parameters exactly representable in BF16 so both sides use the same weights
     bf = lambda a: torch.from_numpy(np.asarray(a, np.float32)).bfloat16().float().numpy()
     p = {k: bf(v).astype(np.float64) for k, v in p.items()}
@@ -53,7 +53,7 @@ def test_gpu_gradients_match_oracle_backward(nb, ctx):
     ref = mlp.backward(p, X, T)
     lref = mlp.loss(p, X, T)
     assert abs(loss - lref) <= 1e-2 * lref
-    for k in ("W1", "b1", "W2", "b2"):
+    for k in ("W", "a"):
         c = _cos(g[k].astype(np.float64), ref[k])
         rel = np.linalg.norm(g[k] - ref[k]) / np.linalg.norm(ref[k])
         print(f"grad {k}: cosine {c:.6f}, relative error {rel:.2e}")
@@ -101,9 +101,9 @@ def _rhs(nb, mesh, box, seed):
     return b
 
 
-def _pipeline(nb, ctx, box, train_seeds, snaps, per_snap, epochs, rounds, hidden=48):
-    """Pairs from Jacobi-PCG iterates, training, then rounds in which the
-    flexible CG with the current network produces the residuals."""
+def _pipeline(nb, ctx, box, train_seeds, snaps, per_snap, epochs, hidden=48):
+    """Pairs from the Jacobi-PCG iterates of the training seeds, then Adam
+    (two thirds of the epochs at 1e-3, the rest at 3e-4)."""
     import torch
     mesh = nb.Mesh.from_box(ctx, box)
     model = nb.Model(ctx, box.N, hidden, seed=7)
@@ -112,17 +112,11 @@ def _pipeline(nb, ctx, box, train_seeds, snaps, per_snap, epochs, rounds, hidden
         X, T = nb.Model.collect(mesh, _rhs(nb, mesh, box, s), snaps, per_snap, seed=s)
         Xs.append(X)
         Ts.append(T)
-    loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=epochs, batch=256, lr=1e-3)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    model.train(X, T, epochs=2 * epochs // 3, batch=256, lr=1e-3)
+    loss = model.train(X, T, epochs=epochs - 2 * epochs // 3, batch=256, lr=3e-4)
     model.attach(mesh)
-    for rnd in range(rounds):
-        for s in train_seeds:
-            X, T = nb.Model.collect(mesh, _rhs(nb, mesh, box, s), snaps, per_snap,
-                                    seed=s + 100 * (rnd + 1), use_learned=True)
-            Xs.append(X)
-            Ts.append(T)
-        loss = model.train(torch.cat(Xs), torch.cat(Ts), epochs=max(epochs // 2, 1), batch=256,
-                           lr=5e-4)
-    return mesh, model, loss, int(sum(x.shape[0] for x in Xs))
+    return mesh, model, loss, int(X.shape[0])
 
 
 def _compare(nb, mesh, box, seeds):
@@ -142,34 +136,37 @@ def _compare(nb, mesh, box, seeds):
 
 def test_learned_fcg_small_mesh(nb, ctx):
     box = Box(4, 4, 4, 5, 0.05)
-    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS[:4],
-                                          [1, 2, 4, 8, 16, 32, 64], 64, epochs=60, rounds=2)
+    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS,
+                                          [1, 2, 4, 8, 16, 32, 64, 100], 64, epochs=60)
     P = oracle.Problem(box)
     for s, jac, lrn, b, xl in _compare(nb, mesh, box, HELDOUT_SEEDS[:2]):
         print(f"seed {s}: Jacobi-PCG {jac['iters']} its {jac['seconds']*1e3:.2f} ms; "
               f"learned FCG {lrn['iters']} its {lrn['seconds']*1e3:.2f} ms status {lrn['status']}")
-        assert lrn["status"] in (nb.NB_OK, nb.NB_FELL_BACK)
+        assert lrn["status"] == nb.NB_OK
         assert lrn["rel_res"] < 1e-10
         assert P.true_relres(b.cpu().numpy(), xl.cpu().numpy()) < 1.01e-10
+        assert lrn["iters"] < jac["iters"]  # the network's gain over Jacobi
 
 
 def test_learned_preconditioner_workload(nb, ctx):
     """The learned-preconditioner workload: 16^3 deformed box, N = 7, about
-    10,000 element pairs from the solver's own iterates on 8 training seeds,
-    evaluated on held-out seeds against Jacobi-PCG (iterations and time)."""
+    10,000 element pairs from Jacobi-PCG iterates on 8 training seeds, a
+    network of 49,248 parameters, evaluated on held-out seeds against
+    Jacobi-PCG (iterations and time)."""
     box = LEARNED_16CUBE_N7
-    snaps = [1, 4, 16, 64, 128, 256, 512, 800]  # across the whole ~900-iteration solve
-    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS, snaps, 80, epochs=30,
-                                          rounds=1)
+    snaps = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 800]  # across the ~900-iteration solve
+    mesh, model, loss, npairs = _pipeline(nb, ctx, box, TRAIN_SEEDS, snaps, 120, epochs=60,
+                                          hidden=96)
     assert npairs >= 10000
     out = []
     for s, jac, lrn, b, xl in _compare(nb, mesh, box, HELDOUT_SEEDS[:2]):
         out.append(dict(seed=s, jacobi_iters=jac["iters"], jacobi_ms=jac["seconds"] * 1e3,
                         learned_iters=lrn["iters"], learned_ms=lrn["seconds"] * 1e3,
                         learned_status=lrn["status"], learned_rel_res=lrn["rel_res"]))
-        assert lrn["status"] in (nb.NB_OK, nb.NB_FELL_BACK)
+        assert lrn["status"] == nb.NB_OK
         assert lrn["rel_res"] < 1e-10
-    summary = dict(pairs=npairs, final_train_loss=loss, results=out)
+        assert lrn["iters"] < jac["iters"]  # the network's gain over Jacobi
+    summary = dict(pairs=npairs, params=model.nparam, final_train_loss=loss, results=out)
     print("learned workload:", json.dumps(summary))
     os.makedirs("gpurun_out", exist_ok=True)
     with open(os.path.join("gpurun_out", "learned_workload.json"), "w") as f:
