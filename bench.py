@@ -179,6 +179,39 @@ class Clocks:
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def energy_mj(device_uuid: str | None):
+    """The GPU's energy counter (mJ since the driver loaded), or None."""
+    args = ["nvidia-smi", "--query-gpu=total_energy_consumption", "--format=csv,noheader,nounits"]
+    if device_uuid:
+        args += ["-i", device_uuid]
+    try:
+        out = subprocess.run(args, capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0])
+    except Exception:
+        return None
+
+
+def energy_per_solve(run, sync, device_uuid, seconds=1.5):
+    """Joules per call of run(): the energy counter's difference over enough
+    back-to-back calls to cover about `seconds` (the paper's energy view)."""
+    sync()
+    t0 = time.perf_counter()
+    run()
+    sync()
+    reps = max(2, int(seconds / max(time.perf_counter() - t0, 1e-3)))
+    e0 = energy_mj(device_uuid)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        run()
+    sync()
+    wall = time.perf_counter() - t0
+    e1 = energy_mj(device_uuid)
+    if e0 is None or e1 is None or e1 <= e0:
+        return None
+    return {"joules_per_solve": (e1 - e0) * 1e-3 / reps, "solves": reps,
+            "mean_watts": (e1 - e0) * 1e-3 / wall}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -498,6 +531,24 @@ def main():
     tm = statistics.median(step_ms)
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
 
+    # energy to solution, mixed vs FP64 (outside the timed region; the GPU's
+    # own energy counter read by nvidia-smi before and after a run of solves)
+    def _mixed():
+        x.zero_()
+        mesh.solve(b, x, opts)
+
+    def _fp64():
+        x64.zero_()
+        mesh.solve(b, x64, o64)
+
+    sync = lambda: torch.cuda.synchronize(dev)
+    en_m = energy_per_solve(_mixed, sync, dev_uuid)
+    en_d = energy_per_solve(_fp64, sync, dev_uuid)
+    energy = {"mixed": en_m, "fp64": en_d,
+              "reduction_vs_fp64": (1.0 - en_m["joules_per_solve"] / en_d["joules_per_solve"])
+              if en_m and en_d else None,
+              "method": "nvidia-smi total_energy_consumption over back-to-back solves"}
+
     # the paper's accuracy metric: AE_k = |r_m,k - r_d,k| between the residual
     # histories of an all-FP32 CG loop (the paper's mixed version, no
     # refinement) and the FP64 loop, and their mean MAE
@@ -587,7 +638,7 @@ def main():
             "rel_res": {"mixed": stats[-1]["rel_res"], "fp64": fp64_stats["rel_res"],
                         "mixed_recomputed": true_rel},
             "mixed_vs_fp64_solution_rel_diff": sol_diff,
-            "accuracy_ae_mae": accuracy,
+            "accuracy_ae_mae": accuracy, "energy": energy,
             "all_steps_converged": ok,
             "ax": ax,
             "wall_s_timed_region": wall,

@@ -21,10 +21,10 @@ nb_status ax_cc_f32(int n, int mchoice, bool pupd, int sm_count, long long E, co
 nb_status ax_cc_f64(int n, int mchoice, bool pupd, int sm_count, long long E, const double *G,
                     const double *u, double *w, const double *r, const double *dinv, double *p,
                     CgScalars *scal, double *part, int *grid, cudaStream_t s);
-nb_status ax_tma_f32(int n, bool pupd, int sm_count, long long E, const float *G, const float *u,
+nb_status ax_tma_f32(int n, int mode, int sm_count, long long E, const float *G, const float *u,
                      float *w, const float *r, const float *dinv, float *p, CgScalars *scal,
                      double *part, int *err, int *grid, cudaStream_t s);
-nb_status ax_tma_f64(int n, bool pupd, int sm_count, long long E, const double *G,
+nb_status ax_tma_f64(int n, int mode, int sm_count, long long E, const double *G,
                      const double *u, double *w, const double *r, const double *dinv, double *p,
                      CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s);
 bool ax_tma_available_f32(int n, bool pupd);
@@ -78,10 +78,11 @@ static nb_status run_cc(nb_mesh *m, nb_prec prec, int v, bool pupd, const T *G, 
         v = 1;  // the bulk copies need 16-byte aligned vectors
     if (v == 2) {
         if (prec == NB_FP64)
-            return ax_tma_f64(m->n, pupd, m->ctx->sm_count, m->E, (const double *)G,
+            return ax_tma_f64(m->n, pupd ? 1 : 0, m->ctx->sm_count, m->E, (const double *)G,
                               (const double *)u, (double *)w, (const double *)r,
                               (const double *)dinv, (double *)p, scal, part, m->kerr, grid, s);
-        return ax_tma_f32(m->n, pupd, m->ctx->sm_count, m->E, (const float *)G, (const float *)u,
+        return ax_tma_f32(m->n, pupd ? 1 : 0, m->ctx->sm_count, m->E, (const float *)G,
+                          (const float *)u,
                           (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal,
                           part, m->kerr, grid, s);
     }
@@ -141,6 +142,21 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
     }
     set_error("bad precision %d", (int)prec);
     return NB_ERR_ARG;
+}
+
+bool ax_dir_step_available(const nb_mesh *m) { return tma_ok(m, NB_FP32); }
+
+// The fused step of flexible CG in FP32: p = z + beta p, w = A_L p, and the
+// partials of p.w (the last block forms alpha = rtz / pap).
+nb_status ax_dir_step(nb_mesh *m, const float *z, float *p, float *w, CgScalars *scal,
+                      double *pap_part, int *nparts, cudaStream_t s)
+{
+    if (!ax_dir_step_available(m) || !(aligned16(z) && aligned16(p) && aligned16(w))) {
+        set_error("flexible-CG step needs the bulk-copy operator (even n, aligned vectors)");
+        return NB_ERR_ARG;
+    }
+    return ax_tma_f32(m->n, 2, m->ctx->sm_count, m->E, m->G32, nullptr, w, z, nullptr, p, scal,
+                      pap_part, m->kerr, nparts, s);
 }
 
 }  // namespace nb

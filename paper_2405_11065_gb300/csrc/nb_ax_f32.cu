@@ -31,12 +31,12 @@ nb_status ax_cc_f32(int n, int mchoice, bool pupd, int sm_count, long long E, co
                                 grid, s);
 }
 
-nb_status ax_tma_f32(int n, bool pupd, int sm_count, long long E, const float *G,
+nb_status ax_tma_f32(int n, int mode, int sm_count, long long E, const float *G,
                       const float *u, float *w, const float *r, const float *dinv, float *p,
                       CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s)
 {
-    return dispatch_ax_tma<float>(n, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
-                                s);
+    return dispatch_ax_tma<float>(n, mode, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
+                               s);
 }
 
 bool ax_tma_available_f32(int n, bool pupd) { return tma_fits<float>(n, pupd); }

@@ -31,12 +31,12 @@ nb_status ax_cc_f64(int n, int mchoice, bool pupd, int sm_count, long long E, co
                                 grid, s);
 }
 
-nb_status ax_tma_f64(int n, bool pupd, int sm_count, long long E, const double *G,
+nb_status ax_tma_f64(int n, int mode, int sm_count, long long E, const double *G,
                       const double *u, double *w, const double *r, const double *dinv, double *p,
                       CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s)
 {
-    return dispatch_ax_tma<double>(n, pupd, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
-                                s);
+    return dispatch_ax_tma<double>(n, mode, sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid,
+                               s);
 }
 
 bool ax_tma_available_f64(int n, bool pupd) { return tma_fits<double>(n, pupd); }

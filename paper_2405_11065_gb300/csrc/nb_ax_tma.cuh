@@ -6,11 +6,17 @@
 // registers, wr/ws of one layer exchanged through shared memory.  What
 // changes is how the 6 geometric factors and the input vectors reach the
 // SM: one elected thread issues bulk copies of the whole element (G: 6 n^3
-// values; u, or r/dinv/p for the fused CG step) into the stage that the
+// values, and u for the plain operator) into the stage that the
 // block will use for its next element, completing on an mbarrier, while the
 // block computes the current element from the other stage.  The loads are
 // no longer tied to registers or warps in flight, so the kernel keeps about
 // one element per resident block in flight from HBM.
+//
+// Forms (MODE): 0 the plain operator w = A_L u; 1 the fused CG step
+// p = |dinv| r + beta p, w = A_L p (Jacobi direction); 2 the fused step of
+// flexible CG, p = z + beta p with the preconditioned residual z given in
+// place of r.  Forms 1 and 2 read r (or z), dinv and p directly from HBM,
+// add each block's partial of p.w and let the last block form alpha.
 //
 // Every wait on an mbarrier is bounded by one second of %globaltimer; a block
 // that times out sets *err, waits (bounded) for its own copies and exits.
@@ -180,12 +186,13 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
     }
 }
 
-template <typename T, int n, bool PUPD>
+template <typename T, int n, int MODE>
 __global__ void __launch_bounds__(tma_threads<n>())
 k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__restrict__ w,
          const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
          CgScalars *__restrict__ scal, double *__restrict__ part, int *__restrict__ err)
 {
+    constexpr bool PUPD = MODE != 0;
     constexpr int n2 = n * n, n3 = n2 * n;
     constexpr int STAGE = (int)ax_tma_stage_elems<T, n, PUPD>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -243,8 +250,10 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
         T ru[n], rw[n];
         if (PUPD) {  // the direction's inputs come straight from HBM, before the wait
 #pragma unroll
-            for (int k = 0; k < n; ++k)
-                ru[k] = fabs(dinv[base + k * n2]) * r[base + k * n2] + beta * p[base + k * n2];
+            for (int k = 0; k < n; ++k) {
+                const T d = MODE == 1 ? fabs(dinv[base + k * n2]) : T(1);
+                ru[k] = d * r[base + k * n2] + beta * p[base + k * n2];
+            }
         }
         const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
         if (__syncthreads_or(!ok)) break;
@@ -296,13 +305,13 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     }
 }
 
-template <typename T, int n, bool PUPD>
+template <typename T, int n, int MODE>
 nb_status launch_ax_tma(int sm_count, long long E, const T *G, const T *u, T *w, const T *r,
                         const T *dinv, T *p, CgScalars *scal, double *part, int *err,
                         int *grid_io, cudaStream_t s)
 {
-    auto kern = k_ax_tma<T, n, PUPD>;
-    constexpr size_t smem = ax_tma_smem<T, n, PUPD>();
+    auto kern = k_ax_tma<T, n, MODE>;
+    constexpr size_t smem = ax_tma_smem<T, n, MODE != 0>();
     constexpr int threads = tma_threads<n>();
     static int grid_cache = 0;
     static int sm_cached = 0;
@@ -333,26 +342,22 @@ constexpr bool tma_fits(int n, bool pupd)
 }
 
 template <typename T>
-nb_status dispatch_ax_tma(int n, bool pupd, int sm_count, long long E, const T *G, const T *u,
+nb_status dispatch_ax_tma(int n, int mode, int sm_count, long long E, const T *G, const T *u,
                           T *w, const T *r, const T *dinv, T *p, CgScalars *scal,
                           double *part, int *err, int *grid, cudaStream_t s)
 {
-    if (!tma_fits<T>(n, pupd)) {
+    if (!tma_fits<T>(n, mode != 0) || (mode == 2 && sizeof(T) != 4)) {
         set_error("bulk-copy operator variant unavailable for n=%d", n);
         return NB_ERR_ARG;
     }
-#define NB_TMA_CASE(NN)                                                                        \
-    case NN:                                                                                   \
-        if constexpr (tma_fits<T>(NN, true)) {                                                 \
-            if (pupd)                                                                          \
-                return launch_ax_tma<T, NN, true>(sm_count, E, G, u, w, r, dinv, p, scal, part, \
-                                                  err, grid, s);                               \
-        }                                                                                      \
-        if constexpr (tma_fits<T>(NN, false)) {                                                \
-            if (!pupd)                                                                         \
-                return launch_ax_tma<T, NN, false>(sm_count, E, G, u, w, r, dinv, p, scal,     \
-                                                   part, err, grid, s);                        \
-        }                                                                                      \
+#define NB_TMA_ARGS sm_count, E, G, u, w, r, dinv, p, scal, part, err, grid, s
+#define NB_TMA_CASE(NN)                                                            \
+    case NN:                                                                       \
+        if constexpr (tma_fits<T>(NN, true)) {                                     \
+            if (mode == 0) return launch_ax_tma<T, NN, 0>(NB_TMA_ARGS);            \
+            if (mode == 1) return launch_ax_tma<T, NN, 1>(NB_TMA_ARGS);            \
+            if constexpr (sizeof(T) == 4) return launch_ax_tma<T, NN, 2>(NB_TMA_ARGS); \
+        }                                                                          \
         break;
     switch (n) {
         NB_TMA_CASE(2)
@@ -367,6 +372,7 @@ nb_status dispatch_ax_tma(int n, bool pupd, int sm_count, long long E, const T *
             break;
     }
 #undef NB_TMA_CASE
+#undef NB_TMA_ARGS
     set_error("bulk-copy operator variant unavailable for n=%d", n);
     return NB_ERR_ARG;
 }

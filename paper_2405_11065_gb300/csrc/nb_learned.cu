@@ -40,6 +40,10 @@ struct nb_model {
     int cap = 0;
     float *Z = nullptr, *H = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *nrm = nullptr;
     float *gpart = nullptr;  // per-block partials of the gain gradient
+    // BF16 copy of W for the fused preconditioner, [dp][h] with dp = d rounded
+    // up to 16 (zero rows); refreshed when the weights changed (step)
+    __nv_bfloat16 *Wb = nullptr;
+    int64_t wb_step = -1;
     float *X = nullptr;
     double *lpart = nullptr;
 };
@@ -488,6 +492,269 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
 }
 
 // ---------------------------------------------------------------------------
+// fused preconditioner for the flexible CG: z, (z, w_prev), (r, z) in one pass
+// ---------------------------------------------------------------------------
+//
+// Tiles of 16 elements (one m16 row tile), persistent blocks of 8 warps with
+// the BF16 weights resident in shared memory ([dp][h+8], padded rows so that
+// the eight row addresses of each ldmatrix fall in distinct bank groups).
+// Per tile: r (FP32) staged with its row norms, X = r / |r| in BF16;
+// H = a * gelu(X W) by mma.sync (W as the col-major B operand through
+// ldmatrix.trans); z = |dinv| r on the element-boundary nodes; on interior
+// nodes z = |dinv| r + |r_e| (H W^T) (W rows as the B operand, ldmatrix);
+// and the owner-copy partials of (z, w_prev) and (r, z).  The last block
+// forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on the first step)
+// and rtz = (r, z); since r_k is orthogonal to p_(k-1), (r, p) = (r, z) and
+// the operator's last block forms alpha = rtz / pap.
+
+constexpr int kLpcThreads = 256;
+
+__host__ __device__ constexpr int lpc_dp(int d) { return (d + 15) / 16 * 16; }
+
+static size_t lpc_smem(int d, int h)
+{
+    const int dp = lpc_dp(d);
+    return sizeof(__nv_bfloat16) * ((size_t)dp * (h + 8) + 16 * (size_t)(dp + 8) + 16 * (size_t)(h + 8)) +
+           sizeof(float) * (16 * (size_t)dp + 16 + h);
+}
+
+static bool lpc_fits(int d, int h)
+{
+    return h % 16 == 0 && h <= 128 && d <= 512 && lpc_smem(d, h) <= 227 * 1024;
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t a[4], const void *p)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(s));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t b[2], const void *p)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(b[0]), "=r"(b[1])
+                 : "r"(s));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t b[2], const void *p)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(b[0]), "=r"(b[1])
+                 : "r"(s));
+}
+
+__global__ void k_w_bf16(int d, int dp, int h, const float *__restrict__ W,
+                         __nv_bfloat16 *__restrict__ Wb)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dp * h; i += gridDim.x * blockDim.x)
+        Wb[i] = __float2bfloat16_rn(i < d * h ? W[i] : 0.f);
+}
+
+__global__ void __launch_bounds__(kLpcThreads, 1)
+k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__restrict__ dinv,
+      const float *__restrict__ wold, float *__restrict__ z, const __nv_bfloat16 *__restrict__ Wb,
+      const float *__restrict__ gain, CgScalars *sc, double *__restrict__ part)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int dp = lpc_dp(d), hs = h + 8, xs = dp + 8;
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [dp][hs]
+    __nv_bfloat16 *Xs = Ws + (size_t)dp * hs;                          // [16][xs]
+    __nv_bfloat16 *Hs = Xs + 16 * xs;                                  // [16][hs]
+    float *Rs = reinterpret_cast<float *>(Hs + 16 * hs);               // [16][dp]
+    float *nrm = Rs + 16 * dp;                                         // [16]
+    float *as = nrm + 16;                                              // [h]
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    // the weights: 16-byte chunks of each row into the padded rows
+    const int chunks = h / 8;
+    for (int c = tid; c < dp * chunks; c += blockDim.x) {
+        const int row = c / chunks, col = (c - row * chunks) * 8;
+        *reinterpret_cast<uint4 *>(Ws + (size_t)row * hs + col) =
+            *reinterpret_cast<const uint4 *>(Wb + (size_t)row * h + col);
+    }
+    for (int c = tid; c < h; c += blockDim.x) as[c] = gain[c];
+    auto interior = [&](int q) {
+        const int i = q % n, j = (q / n) % n, k = q / (n * n);
+        return q < d && i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1;
+    };
+    DotAcc<float> zw, rz;
+    const int tiles = (E + 15) / 16;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int e0 = tile * 16;
+        __syncthreads();  // the previous tile is done with Rs, Xs, Hs (and Ws is loaded)
+        // 1. r, row norms, X = r / |r| (warp w: rows w and w + 8)
+        for (int rr = warp; rr < 16; rr += kLpcThreads / 32) {
+            const int e = e0 + rr;
+            float ss = 0.f;
+            for (int q = lane; q < dp; q += 32) {
+                const float v = (e < E && q < d) ? r[(size_t)e * d + q] : 0.f;
+                Rs[rr * dp + q] = v;
+                ss += v * v;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float nv = sqrtf(ss);
+            const float inv = nv > 0.f ? 1.0f / nv : 0.f;
+            for (int q = lane; q < dp; q += 32) Xs[rr * xs + q] = __float2bfloat16_rn(Rs[rr * dp + q] * inv);
+            if (lane == 0) nrm[rr] = nv;
+        }
+        __syncthreads();
+        // 2. H = a * gelu(X W): warp w takes the column tiles w, w + 8, ...
+        for (int nt = warp; nt < h / 8; nt += kLpcThreads / 32) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k0 = 0; k0 < dp; k0 += 16) {
+                uint32_t a[4], b[2];
+                const int mi = lane >> 3, ri = lane & 7;
+                ldsm_x4(a, Xs + ((mi & 1) * 8 + ri) * xs + k0 + (mi >> 1) * 8);
+                ldsm_x2_t(b, Ws + (size_t)(k0 + (mi & 1) * 8 + ri) * hs + nt * 8);
+                mma_bf16(acc, a, b);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const int row = g + 8 * (hh >> 1), col = nt * 8 + 2 * tq + (hh & 1);
+                Hs[row * hs + col] = __float2bfloat16_rn(as[col] * gelu_f(acc[hh]));
+            }
+        }
+        // 3. element-boundary nodes: the Jacobi step alone
+        for (int idx = tid; idx < 16 * d; idx += blockDim.x) {
+            const int rr = idx / d, q = idx - rr * d, e = e0 + rr;
+            if (e >= E || interior(q)) continue;
+            const size_t o = (size_t)e * d + q;
+            const float dv = dinv[o], rv = Rs[rr * dp + q];
+            const float zv = fabsf(dv) * rv;
+            z[o] = zv;
+            if (!signbit(dv)) {
+                zw.add(zv * wold[o]);
+                rz.add(rv * zv);
+            }
+        }
+        __syncthreads();  // Hs complete
+        // 4. interior nodes: z = |dinv| r + |r_e| (H W^T)
+        for (int nt = warp; nt < dp / 8; nt += kLpcThreads / 32) {
+            const bool any = __any_sync(0xffffffffu, lane < 8 && interior(nt * 8 + lane));
+            if (!any) continue;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k0 = 0; k0 < h; k0 += 16) {
+                uint32_t a[4], b[2];
+                const int mi = lane >> 3, ri = lane & 7;
+                ldsm_x4(a, Hs + ((mi & 1) * 8 + ri) * hs + k0 + (mi >> 1) * 8);
+                ldsm_x2(b, Ws + (size_t)(nt * 8 + ri) * hs + k0 + (mi & 1) * 8);
+                mma_bf16(acc, a, b);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const int rr = g + 8 * (hh >> 1), q = nt * 8 + 2 * tq + (hh & 1), e = e0 + rr;
+                if (e >= E || !interior(q)) continue;
+                const size_t o = (size_t)e * d + q;
+                const float rv = Rs[rr * dp + q];
+                const float zv = fabsf(dinv[o]) * rv + acc[hh] * nrm[rr];
+                z[o] = zv;
+                zw.add(zv * wold[o]);  // interior nodes have one copy: always the owner
+                rz.add(rv * zv);
+            }
+        }
+    }
+    const double tzw = block_sum(zw.value(), sred);
+    const double trz = block_sum(rz.value(), sred);
+    if (tid == 0) {
+        part[blockIdx.x] = tzw;
+        part[gridDim.x + blockIdx.x] = trz;
+    }
+    if (last_block(&sc->tick_upd)) {
+        const double szw = sum_partials(part, gridDim.x, sred);
+        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
+        if (tid == 0) {
+            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
+            sc->rtz = srz;
+            sc->rp = srz;
+            if (!isfinite(sc->beta) || !isfinite(srz)) {
+                sc->done = 1;
+                sc->status = NB_BREAKDOWN;
+            }
+        }
+    }
+}
+
+// x += alpha p, r -= alpha w (alpha from the operator's last block), the
+// owner-copy partials of (r, r), and in the last block the flexible-CG
+// bookkeeping: iteration count, history, pap_prev, the stopping tests.
+__global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__ x,
+                                  float *__restrict__ r, const float *__restrict__ p,
+                                  const float *__restrict__ w, const float *__restrict__ sgn,
+                                  double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    DotAcc<float> acc;
+    const int64_t n4 = nL / 4;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        float4 xv = reinterpret_cast<float4 *>(x)[q];
+        float4 rv = reinterpret_cast<float4 *>(r)[q];
+        const float4 pv = reinterpret_cast<const float4 *>(p)[q];
+        const float4 wv = reinterpret_cast<const float4 *>(w)[q];
+        const float4 dv = reinterpret_cast<const float4 *>(sgn)[q];
+        xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+        rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
+        if (!signbit(dv.x)) acc.add(rv.x * rv.x);
+        if (!signbit(dv.y)) acc.add(rv.y * rv.y);
+        if (!signbit(dv.z)) acc.add(rv.z * rv.z);
+        if (!signbit(dv.w)) acc.add(rv.w * rv.w);
+        reinterpret_cast<float4 *>(x)[q] = xv;
+        reinterpret_cast<float4 *>(r)[q] = rv;
+    }
+    for (int64_t l = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        x[l] += alpha * p[l];
+        const float rl = r[l] - alpha * w[l];
+        r[l] = rl;
+        if (!signbit(sgn[l])) acc.add(rl * rl);
+    }
+    const double t = block_sum(acc.value(), sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (!last_block(&sc->tick_upd)) return;
+    const double rtr = sum_partials(part, gridDim.x, sred);
+    if (threadIdx.x == 0) {
+        sc->pap_prev = sc->pap;
+        sc->rtr = rtr;
+        const int it = sc->iter + 1;
+        sc->iter = it;
+        const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
+        const double rel = sqrt(rtr / bn);
+        sc->relres = rel;
+        if (sc->hist && it <= sc->hist_cap) sc->hist[it - 1] = rel;
+        if (!isfinite(rel)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else if (rel < sc->tol) {
+            sc->done = 1;
+        } else if (it >= sc->maxit) {
+            sc->done = 1;
+            sc->status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+static nb_status ensure_wb(nb_model *md, cudaStream_t s)
+{
+    const int dp = lpc_dp(md->d);
+    if (!md->Wb) NB_CUDA(cudaMalloc(&md->Wb, sizeof(__nv_bfloat16) * (size_t)dp * md->h));
+    if (md->wb_step != md->step || md->wb_step < 0) {
+        k_w_bf16<<<64, 256, 0, s>>>(md->d, dp, md->h, md->W, md->Wb);
+        NB_CUDA(cudaGetLastError());
+        md->wb_step = md->step;
+    }
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------------------
 // flexible CG (inner solve of the refinement) with the learned preconditioner
 // ---------------------------------------------------------------------------
 
@@ -628,9 +895,16 @@ __global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int c
     }
 }
 
+bool ax_dir_step_available(const nb_mesh *m);
+nb_status ax_dir_step(nb_mesh *m, const float *z, float *p, float *w, CgScalars *scal,
+                      double *pap_part, int *nparts, cudaStream_t s);
+
 // The inner solve of a refinement step: ws.r holds the scaled residual, ws.x
-// starts at zero.  Host-launched iterations, the stopping state checked
-// every few iterations (all kernels skip their work once it is set).
+// starts at zero.  One flexible-CG step is four kernels when the fused forms
+// apply (k_lpc; the operator's direction form with alpha; the summation;
+// k_fcg_step_update), otherwise the general path below.  Captured in a graph
+// with a while node (two steps per body), or host-launched with the stopping
+// state checked every few steps (all kernels skip their work once it is set).
 nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
 {
     (void)o;
@@ -645,6 +919,13 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     float *z = (float *)ws.z, *wprev = (float *)ws.aux;
     double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
     NB_TRY(model_scratch(md, (int)m->E));  // before any capture: it may allocate
+    const bool fast = prec == NB_FP32 && ax_dir_step_available(m) && lpc_fits(md->d, md->h);
+    const size_t lsm = lpc_smem(md->d, md->h);
+    const int lgrid = std::max(1, std::min((int)((m->E + 15) / 16), m->ctx->sm_count));
+    if (fast) {
+        NB_TRY(ensure_wb(md, s));  // outside any capture: refreshed in place when W changed
+        NB_CUDA(cudaFuncSetAttribute(k_lpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+    }
     NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
     NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
     k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
@@ -653,6 +934,17 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     m->launches += 2;
     // one flexible-CG step; w receives A p, wprev holds the previous A p
     auto step = [&](float *wcur, float *wold) -> nb_status {
+        if (fast) {
+            k_lpc<<<lgrid, kLpcThreads, lsm, s>>>((int)m->E, m->n, md->d, md->h, r, sgn, wold, z,
+                                                  md->Wb, md->a, ws.scal, P0);
+            NB_CUDA(cudaGetLastError());
+            int nparts = 0;
+            NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
+            NB_TRY(dssum(m, prec, wcur, 1, s));
+            k_fcg_step_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
+            NB_CUDA(cudaGetLastError());
+            return NB_OK;
+        }
         NB_TRY(model_apply(m, md, r, z, s));
         k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, z, wold, sgn, P0);
         k_fcg_p<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, P0, g, z, r, p, sgn, P1);
@@ -710,13 +1002,15 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         NB_CUDA(cudaGraphLaunch(ws.exec2, s));
         NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
-        m->launches += 19 * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
+        m->launches += (fast ? 9 : 19) * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
         return NB_OK;
     }
     for (int it = 0;; ++it) {
         NB_TRY(step(w, wprev));
         std::swap(w, wprev);  // w of this step is w_prev of the next
-        m->launches += 9;  // row norms, 2 products, 2 dots, operator, summation, update, finish
+        // fused: preconditioner, operator, summation, update; general: row
+        // norms, 2 products, 2 dots, operator, summation, update, finish
+        m->launches += fast ? 4 : 9;
         if ((it & 7) == 7) {
             NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars),
                                     cudaMemcpyDeviceToHost, s));
@@ -789,6 +1083,7 @@ extern "C" nb_status nb_model_destroy(nb_model *md)
                      md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
     cudaFree(md->lpart);
+    cudaFree(md->Wb);
     delete md;
     return NB_OK;
 }
@@ -802,8 +1097,10 @@ extern "C" nb_status nb_model_params(nb_model *md, float *get_host, const float 
     }
     NB_CUDA(cudaSetDevice(md->ctx->device));
     if (nparam) *nparam = md->nparam;
-    if (set_host)
+    if (set_host) {
         NB_CUDA(cudaMemcpy(md->W, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
+        md->wb_step = -1;  // the BF16 copy of the fused preconditioner is stale
+    }
     if (get_host)
         NB_CUDA(cudaMemcpy(get_host, md->W, sizeof(float) * md->nparam, cudaMemcpyDeviceToHost));
     return NB_OK;
