@@ -426,7 +426,6 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
     cudaStream_t s = m->ctx->stream;
     Workspace &ws = prec == NB_FP64 ? m->ws64 : m->ws32;
     NB_TRY(ensure_ws(m, ws, prec == NB_FP64 ? 8 : 4, 0));
-    NB_CUDA(cudaMemsetAsync(ws.scal, 0, sizeof(CgScalars), s));  // beta = 0, not done
     const int saved = m->ax_cfg[prec].variant;
     if (variant >= 0) m->ax_cfg[prec].variant = variant;
     const void *dinv = prec == NB_FP64 ? (const void *)m->dinv64 : (const void *)m->dinv32;
@@ -436,6 +435,10 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
         if (cudaEventCreate(&e) != cudaSuccess) st = NB_ERR_CUDA;
     for (int r = 0; st == NB_OK && r < reps; ++r) {
         if (flush_dev && flush_bytes) cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, s);
+        // beta = 0 and not done before every launch: the fused step's last
+        // block may stop the scalars (pap <= 0 on arbitrary data), and a
+        // stopped state would let the next launch return at once
+        cudaMemsetAsync(ws.scal, 0, sizeof(CgScalars), s);
         cudaEventRecord(ev[2 * r], s);
         if (cg_step)
             st = ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, nullptr, s);

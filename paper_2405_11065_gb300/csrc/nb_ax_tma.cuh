@@ -23,78 +23,10 @@
 #pragma once
 
 #include "nb_ax_impl.cuh"
+#include "nb_bulk.cuh"
 #include "nb_reduce.cuh"
 
 namespace nb {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_fence()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// Plain arrival: completes the phase of a barrier that expects no bytes.
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Global -> shared bulk copy completing on bar (bytes: multiple of 16, both
-// addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase with the given parity; false after one second.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
-    return true;
-}
 
 template <int n>
 constexpr int tma_threads()
@@ -114,6 +46,18 @@ template <typename T, int n, bool PUPD>
 constexpr size_t ax_tma_smem()
 {
     return sizeof(T) * (2 * ax_tma_stage_elems<T, n, PUPD>() + (PUPD ? n * n * n : 0) + 4 * n * n);
+}
+
+// Blocks per SM that the launch bound asks the compiler to keep room for
+// (registers): as many as shared memory admits, for FP32 at n >= 8.
+template <typename T, int n, bool PUPD>
+constexpr int tma_min_blocks()
+{
+    if (sizeof(T) != 4 || n < 8) return 1;
+    const int by_smem = (int)((228 * 1024) / (ax_tma_smem<T, n, PUPD>() + 1024));
+    const int by_threads = 2048 / tma_threads<n>();
+    const int b = by_smem < by_threads ? by_smem : by_threads;
+    return b < 1 ? 1 : b;
 }
 
 template <typename T>
@@ -187,7 +131,7 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
 }
 
 template <typename T, int n, int MODE>
-__global__ void __launch_bounds__(tma_threads<n>())
+__global__ void __launch_bounds__(tma_threads<n>(), (tma_min_blocks<T, n, MODE != 0>()))
 k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__restrict__ w,
          const T *__restrict__ r, const T *__restrict__ dinv, T *__restrict__ p,
          CgScalars *__restrict__ scal, double *__restrict__ part, int *__restrict__ err)
@@ -241,6 +185,22 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     };
     if (tid == 0 && mine > 0) issue(0);
 
+    // the fused forms read their column of r (or z), dinv and p straight from
+    // HBM, one element ahead: the loads for element t+1 are in flight while
+    // element t is computed (elements own disjoint nodes, so p of t+1 is not
+    // written by t)
+    T nr[n], nd[n], np[n];
+    auto fetch = [&](long long tt) {
+        const size_t b2 = (size_t)(blockIdx.x + tt * gridDim.x) * n3 + ij;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            nr[k] = r[b2 + k * n2];
+            nd[k] = MODE == 1 ? dinv[b2 + k * n2] : T(1);
+            np[k] = p[b2 + k * n2];
+        }
+    };
+    if (PUPD && mine > 0) fetch(0);
+
     double acc = 0.0;
     long long t = 0;
     for (; t < mine; ++t) {
@@ -248,12 +208,10 @@ k_ax_tma(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
         const long long e = blockIdx.x + t * gridDim.x;
         const size_t base = (size_t)e * n3 + ij;
         T ru[n], rw[n];
-        if (PUPD) {  // the direction's inputs come straight from HBM, before the wait
+        if (PUPD) {
 #pragma unroll
-            for (int k = 0; k < n; ++k) {
-                const T d = MODE == 1 ? fabs(dinv[base + k * n2]) : T(1);
-                ru[k] = d * r[base + k * n2] + beta * p[base + k * n2];
-            }
+            for (int k = 0; k < n; ++k) ru[k] = fabs(nd[k]) * nr[k] + beta * np[k];
+            if (t + 1 < mine) fetch(t + 1);
         }
         const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
         if (__syncthreads_or(!ok)) break;

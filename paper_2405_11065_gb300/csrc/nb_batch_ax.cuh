@@ -24,7 +24,7 @@ namespace nb {
 // by one second; on a timeout the block sets *err, stops the element's
 // problem (NB_BREAKDOWN), waits (bounded) for its own copies and exits.
 template <typename T, int n>
-__global__ void __launch_bounds__(tma_threads<n>())
+__global__ void __launch_bounds__(tma_threads<n>(), (tma_min_blocks<T, n, true>()))
 k_bax_tma(long long e_first, const int32_t *__restrict__ list, const int *__restrict__ cnt,
           const T *__restrict__ G, T *__restrict__ w, const T *__restrict__ r,
           const T *__restrict__ dinv, T *__restrict__ p, const int32_t *__restrict__ elem_prob,
@@ -74,6 +74,21 @@ k_bax_tma(long long e_first, const int32_t *__restrict__ list, const int *__rest
         bulk_g2s(stage + (t & 1) * STAGE, G + (size_t)(eb - e_first) * 6 * n3, gbytes, b);
     };
     if (tid == 0 && mine > 0) issue(0);
+    // the next live element's column of r, dinv and p, loaded one element
+    // ahead (elements own disjoint nodes)
+    T nr[n], nd[n], np[n];
+    auto fetch = [&](long long tt) {
+        const long long eb = list[blockIdx.x + tt * gridDim.x];
+        if (bs[elem_prob[eb]].done) return;
+        const size_t b2 = (size_t)(eb - e_first) * n3 + ij;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            nr[k] = r[b2 + k * n2];
+            nd[k] = dinv[b2 + k * n2];
+            np[k] = p[b2 + k * n2];
+        }
+    };
+    if (mine > 0) fetch(0);
     long long t = 0;
     for (; t < mine; ++t) {
         if (tid == 0 && t + 1 < mine) issue(t + 1);  // its stage was released at the end of t-1
@@ -85,9 +100,9 @@ k_bax_tma(long long e_first, const int32_t *__restrict__ list, const int *__rest
         if (live) {
             const T beta = (T)bs[prob].beta;
 #pragma unroll
-            for (int k = 0; k < n; ++k)
-                ru[k] = fabs(dinv[base + k * n2]) * r[base + k * n2] + beta * p[base + k * n2];
+            for (int k = 0; k < n; ++k) ru[k] = fabs(nd[k]) * nr[k] + beta * np[k];
         }
+        if (t + 1 < mine) fetch(t + 1);
         const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
         if (__syncthreads_or(!ok)) break;
         if (!live) continue;  // nothing of this element was read or written

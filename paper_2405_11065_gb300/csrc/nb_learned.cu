@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "nb_bulk.cuh"
 #include "nb_cg_dev.cuh"
 
 struct nb_model {
@@ -495,17 +496,18 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
 // fused preconditioner for the flexible CG: z, (z, w_prev), (r, z) in one pass
 // ---------------------------------------------------------------------------
 //
-// Tiles of 16 elements (one m16 row tile), persistent blocks of 8 warps with
-// the BF16 weights resident in shared memory ([dp][h+8], padded rows so that
-// the eight row addresses of each ldmatrix fall in distinct bank groups).
-// Per tile: r (FP32) staged with its row norms, X = r / |r| in BF16;
-// H = a * gelu(X W) by mma.sync (W as the col-major B operand through
-// ldmatrix.trans); z = |dinv| r on the element-boundary nodes; on interior
-// nodes z = |dinv| r + |r_e| (H W^T) (W rows as the B operand, ldmatrix);
-// and the owner-copy partials of (z, w_prev) and (r, z).  The last block
-// forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on the first step)
-// and rtz = (r, z); since r_k is orthogonal to p_(k-1), (r, p) = (r, z) and
-// the operator's last block forms alpha = rtz / pap.
+// Tiles of 16 consecutive elements (one m16 row tile), persistent blocks of
+// 8 warps with the BF16 weights resident in shared memory ([dp][h+8], padded
+// rows so that the eight row addresses of each ldmatrix fall in distinct
+// bank groups).  Per tile: the tile's residual (16 d contiguous floats) by
+// one bulk copy; row norms and X = r / |r| in BF16; H = a * gelu(X W) by
+// mma.sync (W as the col-major B operand through ldmatrix.trans); the
+// correction C = |r_e| (H W^T) on interior nodes (W rows as the B operand);
+// then one coalesced pass z = |dinv| r + C with the owner-copy partials of
+// (z, w_prev) and (r, z).  The last block forms the flexible-CG
+// beta = -(z, w_prev) / pap_prev (0 on the first step) and rtz = (r, z);
+// since r_k is orthogonal to p_(k-1), (r, p) = (r, z) and the operator's last
+// block forms alpha = rtz / pap.  Needs d a multiple of 4 (n even).
 
 constexpr int kLpcThreads = 256;
 
@@ -514,13 +516,14 @@ __host__ __device__ constexpr int lpc_dp(int d) { return (d + 15) / 16 * 16; }
 static size_t lpc_smem(int d, int h)
 {
     const int dp = lpc_dp(d);
-    return sizeof(__nv_bfloat16) * ((size_t)dp * (h + 8) + 16 * (size_t)(dp + 8) + 16 * (size_t)(h + 8)) +
-           sizeof(float) * (16 * (size_t)dp + 16 + h);
+    return sizeof(__nv_bfloat16) *
+               ((size_t)dp * (h + 8) + 16 * (size_t)(dp + 8) + 16 * (size_t)(h + 8)) +
+           sizeof(float) * (2 * 16 * (size_t)d + 16 + h);
 }
 
 static bool lpc_fits(int d, int h)
 {
-    return h % 16 == 0 && h <= 128 && d <= 512 && lpc_smem(d, h) <= 227 * 1024;
+    return d % 4 == 0 && h % 16 == 0 && h <= 128 && d <= 512 && lpc_smem(d, h) <= 227 * 1024;
 }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t a[4], const void *p)
@@ -557,20 +560,28 @@ __global__ void k_w_bf16(int d, int dp, int h, const float *__restrict__ W,
 __global__ void __launch_bounds__(kLpcThreads, 1)
 k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__restrict__ dinv,
       const float *__restrict__ wold, float *__restrict__ z, const __nv_bfloat16 *__restrict__ Wb,
-      const float *__restrict__ gain, CgScalars *sc, double *__restrict__ part)
+      const float *__restrict__ gain, CgScalars *sc, double *__restrict__ part, int *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int dp = lpc_dp(d), hs = h + 8, xs = dp + 8;
     __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [dp][hs]
     __nv_bfloat16 *Xs = Ws + (size_t)dp * hs;                          // [16][xs]
     __nv_bfloat16 *Hs = Xs + 16 * xs;                                  // [16][hs]
-    float *Rs = reinterpret_cast<float *>(Hs + 16 * hs);               // [16][dp]
-    float *nrm = Rs + 16 * dp;                                         // [16]
+    float *Rs = reinterpret_cast<float *>(Hs + 16 * hs);               // [16][d] (bulk copy)
+    float *Cs = Rs + 16 * d;                                           // [16][d]
+    float *nrm = Cs + 16 * d;                                          // [16]
     float *as = nrm + 16;                                              // [h]
+    __shared__ __align__(8) uint64_t bar;
     __shared__ double sred[32];
+    __shared__ int sbad;
     if (sc->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, tq = lane & 3;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        sbad = 0;
+    }
     // the weights: 16-byte chunks of each row into the padded rows
     const int chunks = h / 8;
     for (int c = tid; c < dp * chunks; c += blockDim.x) {
@@ -585,24 +596,33 @@ k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__re
     };
     DotAcc<float> zw, rz;
     const int tiles = (E + 15) / 16;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int e0 = tile * 16;
-        __syncthreads();  // the previous tile is done with Rs, Xs, Hs (and Ws is loaded)
-        // 1. r, row norms, X = r / |r| (warp w: rows w and w + 8)
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, phase ^= 1u) {
+        const int e0 = tile * 16, rows = min(16, E - e0);
+        __syncthreads();  // the previous tile is done with every buffer (and Ws is loaded)
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)(sizeof(float) * rows * d);  // multiple of 16: d % 4 == 0
+            mbar_expect_tx(&bar, bytes);
+            bulk_g2s(Rs, r + (size_t)e0 * d, bytes, &bar);
+        }
+        for (int q = tid; q < 16 * d; q += blockDim.x) Cs[q] = 0.f;
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) sbad = 1;
+            break;
+        }
+        // 1. row norms, X = r / |r| (warp w: rows w and w + 8)
         for (int rr = warp; rr < 16; rr += kLpcThreads / 32) {
-            const int e = e0 + rr;
             float ss = 0.f;
-            for (int q = lane; q < dp; q += 32) {
-                const float v = (e < E && q < d) ? r[(size_t)e * d + q] : 0.f;
-                Rs[rr * dp + q] = v;
-                ss += v * v;
-            }
+            if (rr < rows)
+                for (int q = lane; q < d; q += 32) ss += Rs[rr * d + q] * Rs[rr * d + q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
             const float nv = sqrtf(ss);
             const float inv = nv > 0.f ? 1.0f / nv : 0.f;
-            for (int q = lane; q < dp; q += 32) Xs[rr * xs + q] = __float2bfloat16_rn(Rs[rr * dp + q] * inv);
-            if (lane == 0) nrm[rr] = nv;
+            for (int q = lane; q < dp; q += 32)
+                Xs[rr * xs + q] = __float2bfloat16_rn((rr < rows && q < d) ? Rs[rr * d + q] * inv : 0.f);
+            if (lane == 0) nrm[rr] = rr < rows ? nv : 0.f;
         }
         __syncthreads();
         // 2. H = a * gelu(X W): warp w takes the column tiles w, w + 8, ...
@@ -621,21 +641,8 @@ k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__re
                 Hs[row * hs + col] = __float2bfloat16_rn(as[col] * gelu_f(acc[hh]));
             }
         }
-        // 3. element-boundary nodes: the Jacobi step alone
-        for (int idx = tid; idx < 16 * d; idx += blockDim.x) {
-            const int rr = idx / d, q = idx - rr * d, e = e0 + rr;
-            if (e >= E || interior(q)) continue;
-            const size_t o = (size_t)e * d + q;
-            const float dv = dinv[o], rv = Rs[rr * dp + q];
-            const float zv = fabsf(dv) * rv;
-            z[o] = zv;
-            if (!signbit(dv)) {
-                zw.add(zv * wold[o]);
-                rz.add(rv * zv);
-            }
-        }
         __syncthreads();  // Hs complete
-        // 4. interior nodes: z = |dinv| r + |r_e| (H W^T)
+        // 3. C = |r_e| (H W^T) on interior nodes
         for (int nt = warp; nt < dp / 8; nt += kLpcThreads / 32) {
             const bool any = __any_sync(0xffffffffu, lane < 8 && interior(nt * 8 + lane));
             if (!any) continue;
@@ -649,16 +656,41 @@ k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__re
             }
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
-                const int rr = g + 8 * (hh >> 1), q = nt * 8 + 2 * tq + (hh & 1), e = e0 + rr;
-                if (e >= E || !interior(q)) continue;
-                const size_t o = (size_t)e * d + q;
-                const float rv = Rs[rr * dp + q];
-                const float zv = fabsf(dinv[o]) * rv + acc[hh] * nrm[rr];
-                z[o] = zv;
-                zw.add(zv * wold[o]);  // interior nodes have one copy: always the owner
-                rz.add(rv * zv);
+                const int rr = g + 8 * (hh >> 1), q = nt * 8 + 2 * tq + (hh & 1);
+                if (rr < rows && interior(q)) Cs[rr * d + q] = acc[hh] * nrm[rr];
             }
         }
+        __syncthreads();  // Cs complete
+        // 4. z = |dinv| r + C over the tile, four nodes per 16-byte access
+        const int n4 = rows * d / 4;
+        const float4 *dv4 = reinterpret_cast<const float4 *>(dinv + (size_t)e0 * d);
+        const float4 *wo4 = reinterpret_cast<const float4 *>(wold + (size_t)e0 * d);
+        float4 *z4 = reinterpret_cast<float4 *>(z + (size_t)e0 * d);
+        const float4 *r4 = reinterpret_cast<const float4 *>(Rs);
+        const float4 *c4 = reinterpret_cast<const float4 *>(Cs);
+        for (int q = tid; q < n4; q += blockDim.x) {
+            const float4 dv = dv4[q], wv = wo4[q], rv = r4[q], cv = c4[q];
+            float4 zv;
+            zv.x = fabsf(dv.x) * rv.x + cv.x;
+            zv.y = fabsf(dv.y) * rv.y + cv.y;
+            zv.z = fabsf(dv.z) * rv.z + cv.z;
+            zv.w = fabsf(dv.w) * rv.w + cv.w;
+            z4[q] = zv;
+            if (!signbit(dv.x)) { zw.add(zv.x * wv.x); rz.add(rv.x * zv.x); }
+            if (!signbit(dv.y)) { zw.add(zv.y * wv.y); rz.add(rv.y * zv.y); }
+            if (!signbit(dv.z)) { zw.add(zv.z * wv.z); rz.add(rv.z * zv.z); }
+            if (!signbit(dv.w)) { zw.add(zv.w * wv.w); rz.add(rv.w * zv.w); }
+        }
+    }
+    __syncthreads();
+    if (sbad) {  // the residual tile never arrived: record it, let the copy land, stop
+        if (tid == 0) {
+            atomicExch(err, 1);
+            sc->status = NB_BREAKDOWN;
+            sc->done = 1;
+            mbar_wait_bounded(&bar, phase);
+        }
+        return;
     }
     const double tzw = block_sum(zw.value(), sred);
     const double trz = block_sum(rz.value(), sred);
@@ -936,7 +968,7 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     auto step = [&](float *wcur, float *wold) -> nb_status {
         if (fast) {
             k_lpc<<<lgrid, kLpcThreads, lsm, s>>>((int)m->E, m->n, md->d, md->h, r, sgn, wold, z,
-                                                  md->Wb, md->a, ws.scal, P0);
+                                                  md->Wb, md->a, ws.scal, P0, m->kerr);
             NB_CUDA(cudaGetLastError());
             int nparts = 0;
             NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
