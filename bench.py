@@ -179,37 +179,49 @@ class Clocks:
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def energy_mj(device_uuid: str | None):
-    """The GPU's energy counter (mJ since the driver loaded), or None."""
-    args = ["nvidia-smi", "--query-gpu=total_energy_consumption", "--format=csv,noheader,nounits"]
-    if device_uuid:
-        args += ["-i", device_uuid]
-    try:
-        out = subprocess.run(args, capture_output=True, text=True, timeout=20).stdout.strip()
-        return float(out.splitlines()[0])
-    except Exception:
-        return None
-
-
-def energy_per_solve(run, sync, device_uuid, seconds=1.5):
-    """Joules per call of run(): the energy counter's difference over enough
-    back-to-back calls to cover about `seconds` (the paper's energy view)."""
+def energy_per_solve(run, sync, device_uuid, seconds=2.0):
+    """Joules per call of run() (the paper's energy view): nvidia-smi samples
+    the board power every 50 ms during enough back-to-back calls to cover
+    about `seconds`; energy = mean power x wall time / calls."""
     sync()
     t0 = time.perf_counter()
     run()
     sync()
     reps = max(2, int(seconds / max(time.perf_counter() - t0, 1e-3)))
-    e0 = energy_mj(device_uuid)
+    path = tempfile.mktemp(suffix=".csv")
+    args = ["nvidia-smi", "--query-gpu=power.draw", "--format=csv,noheader,nounits", "-lms", "50"]
+    if device_uuid:
+        args += ["-i", device_uuid]
+    try:
+        fh = open(path, "w")
+        proc = subprocess.Popen(args, stdout=fh, stderr=subprocess.DEVNULL)
+    except Exception:
+        return None
+    time.sleep(0.3)  # the sampler's first reading
     t0 = time.perf_counter()
     for _ in range(reps):
         run()
     sync()
     wall = time.perf_counter() - t0
-    e1 = energy_mj(device_uuid)
-    if e0 is None or e1 is None or e1 <= e0:
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    fh.close()
+    watts = []
+    for line in open(path):
+        try:
+            watts.append(float(line.strip()))
+        except ValueError:
+            pass
+    os.unlink(path)
+    if len(watts) < 3:
         return None
-    return {"joules_per_solve": (e1 - e0) * 1e-3 / reps, "solves": reps,
-            "mean_watts": (e1 - e0) * 1e-3 / wall}
+    watts = watts[1:]  # drop the reading taken before the loop started
+    mean_w = statistics.mean(watts)
+    return {"joules_per_solve": mean_w * wall / reps, "solves": reps, "mean_watts": mean_w,
+            "samples": len(watts)}
 
 
 def measured_peaks():
@@ -363,6 +375,25 @@ def run_batched(args):
         times.append(out["seconds"])
     iters = [p["iters"] for p in out["problems"]]
     t = statistics.median(times)
+    # the same problems solved one after the other by the single-problem path
+    # (each with its own graph-captured solve), for comparison
+    seq_ms = 0.0
+    stream = torch.cuda.current_stream(dev)
+    for p, (bx, _) in enumerate(probs):
+        mesh = nb.Mesh.from_box(ctx, bx)
+        lo = int(batch.l_off[p])
+        bp = b[lo:lo + bx.n_local].contiguous()
+        xp = torch.zeros_like(bp)
+        mesh.solve(bp, xp, opts)
+        xp.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.solve(bp, xp, opts)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += e0.elapsed_time(e1)
+        mesh.close()
     line = {"mode": "batched", "problems": len(boxes), "n_local": batch.n_local,
             "n_global": batch.n_global, "orders": sorted(set(bx.N for bx in boxes)),
             "setup_s": setup_s, "solve_ms": t * 1e3,
@@ -370,6 +401,7 @@ def run_batched(args):
             "batched_iterations": out["iters"], "max_problem_iters": max(iters),
             "median_problem_iters": float(np.median(iters)), "status": out["status"],
             "worst_rel_res": out["rel_res"], "launches": out["launches"],
+            "sequential_single_solves_ms": seq_ms,
             "all_ok": all(p["status"] == 0 for p in out["problems"])}
     print(json.dumps(line), flush=True)
     return 0
@@ -547,7 +579,8 @@ def main():
     energy = {"mixed": en_m, "fp64": en_d,
               "reduction_vs_fp64": (1.0 - en_m["joules_per_solve"] / en_d["joules_per_solve"])
               if en_m and en_d else None,
-              "method": "nvidia-smi total_energy_consumption over back-to-back solves"}
+              "method": "board power sampled by nvidia-smi every 50 ms over back-to-back solves "
+                        "x their wall time"}
 
     # the paper's accuracy metric: AE_k = |r_m,k - r_d,k| between the residual
     # histories of an all-FP32 CG loop (the paper's mixed version, no

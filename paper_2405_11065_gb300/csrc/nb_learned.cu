@@ -500,7 +500,8 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
 // 8 warps with the BF16 weights resident in shared memory ([dp][h+8], padded
 // rows so that the eight row addresses of each ldmatrix fall in distinct
 // bank groups).  Per tile: the tile's residual (16 d contiguous floats) by
-// one bulk copy; row norms and X = r / |r| in BF16; H = a * gelu(X W) by
+// one bulk copy into one of two buffers (the next tile's copy is issued when
+// a tile starts); row norms and X = r / |r| in BF16; H = a * gelu(X W) by
 // mma.sync (W as the col-major B operand through ldmatrix.trans); the
 // correction C = |r_e| (H W^T) on interior nodes (W rows as the B operand);
 // then one coalesced pass z = |dinv| r + C with the owner-copy partials of
@@ -518,7 +519,7 @@ static size_t lpc_smem(int d, int h)
     const int dp = lpc_dp(d);
     return sizeof(__nv_bfloat16) *
                ((size_t)dp * (h + 8) + 16 * (size_t)(dp + 8) + 16 * (size_t)(h + 8)) +
-           sizeof(float) * (2 * 16 * (size_t)d + 16 + h);
+           sizeof(float) * (3 * 16 * (size_t)d + 16 + h);
 }
 
 static bool lpc_fits(int d, int h)
@@ -557,56 +558,80 @@ __global__ void k_w_bf16(int d, int dp, int h, const float *__restrict__ W,
         Wb[i] = __float2bfloat16_rn(i < d * h ? W[i] : 0.f);
 }
 
+template <int n>
 __global__ void __launch_bounds__(kLpcThreads, 1)
-k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__restrict__ dinv,
+k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
       const float *__restrict__ wold, float *__restrict__ z, const __nv_bfloat16 *__restrict__ Wb,
       const float *__restrict__ gain, CgScalars *sc, double *__restrict__ part, int *err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int dp = lpc_dp(d), hs = h + 8, xs = dp + 8;
+    constexpr int d = n * n * n, dp = lpc_dp(d), xs = dp + 8;
+    const int hs = h + 8;
     __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [dp][hs]
     __nv_bfloat16 *Xs = Ws + (size_t)dp * hs;                          // [16][xs]
     __nv_bfloat16 *Hs = Xs + 16 * xs;                                  // [16][hs]
-    float *Rs = reinterpret_cast<float *>(Hs + 16 * hs);               // [16][d] (bulk copy)
-    float *Cs = Rs + 16 * d;                                           // [16][d]
+    float *Rbuf = reinterpret_cast<float *>(Hs + 16 * hs);             // [2][16][d] (bulk copies)
+    float *Cs = Rbuf + 2 * 16 * d;                                     // [16][d]
     float *nrm = Cs + 16 * d;                                          // [16]
     float *as = nrm + 16;                                              // [h]
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ double sred[32];
     __shared__ int sbad;
     if (sc->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, tq = lane & 3;
+    const int tiles = (E + 15) / 16;
+    // tile number u of this block (u = 0, 1, ...) goes to buffer u & 1
+    auto issue = [&](int u) {
+        const int e0 = (blockIdx.x + u * gridDim.x) * 16, rows = min(16, E - e0);
+        const uint32_t bytes = (uint32_t)(sizeof(float) * rows * d);  // multiple of 16: d % 4 == 0
+        mbar_expect_tx(&bar[u & 1], bytes);
+        bulk_g2s(Rbuf + (u & 1) * 16 * d, r + (size_t)e0 * d, bytes, &bar[u & 1]);
+    };
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         mbar_init_fence();
         sbad = 0;
+        if ((int)blockIdx.x < tiles) issue(0);
     }
-    // the weights: 16-byte chunks of each row into the padded rows
-    const int chunks = h / 8;
-    for (int c = tid; c < dp * chunks; c += blockDim.x) {
-        const int row = c / chunks, col = (c - row * chunks) * 8;
-        *reinterpret_cast<uint4 *>(Ws + (size_t)row * hs + col) =
-            *reinterpret_cast<const uint4 *>(Wb + (size_t)row * h + col);
+    // the weights: 16-byte chunks of each row into the padded rows, four
+    // loads in flight per thread
+    const int chunks = h / 8, nchunk = dp * chunks;
+    for (int c0 = tid; c0 < nchunk; c0 += 4 * blockDim.x) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c < nchunk) {
+                const int row = c / chunks, col = (c - row * chunks) * 8;
+                v[u] = *reinterpret_cast<const uint4 *>(Wb + (size_t)row * h + col);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c < nchunk) {
+                const int row = c / chunks, col = (c - row * chunks) * 8;
+                *reinterpret_cast<uint4 *>(Ws + (size_t)row * hs + col) = v[u];
+            }
+        }
     }
     for (int c = tid; c < h; c += blockDim.x) as[c] = gain[c];
-    auto interior = [&](int q) {
+    auto interior = [](int q) {  // n is a compile-time constant: no divisions
         const int i = q % n, j = (q / n) % n, k = q / (n * n);
         return q < d && i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1;
     };
     DotAcc<float> zw, rz;
-    const int tiles = (E + 15) / 16;
-    uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, phase ^= 1u) {
+    int u = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++u) {
         const int e0 = tile * 16, rows = min(16, E - e0);
+        float *Rs = Rbuf + (u & 1) * 16 * d;
         __syncthreads();  // the previous tile is done with every buffer (and Ws is loaded)
-        if (tid == 0) {
-            const uint32_t bytes = (uint32_t)(sizeof(float) * rows * d);  // multiple of 16: d % 4 == 0
-            mbar_expect_tx(&bar, bytes);
-            bulk_g2s(Rs, r + (size_t)e0 * d, bytes, &bar);
-        }
+        // the next tile's residual into the other buffer, free since tile u-1 ended
+        if (tid == 0 && tile + (int)gridDim.x < tiles) issue(u + 1);
         for (int q = tid; q < 16 * d; q += blockDim.x) Cs[q] = 0.f;
-        const bool ok = mbar_wait_bounded(&bar, phase);
+        const bool ok = mbar_wait_bounded(&bar[u & 1], (uint32_t)((u >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) sbad = 1;
             break;
@@ -625,39 +650,77 @@ k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__re
             if (lane == 0) nrm[rr] = rr < rows ? nv : 0.f;
         }
         __syncthreads();
-        // 2. H = a * gelu(X W): warp w takes the column tiles w, w + 8, ...
-        for (int nt = warp; nt < h / 8; nt += kLpcThreads / 32) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int k0 = 0; k0 < dp; k0 += 16) {
-                uint32_t a[4], b[2];
+        // 2. H = a * gelu(X W): warp w takes the column tiles w and w + 8 (h <= 128),
+        //    both accumulated in one pass over k (independent mma chains)
+        {
+            constexpr int NW = kLpcThreads / 32;
+            const int nts = h / 8;
+            const bool two = warp + NW < nts;
+            if (warp < nts) {
+                float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
                 const int mi = lane >> 3, ri = lane & 7;
-                ldsm_x4(a, Xs + ((mi & 1) * 8 + ri) * xs + k0 + (mi >> 1) * 8);
-                ldsm_x2_t(b, Ws + (size_t)(k0 + (mi & 1) * 8 + ri) * hs + nt * 8);
-                mma_bf16(acc, a, b);
-            }
+#pragma unroll 4
+                for (int k0 = 0; k0 < dp; k0 += 16) {
+                    uint32_t a[4], b0[2], b1[2];
+                    ldsm_x4(a, Xs + ((mi & 1) * 8 + ri) * xs + k0 + (mi >> 1) * 8);
+                    const __nv_bfloat16 *wrow = Ws + (size_t)(k0 + (mi & 1) * 8 + ri) * hs;
+                    ldsm_x2_t(b0, wrow + warp * 8);
+                    mma_bf16(acc0, a, b0);
+                    if (two) {
+                        ldsm_x2_t(b1, wrow + (warp + NW) * 8);
+                        mma_bf16(acc1, a, b1);
+                    }
+                }
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-                const int row = g + 8 * (hh >> 1), col = nt * 8 + 2 * tq + (hh & 1);
-                Hs[row * hs + col] = __float2bfloat16_rn(as[col] * gelu_f(acc[hh]));
+                for (int hh = 0; hh < 4; ++hh) {
+                    const int row = g + 8 * (hh >> 1), col = warp * 8 + 2 * tq + (hh & 1);
+                    Hs[row * hs + col] = __float2bfloat16_rn(as[col] * gelu_f(acc0[hh]));
+                    if (two) {
+                        const int c1 = col + NW * 8;
+                        Hs[row * hs + c1] = __float2bfloat16_rn(as[c1] * gelu_f(acc1[hh]));
+                    }
+                }
             }
         }
         __syncthreads();  // Hs complete
-        // 3. C = |r_e| (H W^T) on interior nodes
-        for (int nt = warp; nt < dp / 8; nt += kLpcThreads / 32) {
-            const bool any = __any_sync(0xffffffffu, lane < 8 && interior(nt * 8 + lane));
-            if (!any) continue;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // 3. C = |r_e| (H W^T) on interior nodes: warp w takes the column tiles
+        //    w, w + 8, ... that hold an interior node, all accumulated in one
+        //    pass over k
+        {
+            constexpr int NW = kLpcThreads / 32, NT = (dp / 8 + NW - 1) / NW;
+            float acc[NT][4];
+            bool use[NT];
+#pragma unroll
+            for (int m = 0; m < NT; ++m) {
+                const int nt = warp + m * NW;
+                bool any = false;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) any |= nt < dp / 8 && interior(nt * 8 + c);
+                use[m] = any;
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) acc[m][hh] = 0.f;
+            }
+            const int mi = lane >> 3, ri = lane & 7;
             for (int k0 = 0; k0 < h; k0 += 16) {
-                uint32_t a[4], b[2];
-                const int mi = lane >> 3, ri = lane & 7;
+                uint32_t a[4];
                 ldsm_x4(a, Hs + ((mi & 1) * 8 + ri) * hs + k0 + (mi >> 1) * 8);
-                ldsm_x2(b, Ws + (size_t)(nt * 8 + ri) * hs + k0 + (mi & 1) * 8);
-                mma_bf16(acc, a, b);
+#pragma unroll
+                for (int m = 0; m < NT; ++m) {
+                    if (!use[m]) continue;
+                    uint32_t b[2];
+                    ldsm_x2(b, Ws + (size_t)((warp + m * NW) * 8 + ri) * hs + k0 + (mi & 1) * 8);
+                    mma_bf16(acc[m], a, b);
+                }
             }
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-                const int rr = g + 8 * (hh >> 1), q = nt * 8 + 2 * tq + (hh & 1);
-                if (rr < rows && interior(q)) Cs[rr * d + q] = acc[hh] * nrm[rr];
+            for (int m = 0; m < NT; ++m) {
+                if (!use[m]) continue;
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) {
+                    const int rr = g + 8 * (hh >> 1);
+                    const int q = (warp + m * NW) * 8 + 2 * tq + (hh & 1);
+                    if (rr < rows && interior(q)) Cs[rr * d + q] = acc[m][hh] * nrm[rr];
+                }
             }
         }
         __syncthreads();  // Cs complete
@@ -668,27 +731,43 @@ k_lpc(int E, int n, int d, int h, const float *__restrict__ r, const float *__re
         float4 *z4 = reinterpret_cast<float4 *>(z + (size_t)e0 * d);
         const float4 *r4 = reinterpret_cast<const float4 *>(Rs);
         const float4 *c4 = reinterpret_cast<const float4 *>(Cs);
-        for (int q = tid; q < n4; q += blockDim.x) {
-            const float4 dv = dv4[q], wv = wo4[q], rv = r4[q], cv = c4[q];
-            float4 zv;
-            zv.x = fabsf(dv.x) * rv.x + cv.x;
-            zv.y = fabsf(dv.y) * rv.y + cv.y;
-            zv.z = fabsf(dv.z) * rv.z + cv.z;
-            zv.w = fabsf(dv.w) * rv.w + cv.w;
-            z4[q] = zv;
-            if (!signbit(dv.x)) { zw.add(zv.x * wv.x); rz.add(rv.x * zv.x); }
-            if (!signbit(dv.y)) { zw.add(zv.y * wv.y); rz.add(rv.y * zv.y); }
-            if (!signbit(dv.z)) { zw.add(zv.z * wv.z); rz.add(rv.z * zv.z); }
-            if (!signbit(dv.w)) { zw.add(zv.w * wv.w); rz.add(rv.w * zv.w); }
+        for (int q0 = tid; q0 < n4; q0 += 4 * blockDim.x) {  // four float4 of each in flight
+            float4 dv[4], wv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = q0 + k * blockDim.x;
+                if (q < n4) {
+                    dv[k] = dv4[q];
+                    wv[k] = wo4[q];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = q0 + k * blockDim.x;
+                if (q >= n4) continue;
+                const float4 rv = r4[q], cv = c4[q];
+                float4 zv;
+                zv.x = fabsf(dv[k].x) * rv.x + cv.x;
+                zv.y = fabsf(dv[k].y) * rv.y + cv.y;
+                zv.z = fabsf(dv[k].z) * rv.z + cv.z;
+                zv.w = fabsf(dv[k].w) * rv.w + cv.w;
+                z4[q] = zv;
+                if (!signbit(dv[k].x)) { zw.add(zv.x * wv[k].x); rz.add(rv.x * zv.x); }
+                if (!signbit(dv[k].y)) { zw.add(zv.y * wv[k].y); rz.add(rv.y * zv.y); }
+                if (!signbit(dv[k].z)) { zw.add(zv.z * wv[k].z); rz.add(rv.z * zv.z); }
+                if (!signbit(dv[k].w)) { zw.add(zv.w * wv[k].w); rz.add(rv.w * zv.w); }
+            }
         }
     }
     __syncthreads();
-    if (sbad) {  // the residual tile never arrived: record it, let the copy land, stop
+    if (sbad) {  // a residual tile never arrived: record it, let the copies land, stop
         if (tid == 0) {
             atomicExch(err, 1);
             sc->status = NB_BREAKDOWN;
             sc->done = 1;
-            mbar_wait_bounded(&bar, phase);
+            mbar_wait_bounded(&bar[u & 1], (uint32_t)((u >> 1) & 1));
+            if ((int)blockIdx.x + (u + 1) * (int)gridDim.x < tiles)
+                mbar_wait_bounded(&bar[(u + 1) & 1], (uint32_t)(((u + 1) >> 1) & 1));
         }
         return;
     }
@@ -772,6 +851,39 @@ __global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__
             sc->status = NB_NOT_CONVERGED;
         }
     }
+}
+
+// k_lpc for the orders it is built for (d = n^3 <= 512, n even).
+static bool lpc_order(int n) { return n == 2 || n == 4 || n == 6 || n == 8; }
+
+static nb_status lpc_attr(int n, size_t smem)
+{
+    switch (n) {
+        case 2: NB_CUDA(cudaFuncSetAttribute(k_lpc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 4: NB_CUDA(cudaFuncSetAttribute(k_lpc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 6: NB_CUDA(cudaFuncSetAttribute(k_lpc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 8: NB_CUDA(cudaFuncSetAttribute(k_lpc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        default: set_error("fused preconditioner unavailable for n=%d", n); return NB_ERR_ARG;
+    }
+    return NB_OK;
+}
+
+static nb_status launch_lpc(int n, int grid, size_t smem, cudaStream_t s, int E, int h,
+                            const float *r, const float *dinv, const float *wold, float *z,
+                            const __nv_bfloat16 *Wb, const float *gain, CgScalars *sc,
+                            double *part, int *err)
+{
+#define NB_LPC(NN) k_lpc<NN><<<grid, kLpcThreads, smem, s>>>(E, h, r, dinv, wold, z, Wb, gain, sc, part, err)
+    switch (n) {
+        case 2: NB_LPC(2); break;
+        case 4: NB_LPC(4); break;
+        case 6: NB_LPC(6); break;
+        case 8: NB_LPC(8); break;
+        default: set_error("fused preconditioner unavailable for n=%d", n); return NB_ERR_ARG;
+    }
+#undef NB_LPC
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
 }
 
 static nb_status ensure_wb(nb_model *md, cudaStream_t s)
@@ -951,12 +1063,13 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     float *z = (float *)ws.z, *wprev = (float *)ws.aux;
     double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
     NB_TRY(model_scratch(md, (int)m->E));  // before any capture: it may allocate
-    const bool fast = prec == NB_FP32 && ax_dir_step_available(m) && lpc_fits(md->d, md->h);
+    const bool fast = prec == NB_FP32 && ax_dir_step_available(m) && lpc_order(m->n) &&
+                      lpc_fits(md->d, md->h);
     const size_t lsm = lpc_smem(md->d, md->h);
     const int lgrid = std::max(1, std::min((int)((m->E + 15) / 16), m->ctx->sm_count));
     if (fast) {
         NB_TRY(ensure_wb(md, s));  // outside any capture: refreshed in place when W changed
-        NB_CUDA(cudaFuncSetAttribute(k_lpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+        NB_TRY(lpc_attr(m->n, lsm));
     }
     NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
     NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
@@ -967,9 +1080,8 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     // one flexible-CG step; w receives A p, wprev holds the previous A p
     auto step = [&](float *wcur, float *wold) -> nb_status {
         if (fast) {
-            k_lpc<<<lgrid, kLpcThreads, lsm, s>>>((int)m->E, m->n, md->d, md->h, r, sgn, wold, z,
-                                                  md->Wb, md->a, ws.scal, P0, m->kerr);
-            NB_CUDA(cudaGetLastError());
+            NB_TRY(launch_lpc(m->n, lgrid, lsm, s, (int)m->E, md->h, r, sgn, wold, z, md->Wb,
+                              md->a, ws.scal, P0, m->kerr));
             int nparts = 0;
             NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
             NB_TRY(dssum(m, prec, wcur, 1, s));
