@@ -16,6 +16,10 @@ the textbook spectral-element definition, cited at its C implementation in
 * the local operator ``ax`` and its diagonal, ``dssum`` + mask, ``glsc3``
 * Jacobi-PCG in Table 1 order (``Problem.pcg``) and flexible CG
   (``Problem.fcg``, Notay 2000) with a user-supplied preconditioner.
+* emulated reduced precision (Section 2, the VPREC backend; Section 4.2):
+  ``vround`` rounds a binary64 value to t mantissa bits, and
+  ``Problem.apply_vprec`` / ``Problem.cg_vprec`` run the operator and the CG
+  loop with every arithmetic operation so rounded.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, exactness properties, an independently assembled dense
@@ -81,6 +85,15 @@ def lib():
         L.nbo_pcg.restype = C.c_int
         L.nbo_pcg.argtypes = [C.POINTER(_Op), _dp, _dp, C.c_int, C.c_double, C.c_int,
                               C.c_void_p, C.POINTER(C.c_double)]
+        L.nbo_vround.restype = C.c_double
+        L.nbo_vround.argtypes = [C.c_double, C.c_int]
+        L.nbo_apply_vprec.restype = None
+        L.nbo_apply_vprec.argtypes = [C.POINTER(_Op), C.c_int, _dp, _dp]
+        L.nbo_glsc3_vprec.restype = C.c_double
+        L.nbo_glsc3_vprec.argtypes = [_dp, _dp, _dp, C.c_longlong, C.c_int]
+        L.nbo_cg_vprec.restype = C.c_double
+        L.nbo_cg_vprec.argtypes = [C.POINTER(_Op), _dp, _dp, C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p]
         _lib = L
     return _lib
 
@@ -185,6 +198,11 @@ def dssum(gid: np.ndarray, nG: int, u: np.ndarray, mask=None) -> np.ndarray:
     lib().nbo_dssum(len(out), nG, np.ascontiguousarray(gid, dtype=np.int64),
                     None if m is None else m.ctypes.data, out, work)
     return out
+
+
+def vround(x: float, t: int) -> float:
+    """x rounded to t mantissa bits (round to nearest, ties to even)."""
+    return lib().nbo_vround(float(x), int(t))
 
 
 def glsc3(a, b, c) -> float:
@@ -298,10 +316,27 @@ class Problem:
                 break
         return x, it, rel, np.array(hist)
 
+    def apply_vprec(self, u: np.ndarray, t: int) -> np.ndarray:
+        """Assembled operator with every +, -, *, / rounded to t bits."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros_like(u)
+        lib().nbo_apply_vprec(C.byref(self._op), t, u, w)
+        return w
+
+    def cg_vprec(self, b: np.ndarray, iters: int, t: int, precond: str = "none"):
+        """`iters` CG iterations (Table 1 order) with every arithmetic
+        operation of the loop rounded to t mantissa bits.  Returns (x, hist)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        hist = np.zeros(max(iters, 1))
+        lib().nbo_cg_vprec(C.byref(self._op), b, x, iters, t, 1 if precond == "jacobi" else 0,
+                           hist.ctypes.data)
+        return x, hist[:iters].copy()
+
     def true_relres(self, b: np.ndarray, x: np.ndarray) -> float:
         r = b - self.apply(x)
         return math.sqrt(self.glsc3(r, r)) / (math.sqrt(self.glsc3(b, b)) or 1.0)
 
 
 __all__ = ["lib", "legendre", "gll", "deriv", "element_coords", "geom", "numbering",
-           "csr", "ax_local", "diag_local", "dssum", "glsc3", "Problem"]
+           "csr", "ax_local", "diag_local", "dssum", "glsc3", "vround", "Problem"]

@@ -445,3 +445,131 @@ int nbo_pcg(const nbo_op *op, const double *b, double *x, int maxit, double tol,
     if (relres) *relres = rel;
     return iter;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Emulated reduced precision (Section 2, the VPREC backend; Section 4.2)    */
+/* ------------------------------------------------------------------------ */
+
+/* x rounded to a pseudo-mantissa of t bits (1 <= t <= 52): round to nearest,
+ * ties to even, applied to the binary64 representation.  The exponent range
+ * of binary64 is kept (no emulated range); a carry out of the mantissa raises
+ * the exponent as the rounding of the real value requires, up to infinity.
+ * NaN and infinities pass unchanged; t >= 52 is the identity. */
+double nbo_vround(double x, int t)
+{
+    if (t >= 52) return x;
+    if (t < 1) t = 1;
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    if (((b >> 52) & 0x7ff) == 0x7ff) return x;
+    const int drop = 52 - t;
+    const uint64_t mask = ((uint64_t)1 << drop) - 1, half = (uint64_t)1 << (drop - 1);
+    const uint64_t rem = b & mask;
+    b &= ~mask;
+    if (rem > half || (rem == half && ((b >> drop) & 1))) b += (uint64_t)1 << drop;
+    memcpy(&x, &b, sizeof x);
+    return x;
+}
+
+#define VR(v) nbo_vround((v), t)
+
+/* w = M Q Q^T A_L u with every +, -, *, / rounded to t bits, in the order of
+ * nbo_ax_local and nbo_dssum (products and sums of each loop in turn). */
+void nbo_apply_vprec(const nbo_op *op, int t, const double *u, double *w)
+{
+    const int N = op->N, n = N + 1, n3 = n * n * n;
+    const double *D = op->D;
+    double *wr = (double *)malloc(sizeof(double) * 3 * n3);
+    double *ws = wr + n3, *wt = wr + 2 * n3;
+    for (i64 e = 0; e < op->E; ++e) {
+        const double *ue = u + e * n3;
+        const double *Ge = op->G + e * 6 * (i64)n3;
+        double *we = w + e * n3;
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    double ur = 0.0, us = 0.0, ut = 0.0;
+                    for (int l = 0; l < n; ++l) {
+                        ur = VR(ur + VR(D[i * n + l] * ue[(k * n + j) * n + l]));
+                        us = VR(us + VR(D[j * n + l] * ue[(k * n + l) * n + i]));
+                        ut = VR(ut + VR(D[k * n + l] * ue[(l * n + j) * n + i]));
+                    }
+                    const int q = (k * n + j) * n + i;
+                    const double grr = Ge[0 * n3 + q], grs = Ge[1 * n3 + q], grt = Ge[2 * n3 + q];
+                    const double gss = Ge[3 * n3 + q], gst = Ge[4 * n3 + q], gtt = Ge[5 * n3 + q];
+                    wr[q] = VR(VR(VR(grr * ur) + VR(grs * us)) + VR(grt * ut));
+                    ws[q] = VR(VR(VR(grs * ur) + VR(gss * us)) + VR(gst * ut));
+                    wt[q] = VR(VR(VR(grt * ur) + VR(gst * us)) + VR(gtt * ut));
+                }
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    double s = 0.0;
+                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + i] * wr[(k * n + j) * n + l]));
+                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + j] * ws[(k * n + l) * n + i]));
+                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + k] * wt[(l * n + j) * n + i]));
+                    we[(k * n + j) * n + i] = s;
+                }
+    }
+    free(wr);
+    double *work = op->work;
+    for (i64 g = 0; g < op->nG; ++g) work[g] = 0.0;
+    for (i64 l = 0; l < op->nL; ++l) work[op->gid[l]] = VR(work[op->gid[l]] + w[l]);
+    for (i64 l = 0; l < op->nL; ++l) {
+        const i64 g = op->gid[l];
+        w[l] = (op->mask && !op->mask[g]) ? 0.0 : work[g];
+    }
+}
+
+/* glsc3 with every operation rounded: s = R(s + R(R(a b) c)), ascending l. */
+double nbo_glsc3_vprec(const double *a, const double *b, const double *c, i64 n, int t)
+{
+    double s = 0.0;
+    for (i64 l = 0; l < n; ++l) s = VR(s + VR(VR(a[l] * b[l]) * c[l]));
+    return s;
+}
+
+/* The CG loop of nbo_pcg with every +, -, *, / of the loop rounded to t bits
+ * (the paper's "only CG" instrumentation: set-up -- geometry, the Jacobi
+ * diagonal, the initial residual and |b| -- stays in binary64; sqrt is not an
+ * arithmetic operation and is not rounded).  Runs exactly `iters` iterations
+ * (Nekbone's fixed iteration count); hist (may be NULL) receives the loop's
+ * relative residual sqrt(rtr)/|b| after each.  Returns the last one. */
+double nbo_cg_vprec(const nbo_op *op, const double *b, double *x, int iters, int t,
+                    int precond, double *hist)
+{
+    const i64 n = op->nL;
+    double *r = (double *)malloc(sizeof(double) * 4 * n);
+    double *z = r + n, *p = r + 2 * n, *w = r + 3 * n;
+    nbo_apply(op, x, w);
+    for (i64 l = 0; l < n; ++l) {
+        r[l] = b[l] - w[l];
+        p[l] = 0.0;
+    }
+    double bnorm = sqrt(nbo_glsc3(b, op->c, b, n));
+    if (bnorm == 0.0) bnorm = 1.0;
+    double rtz1 = 1.0, rtz2, rel = sqrt(nbo_glsc3(r, op->c, r, n)) / bnorm;
+    for (int it = 1; it <= iters; ++it) {
+        if (precond == 1) {
+            for (i64 l = 0; l < n; ++l) z[l] = VR(op->dinv[l] * r[l]);
+        } else {
+            for (i64 l = 0; l < n; ++l) z[l] = r[l];
+        }
+        rtz2 = rtz1;
+        rtz1 = nbo_glsc3_vprec(r, op->c, z, n, t);
+        const double beta = (it == 1) ? 0.0 : VR(rtz1 / rtz2);
+        for (i64 l = 0; l < n; ++l) p[l] = VR(VR(beta * p[l]) + z[l]);
+        nbo_apply_vprec(op, t, p, w);
+        const double pap = nbo_glsc3_vprec(w, op->c, p, n, t);
+        const double alpha = VR(rtz1 / pap);
+        for (i64 l = 0; l < n; ++l) x[l] = VR(x[l] + VR(alpha * p[l]));
+        for (i64 l = 0; l < n; ++l) r[l] = VR(r[l] - VR(alpha * w[l]));
+        const double rtr = nbo_glsc3_vprec(r, op->c, r, n, t);
+        rel = VR(sqrt(rtr) / bnorm);
+        if (hist) hist[it - 1] = rel;
+    }
+    free(r);
+    return rel;
+}
+
+#undef VR
