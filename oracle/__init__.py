@@ -19,7 +19,9 @@ the textbook spectral-element definition, cited at its C implementation in
 * emulated reduced precision (Section 2, the VPREC backend; Section 4.2):
   ``vround`` rounds a binary64 value to t mantissa bits, and
   ``Problem.apply_vprec`` / ``Problem.cg_vprec`` run the operator and the CG
-  loop with every arithmetic operation so rounded.
+  loop with every arithmetic operation so rounded; ``inexact`` and
+  ``Problem.cg_mca`` do the same with Monte Carlo Arithmetic (the MCA
+  backend's random-rounding and full modes).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, exactness properties, an independently assembled dense
@@ -94,6 +96,11 @@ def lib():
         L.nbo_cg_vprec.restype = C.c_double
         L.nbo_cg_vprec.argtypes = [C.POINTER(_Op), _dp, _dp, C.c_int, C.c_int, C.c_int,
                                    C.c_void_p]
+        L.nbo_cg_emu.restype = C.c_double
+        L.nbo_cg_emu.argtypes = [C.POINTER(_Op), _dp, _dp, C.c_int, C.c_int, C.c_int,
+                                 C.c_uint64, C.c_int, C.c_void_p]
+        L.nbo_inexact.restype = C.c_double
+        L.nbo_inexact.argtypes = [C.c_double, C.c_int, C.POINTER(C.c_uint64)]
         _lib = L
     return _lib
 
@@ -203,6 +210,14 @@ def dssum(gid: np.ndarray, nG: int, u: np.ndarray, mask=None) -> np.ndarray:
 def vround(x: float, t: int) -> float:
     """x rounded to t mantissa bits (round to nearest, ties to even)."""
     return lib().nbo_vround(float(x), int(t))
+
+
+def inexact(x: float, t: int, state: int):
+    """Monte Carlo Arithmetic perturbation of x at virtual precision t with
+    the SplitMix64 state; returns (value, new state)."""
+    st = C.c_uint64(state)
+    v = lib().nbo_inexact(float(x), int(t), C.byref(st))
+    return v, st.value
 
 
 def glsc3(a, b, c) -> float:
@@ -333,10 +348,22 @@ class Problem:
                            hist.ctypes.data)
         return x, hist[:iters].copy()
 
+    def cg_mca(self, b: np.ndarray, iters: int, t: int, mode: str, seed: int,
+               precond: str = "none"):
+        """`iters` CG iterations with Monte Carlo Arithmetic on every operation
+        of the loop (mode "rr": results perturbed; "mca": operands and results),
+        virtual precision t, SplitMix64 seed.  Returns (x, hist)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        hist = np.zeros(max(iters, 1))
+        lib().nbo_cg_emu(C.byref(self._op), b, x, iters, {"rr": 1, "mca": 2}[mode], t, seed,
+                         1 if precond == "jacobi" else 0, hist.ctypes.data)
+        return x, hist[:iters].copy()
+
     def true_relres(self, b: np.ndarray, x: np.ndarray) -> float:
         r = b - self.apply(x)
         return math.sqrt(self.glsc3(r, r)) / (math.sqrt(self.glsc3(b, b)) or 1.0)
 
 
 __all__ = ["lib", "legendre", "gll", "deriv", "element_coords", "geom", "numbering",
-           "csr", "ax_local", "diag_local", "dssum", "glsc3", "vround", "Problem"]
+           "csr", "ax_local", "diag_local", "dssum", "glsc3", "vround", "inexact", "Problem"]

@@ -471,11 +471,75 @@ double nbo_vround(double x, int t)
     return x;
 }
 
-#define VR(v) nbo_vround((v), t)
+/* Monte Carlo Arithmetic (Section 2, the MCA backend; Parker, 1997):
+ * inexact(x) = x + 2^(e_x - t) xi with xi uniform on (-1/2, 1/2) and e_x the
+ * exponent of x (2^(e_x - 1) <= |x| < 2^e_x); zero and non-finite values are
+ * left alone.  Random rounding ("rr") perturbs the result of every operation,
+ * full MCA ("mca") its operands and its result.  Random numbers: SplitMix64
+ * (Steele, Lea and Flood, 2014), 53-bit uniforms, one stream per run. */
+typedef struct {
+    int mode;   /* 0: round to t bits (VPREC), 1: rr, 2: mca */
+    int t;
+    uint64_t s; /* SplitMix64 state */
+} nbo_emu;
 
-/* w = M Q Q^T A_L u with every +, -, *, / rounded to t bits, in the order of
+static double emu_u01(nbo_emu *m)
+{
+    uint64_t z = (m->s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+double nbo_inexact(double x, int t, uint64_t *state)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    nbo_emu m = {1, t, *state};
+    int e;
+    frexp(x, &e);
+    const double r = x + ldexp(emu_u01(&m) - 0.5, e - t);
+    *state = m.s;
+    return r;
+}
+
+static double emu_in(nbo_emu *m, double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(x, &e);
+    return x + ldexp(emu_u01(m) - 0.5, e - m->t);
+}
+
+static double emu_out(nbo_emu *m, double r)
+{
+    return m->mode == 0 ? nbo_vround(r, m->t) : emu_in(m, r);
+}
+
+static double eadd(nbo_emu *m, double a, double b)
+{
+    if (m->mode == 2) { a = emu_in(m, a); b = emu_in(m, b); }
+    return emu_out(m, a + b);
+}
+static double esub(nbo_emu *m, double a, double b)
+{
+    if (m->mode == 2) { a = emu_in(m, a); b = emu_in(m, b); }
+    return emu_out(m, a - b);
+}
+static double emul(nbo_emu *m, double a, double b)
+{
+    if (m->mode == 2) { a = emu_in(m, a); b = emu_in(m, b); }
+    return emu_out(m, a * b);
+}
+static double ediv(nbo_emu *m, double a, double b)
+{
+    if (m->mode == 2) { a = emu_in(m, a); b = emu_in(m, b); }
+    return emu_out(m, a / b);
+}
+
+/* w = M Q Q^T A_L u with every +, -, *, / emulated, in the order of
  * nbo_ax_local and nbo_dssum (products and sums of each loop in turn). */
-void nbo_apply_vprec(const nbo_op *op, int t, const double *u, double *w)
+static void apply_emu(const nbo_op *op, nbo_emu *m, const double *u, double *w)
 {
     const int N = op->N, n = N + 1, n3 = n * n * n;
     const double *D = op->D;
@@ -490,54 +554,69 @@ void nbo_apply_vprec(const nbo_op *op, int t, const double *u, double *w)
                 for (int i = 0; i < n; ++i) {
                     double ur = 0.0, us = 0.0, ut = 0.0;
                     for (int l = 0; l < n; ++l) {
-                        ur = VR(ur + VR(D[i * n + l] * ue[(k * n + j) * n + l]));
-                        us = VR(us + VR(D[j * n + l] * ue[(k * n + l) * n + i]));
-                        ut = VR(ut + VR(D[k * n + l] * ue[(l * n + j) * n + i]));
+                        ur = eadd(m, ur, emul(m, D[i * n + l], ue[(k * n + j) * n + l]));
+                        us = eadd(m, us, emul(m, D[j * n + l], ue[(k * n + l) * n + i]));
+                        ut = eadd(m, ut, emul(m, D[k * n + l], ue[(l * n + j) * n + i]));
                     }
                     const int q = (k * n + j) * n + i;
                     const double grr = Ge[0 * n3 + q], grs = Ge[1 * n3 + q], grt = Ge[2 * n3 + q];
                     const double gss = Ge[3 * n3 + q], gst = Ge[4 * n3 + q], gtt = Ge[5 * n3 + q];
-                    wr[q] = VR(VR(VR(grr * ur) + VR(grs * us)) + VR(grt * ut));
-                    ws[q] = VR(VR(VR(grs * ur) + VR(gss * us)) + VR(gst * ut));
-                    wt[q] = VR(VR(VR(grt * ur) + VR(gst * us)) + VR(gtt * ut));
+                    wr[q] = eadd(m, eadd(m, emul(m, grr, ur), emul(m, grs, us)), emul(m, grt, ut));
+                    ws[q] = eadd(m, eadd(m, emul(m, grs, ur), emul(m, gss, us)), emul(m, gst, ut));
+                    wt[q] = eadd(m, eadd(m, emul(m, grt, ur), emul(m, gst, us)), emul(m, gtt, ut));
                 }
         for (int k = 0; k < n; ++k)
             for (int j = 0; j < n; ++j)
                 for (int i = 0; i < n; ++i) {
                     double s = 0.0;
-                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + i] * wr[(k * n + j) * n + l]));
-                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + j] * ws[(k * n + l) * n + i]));
-                    for (int l = 0; l < n; ++l) s = VR(s + VR(D[l * n + k] * wt[(l * n + j) * n + i]));
+                    for (int l = 0; l < n; ++l) s = eadd(m, s, emul(m, D[l * n + i], wr[(k * n + j) * n + l]));
+                    for (int l = 0; l < n; ++l) s = eadd(m, s, emul(m, D[l * n + j], ws[(k * n + l) * n + i]));
+                    for (int l = 0; l < n; ++l) s = eadd(m, s, emul(m, D[l * n + k], wt[(l * n + j) * n + i]));
                     we[(k * n + j) * n + i] = s;
                 }
     }
     free(wr);
     double *work = op->work;
     for (i64 g = 0; g < op->nG; ++g) work[g] = 0.0;
-    for (i64 l = 0; l < op->nL; ++l) work[op->gid[l]] = VR(work[op->gid[l]] + w[l]);
+    for (i64 l = 0; l < op->nL; ++l) work[op->gid[l]] = eadd(m, work[op->gid[l]], w[l]);
     for (i64 l = 0; l < op->nL; ++l) {
         const i64 g = op->gid[l];
         w[l] = (op->mask && !op->mask[g]) ? 0.0 : work[g];
     }
 }
 
-/* glsc3 with every operation rounded: s = R(s + R(R(a b) c)), ascending l. */
-double nbo_glsc3_vprec(const double *a, const double *b, const double *c, i64 n, int t)
+static double glsc3_emu(nbo_emu *m, const double *a, const double *b, const double *c, i64 n)
 {
     double s = 0.0;
-    for (i64 l = 0; l < n; ++l) s = VR(s + VR(VR(a[l] * b[l]) * c[l]));
+    for (i64 l = 0; l < n; ++l) s = eadd(m, s, emul(m, emul(m, a[l], b[l]), c[l]));
     return s;
 }
 
-/* The CG loop of nbo_pcg with every +, -, *, / of the loop rounded to t bits
- * (the paper's "only CG" instrumentation: set-up -- geometry, the Jacobi
- * diagonal, the initial residual and |b| -- stays in binary64; sqrt is not an
- * arithmetic operation and is not rounded).  Runs exactly `iters` iterations
- * (Nekbone's fixed iteration count); hist (may be NULL) receives the loop's
- * relative residual sqrt(rtr)/|b| after each.  Returns the last one. */
-double nbo_cg_vprec(const nbo_op *op, const double *b, double *x, int iters, int t,
-                    int precond, double *hist)
+void nbo_apply_vprec(const nbo_op *op, int t, const double *u, double *w)
 {
+    nbo_emu m = {0, t, 0};
+    apply_emu(op, &m, u, w);
+}
+
+/* glsc3 with every operation rounded: s = R(s + R(R(a b) c)), ascending l. */
+double nbo_glsc3_vprec(const double *a, const double *b, const double *c, i64 n, int t)
+{
+    nbo_emu m = {0, t, 0};
+    return glsc3_emu(&m, a, b, c, n);
+}
+
+/* The CG loop of nbo_pcg with every +, -, *, / of the loop emulated
+ * (mode 0: rounded to t bits; 1: random rounding; 2: full MCA, virtual
+ * precision t; seed: the run's SplitMix64 seed) -- the paper's "only CG"
+ * instrumentation: set-up (geometry, the Jacobi diagonal, the initial
+ * residual and |b|) stays in binary64; sqrt is not an arithmetic operation.
+ * Runs exactly `iters` iterations (Nekbone's fixed iteration count); hist
+ * (may be NULL) receives the loop's relative residual sqrt(rtr)/|b| after
+ * each.  Returns the last one. */
+double nbo_cg_emu(const nbo_op *op, const double *b, double *x, int iters, int mode, int t,
+                  uint64_t seed, int precond, double *hist)
+{
+    nbo_emu m = {mode, t, seed};
     const i64 n = op->nL;
     double *r = (double *)malloc(sizeof(double) * 4 * n);
     double *z = r + n, *p = r + 2 * n, *w = r + 3 * n;
@@ -551,25 +630,31 @@ double nbo_cg_vprec(const nbo_op *op, const double *b, double *x, int iters, int
     double rtz1 = 1.0, rtz2, rel = sqrt(nbo_glsc3(r, op->c, r, n)) / bnorm;
     for (int it = 1; it <= iters; ++it) {
         if (precond == 1) {
-            for (i64 l = 0; l < n; ++l) z[l] = VR(op->dinv[l] * r[l]);
+            for (i64 l = 0; l < n; ++l) z[l] = emul(&m, op->dinv[l], r[l]);
         } else {
             for (i64 l = 0; l < n; ++l) z[l] = r[l];
         }
         rtz2 = rtz1;
-        rtz1 = nbo_glsc3_vprec(r, op->c, z, n, t);
-        const double beta = (it == 1) ? 0.0 : VR(rtz1 / rtz2);
-        for (i64 l = 0; l < n; ++l) p[l] = VR(VR(beta * p[l]) + z[l]);
-        nbo_apply_vprec(op, t, p, w);
-        const double pap = nbo_glsc3_vprec(w, op->c, p, n, t);
-        const double alpha = VR(rtz1 / pap);
-        for (i64 l = 0; l < n; ++l) x[l] = VR(x[l] + VR(alpha * p[l]));
-        for (i64 l = 0; l < n; ++l) r[l] = VR(r[l] - VR(alpha * w[l]));
-        const double rtr = nbo_glsc3_vprec(r, op->c, r, n, t);
-        rel = VR(sqrt(rtr) / bnorm);
+        rtz1 = glsc3_emu(&m, r, op->c, z, n);
+        const double beta = (it == 1) ? 0.0 : ediv(&m, rtz1, rtz2);
+        for (i64 l = 0; l < n; ++l) p[l] = eadd(&m, emul(&m, beta, p[l]), z[l]);
+        apply_emu(op, &m, p, w);
+        const double pap = glsc3_emu(&m, w, op->c, p, n);
+        const double alpha = ediv(&m, rtz1, pap);
+        for (i64 l = 0; l < n; ++l) x[l] = eadd(&m, x[l], emul(&m, alpha, p[l]));
+        for (i64 l = 0; l < n; ++l) r[l] = esub(&m, r[l], emul(&m, alpha, w[l]));
+        const double rtr = glsc3_emu(&m, r, op->c, r, n);
+        rel = ediv(&m, sqrt(rtr), bnorm);
         if (hist) hist[it - 1] = rel;
     }
     free(r);
     return rel;
 }
 
-#undef VR
+double nbo_cg_vprec(const nbo_op *op, const double *b, double *x, int iters, int t,
+                    int precond, double *hist)
+{
+    return nbo_cg_emu(op, b, x, iters, 0, t, 0, precond, hist);
+}
+
+

@@ -1,7 +1,8 @@
 """Pins of the emulated-precision oracle (Section 2, the VPREC backend;
 Section 4.2): rounding to t mantissa bits against IEEE binary32, binary16 and
 bfloat16 conversions, its error bound, and the emulated CG loop against the
-binary64 loop (t = 52) and against the same loop written in binary32 (t = 23)."""
+binary64 loop (t = 52) and against the same loop written in binary32 (t = 23);
+the Monte Carlo Arithmetic perturbation against its distribution."""
 import math
 
 import numpy as np
@@ -171,3 +172,36 @@ def test_cg_residual_floor_falls_with_precision():
         x, hist = P.cg_vprec(b, 60, t)
         finals[t] = P.true_relres(b, x)
     assert finals[8] > finals[23] > finals[52]
+
+
+def test_inexact_is_unbiased_and_bounded():
+    """inexact(x) = x + 2^(e_x - t) xi, xi uniform on (-1/2, 1/2), e_x the
+    exponent with 2^(e_x - 1) <= |x| < 2^e_x: every value within half a unit
+    of 2^(e_x - t) of x, mean x, variance 2^(2(e_x - t)) / 12."""
+    for x, t in ((1.5, 10), (-3.0e-5, 20), (7.0e8, 23)):
+        e = math.frexp(x)[1]
+        unit = 2.0 ** (e - t)
+        state = 12345
+        vals = []
+        for _ in range(20000):
+            v, state = oracle.inexact(x, t, state)
+            vals.append(v)
+        vals = np.array(vals)
+        assert np.all(np.abs(vals - x) <= 0.5 * unit)
+        assert abs(vals.mean() - x) <= 4 * unit / math.sqrt(12 * vals.size)
+        assert abs(vals.var() / (unit ** 2 / 12) - 1.0) < 0.05
+    assert oracle.inexact(0.0, 10, 1)[0] == 0.0
+
+
+def test_mca_runs_are_reproducible_and_close_to_binary64_at_t52():
+    box = Box(2, 2, 1, 4, 0.05)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 6))
+    _, h64 = P.cg_vprec(b, 20, 52)
+    for mode in ("rr", "mca"):
+        _, h1 = P.cg_mca(b, 20, 52, mode, seed=7)
+        _, h2 = P.cg_mca(b, 20, 52, mode, seed=7)
+        _, h3 = P.cg_mca(b, 20, 52, mode, seed=8)
+        assert np.array_equal(h1, h2)
+        assert not np.array_equal(h1, h3)
+        np.testing.assert_allclose(h1, h64, rtol=1e-9)
