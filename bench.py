@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,7 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
-    ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned"],
+    ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned", "vprec",
+                                       "learned-step", "batched-step"],
                     default="full",
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture); "
@@ -448,12 +450,107 @@ def run_learned(args):
     return 0
 
 
+def run_learned_step(args):
+    """Profiling aid: `--steps` flexible-CG steps with the learned
+    preconditioner on the learned workload's mesh (E=4096, N=7) and an
+    untrained network of its shape (the kernels' cost does not depend on the
+    weights); host-launched with --no-graph so that a profiler lists every
+    kernel."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    box = W.LEARNED_16CUBE_N7
+    mesh = nb.Mesh.from_box(ctx, box)
+    model = nb.Model(ctx, box.N, 96, seed=7)
+    model.attach(mesh)
+    b = _rhs_local(nb, mesh, box, 0, dev)
+    x = torch.zeros_like(b)
+    o = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_LEARNED, rtol=1e-8, maxiter=args.steps,
+                        max_outer=1, use_graph=0 if args.no_graph else 1)
+    st = mesh.solve(b, x, o)
+    print(json.dumps({"mode": "learned-step", "iters": st["iters"], "ms": st["seconds"] * 1e3}),
+          flush=True)
+    return 0
+
+
+def run_batched_step(args):
+    """Profiling aid: the batched workload's first `--steps` iterations
+    (one refinement step), host-launched with --no-graph so that a profiler
+    lists every kernel."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    probs = W.batched_problems(256)
+    batch = nb.Batch(ctx, [bx for bx, _ in probs])
+    ug = torch.from_numpy(np.concatenate([W.rhs_global(bx, s) for bx, s in probs])).to(dev)
+    b = torch.empty(batch.n_local, dtype=torch.float64, device=dev)
+    batch.to_local(ug, b)
+    x = torch.zeros_like(b)
+    out = batch.solve(b, x, nb.default_opts(prec=nb.NB_FP32, maxiter=args.steps, max_outer=1,
+                                            use_graph=0 if args.no_graph else 1))
+    print(json.dumps({"mode": "batched-step", "iters": out["iters"], "ms": out["seconds"] * 1e3}),
+          flush=True)
+    return 0
+
+
+def run_vprec(args):
+    """The precision study of Section 4.2 on the GPU: 100 CG iterations
+    (Nekbone's fixed count) without preconditioner on the E=4096, N=9
+    deformed box, every arithmetic operation of the loop rounded to t
+    mantissa bits, t = 3 .. 52; the loop's final relative residual and the
+    true binary64 one, |b - A x| / |b|."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    box = W.MIXED_16CUBE_N9
+    mesh = nb.Mesh.from_box(ctx, box)
+    b = _rhs_local(nb, mesh, box, 0, dev)
+    x = torch.zeros_like(b)
+    w = torch.empty_like(b)
+    bn = math.sqrt(mesh.glsc3(nb.NB_FP64, b, b))
+    rows = []
+    t0 = time.perf_counter()
+    for t in list(range(3, 53)):
+        h = mesh.cg_vprec(t, 100, b, x)
+        mesh.ax(nb.NB_FP64, x, w, assemble=True)
+        r = b - w
+        true_rel = math.sqrt(mesh.glsc3(nb.NB_FP64, r, r)) / bn
+        rows.append({"t": t, "loop_rel_res": float(h[-1]), "true_rel_res": true_rel})
+    ref = rows[-1]["true_rel_res"]
+    stable = next((r["t"] for r in rows
+                   if all(abs(q["true_rel_res"] - ref) <= 0.1 * ref for q in rows if q["t"] >= r["t"])),
+                  None)
+    # Monte Carlo Arithmetic at t = 23, 20 runs per mode (Section 4.2): the
+    # residual history's mean, minimum and maximum, and the significant bits
+    # s2 = -log2(sigma / |mu|) of the final residual over the runs
+    mca = {}
+    for mode in ("rr", "mca"):
+        hs = np.array([mesh.cg_mca(mode, 23, 1000 + k, 100, b, x) for k in range(20)])
+        mu, sd = hs.mean(axis=0), hs.std(axis=0, ddof=1)
+        at = [9, 24, 49, 99]
+        mca[mode] = {"iterations": [i + 1 for i in at],
+                     "mean": [float(mu[i]) for i in at], "min": [float(hs[:, i].min()) for i in at],
+                     "max": [float(hs[:, i].max()) for i in at],
+                     "significant_bits_final": float(-math.log2(sd[-1] / abs(mu[-1])))
+                     if sd[-1] > 0 else 52.0}
+    line = {"mode": "vprec", "E": box.E, "N": box.N, "iterations": 100, "preconditioner": "none",
+            "stable_from_t": stable, "seconds": time.perf_counter() - t0, "results": rows,
+            "mca_t23_20_runs": mca}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode in ("sweep", "batched", "learned"):
-        return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned}[args.mode](args)
+    if args.mode in ("sweep", "batched", "learned", "vprec", "learned-step", "batched-step"):
+        return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned,
+                "vprec": run_vprec, "learned-step": run_learned_step,
+                "batched-step": run_batched_step}[args.mode](args)
     rank, world, local = dist_env()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

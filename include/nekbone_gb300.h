@@ -339,6 +339,44 @@ nb_status nb_learned_attach(nb_mesh *mesh, nb_model *model);
 /* Apply the attached preconditioner once: z = B(r), FP32 L-vectors. */
 nb_status nb_learned_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
 
+/* ------------------------------------------------------------------------
+ * Emulated reduced precision (Section 2: Verificarlo's VPREC backend
+ * computes every floating-point operation in the original type and rounds
+ * its result to a pseudo-mantissa of t bits; Section 4.2 sweeps t from 3 to
+ * 52 over the CG loop).  Here: binary64 with every +, -, *, / of the loop
+ * rounded to t bits (1 <= t <= 52), round to nearest, ties to even, the
+ * binary64 exponent range kept.  The operator and the direct-stiffness
+ * summation take their operations in the order of the plain definitions
+ * (per node the l-loops in turn; per global node the copies in ascending
+ * local index); dot products are summed per thread, per block in a fixed
+ * tree and over blocks in index order.  A study tool, not a fast path.
+ * ------------------------------------------------------------------------ */
+
+/* w = M Q Q^T A_L u with every operation rounded to t bits (FP64 L-vectors,
+ * device).  Errors: NB_ERR_ARG (t outside 1..52, NULL), NB_ERR_STATE. */
+nb_status nb_apply_vprec(nb_mesh *mesh, int t, const double *u_dev, double *w_dev);
+
+/* `iters` CG iterations from x = 0 (Nekbone's fixed iteration count) with
+ * every operation of the loop rounded to t bits; pc: NB_PC_NONE (the
+ * paper's no-preconditioner case) or NB_PC_JACOBI.  b_dev: FP64 L-vector
+ * (continuous, masked); x_dev receives the iterate.  hist_host (may be NULL,
+ * iters doubles) receives the loop's relative residual sqrt(rtr)/|b| after
+ * each iteration; *relres (may be NULL) the last.  |b| and the set-up stay
+ * in binary64.  Allocates and frees its own scratch. */
+nb_status nb_cg_vprec(nb_mesh *mesh, int t, int iters, nb_pc pc, const double *b_dev,
+                      double *x_dev, double *hist_host, double *relres);
+
+/* The same loop with Monte Carlo Arithmetic instead of rounding (Section 2,
+ * the MCA backend; Section 4.2 runs it at t = 23, 20 samples): every
+ * operation is computed in binary64 and its result (mode 1, random
+ * rounding) or its operands and result (mode 2, full MCA) are perturbed,
+ * inexact(x) = x + 2^(e_x - t) xi, xi uniform on (-1/2, 1/2),
+ * 2^(e_x - 1) <= |x| < 2^e_x.  Random numbers: SplitMix64 streams keyed by
+ * seed, launch and thread, so a run is reproducible for a given seed and
+ * launch shape.  Arguments as nb_cg_vprec; NB_ERR_ARG for another mode. */
+nb_status nb_cg_mca(nb_mesh *mesh, int mode, int t, uint64_t seed, int iters, nb_pc pc,
+                    const double *b_dev, double *x_dev, double *hist_host, double *relres);
+
 /* nb_glsc3 for callers that cannot let a library allocate memory: a
  * framework whose caching allocator owns the device memory, a process under
  * a hard memory budget, or a latency-critical loop that must not pay for

@@ -94,6 +94,9 @@ def _load():
         "nb_time_ax": (i32, [vp, i32, i32, i32, i32, vp, C.c_size_t, C.POINTER(dbl)]),
         "nb_ax_variants": (i32, [vp, i32]),
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
+        "nb_apply_vprec": (i32, [vp, i32, vp, vp]),
+        "nb_cg_vprec": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(dbl)]),
+        "nb_cg_mca": (i32, [vp, i32, i32, C.c_uint64, i32, i32, vp, vp, vp, C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -276,6 +279,30 @@ class Mesh:
         fp, fb = (_ptr(flush), flush.numel() * flush.element_size()) if flush is not None else (None, 0)
         check(lib.nb_time_ax(self.h, prec, int(cg_step), variant, reps, fp, fb, C.byref(ms)))
         return ms.value
+
+    def apply_vprec(self, t, u, w):
+        """w = A u with every operation rounded to t mantissa bits (FP64)."""
+        check(lib.nb_apply_vprec(self.h, int(t), self._vec(u, NB_FP64), self._vec(w, NB_FP64)))
+
+    def cg_vprec(self, t, iters, b, x, pc=None):
+        """`iters` CG iterations from zero with every operation of the loop
+        rounded to t mantissa bits; returns the loop's relative residuals."""
+        hist = np.zeros(max(int(iters), 1))
+        rel = C.c_double()
+        check(lib.nb_cg_vprec(self.h, int(t), int(iters), NB_PC_NONE if pc is None else pc,
+                              self._vec(b, NB_FP64), self._vec(x, NB_FP64), hist.ctypes.data,
+                              C.byref(rel)))
+        return hist[:int(iters)]
+
+    def cg_mca(self, mode, t, seed, iters, b, x, pc=None):
+        """Monte Carlo Arithmetic CG loop (mode "rr" or "mca", virtual
+        precision t); returns the loop's relative residuals."""
+        hist = np.zeros(max(int(iters), 1))
+        rel = C.c_double()
+        check(lib.nb_cg_mca(self.h, {"rr": 1, "mca": 2}[mode], int(t), int(seed), int(iters),
+                            NB_PC_NONE if pc is None else pc, self._vec(b, NB_FP64),
+                            self._vec(x, NB_FP64), hist.ctypes.data, C.byref(rel)))
+        return hist[:int(iters)]
 
     def ax_variants(self, prec) -> int:
         return lib.nb_ax_variants(self.h, prec)
