@@ -1,0 +1,155 @@
+"""FP64 reference of the overlapping Schwarz preconditioner with fast
+diagonalisation (the smoother of Nekbone's multigrid preconditioner, whose
+routines the paper names in Section 4.1 -- h1mg_schwarz, h1mg_fdm,
+h1mg_extrude, h1mg_do_fast, h1mg_tnsr3d_el -- without giving the algorithm).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+What it computes (the textbook one-level overlapping Schwarz method with
+minimal overlap; Fischer, J. Comput. Phys. 133, 1997; Lynch, Rice and Thomas,
+Numer. Math. 6, 1964 for the fast diagonalisation):
+
+* subdomains: every element extended by one GLL node layer into each
+  neighbour, i.e. the (n+2)^3 lattice points [ex N - 1, ex N + N + 1] x ... of
+  the global GLL lattice; lattice points outside the domain or on its
+  (Dirichlet) boundary carry no unknown;
+* local operator: the separable approximation
+  A_e = Bz (x) By (x) Ax + Bz (x) Ay (x) Bx + Az (x) By (x) Bx, with Ad and Bd the
+  1D stiffness and (diagonal GLL) mass matrices assembled over the element
+  and its two neighbours in direction d and restricted to the n+2 extended
+  nodes, on the undeformed box (element length 1 / n_d) -- exact for an
+  undeformed box;
+* fast diagonalisation: Ad S = Bd S Lam (S^T Bd S = I), so
+  A_e^-1 = (Sz (x) Sy (x) Sx) diag(1 / (lx + ly + lz)) (Sz (x) Sy (x) Sx)^T;
+* additive combination: z = sum_e R_e^T A_e^-1 R_e r with R_e the restriction
+  of the global vector to subdomain e (symmetric positive definite).
+
+Pinned by ``tests/test_oracle_schwarz.py``: the fast diagonalisation against
+a dense solve of the Kronecker operator, the single-element box (where the
+preconditioner is the exact inverse and CG converges in one step),
+symmetry, and the 1D operators against the element's GLL matrices.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import deriv, gll
+
+
+def gll_1d(N: int):
+    """1D GLL stiffness and mass on [-1, 1]: K[i][j] = sum_q w_q D[q][i] D[q][j],
+    M = diag(w)."""
+    xi, w = gll(N)
+    D = deriv(N, xi)
+    K = (D.T * w) @ D
+    return K, np.diag(w)
+
+
+def fdm_1d(N: int, L: float, left: bool, right: bool):
+    """Extended 1D operators for an element of length L with a neighbour of the
+    same length on the left / right (flags), on the n+2 nodes
+    [x_{-1}, x_0 .. x_N, x_{N+1}]; nodes without an unknown (outside the
+    domain, or the domain's Dirichlet face) are decoupled as identity rows.
+    Returns (S, lam, active): S^T B S = I, S^T A S = diag(lam)."""
+    n = N + 1
+    m = n + 2
+    K, M = gll_1d(N)
+    A = np.zeros((m, m))
+    B = np.zeros((m, m))
+    sk, sm = 2.0 / L, L / 2.0
+    # the element: nodes 1..n of the extended grid
+    A[1:n + 1, 1:n + 1] += sk * K
+    B[1:n + 1, 1:n + 1] += sm * M
+    if left:  # left neighbour's nodes N-1, N = extended nodes 0, 1
+        A[0:2, 0:2] += sk * K[N - 1:N + 1, N - 1:N + 1]
+        B[0:2, 0:2] += sm * M[N - 1:N + 1, N - 1:N + 1]
+    if right:  # right neighbour's nodes 0, 1 = extended nodes n, n+1
+        A[n:n + 2, n:n + 2] += sk * K[0:2, 0:2]
+        B[n:n + 2, n:n + 2] += sm * M[0:2, 0:2]
+    active = np.ones(m, dtype=bool)
+    if not left:
+        active[0] = False
+        active[1] = False  # the domain's face: Dirichlet
+    if not right:
+        active[n + 1] = False
+        active[n] = False
+    A[~active, :] = 0.0
+    A[:, ~active] = 0.0
+    B[~active, :] = 0.0
+    B[:, ~active] = 0.0
+    idx = np.nonzero(~active)[0]
+    A[idx, idx] = 1.0
+    B[idx, idx] = 1.0
+    lam, S = sla.eigh(A, B)
+    return S, lam, active
+
+
+def _element_fdm(N, box, ex, ey, ez):
+    out = []
+    for e_d, n_d in ((ex, box.nx), (ey, box.ny), (ez, box.nz)):
+        out.append(fdm_1d(N, 1.0 / n_d, e_d > 0, e_d < n_d - 1))
+    return out
+
+
+def local_solve(fdm, rt: np.ndarray) -> np.ndarray:
+    """A_e^-1 rt for an extended array rt[c][b][a] (a fastest) by fast
+    diagonalisation; entries without an unknown stay zero."""
+    (Sx, lx, ax), (Sy, ly, ay), (Sz, lz, az) = fdm
+    act = az[:, None, None] & ay[None, :, None] & ax[None, None, :]
+    r = np.where(act, rt, 0.0)
+    t = np.einsum("ia,cbi->cba", Sx, r)      # apply Sx^T along a
+    t = np.einsum("jb,cja->cba", Sy, t)
+    t = np.einsum("kc,kba->cba", Sz, t)
+    t = t / (lx[None, None, :] + ly[None, :, None] + lz[:, None, None])
+    t = np.einsum("ai,cbi->cba", Sx, t)      # apply Sx along a
+    t = np.einsum("bj,cja->cba", Sy, t)
+    t = np.einsum("ck,kba->cba", Sz, t)
+    return np.where(act, t, 0.0)
+
+
+def precondition(P, r: np.ndarray) -> np.ndarray:
+    """z = sum_e R_e^T A_e^-1 R_e r for a continuous, masked L-vector r
+    (oracle.Problem P); returns the L-vector z (continuous, masked)."""
+    box, N = P.box, P.N
+    n = N + 1
+    gx_n, gy_n, gz_n = box.nx * N + 1, box.ny * N + 1, box.nz * N + 1
+    rg = P.to_global(r).reshape(gz_n, gy_n, gx_n)
+    zg = np.zeros_like(rg)
+    m = n + 2
+    for ez in range(box.nz):
+        for ey in range(box.ny):
+            for ex in range(box.nx):
+                fdm = _element_fdm(N, box, ex, ey, ez)
+                x0, y0, z0 = ex * N - 1, ey * N - 1, ez * N - 1
+                rt = np.zeros((m, m, m))
+                xs = np.arange(x0, x0 + m)
+                ys = np.arange(y0, y0 + m)
+                zs = np.arange(z0, z0 + m)
+                okx = (xs >= 0) & (xs < gx_n)
+                oky = (ys >= 0) & (ys < gy_n)
+                okz = (zs >= 0) & (zs < gz_n)
+                sub = np.ix_(zs[okz], ys[oky], xs[okx])
+                loc = np.ix_(np.nonzero(okz)[0], np.nonzero(oky)[0], np.nonzero(okx)[0])
+                rt[loc] = rg[sub]
+                zt = local_solve(fdm, rt)
+                zg[sub] += zt[loc]
+    z = P.to_local(zg.reshape(-1), masked=True)
+    return z
+
+
+def dense_local_operator(fdm) -> np.ndarray:
+    """The separable extended-element operator as a dense matrix on the
+    active extended nodes (for the pins)."""
+    (Sx, lx, ax), (Sy, ly, ay), (Sz, lz, az) = fdm
+    mats = []
+    for S, lam in ((Sx, lx), (Sy, ly), (Sz, lz)):
+        Binv = S @ S.T          # S S^T = B^-1
+        B = np.linalg.inv(Binv)
+        A = B @ S @ np.diag(lam) @ S.T @ B
+        mats.append((A, B))
+    (Ax, Bx), (Ay, By), (Az, Bz) = mats
+    full = (np.kron(Bz, np.kron(By, Ax)) + np.kron(Bz, np.kron(Ay, Bx)) +
+            np.kron(Az, np.kron(By, Bx)))
+    act = (az[:, None, None] & ay[None, :, None] & ax[None, None, :]).reshape(-1)
+    return full[np.ix_(act, act)], act

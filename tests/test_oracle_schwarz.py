@@ -1,0 +1,131 @@
+"""Pins of the Schwarz / fast-diagonalisation oracle: the 1D GLL matrices
+against exact integrals, the extended 1D operator against a separately
+assembled three-element chain, the fast diagonalisation against a dense solve
+of the Kronecker operator, the single-element box (exact inverse), symmetry,
+and the iteration count against Jacobi."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import schwarz
+from workloads import Box, rhs_global
+
+
+@pytest.mark.parametrize("N", [2, 4, 7])
+def test_gll_1d_matrices(N):
+    K, M = schwarz.gll_1d(N)
+    xi, w = oracle.gll(N)
+    np.testing.assert_allclose(K, K.T, atol=1e-13)
+    assert np.abs(K @ np.ones(N + 1)).max() < 1e-12
+    # (K x)_i = int phi_i' dx = phi_i(1) - phi_i(-1)
+    ref = np.zeros(N + 1)
+    ref[0], ref[-1] = -1.0, 1.0
+    np.testing.assert_allclose(K @ xi, ref, atol=1e-12)
+    # exact energy of x^2: int (2x)^2 = 8/3
+    assert abs(xi ** 2 @ K @ xi ** 2 - 8.0 / 3.0) < 1e-12
+    assert abs(np.trace(M) - 2.0) < 1e-14
+
+
+def _chain(N, L, count):
+    """1D stiffness and mass of `count` elements of length L, assembled."""
+    K, M = schwarz.gll_1d(N)
+    nn = count * N + 1
+    A = np.zeros((nn, nn))
+    B = np.zeros((nn, nn))
+    for e in range(count):
+        s = slice(e * N, e * N + N + 1)
+        A[s, s] += (2.0 / L) * K
+        B[s, s] += (L / 2.0) * M
+    return A, B
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_extended_1d_operator_is_the_chain_window(N):
+    L = 0.25
+    A3, B3 = _chain(N, L, 3)
+    # interior element: window from the left neighbour's node N-1 to the right
+    # neighbour's node 1, Dirichlet beyond (rows / columns outside dropped)
+    lo, hi = N - 1, 2 * N + 1
+    S, lam, act = schwarz.fdm_1d(N, L, True, True)
+    assert act.all()
+    A = A3[lo:hi + 1, lo:hi + 1]
+    B = B3[lo:hi + 1, lo:hi + 1]
+    # B S Lam S^T B = A and S^T B S = I reconstruct the window
+    np.testing.assert_allclose(S.T @ B @ S, np.eye(N + 3), atol=1e-11)
+    np.testing.assert_allclose(S.T @ A @ S, np.diag(lam), atol=1e-9 * np.abs(lam).max())
+    # a boundary element (no left neighbour): its face node and the node
+    # beyond carry no unknown
+    S, lam, act = schwarz.fdm_1d(N, L, False, True)
+    assert not act[0] and not act[1] and act[2:].all()
+
+
+def _kron_operator(N, box, ex, ey, ez):
+    """The separable operator built from the chain windows directly."""
+    mats = []
+    for e_d, n_d in ((ex, box.nx), (ey, box.ny), (ez, box.nz)):
+        L = 1.0 / n_d
+        A3, B3 = _chain(N, L, 3)
+        A = A3[N - 1:2 * N + 2, N - 1:2 * N + 2].copy()
+        B = B3[N - 1:2 * N + 2, N - 1:2 * N + 2].copy()
+        act = np.ones(N + 3, dtype=bool)
+        if e_d == 0:
+            act[:2] = False
+        if e_d == n_d - 1:
+            act[-2:] = False
+        mats.append((A, B, act))
+    (Ax, Bx, ax), (Ay, By, ay), (Az, Bz, az) = mats
+    full = (np.kron(Bz, np.kron(By, Ax)) + np.kron(Bz, np.kron(Ay, Bx)) +
+            np.kron(Az, np.kron(By, Bx)))
+    act = (az[:, None, None] & ay[None, :, None] & ax[None, None, :]).reshape(-1)
+    return full[np.ix_(act, act)], act
+
+
+@pytest.mark.parametrize("pos", [(1, 1, 1), (0, 1, 2), (2, 0, 0)])
+def test_fast_diagonalisation_equals_dense_solve(pos):
+    N = 3
+    box = Box(3, 3, 3, N, 0.0)
+    fdm = schwarz._element_fdm(N, box, *pos)
+    Ad, act = _kron_operator(N, box, *pos)
+    rng = np.random.default_rng(1)
+    m = N + 3
+    rt = rng.uniform(-1, 1, (m, m, m))
+    z = schwarz.local_solve(fdm, rt)
+    ref = np.linalg.solve(Ad, rt.reshape(-1)[act])
+    np.testing.assert_allclose(z.reshape(-1)[act], ref, atol=1e-10 * np.abs(ref).max())
+    assert np.all(z.reshape(-1)[~act] == 0)
+
+
+def test_single_element_box_is_the_exact_inverse():
+    """One undeformed element with Dirichlet faces: the subdomain is the
+    domain and the separable operator is exact, so z = A^-1 r and CG with the
+    preconditioner converges in one step."""
+    box = Box(1, 1, 1, 5, 0.0)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 0))
+    z = schwarz.precondition(P, b)
+    np.testing.assert_allclose(P.apply(z), b, atol=1e-11 * np.abs(b).max())
+    x, it, rel, _ = P.fcg(b, lambda r: schwarz.precondition(P, r), tol=1e-10, maxit=10)
+    assert it == 1 and rel < 1e-10
+
+
+def test_preconditioner_is_symmetric_and_positive():
+    box = Box(3, 2, 2, 4, 0.05)
+    P = oracle.Problem(box)
+    u = P.to_local(rhs_global(box, 1))
+    v = P.to_local(rhs_global(box, 2))
+    Mu = schwarz.precondition(P, u)
+    Mv = schwarz.precondition(P, v)
+    a, b = P.glsc3(v, Mu), P.glsc3(u, Mv)
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+    assert P.glsc3(u, Mu) > 0 and P.glsc3(v, Mv) > 0
+
+
+def test_fewer_iterations_than_jacobi():
+    box = Box(4, 4, 4, 5, 0.05)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 3))
+    _, it_j, _, _ = P.pcg(b, tol=1e-8, maxit=2000)
+    _, it_s, rel, _ = P.fcg(b, lambda r: schwarz.precondition(P, r), tol=1e-8, maxit=2000)
+    print(f"Jacobi {it_j} iterations, Schwarz {it_s}")
+    assert rel < 1e-8
+    assert it_s < 0.6 * it_j
