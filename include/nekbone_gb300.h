@@ -70,7 +70,10 @@ typedef enum {
 typedef enum {
     NB_PC_NONE = 0,    /* solveM is a copy (the paper's no-multigrid case) */
     NB_PC_JACOBI = 1,  /* z = diag(A)^-1 r */
-    NB_PC_LEARNED = 2  /* per-element network inside flexible CG */
+    NB_PC_LEARNED = 2, /* per-element network inside flexible CG */
+    NB_PC_SCHWARZ = 3  /* overlapping Schwarz, fast-diagonalisation local solves
+                          (the smoother of Nekbone's multigrid solveM); FP32
+                          refinement steps, even n, orders N <= 11 */
 } nb_pc;
 
 typedef struct {
@@ -376,6 +379,20 @@ nb_status nb_cg_vprec(nb_mesh *mesh, int t, int iters, nb_pc pc, const double *b
  * launch shape.  Arguments as nb_cg_vprec; NB_ERR_ARG for another mode. */
 nb_status nb_cg_mca(nb_mesh *mesh, int mode, int t, uint64_t seed, int iters, nb_pc pc,
                     const double *b_dev, double *x_dev, double *hist_host, double *relres);
+
+/* ------------------------------------------------------------------------
+ * Overlapping Schwarz preconditioner (Section 4.1 names Nekbone's multigrid
+ * solveM routines h1mg_schwarz, h1mg_fdm, h1mg_extrude, h1mg_do_fast,
+ * h1mg_tnsr3d_el; the paper gives no algorithm, this is the textbook
+ * one-level method with minimal overlap): z = sum_e R_e^T A_e^-1 R_e r, R_e
+ * the restriction to element e extended by one GLL layer into each
+ * neighbour, A_e the separable operator on the undeformed box inverted by
+ * fast diagonalisation.  Symmetric positive definite; used by NB_PC_SCHWARZ.
+ * ------------------------------------------------------------------------ */
+
+/* z = M r once, FP32 L-vectors (continuous, masked), device.  Builds the 1D
+ * eigenvectors and the scratch on first use (allocates).  Orders N <= 11. */
+nb_status nb_schwarz_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
 
 /* nb_glsc3 for callers that cannot let a library allocate memory: a
  * framework whose caching allocator owns the device memory, a process under

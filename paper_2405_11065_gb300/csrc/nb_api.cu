@@ -50,6 +50,7 @@ static void free_ws(Workspace &ws)
 }
 
 void learned_free(nb_mesh *m);  // nb_learned.cu
+void schwarz_free(nb_mesh *m);  // nb_schwarz.cu
 
 }  // namespace nb
 
@@ -117,6 +118,7 @@ nb_status nb_mesh_destroy(nb_mesh *m)
     cudaSetDevice(m->ctx->device);
     cudaStreamSynchronize(m->ctx->stream);
     learned_free(m);
+    schwarz_free(m);
     free_ws(m->ws64);
     free_ws(m->ws32);
     void *bufs[] = {m->D64, m->D32, m->G64, m->G32, m->gid, m->gs_off, m->gs_loc, m->gs_gid,
@@ -343,7 +345,7 @@ static nb_status check_opts(const nb_opts *o)
 {
     if (!o) return arg_error("opts is NULL");
     if (!prec_ok(o->prec)) return arg_error("opts.prec");
-    if (o->pc < NB_PC_NONE || o->pc > NB_PC_LEARNED) return arg_error("opts.pc");
+    if (o->pc < NB_PC_NONE || o->pc > NB_PC_SCHWARZ) return arg_error("opts.pc");
     if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return arg_error("opts.rtol must be in (0,1)");
     if (o->maxiter < 0) return arg_error("opts.maxiter");
     if (o->prec != NB_FP64 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0)))
@@ -351,6 +353,8 @@ static nb_status check_opts(const nb_opts *o)
     if (o->max_outer < 0) return arg_error("opts.max_outer");
     if (o->pc == NB_PC_LEARNED && o->prec == NB_FP64)
         return arg_error("the learned preconditioner runs inside refinement (prec != NB_FP64)");
+    if (o->pc == NB_PC_SCHWARZ && o->prec != NB_FP32)
+        return arg_error("the Schwarz preconditioner runs inside FP32 refinement (prec = NB_FP32)");
     return NB_OK;
 }
 

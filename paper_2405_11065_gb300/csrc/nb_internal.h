@@ -150,6 +150,8 @@ struct nb_mesh {
     int64_t launches = 0;            // kernels issued by the current solve
     // learned preconditioner (optional)
     void *learned = nullptr;
+    // Schwarz preconditioner data (built on first use)
+    void *schwarz = nullptr;
 };
 
 namespace nb {

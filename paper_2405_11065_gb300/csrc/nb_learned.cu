@@ -1167,6 +1167,142 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     return NB_OK;
 }
 
+// Owner-copy partials of (z, w_prev) and (r, z) of a preconditioned residual
+// z; the last block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on
+// the first step) and rtz = (r, z), as k_lpc does for the learned
+// preconditioner.
+__global__ void k_zdots(int64_t n, const float *__restrict__ r, const float *__restrict__ z,
+                        const float *__restrict__ wold, const float *__restrict__ sgn,
+                        CgScalars *sc, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    if (sc->done) return;
+    DotAcc<float> zw, rz;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        if (!signbit(sgn[l])) {
+            zw.add(z[l] * wold[l]);
+            rz.add(r[l] * z[l]);
+        }
+    const double tzw = block_sum(zw.value(), sred);
+    const double trz = block_sum(rz.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tzw;
+        part[gridDim.x + blockIdx.x] = trz;
+    }
+    if (last_block(&sc->tick_upd)) {
+        const double szw = sum_partials(part, gridDim.x, sred);
+        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
+        if (threadIdx.x == 0) {
+            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
+            sc->rtz = srz;
+            sc->rp = srz;
+            if (!isfinite(sc->beta) || !isfinite(srz) || !(srz > 0.0)) {
+                sc->done = 1;
+                sc->status = NB_BREAKDOWN;
+            }
+        }
+    }
+}
+
+nb_status schwarz_setup(nb_mesh *m);
+nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s);
+
+// The inner solve of a refinement step with the Schwarz preconditioner (FP32,
+// even n): flexible CG -- for this linear, symmetric preconditioner it is
+// preconditioned CG up to rounding -- one step being the preconditioner
+// (three kernels), k_zdots, the operator's direction form with alpha, the
+// summation and k_fcg_step_update.  Graph-captured like fcg_learned.
+nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
+{
+    if (prec != NB_FP32 || !ax_dir_step_available(m)) {
+        set_error("the Schwarz preconditioner runs in FP32 refinement steps with even n");
+        return NB_ERR_ARG;
+    }
+    NB_TRY(schwarz_setup(m));  // before any capture: it allocates once
+    const int g = vec_grid(m->ctx, m->nL);
+    const float *sgn = m->dinv32;
+    float *x = (float *)ws.x, *r = (float *)ws.r, *p = (float *)ws.p, *w = (float *)ws.w;
+    float *z = (float *)ws.z, *wprev = (float *)ws.aux;
+    double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
+    NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
+    NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
+    k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
+    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
+    NB_CUDA(cudaGetLastError());
+    m->launches += 2;
+    auto step = [&](float *wcur, float *wold) -> nb_status {
+        NB_TRY(schwarz_apply(m, r, z, s));
+        k_zdots<<<g, kVecThreads, 0, s>>>(m->nL, r, z, wold, sgn, ws.scal, P0);
+        NB_CUDA(cudaGetLastError());
+        int nparts = 0;
+        NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
+        NB_TRY(dssum(m, prec, wcur, 1, s));
+        k_fcg_step_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
+        NB_CUDA(cudaGetLastError());
+        return NB_OK;
+    };
+    constexpr int kPerStep = 7;  // three preconditioner kernels, dots, operator, summation, update
+    if (o->use_graph) {
+        const intptr_t key = (intptr_t)m->schwarz;
+        if (!ws.exec2 || ws.graph2_key != key) {
+            if (ws.exec2) NB_CUDA(cudaGraphExecDestroy(ws.exec2));
+            if (ws.graph2) NB_CUDA(cudaGraphDestroy(ws.graph2));
+            ws.exec2 = nullptr;
+            ws.graph2 = nullptr;
+            cudaGraph_t gr;
+            NB_CUDA(cudaGraphCreate(&gr, 0));
+            cudaGraphConditionalHandle h;
+            NB_CUDA(cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            NB_CUDA(cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+            nb_status st = step(w, wprev);
+            if (st == NB_OK) st = step(wprev, w);
+            if (st == NB_OK) {
+                k_fcg_cond<<<1, 1, 0, s>>>(ws.scal, h);
+                if (cudaGetLastError() != cudaSuccess) st = NB_ERR_CUDA;
+            }
+            cudaGraph_t captured = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(s, &captured);
+            if (st != NB_OK || ce != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                if (st != NB_OK) return st;
+                set_error("Schwarz flexible-CG graph capture failed: %s", cudaGetErrorString(ce));
+                return NB_ERR_CUDA;
+            }
+            NB_CUDA(cudaGraphInstantiate(&ws.exec2, gr, 0));
+            ws.graph2 = gr;
+            ws.graph2_key = key;
+        }
+        NB_CUDA(cudaGraphLaunch(ws.exec2, s));
+        NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        NB_CUDA(cudaStreamSynchronize(s));
+        m->launches += (2 * kPerStep + 1) * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
+        return NB_OK;
+    }
+    for (int it = 0;; ++it) {
+        NB_TRY(step(w, wprev));
+        std::swap(w, wprev);
+        m->launches += kPerStep;
+        if ((it & 7) == 7) {
+            NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars),
+                                    cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaStreamSynchronize(s));
+            if (ws.scal_host->done) break;
+            if (it > ws.scal_host->maxit + 8) break;  // bounded even if the state is stuck
+        }
+    }
+    return NB_OK;
+}
+
 void learned_free(nb_mesh *m) { m->learned = nullptr; }
 
 }  // namespace nb

@@ -29,6 +29,8 @@ namespace nb {
 
 nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
                       cudaStream_t s);  // nb_learned.cu
+nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
+                      cudaStream_t s);  // nb_learned.cu
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -488,7 +490,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         if (rel < o->rtol) { result = NB_OK; break; }
         if (outer == o->max_outer || used >= o->maxiter) { result = NB_NOT_CONVERGED; break; }
         if (rel > 0.5 * prev) {
-            if (o->pc == NB_PC_LEARNED && !fell_back) {
+            if ((o->pc == NB_PC_LEARNED || o->pc == NB_PC_SCHWARZ) && !fell_back) {
                 fell_back = true;  // the learned steps stopped paying: Jacobi-PCG takes over
                 stagn = 0;
             } else if (++stagn >= 3) {
@@ -507,8 +509,15 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // the inner solve only has to close the remaining gap to rtol (with a
         // factor 2 of margin), and never less than inner_rtol per step
         const double tau = std::min(0.5, std::max(o->inner_rtol, 0.5 * o->rtol / rel));
-        const bool use_learned = o->pc == NB_PC_LEARNED && !fell_back;
-        if (use_learned) {
+        const bool use_learned = (o->pc == NB_PC_LEARNED || o->pc == NB_PC_SCHWARZ) && !fell_back;
+        if (use_learned && o->pc == NB_PC_SCHWARZ) {
+            // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, remaining,
+                                       o->record_history ? ws.hist : nullptr,
+                                       o->record_history ? ws.hist_cap : 0);
+            NB_CUDA(cudaGetLastError());
+            NB_TRY(fcg_schwarz(m, o->prec, ws, o, s));
+        } else if (use_learned) {
             // flexible CG with the learned preconditioner (nb_learned.cu), on a
             // bounded budget; Jacobi-PCG takes over if it fails
             k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, kLearnedBudget),
