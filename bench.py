@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
     ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned", "vprec",
-                                       "learned-step", "batched-step"],
+                                       "learned-step", "batched-step", "schwarz-step"],
                     default="full",
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture); "
@@ -474,6 +474,25 @@ def run_learned_step(args):
     return 0
 
 
+def run_schwarz_step(args):
+    """Profiling aid: `--steps` flexible-CG steps with the Schwarz
+    preconditioner on the main workload's mesh (E=4096, N=9), host-launched
+    with --no-graph so that a profiler lists every kernel."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    mesh = nb.Mesh.from_box(ctx, BOX)
+    b = _rhs_local(nb, mesh, BOX, 0, dev)
+    x = torch.zeros_like(b)
+    o = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_SCHWARZ, rtol=1e-10, maxiter=args.steps,
+                        max_outer=1, use_graph=0 if args.no_graph else 1)
+    st = mesh.solve(b, x, o)
+    print(json.dumps({"mode": "schwarz-step", "iters": st["iters"], "ms": st["seconds"] * 1e3}),
+          flush=True)
+    return 0
+
+
 def run_batched_step(args):
     """Profiling aid: the batched workload's first `--steps` iterations
     (one refinement step), host-launched with --no-graph so that a profiler
@@ -547,10 +566,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode in ("sweep", "batched", "learned", "vprec", "learned-step", "batched-step"):
+    if args.mode in ("sweep", "batched", "learned", "vprec", "learned-step", "batched-step",
+                     "schwarz-step"):
         return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned,
                 "vprec": run_vprec, "learned-step": run_learned_step,
-                "batched-step": run_batched_step}[args.mode](args)
+                "batched-step": run_batched_step, "schwarz-step": run_schwarz_step}[args.mode](args)
     rank, world, local = dist_env()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -658,6 +678,22 @@ def main():
         fp64_ms.append(e0.elapsed_time(e1))
     t64 = statistics.median(fp64_ms)
     tm = statistics.median(step_ms)
+    # the same mixed solve with the overlapping Schwarz preconditioner (the
+    # smoother of the paper's multigrid solveM)
+    osw = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_SCHWARZ, rtol=RTOL)
+    xs = torch.zeros_like(b)
+    mesh.solve(b, xs, osw)
+    sw_ms, sw_stats = [], None
+    for _ in range(3):
+        flush.fill_(3)
+        xs.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sw_stats = mesh.solve(b, xs, osw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sw_ms.append(e0.elapsed_time(e1))
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
 
     # energy to solution, mixed vs FP64 (outside the timed region; the GPU's
@@ -760,7 +796,10 @@ def main():
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": launches,
-            "time_to_solution_ms": {"mixed_fp32_refined": tm, "fp64_pcg": t64},
+            "time_to_solution_ms": {"mixed_fp32_refined": tm, "fp64_pcg": t64,
+                                    "mixed_schwarz": statistics.median(sw_ms)},
+            "schwarz": {"iters": sw_stats["iters"], "outer": sw_stats["outer_iters"],
+                        "rel_res": sw_stats["rel_res"], "status": sw_stats["status"]},
             "gain_vs_fp64": (t64 - tm) / t64,
             "speedup_vs_fp64": t64 / tm,
             "iterations": {"mixed_inner": stats[-1]["iters"], "mixed_outer": stats[-1]["outer_iters"],

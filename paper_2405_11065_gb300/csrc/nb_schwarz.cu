@@ -136,90 +136,120 @@ __device__ __forceinline__ int sw_variant(int e_d, int n_d)
     return (e_d == 0 ? 1 : 0) + (e_d == n_d - 1 ? 2 : 0);
 }
 
-// A_e^-1 R_e r for every element (one block per element): zt[e][c][b][a].
+// One line of a tensor contraction: out[q] = sum_i M[i][q] v[i], M in padded
+// rows of P values (16-byte loads, the same row for every thread: broadcast).
+template <int m, int P>
+__device__ __forceinline__ void sw_line(const float *__restrict__ M, const float (&v)[m],
+                                        float (&out)[m])
+{
+#pragma unroll
+    for (int q = 0; q < m; ++q) out[q] = 0.f;
+#pragma unroll
+    for (int i = 0; i < m; ++i) {
+        const float4 *row = reinterpret_cast<const float4 *>(M + i * P);
+#pragma unroll
+        for (int q4 = 0; q4 < P / 4; ++q4) {
+            const float4 s = row[q4];
+            if (4 * q4 + 0 < m) out[4 * q4 + 0] += s.x * v[i];
+            if (4 * q4 + 1 < m) out[4 * q4 + 1] += s.y * v[i];
+            if (4 * q4 + 2 < m) out[4 * q4 + 2] += s.z * v[i];
+            if (4 * q4 + 3 < m) out[4 * q4 + 3] += s.w * v[i];
+        }
+    }
+}
+
+// A_e^-1 R_e r for every element: one block per element, one thread per line
+// of the extended box (m^2 lines per direction), each contraction done by a
+// thread for a whole line held in registers (the 1D matrices in shared
+// memory, read as broadcast 16-byte rows).  Phases: a-lines (the gather from
+// the global vector, S^T), b-lines (S^T), c-lines (S^T and the eigenvalue
+// scaling), a-lines (S), b-lines (S), c-lines (S, stored).  zt[e][c][b][a].
 template <int m>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__((m * m + 31) / 32 * 32)
 k_sw_local(int64_t E, int nx, int ny, int nz, int N, const float *__restrict__ rg,
            const float *__restrict__ Sall, const float *__restrict__ lall,
            float *__restrict__ zt)
 {
-    constexpr int m2 = m * m, m3 = m2 * m;
-    __shared__ float t0[m3], t1[m3];
-    __shared__ float Sx[m2], Sy[m2], Sz[m2], lx[m], ly[m], lz[m];
+    constexpr int m2 = m * m, m3 = m2 * m, P = (m + 3) / 4 * 4;
+    __shared__ __align__(16) float t0[m3], t1[m3];
+    // per direction: S^T rows (M[i][q] = S[i][q]) and S rows (M[i][q] = S[q][i])
+    __shared__ __align__(16) float St[3][m * P], Sf[3][m * P];
+    __shared__ float lam[3][m];
     const int gxn = nx * N + 1, gyn = ny * N + 1, gzn = nz * N + 1;
+    const int tid = threadIdx.x;
+    const bool act = tid < m2;
+    const int hi = act ? tid / m : 0, lo = act ? tid % m : 0;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-        const int vx = sw_variant(ex, nx), vy = sw_variant(ey, ny), vz = sw_variant(ez, nz);
-        __syncthreads();  // the previous element is done with the buffers
-        for (int q = threadIdx.x; q < m2; q += blockDim.x) {
-            Sx[q] = Sall[(0 * 4 + vx) * m2 + q];
-            Sy[q] = Sall[(1 * 4 + vy) * m2 + q];
-            Sz[q] = Sall[(2 * 4 + vz) * m2 + q];
+        const int var[3] = {sw_variant(ex, nx), sw_variant(ey, ny), sw_variant(ez, nz)};
+        __syncthreads();  // the previous element is done with the matrices
+        for (int q = tid; q < 3 * m2; q += blockDim.x) {
+            const int d = q / m2, r = q % m2, i = r / m, c = r % m;
+            const float v = Sall[(d * 4 + var[d]) * m2 + r];  // S[i][c]
+            St[d][i * P + c] = v;
+            Sf[d][c * P + i] = v;
         }
-        for (int q = threadIdx.x; q < m; q += blockDim.x) {
-            lx[q] = lall[(0 * 4 + vx) * m + q];
-            ly[q] = lall[(1 * 4 + vy) * m + q];
-            lz[q] = lall[(2 * 4 + vz) * m + q];
-        }
-        // the extended box from the global lattice (zero outside the domain)
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, b = (q / m) % m, c = q / m2;
-            const int gx = ex * N - 1 + a, gy = ey * N - 1 + b, gz = ez * N - 1 + c;
-            float v = 0.f;
-            if (gx >= 0 && gx < gxn && gy >= 0 && gy < gyn && gz >= 0 && gz < gzn)
-                v = rg[((int64_t)gz * gyn + gy) * gxn + gx];
-            t0[q] = v;
+        for (int q = tid; q < 3 * m; q += blockDim.x)
+            lam[q / m][q % m] = lall[(q / m * 4 + var[q / m]) * m + q % m];
+        __syncthreads();
+        float v[m], o[m];
+        // a-lines (c, b) = (hi, lo): the extended box row from the global lattice
+        if (act) {
+            const int gy = ey * N - 1 + lo, gz = ez * N - 1 + hi;
+            const bool okyz = gy >= 0 && gy < gyn && gz >= 0 && gz < gzn;
+#pragma unroll
+            for (int a = 0; a < m; ++a) {
+                const int gx = ex * N - 1 + a;
+                v[a] = (okyz && gx >= 0 && gx < gxn) ? rg[((int64_t)gz * gyn + gy) * gxn + gx] : 0.f;
+            }
+            sw_line<m, P>(St[0], v, o);
+#pragma unroll
+            for (int a = 0; a < m; ++a) t0[(hi * m + lo) * m + a] = o[a];
         }
         __syncthreads();
-        // S^T along a, b, c
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, cb = q - a;
-            float s = 0.f;
+        // b-lines (c, a) = (hi, lo)
+        if (act) {
 #pragma unroll
-            for (int i = 0; i < m; ++i) s += Sx[i * m + a] * t0[cb + i];
-            t1[q] = s;
+            for (int j = 0; j < m; ++j) v[j] = t0[(hi * m + j) * m + lo];
+            sw_line<m, P>(St[1], v, o);
+#pragma unroll
+            for (int b = 0; b < m; ++b) t1[(hi * m + b) * m + lo] = o[b];
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, b = (q / m) % m, c = q / m2;
-            float s = 0.f;
+        // c-lines (b, a) = (hi, lo), then the scaling by 1 / (lx + ly + lz)
+        if (act) {
 #pragma unroll
-            for (int j = 0; j < m; ++j) s += Sy[j * m + b] * t1[(c * m + j) * m + a];
-            t0[q] = s;
+            for (int k = 0; k < m; ++k) v[k] = t1[(k * m + hi) * m + lo];
+            sw_line<m, P>(St[2], v, o);
+            const float lab = lam[0][lo] + lam[1][hi];
+#pragma unroll
+            for (int c = 0; c < m; ++c) t0[(c * m + hi) * m + lo] = o[c] / (lab + lam[2][c]);
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, b = (q / m) % m, c = q / m2;
-            float s = 0.f;
+        // back: a-lines with S
+        if (act) {
 #pragma unroll
-            for (int k = 0; k < m; ++k) s += Sz[k * m + c] * t0[(k * m + b) * m + a];
-            t1[q] = s / (lx[a] + ly[b] + lz[c]);
+            for (int a = 0; a < m; ++a) v[a] = t0[(hi * m + lo) * m + a];
+            sw_line<m, P>(Sf[0], v, o);
+#pragma unroll
+            for (int a = 0; a < m; ++a) t1[(hi * m + lo) * m + a] = o[a];
         }
         __syncthreads();
-        // S along a, b, c
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, cb = q - a;
-            float s = 0.f;
+        if (act) {
 #pragma unroll
-            for (int i = 0; i < m; ++i) s += Sx[a * m + i] * t1[cb + i];
-            t0[q] = s;
+            for (int j = 0; j < m; ++j) v[j] = t1[(hi * m + j) * m + lo];
+            sw_line<m, P>(Sf[1], v, o);
+#pragma unroll
+            for (int b = 0; b < m; ++b) t0[(hi * m + b) * m + lo] = o[b];
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, b = (q / m) % m, c = q / m2;
-            float s = 0.f;
+        if (act) {
 #pragma unroll
-            for (int j = 0; j < m; ++j) s += Sy[b * m + j] * t0[(c * m + j) * m + a];
-            t1[q] = s;
-        }
-        __syncthreads();
-        float *out = zt + e * m3;
-        for (int q = threadIdx.x; q < m3; q += blockDim.x) {
-            const int a = q % m, b = (q / m) % m, c = q / m2;
-            float s = 0.f;
+            for (int k = 0; k < m; ++k) v[k] = t0[(k * m + hi) * m + lo];
+            sw_line<m, P>(Sf[2], v, o);
+            float *out = zt + e * m3;
 #pragma unroll
-            for (int k = 0; k < m; ++k) s += Sz[c * m + k] * t1[(k * m + b) * m + a];
-            out[q] = s;
+            for (int c = 0; c < m; ++c) out[(c * m + hi) * m + lo] = o[c];
         }
     }
 }
@@ -261,7 +291,7 @@ static nb_status sw_launch_local(int m, int grid, int64_t E, int nx, int ny, int
                                  const float *rg, const float *S, const float *lam, float *zt,
                                  cudaStream_t s)
 {
-#define NB_SW(MM) k_sw_local<MM><<<grid, 256, 0, s>>>(E, nx, ny, nz, N, rg, S, lam, zt)
+#define NB_SW(MM) k_sw_local<MM><<<grid, (MM * MM + 31) / 32 * 32, 0, s>>>(E, nx, ny, nz, N, rg, S, lam, zt)
     switch (m) {
         case 4: NB_SW(4); break;
         case 5: NB_SW(5); break;
@@ -349,7 +379,7 @@ nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s)
     const int g = vec_grid(m->ctx, m->nL);
     k_sw_global<<<g, kVecThreads, 0, s>>>(m->nL, r, m->dinv32, m->gid, d->rg);
     NB_CUDA(cudaGetLastError());
-    const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
+    const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 12);
     NB_TRY(sw_launch_local(d->m, grid, m->E, m->nx, m->ny, m->nz, m->N, d->rg, d->S, d->lam,
                            d->zt, s));
     k_sw_sum<<<g, kVecThreads, 0, s>>>(m->nL, m->nx, m->ny, m->nz, m->N, d->m, d->zt, m->dinv32, z);
