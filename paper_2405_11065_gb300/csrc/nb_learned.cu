@@ -795,10 +795,12 @@ k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
 // x += alpha p, r -= alpha w (alpha from the operator's last block), the
 // owner-copy partials of (r, r), and in the last block the flexible-CG
 // bookkeeping: iteration count, history, pap_prev, the stopping tests.
+template <bool SCATTER>
 __global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__ x,
                                   float *__restrict__ r, const float *__restrict__ p,
                                   const float *__restrict__ w, const float *__restrict__ sgn,
-                                  double *__restrict__ part)
+                                  double *__restrict__ part, float *__restrict__ rg = nullptr,
+                                  const int32_t *__restrict__ gid = nullptr)
 {
     __shared__ double sred[32];
     if (sc->done) return;
@@ -820,13 +822,23 @@ __global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__
         if (!signbit(dv.w)) acc.add(rv.w * rv.w);
         reinterpret_cast<float4 *>(x)[q] = xv;
         reinterpret_cast<float4 *>(r)[q] = rv;
+        if (SCATTER) {  // owner values of the new residual into the global vector
+            const int4 gv = reinterpret_cast<const int4 *>(gid)[q];
+            if (!signbit(dv.x)) rg[gv.x] = rv.x;
+            if (!signbit(dv.y)) rg[gv.y] = rv.y;
+            if (!signbit(dv.z)) rg[gv.z] = rv.z;
+            if (!signbit(dv.w)) rg[gv.w] = rv.w;
+        }
     }
     for (int64_t l = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
          l += (int64_t)gridDim.x * blockDim.x) {
         x[l] += alpha * p[l];
         const float rl = r[l] - alpha * w[l];
         r[l] = rl;
-        if (!signbit(sgn[l])) acc.add(rl * rl);
+        if (!signbit(sgn[l])) {
+            acc.add(rl * rl);
+            if (SCATTER) rg[gid[l]] = rl;
+        }
     }
     const double t = block_sum(acc.value(), sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
@@ -1085,7 +1097,7 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
             int nparts = 0;
             NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
             NB_TRY(dssum(m, prec, wcur, 1, s));
-            k_fcg_step_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
+            k_fcg_step_update<false><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
             NB_CUDA(cudaGetLastError());
             return NB_OK;
         }
@@ -1167,52 +1179,19 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     return NB_OK;
 }
 
-// Owner-copy partials of (z, w_prev) and (r, z) of a preconditioned residual
-// z; the last block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on
-// the first step) and rtz = (r, z), as k_lpc does for the learned
-// preconditioner.
-__global__ void k_zdots(int64_t n, const float *__restrict__ r, const float *__restrict__ z,
-                        const float *__restrict__ wold, const float *__restrict__ sgn,
-                        CgScalars *sc, double *__restrict__ part)
-{
-    __shared__ double sred[32];
-    if (sc->done) return;
-    DotAcc<float> zw, rz;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
-         l += (int64_t)gridDim.x * blockDim.x)
-        if (!signbit(sgn[l])) {
-            zw.add(z[l] * wold[l]);
-            rz.add(r[l] * z[l]);
-        }
-    const double tzw = block_sum(zw.value(), sred);
-    const double trz = block_sum(rz.value(), sred);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = tzw;
-        part[gridDim.x + blockIdx.x] = trz;
-    }
-    if (last_block(&sc->tick_upd)) {
-        const double szw = sum_partials(part, gridDim.x, sred);
-        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
-        if (threadIdx.x == 0) {
-            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
-            sc->rtz = srz;
-            sc->rp = srz;
-            if (!isfinite(sc->beta) || !isfinite(srz) || !(srz > 0.0)) {
-                sc->done = 1;
-                sc->status = NB_BREAKDOWN;
-            }
-        }
-    }
-}
-
 nb_status schwarz_setup(nb_mesh *m);
-nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s);
+nb_status schwarz_gather(nb_mesh *m, const float *r, cudaStream_t s);
+nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *wold,
+                            CgScalars *sc, double *part, cudaStream_t s);
+float *schwarz_rg(nb_mesh *m);
 
 // The inner solve of a refinement step with the Schwarz preconditioner (FP32,
 // even n): flexible CG -- for this linear, symmetric preconditioner it is
-// preconditioned CG up to rounding -- one step being the preconditioner
-// (three kernels), k_zdots, the operator's direction form with alpha, the
-// summation and k_fcg_step_update.  Graph-captured like fcg_learned.
+// preconditioned CG up to rounding -- one step being the local solves, their
+// sum with the flexible-CG dots (z, w_prev), (r, z) and beta, the operator's
+// direction form with alpha, the summation, and the update, which also
+// scatters the new residual's owner values for the next local solves.
+// Graph-captured like fcg_learned.
 nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
 {
     if (prec != NB_FP32 || !ax_dir_step_available(m)) {
@@ -1227,22 +1206,23 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
     NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
     NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
+    float *rg = schwarz_rg(m);
     k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
     k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
     NB_CUDA(cudaGetLastError());
-    m->launches += 2;
+    NB_TRY(schwarz_gather(m, r, s));
+    m->launches += 3;
     auto step = [&](float *wcur, float *wold) -> nb_status {
-        NB_TRY(schwarz_apply(m, r, z, s));
-        k_zdots<<<g, kVecThreads, 0, s>>>(m->nL, r, z, wold, sgn, ws.scal, P0);
-        NB_CUDA(cudaGetLastError());
+        NB_TRY(schwarz_solve_sum(m, r, z, wold, ws.scal, P0, s));
         int nparts = 0;
         NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
         NB_TRY(dssum(m, prec, wcur, 1, s));
-        k_fcg_step_update<<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
+        k_fcg_step_update<true><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2,
+                                                           rg, m->gid);
         NB_CUDA(cudaGetLastError());
         return NB_OK;
     };
-    constexpr int kPerStep = 7;  // three preconditioner kernels, dots, operator, summation, update
+    constexpr int kPerStep = 5;  // local solves, their sum, operator, summation, update
     if (o->use_graph) {
         const intptr_t key = (intptr_t)m->schwarz;
         if (!ws.exec2 || ws.graph2_key != key) {

@@ -11,11 +11,13 @@
 // in each direction on the undeformed box, inverted by fast diagonalisation
 // (Ad S = Bd S Lam, S^T Bd S = I; Lynch, Rice and Thomas 1964).
 //
-// Per application, three kernels: the owner copies of r into a global vector;
-// per element, the extended box gathered from it, six tensor contractions and
-// the eigenvalue scaling in shared memory, the result stored per element; per
-// local node, the sum of the results of the (at most 8) subdomains covering
-// its lattice point in a fixed order, masked.  The 1D eigenproblems are
+// Per application, three kernels: the owner copies of r into a global vector
+// (inside flexible CG, the update kernel writes them); per element, the
+// extended box gathered from it, six tensor contractions (one thread per line)
+// and the eigenvalue scaling, the result stored per element; per element
+// block, the sum at each node of the results of the (at most 8) subdomains
+// covering its lattice point in a fixed order, masked (inside flexible CG with
+// the step's dot products).  The 1D eigenproblems are
 // solved once per mesh on the host (cyclic Jacobi rotations on
 // B^-1/2 A B^-1/2, B diagonal) in binary64.
 #include <math.h>
@@ -32,7 +34,9 @@ struct SchwarzData {
     float *S = nullptr;  // [3 dirs][4 variants][m][m]
     float *lam = nullptr;  // [3][4][m]
     float *rg = nullptr;   // [nG] owner values of r
-    float *zt = nullptr;   // [E][m^3] local solutions
+    float *zt = nullptr;   // [E][m][Mp][Mp] local solutions, [c][b][a], rows padded to Mp
+    int grid_local = 1;    // blocks of k_sw_local
+    int grid_sum = 1;      // blocks of k_sw_sum (at most kMaxPartials / 2)
 };
 
 // Cyclic Jacobi eigenvalue iteration for a symmetric m x m matrix (Golub and
@@ -136,181 +140,345 @@ __device__ __forceinline__ int sw_variant(int e_d, int n_d)
     return (e_d == 0 ? 1 : 0) + (e_d == n_d - 1 ? 2 : 0);
 }
 
-// One line of a tensor contraction: out[q] = sum_i M[i][q] v[i], M in padded
-// rows of P values (16-byte loads, the same row for every thread: broadcast).
-template <int m, int P>
-__device__ __forceinline__ void sw_line(const float *__restrict__ M, const float (&v)[m],
-                                        float (&out)[m])
+// Shapes of the local-solve kernel for m = n + 2 points per direction.  A
+// phase contracts the outer axis X of a box stored as [X][Y][Z] (strides SX,
+// SY, 1) with a 1D matrix M[i][q] (rows padded to Mp = m rounded up to 4) and
+// stores the result as [Y][Z][X'], which is the next phase's [X][Y][Z]: three
+// phases rotate the axes back.  A thread owns 4 consecutive lines (Z) at one
+// Y and all Mp outputs, so every 16-byte matrix row it reads serves 16 FMAs,
+// and its 4 inputs at one i are one 16-byte load.  SY / 4 and SX / 4 are odd,
+// so the 8 threads of a 16-byte access hit distinct bank groups.
+template <int m>
+struct SwCfg {
+    static constexpr int Mp = (m + 3) / 4 * 4;
+    static constexpr int Q = Mp / 4;
+    static constexpr int SY = (Q % 2) ? Mp : Mp + 4;
+    static constexpr int SX = ((Mp * SY / 4) % 2) ? Mp * SY : Mp * SY + 4;
+    static constexpr int BUF = m * SX;             // floats per box buffer
+    static constexpr int TPE = m * Q;              // threads per element
+    static constexpr int MAT = 24 * m * Mp;        // 3 dirs x 4 variants x (S^T, S) rows
+    static constexpr int LAM = 12 * Mp;            // 3 dirs x 4 variants
+    static constexpr int EPB0 = (100 * 1024 / 4 - MAT - LAM) / (2 * BUF);
+    static constexpr int EPB1 = 256 / TPE;
+    static constexpr int EPB = EPB0 < EPB1 ? (EPB0 < 1 ? 1 : EPB0) : EPB1;  // elements per block
+    static constexpr int THREADS = EPB * TPE;
+    static constexpr size_t SMEM = sizeof(float) * (size_t)(MAT + LAM + 2 * EPB * BUF);
+    static constexpr int ZS = m * Mp * Mp;         // floats per element of zt: [c][b][a]
+};
+
+// acc[z][q] = sum_i M[i][q] in[i][Y][4 Zq + z]
+template <int m>
+__device__ __forceinline__ void sw_phase(const float *__restrict__ in, const float *__restrict__ M,
+                                         int Y, int Zq, float (&acc)[4][SwCfg<m>::Mp])
 {
+    using C = SwCfg<m>;
 #pragma unroll
-    for (int q = 0; q < m; ++q) out[q] = 0.f;
+    for (int z = 0; z < 4; ++z)
 #pragma unroll
+        for (int q = 0; q < C::Mp; ++q) acc[z][q] = 0.f;
+#pragma unroll 4
     for (int i = 0; i < m; ++i) {
-        const float4 *row = reinterpret_cast<const float4 *>(M + i * P);
+        const float4 v = *reinterpret_cast<const float4 *>(in + i * C::SX + Y * C::SY + 4 * Zq);
 #pragma unroll
-        for (int q4 = 0; q4 < P / 4; ++q4) {
-            const float4 s = row[q4];
-            if (4 * q4 + 0 < m) out[4 * q4 + 0] += s.x * v[i];
-            if (4 * q4 + 1 < m) out[4 * q4 + 1] += s.y * v[i];
-            if (4 * q4 + 2 < m) out[4 * q4 + 2] += s.z * v[i];
-            if (4 * q4 + 3 < m) out[4 * q4 + 3] += s.w * v[i];
+        for (int qq = 0; qq < C::Q; ++qq) {
+            const float4 w = *reinterpret_cast<const float4 *>(M + i * C::Mp + 4 * qq);
+            acc[0][4 * qq + 0] += v.x * w.x; acc[0][4 * qq + 1] += v.x * w.y;
+            acc[0][4 * qq + 2] += v.x * w.z; acc[0][4 * qq + 3] += v.x * w.w;
+            acc[1][4 * qq + 0] += v.y * w.x; acc[1][4 * qq + 1] += v.y * w.y;
+            acc[1][4 * qq + 2] += v.y * w.z; acc[1][4 * qq + 3] += v.y * w.w;
+            acc[2][4 * qq + 0] += v.z * w.x; acc[2][4 * qq + 1] += v.z * w.y;
+            acc[2][4 * qq + 2] += v.z * w.z; acc[2][4 * qq + 3] += v.z * w.w;
+            acc[3][4 * qq + 0] += v.w * w.x; acc[3][4 * qq + 1] += v.w * w.y;
+            acc[3][4 * qq + 2] += v.w * w.z; acc[3][4 * qq + 3] += v.w * w.w;
         }
     }
 }
 
-// A_e^-1 R_e r for every element: one block per element, one thread per line
-// of the extended box (m^2 lines per direction), each contraction done by a
-// thread for a whole line held in registers (the 1D matrices in shared
-// memory, read as broadcast 16-byte rows).  Phases: a-lines (the gather from
-// the global vector, S^T), b-lines (S^T), c-lines (S^T and the eigenvalue
-// scaling), a-lines (S), b-lines (S), c-lines (S, stored).  zt[e][c][b][a].
+// out[Y][4 Zq + z][q] = acc[z][q] in the rotated layout (strides SX, SY).
 template <int m>
-__global__ void __launch_bounds__((m * m + 31) / 32 * 32)
+__device__ __forceinline__ void sw_store(float *__restrict__ out, const float (&acc)[4][SwCfg<m>::Mp],
+                                         int Y, int Zq)
+{
+    using C = SwCfg<m>;
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int qq = 0; qq < C::Q; ++qq)
+            *reinterpret_cast<float4 *>(out + Y * C::SX + (4 * Zq + z) * C::SY + 4 * qq) =
+                make_float4(acc[z][4 * qq], acc[z][4 * qq + 1], acc[z][4 * qq + 2], acc[z][4 * qq + 3]);
+}
+
+// A_e^-1 R_e r for every element.  EPB elements per block, TPE threads each;
+// the 1D matrices of all variants stay in shared memory for the block's life.
+// Per element: the extended box gathered from the global vector as [c][b][a],
+// then six phases -- S_z^T, S_y^T, S_x^T with the eigenvalue scaling, S_z,
+// S_y, S_x -- the last stored to zt[e][c][b][a] (row stride Mp).
+template <int m>
+__global__ void __launch_bounds__(SwCfg<m>::THREADS)
 k_sw_local(int64_t E, int nx, int ny, int nz, int N, const float *__restrict__ rg,
            const float *__restrict__ Sall, const float *__restrict__ lall,
-           float *__restrict__ zt)
+           float *__restrict__ zt, const CgScalars *sc)
 {
-    constexpr int m2 = m * m, m3 = m2 * m, P = (m + 3) / 4 * 4;
-    __shared__ __align__(16) float t0[m3], t1[m3];
-    // per direction: S^T rows (M[i][q] = S[i][q]) and S rows (M[i][q] = S[q][i])
-    __shared__ __align__(16) float St[3][m * P], Sf[3][m * P];
-    __shared__ float lam[3][m];
-    const int gxn = nx * N + 1, gyn = ny * N + 1, gzn = nz * N + 1;
+    using C = SwCfg<m>;
+    constexpr int m2 = m * m, Mp = C::Mp;
+    extern __shared__ __align__(16) float sw_smem[];
+    float *mat = sw_smem;                 // [(dir * 4 + var) * 2 + (0: S^T, 1: S)][m][Mp]
+    float *lam = mat + C::MAT;            // [dir * 4 + var][Mp], padding 1
     const int tid = threadIdx.x;
-    const bool act = tid < m2;
-    const int hi = act ? tid / m : 0, lo = act ? tid % m : 0;
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-        const int var[3] = {sw_variant(ex, nx), sw_variant(ey, ny), sw_variant(ez, nz)};
-        __syncthreads();  // the previous element is done with the matrices
-        for (int q = tid; q < 3 * m2; q += blockDim.x) {
-            const int d = q / m2, r = q % m2, i = r / m, c = r % m;
-            const float v = Sall[(d * 4 + var[d]) * m2 + r];  // S[i][c]
-            St[d][i * P + c] = v;
-            Sf[d][c * P + i] = v;
-        }
-        for (int q = tid; q < 3 * m; q += blockDim.x)
-            lam[q / m][q % m] = lall[(q / m * 4 + var[q / m]) * m + q % m];
-        __syncthreads();
-        float v[m], o[m];
-        // a-lines (c, b) = (hi, lo): the extended box row from the global lattice
-        if (act) {
-            const int gy = ey * N - 1 + lo, gz = ez * N - 1 + hi;
-            const bool okyz = gy >= 0 && gy < gyn && gz >= 0 && gz < gzn;
+    const int slot = tid / C::TPE, lt = tid - slot * C::TPE;
+    const int Zq = lt / m, Y = lt - Zq * m;
+    float *A = lam + C::LAM + slot * 2 * C::BUF, *B = A + C::BUF;
+    if (sc && sc->done) return;  // the flexible-CG loop has stopped
+    for (int q = tid; q < C::MAT; q += blockDim.x) mat[q] = 0.f;
+    __syncthreads();
+    for (int q = tid; q < 12 * m2; q += blockDim.x) {
+        const int dv = q / m2, r = q - dv * m2, i = r / m, c = r - i * m;
+        const float v = Sall[q];  // S[i][c] of direction / variant dv
+        mat[(dv * 2 + 0) * m * Mp + i * Mp + c] = v;
+        mat[(dv * 2 + 1) * m * Mp + c * Mp + i] = v;
+    }
+    for (int q = tid; q < C::LAM; q += blockDim.x) {
+        const int dv = q / Mp, c = q - dv * Mp;
+        lam[q] = c < m ? lall[dv * m + c] : 1.f;
+    }
+    __syncthreads();
+    const int gxn = nx * N + 1, gyn = ny * N + 1, gzn = nz * N + 1;
+    for (int64_t e0 = (int64_t)blockIdx.x * C::EPB; e0 < E; e0 += (int64_t)gridDim.x * C::EPB) {
+        const int64_t e = e0 + slot;
+        const bool ok = e < E;
+        const int ex = ok ? (int)(e % nx) : 0, ey = ok ? (int)((e / nx) % ny) : 0;
+        const int ez = ok ? (int)(e / ((int64_t)nx * ny)) : 0;
+        const int vx = sw_variant(ex, nx), vy = sw_variant(ey, ny), vz = sw_variant(ez, nz);
+        if (ok) {  // one row (c, b) of the box per thread and pass: m loads in flight
+            const int gx0 = ex * N - 1;
+            for (int rr = lt; rr < m2; rr += C::TPE) {
+                const int c = rr / m, b = rr - c * m;
+                const int gy = ey * N - 1 + b, gz = ez * N - 1 + c;
+                const bool row = gy >= 0 && gy < gyn && gz >= 0 && gz < gzn;
+                const int64_t r0 = ((int64_t)gz * gyn + gy) * gxn + gx0;
+                float v[m];
 #pragma unroll
-            for (int a = 0; a < m; ++a) {
-                const int gx = ex * N - 1 + a;
-                v[a] = (okyz && gx >= 0 && gx < gxn) ? rg[((int64_t)gz * gyn + gy) * gxn + gx] : 0.f;
+                for (int a = 0; a < m; ++a)
+                    v[a] = (row && gx0 + a >= 0 && gx0 + a < gxn) ? rg[r0 + a] : 0.f;
+                float *dst = A + c * C::SX + b * C::SY;
+#pragma unroll
+                for (int a = 0; a < Mp; ++a) dst[a] = a < m ? v[a] : 0.f;
             }
-            sw_line<m, P>(St[0], v, o);
-#pragma unroll
-            for (int a = 0; a < m; ++a) t0[(hi * m + lo) * m + a] = o[a];
         }
         __syncthreads();
-        // b-lines (c, a) = (hi, lo)
-        if (act) {
+        // phases 0..5: S_z^T, S_y^T, S_x^T (then the eigenvalue scaling), S_z,
+        // S_y, S_x; buffers A -> B -> A ...; one copy of the phase code
+#pragma unroll 1
+        for (int ph = 0; ph < 6; ++ph) {
+            const int dir = 2 - ph % 3, var = dir == 0 ? vx : (dir == 1 ? vy : vz);
+            const float *in = (ph & 1) ? B : A;
+            float *out = (ph & 1) ? A : B;
+            if (ok) {
+                float acc[4][Mp];
+                sw_phase<m>(in, mat + ((dir * 4 + var) * 2 + ph / 3) * m * Mp, Y, Zq, acc);
+                if (ph == 2) {  // 1 / (lx[a] + ly[b] + lz[c]) with (Y, Z, X') = (c, b, a)
+                    const float *lx = lam + (0 * 4 + vx) * Mp, *ly = lam + (1 * 4 + vy) * Mp;
+                    const float lz = lam[(2 * 4 + vz) * Mp + Y];
 #pragma unroll
-            for (int j = 0; j < m; ++j) v[j] = t0[(hi * m + j) * m + lo];
-            sw_line<m, P>(St[1], v, o);
+                    for (int z = 0; z < 4; ++z) {
+                        const float lyz = lz + ly[4 * Zq + z];
 #pragma unroll
-            for (int b = 0; b < m; ++b) t1[(hi * m + b) * m + lo] = o[b];
-        }
-        __syncthreads();
-        // c-lines (b, a) = (hi, lo), then the scaling by 1 / (lx + ly + lz)
-        if (act) {
+                        for (int q = 0; q < Mp; ++q) acc[z][q] = __fdividef(acc[z][q], lyz + lx[q]);
+                    }
+                }
+                if (ph < 5) {
+                    sw_store<m>(out, acc, Y, Zq);
+                } else {  // zt[e][c][b][a] with (Y, Z, X') = (c, b, a)
+                    float *o = zt + e * C::ZS + Y * Mp * Mp;
 #pragma unroll
-            for (int k = 0; k < m; ++k) v[k] = t1[(k * m + hi) * m + lo];
-            sw_line<m, P>(St[2], v, o);
-            const float lab = lam[0][lo] + lam[1][hi];
+                    for (int z = 0; z < 4; ++z)
+                        if (4 * Zq + z < m)
 #pragma unroll
-            for (int c = 0; c < m; ++c) t0[(c * m + hi) * m + lo] = o[c] / (lab + lam[2][c]);
-        }
-        __syncthreads();
-        // back: a-lines with S
-        if (act) {
-#pragma unroll
-            for (int a = 0; a < m; ++a) v[a] = t0[(hi * m + lo) * m + a];
-            sw_line<m, P>(Sf[0], v, o);
-#pragma unroll
-            for (int a = 0; a < m; ++a) t1[(hi * m + lo) * m + a] = o[a];
-        }
-        __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int j = 0; j < m; ++j) v[j] = t1[(hi * m + j) * m + lo];
-            sw_line<m, P>(Sf[1], v, o);
-#pragma unroll
-            for (int b = 0; b < m; ++b) t0[(hi * m + b) * m + lo] = o[b];
-        }
-        __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < m; ++k) v[k] = t0[(k * m + hi) * m + lo];
-            sw_line<m, P>(Sf[2], v, o);
-            float *out = zt + e * m3;
-#pragma unroll
-            for (int c = 0; c < m; ++c) out[(c * m + hi) * m + lo] = o[c];
+                            for (int qq = 0; qq < C::Q; ++qq)
+                                *reinterpret_cast<float4 *>(o + (4 * Zq + z) * Mp + 4 * qq) =
+                                    make_float4(acc[z][4 * qq], acc[z][4 * qq + 1],
+                                                acc[z][4 * qq + 2], acc[z][4 * qq + 3]);
+                }
+            }
+            if (ph < 5) __syncthreads();
         }
     }
 }
 
 // z[l] = mask * sum over the subdomains covering l's lattice point of their
-// local solutions there, subdomains in ascending element order.
-__global__ void k_sw_sum(int64_t nL, int nx, int ny, int nz, int N, int m,
-                         const float *__restrict__ zt, const float *__restrict__ sgn,
-                         float *__restrict__ z)
+// local solutions there, subdomains in ascending element order.  One block
+// per element (grid-stride), its threads over the element's n^3 nodes.  With
+// DOTS, also the owner-copy partials of (z, w_prev) and (r, z), and the last
+// block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on the first
+// step) and rtz = (r, z).
+template <int n, bool DOTS>
+__global__ void __launch_bounds__(256)
+k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
+         const float *__restrict__ sgn, float *__restrict__ z, const float *__restrict__ r,
+         const float *__restrict__ wold, CgScalars *sc, double *__restrict__ part)
 {
-    const int n = N + 1, n3 = n * n * n, m3 = m * m * m;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
-         l += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = l / n3;
-        const int q = (int)(l - e * n3);
-        const int i = q % n, j = (q / n) % n, k = q / (n * n);
+    constexpr int N = n - 1, n3 = n * n * n, Mp = SwCfg<n + 2>::Mp, ZS = SwCfg<n + 2>::ZS;
+    // subdomains covering a node per direction: 2 for N >= 3 (3 for N = 2, 4 for N = 1)
+    constexpr int KD = N >= 3 ? 2 : (N == 2 ? 3 : 4);
+    constexpr int QS = (n3 + 255) / 256;  // nodes of an element per thread (256 threads)
+    __shared__ double sred[32];
+    if (DOTS && sc->done) return;
+    // offsets in zt (E * ZS < 2^31, checked at set-up) of the same lattice
+    // point in the next element along x, y, z
+    const int dX = ZS - N, dY = nx * ZS - N * Mp, dZ = nx * ny * ZS - N * Mp * Mp;
+    DotAcc<float> zw, rz;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-        const int gx = ex * N + i, gy = ey * N + j, gz = ez * N + k;
-        float s = 0.f;
-        if (sgn[l] != 0.f) {  // masked (Dirichlet) copies stay zero
-            // elements e' with e'N - 1 <= g <= e'N + N + 1, per direction
-            const int x0 = max(0, (gx - N - 1 + N - 1) / N), x1 = min(nx - 1, (gx + 1) / N);
-            const int y0 = max(0, (gy - N - 1 + N - 1) / N), y1 = min(ny - 1, (gy + 1) / N);
-            const int z0 = max(0, (gz - N - 1 + N - 1) / N), z1 = min(nz - 1, (gz + 1) / N);
-            for (int cz = z0; cz <= z1; ++cz)
-                for (int cy = y0; cy <= y1; ++cy)
-                    for (int cx = x0; cx <= x1; ++cx) {
-                        const int a = gx - (cx * N - 1), b = gy - (cy * N - 1), c = gz - (cz * N - 1);
-                        if (a < 0 || a >= m || b < 0 || b >= m || c < 0 || c >= m) continue;
-                        const int64_t ee = ((int64_t)cz * ny + cy) * nx + cx;
-                        s += zt[ee * m3 + (c * m + b) * m + a];
+        const int eo = (int)e * ZS;
+#pragma unroll
+        for (int s = 0; s < QS; ++s) {
+            const int q = threadIdx.x + 256 * s;
+            if (q >= n3) break;
+            const int i = q % n, j = (q / n) % n, k = q / (n * n);
+            // subdomain c covers offset g - (c N - 1) in [0, N + 2]: lower
+            // neighbours down to e_d - (N + 1 - i) / N, upper up to e_d + (i + 1) / N
+            const int lx = min((N + 1 - i) / N, ex), hx = min((i + 1) / N, nx - 1 - ex);
+            const int ly = min((N + 1 - j) / N, ey), hy = min((j + 1) / N, ny - 1 - ey);
+            const int lz = min((N + 1 - k) / N, ez), hz = min((k + 1) / N, nz - 1 - ez);
+            // the own subdomain's [k + 1][j + 1][i + 1], moved to the lowest covering one
+            const int p0 = eo + ((k + 1) * Mp + j + 1) * Mp + i + 1 - lx * dX - ly * dY - lz * dZ;
+            // all loads issued before the sum, which runs in ascending element order
+            float v[KD][KD][KD];
+#pragma unroll
+            for (int tz = 0; tz < KD; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < KD; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < KD; ++tx) {
+                        const bool ok = tz <= lz + hz && ty <= ly + hy && tx <= lx + hx;
+                        v[tz][ty][tx] = ok ? zt[p0 + tx * dX + ty * dY + tz * dZ] : 0.f;
                     }
+            const int64_t l = e * n3 + q;
+            const float sg = sgn[l];
+            float sum = 0.f;
+#pragma unroll
+            for (int tz = 0; tz < KD; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < KD; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < KD; ++tx) sum += v[tz][ty][tx];
+            sum = sg != 0.f ? sum : 0.f;  // masked (Dirichlet) copies are zero
+            z[l] = sum;
+            if (DOTS && !signbit(sg)) {
+                zw.add(sum * wold[l]);
+                rz.add(r[l] * sum);
+            }
         }
-        z[l] = s;
+    }
+    if (!DOTS) return;
+    const double tzw = block_sum(zw.value(), sred);
+    const double trz = block_sum(rz.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tzw;
+        part[gridDim.x + blockIdx.x] = trz;
+    }
+    if (last_block(&sc->tick_upd)) {
+        const double szw = sum_partials(part, gridDim.x, sred);
+        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
+        if (threadIdx.x == 0) {
+            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
+            sc->rtz = srz;
+            sc->rp = srz;
+            if (!isfinite(sc->beta) || !isfinite(srz) || !(srz > 0.0)) {
+                sc->done = 1;
+                sc->status = NB_BREAKDOWN;
+            }
+        }
     }
 }
 
-static nb_status sw_launch_local(int m, int grid, int64_t E, int nx, int ny, int nz, int N,
-                                 const float *rg, const float *S, const float *lam, float *zt,
-                                 cudaStream_t s)
+// mode 0: grid of k_sw_sum<n, true> (resident blocks x SMs, one wave) out;
+// 1: launch
+template <bool DOTS>
+static nb_status sw_sum(int mode, int m, int sms, int *grid, int64_t E, int nx, int ny, int nz,
+                        const float *zt, const float *sgn, float *z, const float *r,
+                        const float *wold, CgScalars *sc, double *part, cudaStream_t s)
 {
-#define NB_SW(MM) k_sw_local<MM><<<grid, (MM * MM + 31) / 32 * 32, 0, s>>>(E, nx, ny, nz, N, rg, S, lam, zt)
+#define NB_SWS(NN)                                                                                \
+    if (mode == 0) {                                                                              \
+        int per_sm = 0;                                                                           \
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw_sum<NN, true>, 256, 0)); \
+        *grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)sms * std::max(per_sm, 1))); \
+        return NB_OK;                                                                             \
+    }                                                                                             \
+    k_sw_sum<NN, DOTS><<<*grid, 256, 0, s>>>(E, nx, ny, nz, zt, sgn, z, r, wold, sc, part);        \
+    NB_CUDA(cudaGetLastError());                                                                  \
+    return NB_OK
+    switch (m - 2) {
+        case 2: { NB_SWS(2); }
+        case 3: { NB_SWS(3); }
+        case 4: { NB_SWS(4); }
+        case 5: { NB_SWS(5); }
+        case 6: { NB_SWS(6); }
+        case 7: { NB_SWS(7); }
+        case 8: { NB_SWS(8); }
+        case 9: { NB_SWS(9); }
+        case 10: { NB_SWS(10); }
+        case 11: { NB_SWS(11); }
+        case 12: { NB_SWS(12); }
+        default:
+            set_error("Schwarz preconditioner supports orders N = 1..11");
+            return NB_ERR_ARG;
+    }
+#undef NB_SWS
+}
+
+// Shared-memory limit and grid (resident blocks x SMs, at most one block
+// per EPB elements) of k_sw_local<m>; set once per mesh, outside any capture.
+template <int m>
+static nb_status sw_local_prepare(int sms, int64_t E, int *grid)
+{
+    using C = SwCfg<m>;
+    NB_CUDA(cudaFuncSetAttribute(k_sw_local<m>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::SMEM));
+    int per_sm = 0;
+    NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw_local<m>, C::THREADS,
+                                                          C::SMEM));
+    const int64_t groups = (E + C::EPB - 1) / C::EPB;
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)sms * std::max(per_sm, 1)));
+    return NB_OK;
+}
+
+// mode 0: prepare (grid out), 1: launch with that grid
+static nb_status sw_local(int mode, int m, int sms, int *grid, int64_t E, int nx, int ny, int nz,
+                          int N, const float *rg, const float *S, const float *lam, float *zt,
+                          const CgScalars *sc, cudaStream_t s)
+{
+#define NB_SW(MM)                                                                                 \
+    if (mode == 0) return sw_local_prepare<MM>(sms, E, grid);                                    \
+    k_sw_local<MM><<<*grid, SwCfg<MM>::THREADS, SwCfg<MM>::SMEM, s>>>(E, nx, ny, nz, N, rg, S,   \
+                                                                     lam, zt, sc);               \
+    NB_CUDA(cudaGetLastError());                                                                 \
+    return NB_OK
     switch (m) {
-        case 4: NB_SW(4); break;
-        case 5: NB_SW(5); break;
-        case 6: NB_SW(6); break;
-        case 7: NB_SW(7); break;
-        case 8: NB_SW(8); break;
-        case 9: NB_SW(9); break;
-        case 10: NB_SW(10); break;
-        case 11: NB_SW(11); break;
-        case 12: NB_SW(12); break;
-        case 13: NB_SW(13); break;
-        case 14: NB_SW(14); break;
+        case 4: { NB_SW(4); }
+        case 5: { NB_SW(5); }
+        case 6: { NB_SW(6); }
+        case 7: { NB_SW(7); }
+        case 8: { NB_SW(8); }
+        case 9: { NB_SW(9); }
+        case 10: { NB_SW(10); }
+        case 11: { NB_SW(11); }
+        case 12: { NB_SW(12); }
+        case 13: { NB_SW(13); }
+        case 14: { NB_SW(14); }
         default:
             set_error("Schwarz preconditioner supports orders N = 1..11");
             return NB_ERR_ARG;
     }
 #undef NB_SW
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
+}
+
+// floats per element of the local solutions for m points per direction
+static int64_t sw_zt_stride(int m)
+{
+    const int Mp = (m + 3) / 4 * 4;
+    return (int64_t)m * Mp * Mp;
 }
 
 void schwarz_free(nb_mesh *m)
@@ -352,10 +520,15 @@ nb_status schwarz_setup(nb_mesh *m)
             for (int q = 0; q < mm * mm; ++q) Sh[((size_t)dir * 4 + v) * mm * mm + q] = (float)S[q];
             for (int q = 0; q < mm; ++q) lh[((size_t)dir * 4 + v) * mm + q] = (float)lam[q];
         }
+    if (m->E * sw_zt_stride(mm) >= ((int64_t)1 << 31)) {
+        set_error("Schwarz preconditioner: at most %lld elements of order %d",
+                  (long long)((((int64_t)1 << 31) - 1) / sw_zt_stride(mm)), N);
+        return NB_ERR_ARG;
+    }
     SchwarzData *d = new SchwarzData();
     d->m = mm;
     m->schwarz = d;
-    const size_t m3 = (size_t)mm * mm * mm;
+    const size_t m3 = (size_t)sw_zt_stride(mm);
     cudaError_t e = cudaMalloc(&d->S, sizeof(float) * Sh.size());
     if (e == cudaSuccess) e = cudaMalloc(&d->lam, sizeof(float) * lh.size());
     if (e == cudaSuccess) e = cudaMalloc(&d->rg, sizeof(float) * m->nG);
@@ -369,22 +542,48 @@ nb_status schwarz_setup(nb_mesh *m)
         set_error("Schwarz set-up: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
     }
+    nb_status st = sw_local(0, mm, m->ctx->sm_count, &d->grid_local, m->E, 0, 0, 0, 0, nullptr,
+                            nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st == NB_OK)
+        st = sw_sum<true>(0, mm, m->ctx->sm_count, &d->grid_sum, m->E, 0, 0, 0, nullptr, nullptr,
+                          nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != NB_OK) schwarz_free(m);
+    return st;
+}
+
+float *schwarz_rg(nb_mesh *m) { return ((SchwarzData *)m->schwarz)->rg; }
+
+// The owner values of the FP32 L-vector r into the global vector the local
+// solves gather from.
+nb_status schwarz_gather(nb_mesh *m, const float *r, cudaStream_t s)
+{
+    SchwarzData *d = (SchwarzData *)m->schwarz;
+    k_sw_global<<<vec_grid(m->ctx, m->nL), kVecThreads, 0, s>>>(m->nL, r, m->dinv32, m->gid, d->rg);
+    NB_CUDA(cudaGetLastError());
     return NB_OK;
+}
+
+// Local solves from the gathered global vector and their masked sum into z;
+// with sc, also the flexible-CG dots of z with r and w_prev (partials in
+// part, 2 x the sum's grid entries) and beta, rtz in sc.
+nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *wold,
+                            CgScalars *sc, double *part, cudaStream_t s)
+{
+    SchwarzData *d = (SchwarzData *)m->schwarz;
+    NB_TRY(sw_local(1, d->m, m->ctx->sm_count, &d->grid_local, m->E, m->nx, m->ny, m->nz, m->N,
+                    d->rg, d->S, d->lam, d->zt, sc, s));
+    if (sc)
+        return sw_sum<true>(1, d->m, 0, &d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32,
+                            z, r, wold, sc, part, s);
+    return sw_sum<false>(1, d->m, 0, &d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32, z,
+                         r, wold, sc, part, s);
 }
 
 // z = M r for FP32 L-vectors r (continuous, masked).
 nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s)
 {
-    SchwarzData *d = (SchwarzData *)m->schwarz;
-    const int g = vec_grid(m->ctx, m->nL);
-    k_sw_global<<<g, kVecThreads, 0, s>>>(m->nL, r, m->dinv32, m->gid, d->rg);
-    NB_CUDA(cudaGetLastError());
-    const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 12);
-    NB_TRY(sw_launch_local(d->m, grid, m->E, m->nx, m->ny, m->nz, m->N, d->rg, d->S, d->lam,
-                           d->zt, s));
-    k_sw_sum<<<g, kVecThreads, 0, s>>>(m->nL, m->nx, m->ny, m->nz, m->N, d->m, d->zt, m->dinv32, z);
-    NB_CUDA(cudaGetLastError());
-    return NB_OK;
+    NB_TRY(schwarz_gather(m, r, s));
+    return schwarz_solve_sum(m, r, z, nullptr, nullptr, nullptr, s);
 }
 
 }  // namespace nb
