@@ -93,19 +93,25 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
         const T g0 = Gs[0 * n3 + k * n2 + ij], g1 = Gs[1 * n3 + k * n2 + ij];
         const T g2 = Gs[2 * n3 + k * n2 + ij], g3 = Gs[3 * n3 + k * n2 + ij];
         const T g4 = Gs[4 * n3 + k * n2 + ij], g5 = Gs[5 * n3 + k * n2 + ij];
-        T ur = T(0), us = T(0), ut = T(0);
+        // even / odd partial sums: six independent chains for latency
+        T ur = T(0), us = T(0), ut = T(0), ur1 = T(0), us1 = T(0), ut1 = T(0);
         const V2 *urow = reinterpret_cast<const V2 *>(su + k * n2 + j * n);
 #pragma unroll
         for (int l = 0; l < n; l += 2) {
             const V2 v = urow[l / 2];
             ur += Di[l] * v.x;
-            ur += Di[l + 1] * v.y;
+            ur1 += Di[l + 1] * v.y;
         }
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
+        for (int l = 0; l < n; l += 2) {
             us += Dj[l] * su[k * n2 + l * n + i];
+            us1 += Dj[l + 1] * su[k * n2 + (l + 1) * n + i];
             ut += dtab<T>(n, k, l) * ru[l];
+            ut1 += dtab<T>(n, k, l + 1) * ru[l + 1];
         }
+        ur += ur1;
+        us += us1;
+        ut += ut1;
         const T wr = g0 * ur + g1 * us + g2 * ut;
         const T ws = g1 * ur + g3 * us + g4 * ut;
         const T wt = g2 * ur + g4 * us + g5 * ut;
@@ -114,7 +120,8 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
             wsb[ij] = ws;
         }
         __syncthreads();
-        T a = T(0);
+        // two independent chains (the wr and ws terms) for latency
+        T a = T(0), b = T(0);
         const V2 *wrow = reinterpret_cast<const V2 *>(wrb + j * n);
 #pragma unroll
         for (int l = 0; l < n; l += 2) {
@@ -123,8 +130,8 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
             a += DTi[l + 1] * v.y;
         }
 #pragma unroll
-        for (int l = 0; l < n; ++l) a += DTj[l] * wsb[l * n + i];
-        rw[k] += a;
+        for (int l = 0; l < n; ++l) b += DTj[l] * wsb[l * n + i];
+        rw[k] += a + b;
 #pragma unroll
         for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
     }
