@@ -3,15 +3,16 @@
 // The iteration follows Table 1 of the case study: z = solveM(r);
 // rtz1 = glsc3(r,c,z); p = beta p + z (add2s1); w = ax(p) with dssum;
 // pap = glsc3(w,c,p); x += alpha p, r -= alpha w (add2s2); rtr = glsc3(r,c,r).
-// On the GPU the nine lines become three kernels per iteration:
+// On the GPU the nine lines become two kernels per iteration:
 //   1. ax_cg_step: p = dinv*r + beta*p, w_L = A_L p, partials of p.w_L (= pap);
 //      its last block sums them: alpha = rtz/pap (breakdown check)
-//   2. dssum + mask of w
-//   3. update: x += alpha p, r -= alpha w, partials of (r,c,dinv r), (r,c,r);
-//      its last block sums them: beta, convergence, iteration limit
+//   2. update with dssum + mask of w folded in: x += alpha p, r -= alpha w,
+//      partials of (r,c,dinv r), (r,c,r); its last block sums them: beta,
+//      convergence, iteration limit (in FP64, and outside the built orders,
+//      a separate dssum kernel and update)
 // All scalars live in device memory, so the iteration is captured once in a
-// CUDA graph whose while-node repeats it (a fourth, one-thread kernel sets the
-// loop condition) until converged, at the iteration limit, or on breakdown:
+// CUDA graph whose while-node repeats it (a one-thread kernel sets the loop
+// condition) until converged, at the iteration limit, or on breakdown:
 // one graph launch per solve.
 //
 // Mixed precision (Section 6 runs the CG loop in single precision, set-up in
@@ -169,6 +170,200 @@ __global__ void k_cg_update(int64_t nL, CgScalars *__restrict__ sc, T *__restric
     if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
+// The update with the direct-stiffness summation of w folded in: for each
+// local node, w_asm = mask * (sum of w over the node's copies in ascending
+// local index), then x += alpha p, r -= alpha w_asm and the partials of
+// (r, c, dinv r), (r, c, r) as in k_cg_update.  On the box mesh the copies of
+// a node are its mirror nodes in the neighbouring elements: along x the node
+// with i = 0 is node i = N of element ex - 1 (offset -(n^3 - N)), i = N is
+// node 0 of ex + 1, and likewise along y and z; a node has 1, 2, 4 or 8 of
+// them, summed in ascending element order -- the order of the separate
+// summation kernel, so the result is bit-identical to dssum + k_cg_update.
+// The mask is read from dinv (0 exactly on Dirichlet nodes, also in the
+// identity preconditioner's array).  One block per element (grid-stride),
+// its threads over the element's nodes.
+template <typename T, int n>
+__global__ void __launch_bounds__(256)
+k_cg_update_gs(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T *__restrict__ x,
+               T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ w,
+               const T *__restrict__ dinv, double *__restrict__ part)
+{
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n;
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const int64_t sx = n3 - N, sy = (int64_t)nx * n3 - N * n, sz = (int64_t)nx * ny * n3 - N * n2;
+    DotAcc<T> a, b;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+            const int i = q % n, j = (q / n) % n, k = q / n2;
+            const int64_t l = e * n3 + q;
+            const int lx = i == 0 && ex > 0, hx = i == N && ex < nx - 1;
+            const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
+            const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
+            const T *w0 = w + (l - lx * sx - ly * sy - lz * sz);
+            T v[2][2][2];
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 2; ++tx) {
+                        const bool ok = tz <= lz + hz && ty <= ly + hy && tx <= lx + hx;
+                        v[tz][ty][tx] = ok ? w0[tx * sx + ty * sy + tz * sz] : T(0);
+                    }
+            const T d = dinv[l];
+            T xl = x[l], rl = r[l];
+            const T pl = p[l];
+            T wl = T(0);
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 2; ++tx) wl += v[tz][ty][tx];
+            if (d == T(0)) wl = T(0);  // Dirichlet node
+            xl = xl + alpha * pl;
+            rl = rl - alpha * wl;
+            if (owner_copy(d)) {
+                a.add(rl * (d * rl));
+                b.add(rl * rl);
+            }
+            x[l] = xl;
+            r[l] = rl;
+        }
+    }
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+}
+
+template <typename T>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    using type = float2;
+};
+template <>
+struct Pair2<double> {
+    using type = double2;
+};
+
+// k_cg_update_gs for even n, two nodes (i0, i0 + 1) of a row per thread with
+// 8- / 16-byte accesses.  N is odd, so only the first node of a pair can be
+// on the lower x face (i0 = 0) and only the second on the upper one
+// (i0 + 1 = N); the y / z copies of both nodes are one vector load each.
+// Same sums in the same order as k_cg_update_gs.
+template <typename T, int n>
+__global__ void __launch_bounds__(256)
+k_cg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T *__restrict__ x,
+                T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ w,
+                const T *__restrict__ dinv, double *__restrict__ part)
+{
+    static_assert(n % 2 == 0, "pairs of nodes need an even n");
+    using V = typename Pair2<T>::type;
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const int64_t sx = n3 - N, sy = (int64_t)nx * n3 - N * n, sz = (int64_t)nx * ny * n3 - N * n2;
+    DotAcc<T> a, b;
+    auto node = [&](T &xl, T &rl, T pl, T wl, T d) {
+        if (d == T(0)) wl = T(0);  // Dirichlet node
+        xl = xl + alpha * pl;
+        rl = rl - alpha * wl;
+        if (owner_copy(d)) {
+            a.add(rl * (d * rl));
+            b.add(rl * rl);
+        }
+    };
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
+            const int64_t l = e * n3 + (int64_t)k * n2 + j * n + i0;
+            const bool lxa = i0 == 0 && ex > 0, hxb = i0 + 1 == N && ex < nx - 1;
+            const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
+            const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
+            const int64_t l0 = l - ly * sy - lz * sz;
+            // slots (tz, ty, tx) as in k_cg_update_gs: tx = 0 is the lower x
+            // element; the first node's slots are (partner, own) or (own, -),
+            // the second node's (own, partner) or (own, -)
+            T va[2][2][2], vb[2][2][2];
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty) {
+                    const bool ok = tz <= lz + hz && ty <= ly + hy;
+                    const int64_t o = l0 + ty * sy + tz * sz;
+                    const V own = ok ? *reinterpret_cast<const V *>(w + o) : V{T(0), T(0)};
+                    const T pa = ok && lxa ? w[o - sx] : T(0);
+                    const T pb = ok && hxb ? w[o + 1 + sx] : T(0);
+                    va[tz][ty][0] = lxa ? pa : own.x;
+                    va[tz][ty][1] = lxa ? own.x : T(0);
+                    vb[tz][ty][0] = own.y;
+                    vb[tz][ty][1] = pb;
+                }
+            T wa = T(0), wb = T(0);
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 2; ++tx) {
+                        wa += va[tz][ty][tx];
+                        wb += vb[tz][ty][tx];
+                    }
+            V xv = *reinterpret_cast<V *>(x + l), rv = *reinterpret_cast<V *>(r + l);
+            const V pv = *reinterpret_cast<const V *>(p + l);
+            const V dv = *reinterpret_cast<const V *>(dinv + l);
+            node(xv.x, rv.x, pv.x, wa, dv.x);
+            node(xv.y, rv.y, pv.y, wb, dv.y);
+            *reinterpret_cast<V *>(x + l) = xv;
+            *reinterpret_cast<V *>(r + l) = rv;
+        }
+    }
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+}
+
+// k_cg_update_gs for n = N + 1 in FP32 (returns false where it is not
+// built).  FP64 keeps the separate summation: the folded sum adds every slot,
+// zeros included, which costs little on the FP32 pipe but measured slower
+// than the separate kernel on the FP64 pipe.
+static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, double *part,
+                             cudaStream_t s)
+{
+    // one wave: 8 blocks of 256 threads per SM (32 registers)
+    const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
+#define NB_UGS(K, NN)                                                                           \
+    case NN:                                                                                    \
+        K<float, NN><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal, (float *)ws.x,    \
+                                          (float *)ws.r, (const float *)ws.p,                   \
+                                          (const float *)ws.w, dinv, part);                     \
+        return true;
+    switch (m->n) {
+        NB_UGS(k_cg_update_gs2, 2) NB_UGS(k_cg_update_gs, 3) NB_UGS(k_cg_update_gs2, 4)
+        NB_UGS(k_cg_update_gs, 5) NB_UGS(k_cg_update_gs2, 6) NB_UGS(k_cg_update_gs, 7)
+        NB_UGS(k_cg_update_gs2, 8) NB_UGS(k_cg_update_gs, 9) NB_UGS(k_cg_update_gs2, 10)
+        NB_UGS(k_cg_update_gs, 11) NB_UGS(k_cg_update_gs2, 12) NB_UGS(k_cg_update_gs, 13)
+        NB_UGS(k_cg_update_gs2, 14) NB_UGS(k_cg_update_gs, 15) NB_UGS(k_cg_update_gs2, 16)
+        default:
+            return false;
+    }
+#undef NB_UGS
+}
+
 // The while-node condition of the captured iteration.  It counts executions
 // of the loop body itself, so the loop ends after maxit + 1 bodies even if
 // no other kernel of the body managed to set `done`.
@@ -273,6 +468,13 @@ static nb_status ensure_fp64_bufs(nb_mesh *m)
     return NB_OK;
 }
 
+// Kernels of one captured iteration: operator, update with the summation
+// folded in (or summation and update), loop condition.
+static int cg_body_kernels(const nb_mesh *m, nb_prec prec)
+{
+    return prec != NB_FP64 && m->n >= 2 && m->n <= 16 ? 3 : 4;
+}
+
 // The launches of one iteration (see the file comment): operator (its last
 // block computes alpha), gather-scatter, update (its last block computes
 // beta and the stopping test), and inside a graph the loop condition.
@@ -282,17 +484,21 @@ static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
 {
     int nparts = 0;
     NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
-    NB_TRY(dssum(m, prec, ws.w, 1, s));
-    const int g = vec_grid(m->ctx, m->nL);
     double *up = ws.part + kMaxPartials;
-    k_cg_update<T><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, (T *)ws.x, (T *)ws.r,
-                                             (const T *)ws.p, (const T *)ws.w, dinv, up);
+    bool folded = false;
+    if constexpr (sizeof(T) == 4) folded = launch_update_gs(m, ws, (const float *)dinv, up, s);
+    if (!folded) {
+        NB_TRY(dssum(m, prec, ws.w, 1, s));
+        const int g = vec_grid(m->ctx, m->nL);
+        k_cg_update<T><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, (T *)ws.x, (T *)ws.r,
+                                                 (const T *)ws.p, (const T *)ws.w, dinv, up);
+    }
     NB_CUDA(cudaGetLastError());
     if (use_cond) {
         k_cg_cond<<<1, 1, 0, s>>>(ws.scal, h);
         NB_CUDA(cudaGetLastError());
     } else {
-        m->launches += 3;
+        m->launches += cg_body_kernels(m, prec) - 1;
     }
     return NB_OK;
 }
@@ -437,7 +643,8 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
     }
     const double bn2 = m->red_host[0] > 0 ? m->red_host[0] : 1.0;
     if (st) {
-        if (o->use_graph) m->launches += 4 * (int64_t)std::max(h.iter, 1);
+        if (o->use_graph)
+            m->launches += cg_body_kernels(m, NB_FP64) * (int64_t)std::max(h.iter, 1);
         st->iters = h.iter;
         st->outer_iters = 0;
         st->launches = m->launches;
@@ -537,7 +744,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         const int it = ws.scal_host->iter;
-        if (o->use_graph && !use_learned) m->launches += 4 * (int64_t)std::max(it, 1);
+        if (o->use_graph && !use_learned)
+            m->launches += cg_body_kernels(m, o->prec) * (int64_t)std::max(it, 1);
         if (o->record_history) {
             copy_history(ws, it, hist_off, st, s);
             hist_off += it;
