@@ -75,4 +75,65 @@ __device__ __forceinline__ void cg_finish_iter(CgScalars *sc, const double *part
     }
 }
 
+template <typename T>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    using type = float2;
+};
+template <>
+struct Pair2<double> {
+    using type = double2;
+};
+
+// Direct-stiffness sum of w at two nodes (i0, j, k), (i0 + 1, j, k) of element
+// (ex, ey, ez) of the box mesh, n even (N odd), l the first node's local
+// index.  The copies of a node are its mirror nodes in the neighbouring
+// elements: i = 0 of element ex is i = N of ex - 1 (local offset -sx,
+// sx = n^3 - N), i = N is i = 0 of ex + 1, and likewise along y (sy =
+// nx n^3 - N n) and z (sz = nx ny n^3 - N n^2).  A node has 1, 2, 4 or 8
+// copies; they are summed in ascending local index (slot order (tz, ty, tx)
+// with tx = 0 the lower x element), the order of the row-wise summation
+// kernel, so the sums are bit-identical to it.  Only the first node of a pair
+// can be on a lower x face and only the second on an upper one; the y / z
+// copies of both nodes are one vector load each.  No mask applied.
+template <typename T, int n>
+__device__ __forceinline__ void gs_sum_pair(const T *__restrict__ w, int64_t l, int i0, int j,
+                                            int k, int ex, int ey, int ez, int nx, int ny, int nz,
+                                            int64_t sx, int64_t sy, int64_t sz, T &wa, T &wb)
+{
+    using V = typename Pair2<T>::type;
+    constexpr int N = n - 1;
+    const bool lxa = i0 == 0 && ex > 0, hxb = i0 + 1 == N && ex < nx - 1;
+    const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
+    const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
+    const int64_t l0 = l - ly * sy - lz * sz;
+    T va[2][2][2], vb[2][2][2];
+#pragma unroll
+    for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+        for (int ty = 0; ty < 2; ++ty) {
+            const bool ok = tz <= lz + hz && ty <= ly + hy;
+            const int64_t o = l0 + ty * sy + tz * sz;
+            const V own = ok ? *reinterpret_cast<const V *>(w + o) : V{T(0), T(0)};
+            const T pa = ok && lxa ? w[o - sx] : T(0);
+            const T pb = ok && hxb ? w[o + 1 + sx] : T(0);
+            va[tz][ty][0] = lxa ? pa : own.x;
+            va[tz][ty][1] = lxa ? own.x : T(0);
+            vb[tz][ty][0] = own.y;
+            vb[tz][ty][1] = pb;
+        }
+    wa = T(0);
+    wb = T(0);
+#pragma unroll
+    for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+        for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+            for (int tx = 0; tx < 2; ++tx) {
+                wa += va[tz][ty][tx];
+                wb += vb[tz][ty][tx];
+            }
+}
+
 }  // namespace nb

@@ -752,10 +752,16 @@ k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
                 zv.z = fabsf(dv[k].z) * rv.z + cv.z;
                 zv.w = fabsf(dv[k].w) * rv.w + cv.w;
                 z4[q] = zv;
-                if (!signbit(dv[k].x)) { zw.add(zv.x * wv[k].x); rz.add(rv.x * zv.x); }
-                if (!signbit(dv[k].y)) { zw.add(zv.y * wv[k].y); rz.add(rv.y * zv.y); }
-                if (!signbit(dv[k].z)) { zw.add(zv.z * wv[k].z); rz.add(rv.z * zv.z); }
-                if (!signbit(dv[k].w)) { zw.add(zv.w * wv[k].w); rz.add(rv.w * zv.w); }
+                // (z, w_prev) over every copy: w_prev is the unassembled
+                // A_L p (z continuous); (r, z) over owner copies
+                zw.add(zv.x * wv[k].x);
+                zw.add(zv.y * wv[k].y);
+                zw.add(zv.z * wv[k].z);
+                zw.add(zv.w * wv[k].w);
+                if (!signbit(dv[k].x)) rz.add(rv.x * zv.x);
+                if (!signbit(dv[k].y)) rz.add(rv.y * zv.y);
+                if (!signbit(dv[k].z)) rz.add(rv.z * zv.z);
+                if (!signbit(dv[k].w)) rz.add(rv.w * zv.w);
             }
         }
     }
@@ -792,55 +798,12 @@ k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
     }
 }
 
-// x += alpha p, r -= alpha w (alpha from the operator's last block), the
-// owner-copy partials of (r, r), and in the last block the flexible-CG
-// bookkeeping: iteration count, history, pap_prev, the stopping tests.
-template <bool SCATTER>
-__global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__ x,
-                                  float *__restrict__ r, const float *__restrict__ p,
-                                  const float *__restrict__ w, const float *__restrict__ sgn,
-                                  double *__restrict__ part, float *__restrict__ rg = nullptr,
-                                  const int32_t *__restrict__ gid = nullptr)
+// The block's partial of (r, c, r); the last block: pap_prev, rtr, the
+// iteration count, the relative residual (history) and the stopping tests.
+__device__ __forceinline__ void fcg_step_finish(CgScalars *sc, double mine, double *part,
+                                                double *sred)
 {
-    __shared__ double sred[32];
-    if (sc->done) return;
-    const float alpha = (float)sc->alpha;
-    DotAcc<float> acc;
-    const int64_t n4 = nL / 4;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        float4 xv = reinterpret_cast<float4 *>(x)[q];
-        float4 rv = reinterpret_cast<float4 *>(r)[q];
-        const float4 pv = reinterpret_cast<const float4 *>(p)[q];
-        const float4 wv = reinterpret_cast<const float4 *>(w)[q];
-        const float4 dv = reinterpret_cast<const float4 *>(sgn)[q];
-        xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
-        rv.x -= alpha * wv.x; rv.y -= alpha * wv.y; rv.z -= alpha * wv.z; rv.w -= alpha * wv.w;
-        if (!signbit(dv.x)) acc.add(rv.x * rv.x);
-        if (!signbit(dv.y)) acc.add(rv.y * rv.y);
-        if (!signbit(dv.z)) acc.add(rv.z * rv.z);
-        if (!signbit(dv.w)) acc.add(rv.w * rv.w);
-        reinterpret_cast<float4 *>(x)[q] = xv;
-        reinterpret_cast<float4 *>(r)[q] = rv;
-        if (SCATTER) {  // owner values of the new residual into the global vector
-            const int4 gv = reinterpret_cast<const int4 *>(gid)[q];
-            if (!signbit(dv.x)) rg[gv.x] = rv.x;
-            if (!signbit(dv.y)) rg[gv.y] = rv.y;
-            if (!signbit(dv.z)) rg[gv.z] = rv.z;
-            if (!signbit(dv.w)) rg[gv.w] = rv.w;
-        }
-    }
-    for (int64_t l = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
-         l += (int64_t)gridDim.x * blockDim.x) {
-        x[l] += alpha * p[l];
-        const float rl = r[l] - alpha * w[l];
-        r[l] = rl;
-        if (!signbit(sgn[l])) {
-            acc.add(rl * rl);
-            if (SCATTER) rg[gid[l]] = rl;
-        }
-    }
-    const double t = block_sum(acc.value(), sred);
+    const double t = block_sum(mine, sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!last_block(&sc->tick_upd)) return;
     const double rtr = sum_partials(part, gridDim.x, sred);
@@ -863,6 +826,85 @@ __global__ void k_fcg_step_update(int64_t nL, CgScalars *sc, float *__restrict__
             sc->status = NB_NOT_CONVERGED;
         }
     }
+}
+
+// The flexible-CG update with the direct-stiffness summation of w folded in
+// (FP32, even n, two nodes of a row per thread, gs_sum_pair): w_asm = mask *
+// sum of w over the node's copies, x += alpha p, r -= alpha w_asm, the
+// partial of (r, c, r), and with SCATTER the owner values of the new r into
+// rg (the Schwarz preconditioner's global vector).  w stays unassembled, so
+// the preconditioner kernels form (z, w_prev) over every copy (z continuous).
+template <int n, bool SCATTER>
+__global__ void __launch_bounds__(256)
+k_fcg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *sc, float *__restrict__ x,
+                 float *__restrict__ r, const float *__restrict__ p, const float *__restrict__ w,
+                 const float *__restrict__ sgn, double *__restrict__ part,
+                 float *__restrict__ rg, const int32_t *__restrict__ gid)
+{
+    static_assert(n % 2 == 0, "pairs of nodes need an even n");
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    const int64_t sx = n3 - N, sy = (int64_t)nx * n3 - N * n, sz = (int64_t)nx * ny * n3 - N * n2;
+    DotAcc<float> acc;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
+            const int64_t l = e * n3 + (int64_t)k * n2 + j * n + i0;
+            float wa, wb;
+            gs_sum_pair<float, n>(w, l, i0, j, k, ex, ey, ez, nx, ny, nz, sx, sy, sz, wa, wb);
+            float2 xv = *reinterpret_cast<float2 *>(x + l), rv = *reinterpret_cast<float2 *>(r + l);
+            const float2 pv = *reinterpret_cast<const float2 *>(p + l);
+            const float2 dv = *reinterpret_cast<const float2 *>(sgn + l);
+            if (dv.x == 0.f) wa = 0.f;  // Dirichlet node
+            if (dv.y == 0.f) wb = 0.f;
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            rv.x -= alpha * wa;
+            rv.y -= alpha * wb;
+            if (!signbit(dv.x)) {
+                acc.add(rv.x * rv.x);
+                if (SCATTER) rg[gid[l]] = rv.x;
+            }
+            if (!signbit(dv.y)) {
+                acc.add(rv.y * rv.y);
+                if (SCATTER) rg[gid[l + 1]] = rv.y;
+            }
+            *reinterpret_cast<float2 *>(x + l) = xv;
+            *reinterpret_cast<float2 *>(r + l) = rv;
+        }
+    }
+    fcg_step_finish(sc, acc.value(), part, sred);
+}
+
+// k_fcg_update_gs2 for the mesh's order (even n <= 16; the flexible-CG paths
+// that use it need an even n).
+static nb_status fcg_update_folded(nb_mesh *m, Workspace &ws, float *x, float *r, const float *p,
+                                   const float *w, double *part, float *rg, cudaStream_t s)
+{
+    const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
+    const float *sgn = m->dinv32;
+#define NB_FU(NN)                                                                                 \
+    case NN:                                                                                      \
+        if (rg)                                                                                   \
+            k_fcg_update_gs2<NN, true><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal,   \
+                                                            x, r, p, w, sgn, part, rg, m->gid);   \
+        else                                                                                      \
+            k_fcg_update_gs2<NN, false><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal,  \
+                                                             x, r, p, w, sgn, part, nullptr,      \
+                                                             nullptr);                            \
+        break;
+    switch (m->n) {
+        NB_FU(2) NB_FU(4) NB_FU(6) NB_FU(8) NB_FU(10) NB_FU(12) NB_FU(14) NB_FU(16)
+        default:
+            set_error("flexible-CG update: n=%d not built (even n <= 16)", m->n);
+            return NB_ERR_ARG;
+    }
+#undef NB_FU
+    NB_CUDA(cudaGetLastError());
+    return NB_OK;
 }
 
 // k_lpc for the orders it is built for (d = n^3 <= 512, n even).
@@ -1056,9 +1098,9 @@ nb_status ax_dir_step(nb_mesh *m, const float *z, float *p, float *w, CgScalars 
                       double *pap_part, int *nparts, cudaStream_t s);
 
 // The inner solve of a refinement step: ws.r holds the scaled residual, ws.x
-// starts at zero.  One flexible-CG step is four kernels when the fused forms
-// apply (k_lpc; the operator's direction form with alpha; the summation;
-// k_fcg_step_update), otherwise the general path below.  Captured in a graph
+// starts at zero.  One flexible-CG step is three kernels when the fused forms
+// apply (k_lpc; the operator's direction form with alpha; k_fcg_update_gs2
+// with the summation folded in), otherwise the general path below.  Captured in a graph
 // with a while node (two steps per body), or host-launched with the stopping
 // state checked every few steps (all kernels skip their work once it is set).
 nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
@@ -1096,10 +1138,9 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
                               md->a, ws.scal, P0, m->kerr));
             int nparts = 0;
             NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
-            NB_TRY(dssum(m, prec, wcur, 1, s));
-            k_fcg_step_update<false><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2);
-            NB_CUDA(cudaGetLastError());
-            return NB_OK;
+            // w stays unassembled: the update folds the summation in, and
+            // k_lpc forms (z, w_prev) over every copy
+            return fcg_update_folded(m, ws, x, r, p, wcur, P2, nullptr, s);
         }
         NB_TRY(model_apply(m, md, r, z, s));
         k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, z, wold, sgn, P0);
@@ -1158,15 +1199,16 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         NB_CUDA(cudaGraphLaunch(ws.exec2, s));
         NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
         NB_CUDA(cudaStreamSynchronize(s));
-        m->launches += (fast ? 9 : 19) * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
+        m->launches += (fast ? 7 : 19) * (int64_t)((std::max(ws.scal_host->iter, 1) + 1) / 2);
         return NB_OK;
     }
     for (int it = 0;; ++it) {
         NB_TRY(step(w, wprev));
         std::swap(w, wprev);  // w of this step is w_prev of the next
-        // fused: preconditioner, operator, summation, update; general: row
-        // norms, 2 products, 2 dots, operator, summation, update, finish
-        m->launches += fast ? 4 : 9;
+        // fused: preconditioner, operator, update (summation folded in);
+        // general: row norms, 2 products, 2 dots, operator, summation,
+        // update, finish
+        m->launches += fast ? 3 : 9;
         if ((it & 7) == 7) {
             NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars),
                                     cudaMemcpyDeviceToHost, s));
@@ -1216,13 +1258,11 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         NB_TRY(schwarz_solve_sum(m, r, z, wold, ws.scal, P0, s));
         int nparts = 0;
         NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
-        NB_TRY(dssum(m, prec, wcur, 1, s));
-        k_fcg_step_update<true><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, x, r, p, wcur, sgn, P2,
-                                                           rg, m->gid);
-        NB_CUDA(cudaGetLastError());
-        return NB_OK;
+        // w stays unassembled (the update folds the summation in; the sum
+        // kernel forms (z, w_prev) over every copy)
+        return fcg_update_folded(m, ws, x, r, p, wcur, P2, rg, s);
     };
-    constexpr int kPerStep = 5;  // local solves, their sum, operator, summation, update
+    constexpr int kPerStep = 4;  // local solves, their sum, operator, update
     if (o->use_graph) {
         const intptr_t key = (intptr_t)m->schwarz;
         if (!ws.exec2 || ws.graph2_key != key) {

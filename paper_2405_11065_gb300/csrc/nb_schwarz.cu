@@ -308,7 +308,7 @@ k_sw_local(int64_t E, int nx, int ny, int nz, int N, const float *__restrict__ r
 // z[l] = mask * sum over the subdomains covering l's lattice point of their
 // local solutions there, subdomains in ascending element order.  One block
 // per element (grid-stride), its threads over the element's n^3 nodes.  With
-// DOTS, also the owner-copy partials of (z, w_prev) and (r, z), and the last
+// DOTS, also the partials of (z, w_prev) (w_prev unassembled) and (r, z), and the last
 // block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on the first
 // step) and rtz = (r, z).
 template <int n, bool DOTS>
@@ -364,9 +364,12 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
                     for (int tx = 0; tx < KD; ++tx) sum += v[tz][ty][tx];
             sum = sg != 0.f ? sum : 0.f;  // masked (Dirichlet) copies are zero
             z[l] = sum;
-            if (DOTS && !signbit(sg)) {
+            if (DOTS) {
+                // (z, w_prev) over every copy: w_prev is the unassembled
+                // A_L p of the previous step (z continuous); (r, z) over
+                // owner copies
                 zw.add(sum * wold[l]);
-                rz.add(r[l] * sum);
+                if (!signbit(sg)) rz.add(r[l] * sum);
             }
         }
     }

@@ -243,17 +243,6 @@ k_cg_update_gs(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T 
     if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
-template <typename T>
-struct Pair2;
-template <>
-struct Pair2<float> {
-    using type = float2;
-};
-template <>
-struct Pair2<double> {
-    using type = double2;
-};
-
 // k_cg_update_gs for even n, two nodes (i0, i0 + 1) of a row per thread with
 // 8- / 16-byte accesses.  N is odd, so only the first node of a pair can be
 // on the lower x face (i0 = 0) and only the second on the upper one
@@ -287,38 +276,8 @@ k_cg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
             const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
             const int64_t l = e * n3 + (int64_t)k * n2 + j * n + i0;
-            const bool lxa = i0 == 0 && ex > 0, hxb = i0 + 1 == N && ex < nx - 1;
-            const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
-            const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
-            const int64_t l0 = l - ly * sy - lz * sz;
-            // slots (tz, ty, tx) as in k_cg_update_gs: tx = 0 is the lower x
-            // element; the first node's slots are (partner, own) or (own, -),
-            // the second node's (own, partner) or (own, -)
-            T va[2][2][2], vb[2][2][2];
-#pragma unroll
-            for (int tz = 0; tz < 2; ++tz)
-#pragma unroll
-                for (int ty = 0; ty < 2; ++ty) {
-                    const bool ok = tz <= lz + hz && ty <= ly + hy;
-                    const int64_t o = l0 + ty * sy + tz * sz;
-                    const V own = ok ? *reinterpret_cast<const V *>(w + o) : V{T(0), T(0)};
-                    const T pa = ok && lxa ? w[o - sx] : T(0);
-                    const T pb = ok && hxb ? w[o + 1 + sx] : T(0);
-                    va[tz][ty][0] = lxa ? pa : own.x;
-                    va[tz][ty][1] = lxa ? own.x : T(0);
-                    vb[tz][ty][0] = own.y;
-                    vb[tz][ty][1] = pb;
-                }
-            T wa = T(0), wb = T(0);
-#pragma unroll
-            for (int tz = 0; tz < 2; ++tz)
-#pragma unroll
-                for (int ty = 0; ty < 2; ++ty)
-#pragma unroll
-                    for (int tx = 0; tx < 2; ++tx) {
-                        wa += va[tz][ty][tx];
-                        wb += vb[tz][ty][tx];
-                    }
+            T wa, wb;
+            gs_sum_pair<T, n>(w, l, i0, j, k, ex, ey, ez, nx, ny, nz, sx, sy, sz, wa, wb);
             V xv = *reinterpret_cast<V *>(x + l), rv = *reinterpret_cast<V *>(r + l);
             const V pv = *reinterpret_cast<const V *>(p + l);
             const V dv = *reinterpret_cast<const V *>(dinv + l);
