@@ -302,3 +302,34 @@ def test_failures_are_reported(nb, ctx):
     for prec in (nb.NB_FP64, nb.NB_FP32):
         out = mesh.solve(z, x, nb.default_opts(prec=prec))
         assert out["status"] == 0 and float(x.abs().max()) == 0.0
+
+
+# Odd element counts (ragged last wave of blocks) at even and odd n, through
+# the plain operator and the mixed solve (fused CG step, folded update).
+ODD_E_BOXES = [Box(3, 1, 1, 9, 0.05), Box(3, 3, 1, 5, 0.05), Box(1, 1, 1, 3, 0.0),
+               Box(5, 1, 1, 3, 0.05), Box(3, 1, 1, 7, 0.05)]
+
+
+@pytest.mark.parametrize("box", ODD_E_BOXES, ids=lambda b: f"{b.nx}x{b.ny}x{b.nz}N{b.N}")
+def test_odd_element_counts(nb, ctx, box):
+    import torch
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    rng = np.random.default_rng(11)
+    u = rng.uniform(-1, 1, box.n_local).astype(np.float32)
+    w = torch.empty(box.n_local, dtype=torch.float32, device="cuda")
+    mesh.ax(nb.NB_FP32, _t(u), w)
+    ref = P.ax_local(u.astype(np.float64))
+    err = np.max(np.abs(w.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err <= tol_ax32(box.n), err
+    # the fused CG step and the folded update inside the mixed solve
+    b = P.to_local(rhs_global(box, 0))
+    if not np.any(b):
+        return
+    xo, _, _, _ = P.pcg(b, tol=1e-13, maxit=5000)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, rtol=1e-10))
+    assert out["status"] == 0, out
+    xg = x.cpu().numpy()
+    assert P.true_relres(b, xg) < 1.01e-10
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
