@@ -73,7 +73,8 @@ struct Vec2<double> {
 
 // One element's operator from shared memory: Gs = G[6][n3] and su = u (n3)
 // of the element; ru holds the thread's (i,j) column of u, rw receives that
-// column of A_e u.  wr/ws of layer k go through buffer k&1 of swr/sws, with one
+// column of A_e u.  wr/ws of layer k go through buffer k&1 of swr/sws (ws
+// stored transposed, so that both are read as 8-byte rows), with one
 // barrier per layer: layer k+1 writes the other buffer, and layer k+2 (this
 // buffer again) follows layer k+1's barrier.
 template <typename T, int n>
@@ -117,7 +118,7 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
         const T wt = g2 * ur + g4 * us + g5 * ut;
         if (act) {
             wrb[ij] = wr;
-            wsb[ij] = ws;
+            wsb[i * n + j] = ws;  // transposed: the reads below are rows
         }
         __syncthreads();
         // two independent chains (the wr and ws terms) for latency
@@ -129,8 +130,13 @@ __device__ __forceinline__ void tma_element(const T *Gs, const T *su, const T (&
             a += DTi[l] * v.x;
             a += DTi[l + 1] * v.y;
         }
+        const V2 *wsrow = reinterpret_cast<const V2 *>(wsb + i * n);
 #pragma unroll
-        for (int l = 0; l < n; ++l) b += DTj[l] * wsb[l * n + i];
+        for (int l = 0; l < n; l += 2) {
+            const V2 v = wsrow[l / 2];
+            b += DTj[l] * v.x;
+            b += DTj[l + 1] * v.y;
+        }
         rw[k] += a + b;
 #pragma unroll
         for (int m = 0; m < n; ++m) rw[m] += dtab<T>(n, k, m) * wt;
