@@ -86,6 +86,7 @@ struct nb_batch {
     int32_t *elem_prob = nullptr;  // [E] internal problem index
     int64_t *elem_l0 = nullptr;    // [E + 1]
     int64_t *prob_e0 = nullptr;    // [nprob + 1]
+    int4 *prob_dim = nullptr;      // [nprob] (nx, ny, nz, n) of each problem's box
     nb::BScal *bs = nullptr;       // [nprob]
     nb::BScal *bs_host = nullptr;  // pinned
     int *loops = nullptr;          // graph loop counter
@@ -293,6 +294,81 @@ __global__ void k_bupdate(int64_t E, const int32_t *__restrict__ list, const int
             const T rl = r[l] - alpha * w[l];
             r[l] = rl;
             const T d = dinv[l];
+            if (!signbit(d)) {
+                a.add(rl * (d * rl));
+                c.add(rl * rl);
+            }
+        }
+        const double ta = warp_sum(a.value());
+        const double tc = warp_sum(c.value());
+        if (lane == 0) {
+            part[e] = ta;
+            part[E + e] = tc;
+        }
+    }
+}
+
+// k_bupdate with the direct-stiffness summation of w folded in (FP32): per
+// node, w_asm = mask * the sum of w over the node's copies -- its mirror nodes
+// in the neighbouring elements of the problem's box (i = 0 of element ex is
+// i = N of ex - 1, and so on per direction) -- in ascending local index, the
+// order of k_bgs, so the result is bit-identical to k_bgs + k_bupdate.  The
+// mask is dinv == 0 (Dirichlet).  A warp per active element.
+__global__ void k_bupdate_gs(int64_t E, const int32_t *__restrict__ list, const int *__restrict__ cnt,
+                             const int64_t *__restrict__ el0, const int32_t *__restrict__ eprob,
+                             const int64_t *__restrict__ pe0, const int4 *__restrict__ pdim,
+                             const BScal *__restrict__ bs, float *__restrict__ x,
+                             float *__restrict__ r, const float *__restrict__ p,
+                             const float *__restrict__ w, const float *__restrict__ dinv,
+                             double *__restrict__ part)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ne = list_len(cnt, E);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < ne;
+         i += nwarps) {
+        const int64_t e = list_at(list, i);
+        const int pr = eprob[e];
+        const BScal &b = bs[pr];
+        if (b.done) continue;  // uniform over the warp
+        const float alpha = (float)b.alpha;
+        const int4 dm = pdim[pr];
+        const int nx = dm.x, ny = dm.y, nz = dm.z, n = dm.w, N = n - 1, n2 = n * n, n3 = n2 * n;
+        // batch local indices are below 2^31 (checked at set-up)
+        const int el = (int)(e - pe0[pr]);
+        const int ex = el % nx, ey = (el / nx) % ny, ez = el / (nx * ny);
+        const int sx = n3 - N, sy = nx * n3 - N * n, sz = nx * ny * n3 - N * n2;
+        DotAcc<float> a, c;
+        const int l0 = (int)el0[e];
+        for (int q = lane; q < n3; q += 32) {
+            const int l = l0 + q;
+            const int ii = q % n, jj = (q / n) % n, kk = q / n2;
+            const int lx = ii == 0 && ex > 0, hx = ii == N && ex < nx - 1;
+            const int ly = jj == 0 && ey > 0, hy = jj == N && ey < ny - 1;
+            const int lz = kk == 0 && ez > 0, hz = kk == N && ez < nz - 1;
+            const int w0 = l - lx * sx - ly * sy - lz * sz;
+            float v[2][2][2];
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 2; ++tx) {
+                        const bool ok = tz <= lz + hz && ty <= ly + hy && tx <= lx + hx;
+                        v[tz][ty][tx] = ok ? w[w0 + tx * sx + ty * sy + tz * sz] : 0.f;
+                    }
+            float wl = 0.f;
+#pragma unroll
+            for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+                for (int ty = 0; ty < 2; ++ty)
+#pragma unroll
+                    for (int tx = 0; tx < 2; ++tx) wl += v[tz][ty][tx];
+            const float d = dinv[l];
+            if (d == 0.f) wl = 0.f;  // Dirichlet node
+            x[l] = x[l] + alpha * p[l];
+            const float rl = r[l] - alpha * wl;
+            r[l] = rl;
             if (!signbit(d)) {
                 a.add(rl * (d * rl));
                 c.add(rl * rl);
@@ -540,12 +616,20 @@ static nb_status batch_body(nb_batch *B, BatchWs &ws, const T *dinv, int use_con
     NB_TRY(bax_all<T>(B, true, nullptr, (T *)ws.w, (const T *)ws.r, dinv, (T *)ws.p, B->part_e, s));
     k_bfin_alpha<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->bs);
     NB_CUDA(cudaGetLastError());
-    k_bgs<T><<<chunk_grid(B), 256, 0, s>>>(list_chunks(B), cnt_chunks(B), B->gs_off, B->gs_loc,
-                                           B->gs_mask, B->bs, (T *)ws.w);
-    NB_CUDA(cudaGetLastError());
-    k_bupdate<T><<<warp_elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B), B->elem_l0,
-                                              B->elem_prob, B->bs, (T *)ws.x, (T *)ws.r,
-                                              (const T *)ws.p, (const T *)ws.w, dinv, B->part_e);
+    if constexpr (sizeof(T) == 4) {  // summation folded into the update
+        k_bupdate_gs<<<warp_elem_grid(B), 256, 0, s>>>(
+            B->E, list_all(B), cnt_all(B), B->elem_l0, B->elem_prob, B->prob_e0, B->prob_dim,
+            B->bs, (float *)ws.x, (float *)ws.r, (const float *)ws.p, (const float *)ws.w,
+            (const float *)dinv, B->part_e);
+    } else {
+        k_bgs<T><<<chunk_grid(B), 256, 0, s>>>(list_chunks(B), cnt_chunks(B), B->gs_off,
+                                               B->gs_loc, B->gs_mask, B->bs, (T *)ws.w);
+        NB_CUDA(cudaGetLastError());
+        k_bupdate<T><<<warp_elem_grid(B), 256, 0, s>>>(B->E, list_all(B), cnt_all(B),
+                                                  B->elem_l0, B->elem_prob, B->bs, (T *)ws.x,
+                                                  (T *)ws.r, (const T *)ws.p, (const T *)ws.w,
+                                                  dinv, B->part_e);
+    }
     NB_CUDA(cudaGetLastError());
     k_bfin_iter<<<warp_grid(B->nprob), 256, 0, s>>>(B->nprob, B->prob_e0, B->part_e, B->E, B->bs);
     NB_CUDA(cudaGetLastError());
@@ -580,7 +664,9 @@ static nb_status batch_cg(nb_batch *B, BatchWs &ws, const T *dinv, double tol, i
                           int use_red, int use_graph, int bnorm_from_r, const double *bnorm2,
                           cudaStream_t s, int64_t *launches)
 {
-    const int64_t per_body = (int64_t)B->groups.size() + 4 + (use_graph ? 1 : 0);
+    // operator per order, alpha, (summation,) update, beta, (condition)
+    const int64_t per_body =
+        (int64_t)B->groups.size() + (sizeof(T) == 4 ? 3 : 4) + (use_graph ? 1 : 0);
     *launches += 3;
     k_bsetup<<<(B->nprob + 255) / 256, 256, 0, s>>>(B->nprob, B->bs, tol, maxit, B->red, use_red);
     NB_CUDA(cudaGetLastError());
@@ -696,8 +782,8 @@ extern "C" nb_status nb_batch_destroy(nb_batch *B)
     free_bws(B->ws32);
     free_bws(B->ws64);
     void *bufs[] = {B->G32, B->G64, B->dinv32, B->dinv64, B->gs_off, B->gs_loc, B->gs_mask,
-                    B->elem_prob, B->elem_l0, B->prob_e0, B->bs, B->loops, B->part_e, B->red,
-                    B->r64, B->w64, B->act, B->kerr};
+                    B->elem_prob, B->elem_l0, B->prob_e0, B->prob_dim, B->bs, B->loops,
+                    B->part_e, B->red, B->r64, B->w64, B->act, B->kerr};
     for (void *b : bufs) cudaFree(b);
     if (B->bs_host) cudaFreeHost(B->bs_host);
     if (B->red_host) cudaFreeHost(B->red_host);
@@ -822,6 +908,7 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     NB_BCUDA(cudaMalloc(&B->elem_prob, sizeof(int32_t) * B->E));
     NB_BCUDA(cudaMalloc(&B->elem_l0, sizeof(int64_t) * (B->E + 1)));
     NB_BCUDA(cudaMalloc(&B->prob_e0, sizeof(int64_t) * (nprob + 1)));
+    NB_BCUDA(cudaMalloc(&B->prob_dim, sizeof(int4) * nprob));
     NB_BCUDA(cudaMalloc(&B->bs, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMemset(B->bs, 0, sizeof(BScal) * nprob));
     NB_BCUDA(cudaMallocHost(&B->bs_host, sizeof(BScal) * nprob));
@@ -870,6 +957,13 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     NB_BCUDA(cudaMemcpyAsync(B->elem_l0, el0.data(), sizeof(int64_t) * (B->E + 1),
                              cudaMemcpyHostToDevice, s));
     NB_BCUDA(cudaMemcpyAsync(B->prob_e0, B->prob_e0_host.data(), sizeof(int64_t) * (nprob + 1),
+                             cudaMemcpyHostToDevice, s));
+    std::vector<int4> dims(nprob);
+    for (int q = 0; q < nprob; ++q) {
+        const nb_mesh *m = B->meshes[B->order[q]];
+        dims[q] = make_int4(m->nx, m->ny, m->nz, m->n);
+    }
+    NB_BCUDA(cudaMemcpyAsync(B->prob_dim, dims.data(), sizeof(int4) * nprob,
                              cudaMemcpyHostToDevice, s));
     NB_BCUDA(cudaStreamSynchronize(s));
 #undef NB_BCUDA
