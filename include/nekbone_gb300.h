@@ -88,6 +88,13 @@ typedef struct {
                            while loop; 0: host-launched kernels */
     int record_history; /* 1: keep the recursive residual of each iteration */
     int use_x0;         /* 1: x_dev holds the initial guess; 0: start from zero */
+    int restart;        /* refinement with Jacobi or no preconditioner: 1 restarts
+                           each inner CG from p = 0 (classic iterative refinement,
+                           each inner solve to inner_rtol); 0 (default) keeps the
+                           search direction across the FP64 residual replacement
+                           (reliable update), replacing the residual each time it
+                           has dropped by max(inner_rtol, 1e-2).  The learned and
+                           Schwarz preconditioners and the batch always restart. */
 } nb_opts;
 
 typedef struct {

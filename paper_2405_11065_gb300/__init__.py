@@ -36,7 +36,7 @@ class NbError(RuntimeError):
 class nb_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("pc", C.c_int), ("rtol", C.c_double), ("maxiter", C.c_int),
                 ("inner_rtol", C.c_double), ("max_outer", C.c_int), ("use_graph", C.c_int),
-                ("record_history", C.c_int), ("use_x0", C.c_int)]
+                ("record_history", C.c_int), ("use_x0", C.c_int), ("restart", C.c_int)]
 
 
 class nb_stats(C.Structure):

@@ -339,6 +339,7 @@ void nb_default_opts(nb_opts *o)
     o->use_graph = 1;
     o->record_history = 0;
     o->use_x0 = 0;
+    o->restart = 0;
 }
 
 static nb_status check_opts(const nb_opts *o)
@@ -351,6 +352,7 @@ static nb_status check_opts(const nb_opts *o)
     if (o->prec != NB_FP64 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0)))
         return arg_error("opts.inner_rtol must be in (0,1)");
     if (o->max_outer < 0) return arg_error("opts.max_outer");
+    if (o->restart != 0 && o->restart != 1) return arg_error("opts.restart must be 0 or 1");
     if (o->pc == NB_PC_LEARNED && o->prec == NB_FP64)
         return arg_error("the learned preconditioner runs inside refinement (prec != NB_FP64)");
     if (o->pc == NB_PC_SCHWARZ && o->prec != NB_FP32)

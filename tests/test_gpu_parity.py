@@ -333,3 +333,32 @@ def test_odd_element_counts(nb, ctx, box):
     xg = x.cpu().numpy()
     assert P.true_relres(b, xg) < 1.01e-10
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_reliable_update_keeps_fp64_iteration_count(nb, ctx):
+    """Refinement that keeps the search direction across the FP64 residual
+    replacement (opts.restart = 0) needs about the FP64 PCG iteration count;
+    restarting each inner solve (restart = 1) needs more.  Both reach the
+    FP64 oracle's solution."""
+    import torch
+    box = Box(6, 5, 4, 7, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 2))
+    xo, _, _, _ = P.pcg(b, tol=1e-13, maxit=5000)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    f64 = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, rtol=1e-10))
+    its = {}
+    for restart in (0, 1):
+        x.zero_()
+        out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, rtol=1e-10, restart=restart))
+        assert out["status"] == 0, out
+        xg = x.cpu().numpy()
+        assert P.true_relres(b, xg) < 1.01e-10
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+        its[restart] = out["iters"]
+    print(f"FP64 PCG {f64['iters']}, kept direction {its[0]}, restarted {its[1]}")
+    assert its[0] <= 1.1 * f64["iters"]
+    assert its[0] < its[1]
+    with pytest.raises(nb.NbError):
+        mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, restart=2))
