@@ -88,13 +88,14 @@ typedef struct {
                            while loop; 0: host-launched kernels */
     int record_history; /* 1: keep the recursive residual of each iteration */
     int use_x0;         /* 1: x_dev holds the initial guess; 0: start from zero */
-    int restart;        /* refinement with Jacobi or no preconditioner: 1 restarts
+    int restart;        /* refinement: 1 restarts
                            each inner CG from p = 0 (classic iterative refinement,
                            each inner solve to inner_rtol); 0 (default) keeps the
                            search direction across the FP64 residual replacement
                            (reliable update), replacing the residual each time it
-                           has dropped by max(inner_rtol, 1e-2).  The learned and
-                           Schwarz preconditioners and the batch always restart. */
+                           has dropped by max(inner_rtol, 1e-2).  The same holds
+                           for the flexible CG of the learned (fused form) and
+                           Schwarz preconditioners; the batch always restarts. */
 } nb_opts;
 
 typedef struct {

@@ -787,7 +787,7 @@ k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
         const double szw = sum_partials(part, gridDim.x, sred);
         const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
         if (tid == 0) {
-            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
+            sc->beta = sc->pap_prev > 0.0 ? -szw / sc->pap_prev : 0.0;  // 0: first step
             sc->rtz = srz;
             sc->rp = srz;
             if (!isfinite(sc->beta) || !isfinite(srz)) {
@@ -981,7 +981,7 @@ __global__ void k_fcg_p(int64_t n, CgScalars *sc, const double *__restrict__ par
     __shared__ float sbeta;
     if (sc->done) return;
     const double zw = sum_partials(part_zw, cnt, sred);
-    if (threadIdx.x == 0) sbeta = sc->iter == 0 ? 0.f : (float)(-zw / sc->pap_prev);
+    if (threadIdx.x == 0) sbeta = sc->pap_prev > 0.0 ? (float)(-zw / sc->pap_prev) : 0.f;
     __syncthreads();
     const float beta = sbeta;
     DotAcc<float> acc;
@@ -1074,7 +1074,11 @@ __global__ void k_fcg_cond(CgScalars *sc, cudaGraphConditionalHandle h)
     cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
-__global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int cnt)
+// keep: the iteration resumes after a residual replacement with its previous
+// direction (pap_prev, p and w_prev kept; the flexible-CG beta
+// -(z, A p_prev) / (p_prev, A p_prev) does not depend on the scale of p_prev,
+// so nothing is rescaled); otherwise pap_prev = 0 makes the first beta 0.
+__global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int cnt, int keep)
 {
     __shared__ double sred[32];
     const double rtr = sum_partials(part, cnt, sred);
@@ -1082,7 +1086,7 @@ __global__ void k_fcg_init(CgScalars *sc, const double *__restrict__ part, int c
         sc->rtr = rtr;
         sc->bnorm2 = rtr;
         sc->relres = rtr > 0.0 ? 1.0 : 0.0;
-        sc->pap_prev = 0.0;
+        if (!keep) sc->pap_prev = 0.0;
         if (!isfinite(rtr)) {
             sc->done = 1;
             sc->status = NB_BREAKDOWN;
@@ -1097,13 +1101,31 @@ bool ax_dir_step_available(const nb_mesh *m);
 nb_status ax_dir_step(nb_mesh *m, const float *z, float *p, float *w, CgScalars *scal,
                       double *pap_part, int *nparts, cudaStream_t s);
 
+// Direction state at the start of an inner flexible-CG solve.  Fresh: p = 0,
+// w_prev = 0.  Kept (reliable update): p and the last A p stay; a step writes
+// A p into ws.w on odd and ws.aux on even step numbers and reads w_prev from
+// the other buffer, and every solve starts with an odd step, so after an odd
+// number of steps the last A p is copied from ws.w into ws.aux.
+static nb_status fcg_prepare(nb_mesh *m, Workspace &ws, bool keep, bool odd, cudaStream_t s)
+{
+    const size_t bytes = sizeof(float) * m->nL;
+    if (!keep) {
+        NB_CUDA(cudaMemsetAsync(ws.p, 0, bytes, s));
+        NB_CUDA(cudaMemsetAsync(ws.aux, 0, bytes, s));
+    } else if (odd) {
+        NB_CUDA(cudaMemcpyAsync(ws.aux, ws.w, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return NB_OK;
+}
+
 // The inner solve of a refinement step: ws.r holds the scaled residual, ws.x
 // starts at zero.  One flexible-CG step is three kernels when the fused forms
 // apply (k_lpc; the operator's direction form with alpha; k_fcg_update_gs2
 // with the summation folded in), otherwise the general path below.  Captured in a graph
 // with a while node (two steps per body), or host-launched with the stopping
 // state checked every few steps (all kernels skip their work once it is set).
-nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
+nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, bool keep,
+                      bool odd, cudaStream_t s)
 {
     (void)o;
     nb_model *md = (nb_model *)m->learned;
@@ -1125,10 +1147,10 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         NB_TRY(ensure_wb(md, s));  // outside any capture: refreshed in place when W changed
         NB_TRY(lpc_attr(m->n, lsm));
     }
-    NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
-    NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
+    keep = keep && fast;
+    NB_TRY(fcg_prepare(m, ws, keep, odd, s));
     k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
-    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
+    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g, keep ? 1 : 0);
     NB_CUDA(cudaGetLastError());
     m->launches += 2;
     // one flexible-CG step; w receives A p, wprev holds the previous A p
@@ -1234,7 +1256,8 @@ float *schwarz_rg(nb_mesh *m);
 // direction form with alpha, the summation, and the update, which also
 // scatters the new residual's owner values for the next local solves.
 // Graph-captured like fcg_learned.
-nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, cudaStream_t s)
+nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, bool keep,
+                      bool odd, cudaStream_t s)
 {
     if (prec != NB_FP32 || !ax_dir_step_available(m)) {
         set_error("the Schwarz preconditioner runs in FP32 refinement steps with even n");
@@ -1246,11 +1269,10 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     float *x = (float *)ws.x, *r = (float *)ws.r, *p = (float *)ws.p, *w = (float *)ws.w;
     float *z = (float *)ws.z, *wprev = (float *)ws.aux;
     double *P0 = ws.part, *P1 = ws.part + kMaxPartials, *P2 = ws.part + 2 * kMaxPartials;
-    NB_CUDA(cudaMemsetAsync(p, 0, sizeof(float) * m->nL, s));
-    NB_CUDA(cudaMemsetAsync(wprev, 0, sizeof(float) * m->nL, s));
+    NB_TRY(fcg_prepare(m, ws, keep, odd, s));
     float *rg = schwarz_rg(m);
     k_fdot<<<g, kVecThreads, 0, s>>>(m->nL, r, r, sgn, P2);
-    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g);
+    k_fcg_init<<<1, kFinalizeThreads, 0, s>>>(ws.scal, P2, g, keep ? 1 : 0);
     NB_CUDA(cudaGetLastError());
     NB_TRY(schwarz_gather(m, r, s));
     m->launches += 3;

@@ -384,7 +384,7 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
         const double szw = sum_partials(part, gridDim.x, sred);
         const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
         if (threadIdx.x == 0) {
-            sc->beta = sc->iter == 0 ? 0.0 : -szw / sc->pap_prev;
+            sc->beta = sc->pap_prev > 0.0 ? -szw / sc->pap_prev : 0.0;  // 0: first step
             sc->rtz = srz;
             sc->rp = srz;
             if (!isfinite(sc->beta) || !isfinite(srz) || !(srz > 0.0)) {

@@ -28,10 +28,12 @@
 
 namespace nb {
 
-nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
-                      cudaStream_t s);  // nb_learned.cu
-nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
-                      cudaStream_t s);  // nb_learned.cu
+// keep: resume with the previous direction (reliable update); odd: the
+// previous inner solve ended after an odd number of steps (nb_learned.cu)
+nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, bool keep,
+                      bool odd, cudaStream_t s);
+nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, bool keep,
+                      bool odd, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -688,9 +690,11 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
     }
     int used = 0, outer = 0, stagn = 0, hist_off = 0;
     double prev = INFINITY, rel = INFINITY;
-    // reliable update: the previous inner segment was a Jacobi / plain CG that
-    // converged, its direction is kept; s2_prev is its residual scale squared
-    bool resumable = false;
+    // reliable update: an inner solve of the same kind as the previous one,
+    // which converged, resumes with its direction; s2_prev is the previous
+    // residual scale squared, prev_kind 0 none, 1 (P)CG, 2 learned, 3 Schwarz
+    int prev_kind = 0, prev_iters = 0;
+    bool prev_ok = false;
     double s2_prev = 0.0;
     nb_status result = NB_NOT_CONVERGED;
     bool fell_back = false;
@@ -740,7 +744,10 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // true residual, and the iteration count stays that of FP64 PCG
         // (941 against 936 at E=4096, N=9; 6061 with replacements every 5
         // decades, where the recurrence drifts)
-        const bool keep_dir = !o->restart && !use_learned;
+        const int kind = !use_learned ? 1 : (o->pc == NB_PC_SCHWARZ ? 3 : 2);
+        const bool keep_dir = !o->restart;
+        const bool resume = keep_dir && prev_ok && prev_kind == kind;
+        const bool odd = (prev_iters & 1) != 0;
         const double step_rtol = keep_dir ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
         if (use_learned && o->pc == NB_PC_SCHWARZ) {
@@ -749,7 +756,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
-            NB_TRY(fcg_schwarz(m, o->prec, ws, o, s));
+            NB_TRY(fcg_schwarz(m, o->prec, ws, o, resume, odd, s));
         } else if (use_learned) {
             // flexible CG with the learned preconditioner (nb_learned.cu), on a
             // bounded budget; Jacobi-PCG takes over if it fails
@@ -757,9 +764,9 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
-            NB_TRY(fcg_learned(m, o->prec, ws, o, s));
+            NB_TRY(fcg_learned(m, o->prec, ws, o, resume, odd, s));
         } else {
-            if (keep_dir && resumable)
+            if (resume)
                 NB_TRY(cg_resume<float>(m, ws, dinv, tau, remaining, o->record_history,
                                         sqrt(s2_prev / m->red_host[1]), s));
             else
@@ -782,7 +789,9 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
             hist_off += it;
         }
         used += it;
-        resumable = !use_learned && ws.scal_host->status == 0 && it > 0;
+        prev_kind = kind;
+        prev_ok = ws.scal_host->status == 0 && it > 0;
+        prev_iters = it;
         if (use_learned && ws.scal_host->status != 0) {
             fell_back = true;  // the learned step failed: Jacobi-PCG from here on
             prev = INFINITY;
