@@ -93,9 +93,12 @@ typedef struct {
                            each inner solve to inner_rtol); 0 (default) keeps the
                            search direction across the FP64 residual replacement
                            (reliable update), replacing the residual each time it
-                           has dropped by max(inner_rtol, 1e-2).  The same holds
-                           for the flexible CG of the learned (fused form) and
-                           Schwarz preconditioners; the batch always restarts. */
+                           has dropped by max(inner_rtol, 1e-2), as long as the
+                           inner solves stay below 1000 iterations and resumed
+                           ones converge (else it falls back to restarts).  The
+                           same holds for the flexible CG of the learned (fused
+                           form) and Schwarz preconditioners; the batch always
+                           restarts. */
 } nb_opts;
 
 typedef struct {

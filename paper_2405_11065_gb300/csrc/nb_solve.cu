@@ -670,8 +670,12 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
 }
 
 // Largest inner tolerance of a reliable-update segment (residual replaced at
-// least every 2 decades).
+// least every 2 decades), and the longest inner solve after which the
+// direction is still kept: beyond it (elongated boxes needing thousands of
+// iterations per 2 decades) the FP32 recurrence drifts from the true
+// residual, a resumed solve stagnates, and restarts are faster.
 constexpr double kReliableDrop = 1e-2;
+constexpr int kReliableMaxIters = 1000;
 
 static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, double *x,
                                nb_stats *st, cudaStream_t s)
@@ -695,7 +699,10 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
     // residual scale squared, prev_kind 0 none, 1 (P)CG, 2 learned, 3 Schwarz
     int prev_kind = 0, prev_iters = 0;
     bool prev_ok = false;
-    double s2_prev = 0.0;
+    double s2_prev = 0.0, prev_end = 1.0, rel_start = 1.0;
+    // reliable updates while the solve stays well within FP32's reach; after
+    // a long inner solve or a failed resumption, classic restarted refinement
+    bool reliable = !o->restart;
     nb_status result = NB_NOT_CONVERGED;
     bool fell_back = false;
     constexpr int kLearnedBudget = 3000;  // flexible-CG iterations per refinement step
@@ -745,14 +752,22 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // (941 against 936 at E=4096, N=9; 6061 with replacements every 5
         // decades, where the recurrence drifts)
         const int kind = !use_learned ? 1 : (o->pc == NB_PC_SCHWARZ ? 3 : 2);
-        const bool keep_dir = !o->restart;
-        const bool resume = keep_dir && prev_ok && prev_kind == kind;
+        const bool keep_dir = reliable;
+        // resume only where the FP32 recurrence agreed with the true residual:
+        // the FP64 residual dropped to at most 100x what the recurrence
+        // claimed (else it drifted and the kept direction would mislead the
+        // next solve: restart)
+        const bool agreed = outer > 0 && rel / rel_start <= 100.0 * prev_end;
+        const bool resume = keep_dir && prev_ok && prev_kind == kind && agreed;
+        // a resumed solve that needs more than four times the previous
+        // solve's iterations (plus 100) stops, and the next step restarts
+        const int cap = resume ? 4 * prev_iters + 100 : remaining;
         const bool odd = (prev_iters & 1) != 0;
         const double step_rtol = keep_dir ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
         if (use_learned && o->pc == NB_PC_SCHWARZ) {
             // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
-            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, remaining,
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, cap),
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
@@ -760,14 +775,15 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         } else if (use_learned) {
             // flexible CG with the learned preconditioner (nb_learned.cu), on a
             // bounded budget; Jacobi-PCG takes over if it fails
-            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, kLearnedBudget),
+            k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau,
+                                       std::min(std::min(remaining, cap), kLearnedBudget),
                                        o->record_history ? ws.hist : nullptr,
                                        o->record_history ? ws.hist_cap : 0);
             NB_CUDA(cudaGetLastError());
             NB_TRY(fcg_learned(m, o->prec, ws, o, resume, odd, s));
         } else {
             if (resume)
-                NB_TRY(cg_resume<float>(m, ws, dinv, tau, remaining, o->record_history,
+                NB_TRY(cg_resume<float>(m, ws, dinv, tau, std::min(remaining, cap), o->record_history,
                                         sqrt(s2_prev / m->red_host[1]), s));
             else
                 NB_TRY(cg_start<float>(m, ws, dinv, tau, remaining, 1, o->record_history, s));
@@ -789,10 +805,17 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
             hist_off += it;
         }
         used += it;
+        // an inner solve of more than kReliableMaxIters iterations (an
+        // ill-conditioned problem: the FP32 recurrence drifts over it) or a
+        // resumed one that hit its cap ends the reliable updates of this solve
+        if (it > kReliableMaxIters || (resume && it >= cap)) reliable = false;
         prev_kind = kind;
         prev_ok = ws.scal_host->status == 0 && it > 0;
         prev_iters = it;
-        if (use_learned && ws.scal_host->status != 0) {
+        prev_end = ws.scal_host->relres;  // the recurrence's drop over this solve
+        rel_start = rel;
+        const bool capped = resume && it >= cap && ws.scal_host->status == NB_NOT_CONVERGED;
+        if (use_learned && ws.scal_host->status != 0 && !capped) {
             fell_back = true;  // the learned step failed: Jacobi-PCG from here on
             prev = INFINITY;
             stagn = 0;
