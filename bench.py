@@ -722,7 +722,8 @@ def main():
     h64 = mesh.solve(b, torch.zeros_like(b), nb.default_opts(prec=nb.NB_FP64, rtol=RTOL),
                      history_cap=cap)["history"]
     h32 = mesh.solve(b, torch.zeros_like(b),
-                     nb.default_opts(prec=nb.NB_FP32, rtol=RTOL, inner_rtol=RTOL, max_outer=1),
+                     nb.default_opts(prec=nb.NB_FP32, rtol=RTOL, inner_rtol=RTOL, max_outer=1,
+                                     restart=1),
                      history_cap=cap)["history"]
     kk = min(len(h64), len(h32))
     ae = np.abs(np.asarray(h32[:kk]) - np.asarray(h64[:kk]))
