@@ -47,6 +47,9 @@ def test_version_and_defaults(nb):
     o = nb.default_opts()
     assert o.prec == nb.NB_FP32 and o.pc == nb.NB_PC_JACOBI
     assert o.rtol == 1e-10 and o.use_graph == 1 and o.use_x0 == 0
+    # refinement keeps the search direction by default (reliable updates);
+    # the field is the last of the C struct, so this also checks the layout
+    assert o.restart == 0 and o.inner_rtol == 1e-4 and o.max_outer == 30
 
 
 def test_argument_validation_without_gpu(nb):
