@@ -71,9 +71,13 @@ typedef enum {
     NB_PC_NONE = 0,    /* solveM is a copy (the paper's no-multigrid case) */
     NB_PC_JACOBI = 1,  /* z = diag(A)^-1 r */
     NB_PC_LEARNED = 2, /* per-element network inside flexible CG */
-    NB_PC_SCHWARZ = 3  /* overlapping Schwarz, fast-diagonalisation local solves
+    NB_PC_SCHWARZ = 3, /* overlapping Schwarz, fast-diagonalisation local solves
                           (the smoother of Nekbone's multigrid solveM); FP32
                           refinement steps, even n, orders N <= 11 */
+    NB_PC_SCHWARZ2 = 4 /* the same plus the coarse-grid level (two-level
+                          additive Schwarz, trilinear coarse space on the
+                          element vertices); at most 65 elements per direction
+                          and 24576 interior vertices */
 } nb_pc;
 
 typedef struct {
@@ -404,6 +408,16 @@ nb_status nb_cg_mca(nb_mesh *mesh, int mode, int t, uint64_t seed, int iters, nb
 /* z = M r once, FP32 L-vectors (continuous, masked), device.  Builds the 1D
  * eigenvectors and the scratch on first use (allocates).  Orders N <= 11. */
 nb_status nb_schwarz_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
+
+/* Two-level form: z = sum_e R_e^T A_e^-1 R_e r + R_0^T A_0^-1 R_0 r, with R_0^T the
+ * trilinear interpolation from the interior element vertices to the GLL nodes and
+ * A_0 = R_0 A R_0^T the Galerkin coarse operator of the undeformed box (separable:
+ * Q1 stiffness and mass per direction for N >= 2), inverted by fast
+ * diagonalisation in one thread block (the coarse-grid level of the multigrid
+ * solveM of Section 4.1; textbook two-level additive Schwarz).  Arguments, layout,
+ * ownership and errors as nb_schwarz_apply; NB_ERR_ARG beyond 65 elements per
+ * direction or 24576 interior vertices.  Used by NB_PC_SCHWARZ2. */
+nb_status nb_schwarz2_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
 
 /* nb_glsc3 for callers that cannot let a library allocate memory: a
  * framework whose caching allocator owns the device memory, a process under

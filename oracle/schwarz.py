@@ -22,12 +22,21 @@ Numer. Math. 6, 1964 for the fast diagonalisation):
 * fast diagonalisation: Ad S = Bd S Lam (S^T Bd S = I), so
   A_e^-1 = (Sz (x) Sy (x) Sx) diag(1 / (lx + ly + lz)) (Sz (x) Sy (x) Sx)^T;
 * additive combination: z = sum_e R_e^T A_e^-1 R_e r with R_e the restriction
-  of the global vector to subdomain e (symmetric positive definite).
+  of the global vector to subdomain e (symmetric positive definite);
+* two-level form (the coarse-grid level of the multigrid, textbook two-level
+  additive Schwarz, e.g. Toselli and Widlund, Domain Decomposition Methods,
+  2005, Ch. 3): z += R_0^T A_0^-1 R_0 r, with R_0^T the trilinear (Q1)
+  interpolation from the interior element vertices to the GLL nodes and
+  A_0 = R_0 A R_0^T the Galerkin coarse operator of the undeformed box --
+  separable, Bz(x)By(x)Ax + Bz(x)Ay(x)Bx + Az(x)By(x)Bx with the 1D Galerkin
+  stiffness / mass of the vertex hats (the Q1 matrices for N >= 2).
 
 Pinned by ``tests/test_oracle_schwarz.py``: the fast diagonalisation against
 a dense solve of the Kronecker operator, the single-element box (where the
 preconditioner is the exact inverse and CG converges in one step),
-symmetry, and the 1D operators against the element's GLL matrices.
+symmetry, and the 1D operators against the element's GLL matrices; the
+coarse level against the closed-form Q1 matrices, the Galerkin product of the
+independently assembled fine operator, and exactness on the coarse space.
 """
 from __future__ import annotations
 
@@ -108,9 +117,62 @@ def local_solve(fdm, rt: np.ndarray) -> np.ndarray:
     return np.where(act, t, 0.0)
 
 
-def precondition(P, r: np.ndarray) -> np.ndarray:
-    """z = sum_e R_e^T A_e^-1 R_e r for a continuous, masked L-vector r
-    (oracle.Problem P); returns the L-vector z (continuous, masked)."""
+def coarse_1d(N: int, n_d: int):
+    """The coarse space along one direction of n_d elements of length 1/n_d:
+    R1[v][g] = the hat function of interior vertex v + 1 (v = 0..n_d-2) at
+    global GLL node g (it is (1 + xi_i)/2 on element v, (1 - xi_i)/2 on element
+    v + 1), and the Galerkin stiffness / mass R1 K R1^T, R1 M R1^T with K, M
+    the 1D GLL stiffness / mass assembled over the n_d elements."""
+    xi, _ = gll(N)
+    K, M = gll_1d(N)
+    L = 1.0 / n_d
+    ng = n_d * N + 1
+    Kf = np.zeros((ng, ng))
+    Mf = np.zeros((ng, ng))
+    for e in range(n_d):
+        s = slice(e * N, e * N + N + 1)
+        Kf[s, s] += (2.0 / L) * K
+        Mf[s, s] += (L / 2.0) * M
+    R1 = np.zeros((max(n_d - 1, 0), ng))
+    for v in range(n_d - 1):
+        for i in range(N + 1):
+            R1[v, v * N + i] = (1.0 + xi[i]) / 2.0
+            R1[v, (v + 1) * N + i] = (1.0 - xi[i]) / 2.0
+    return R1, R1 @ Kf @ R1.T, R1 @ Mf @ R1.T
+
+
+def coarse_parts(box):
+    """(R1, Kc, Mc) per direction x, y, z."""
+    return [coarse_1d(box.N, n_d) for n_d in (box.nx, box.ny, box.nz)]
+
+
+def coarse_operator(box) -> np.ndarray:
+    """A_0 = Bz(x)By(x)Ax + Bz(x)Ay(x)Bx + Az(x)By(x)Bx on the interior vertices
+    ([vz][vy][vx], vx fastest), dense."""
+    (_, Kx, Mx), (_, Ky, My), (_, Kz, Mz) = coarse_parts(box)
+    return (np.kron(Mz, np.kron(My, Kx)) + np.kron(Mz, np.kron(Ky, Mx)) +
+            np.kron(Kz, np.kron(My, Mx)))
+
+
+def coarse_correction(P, r: np.ndarray) -> np.ndarray:
+    """R_0^T A_0^-1 R_0 r for a continuous, masked L-vector r; the L-vector
+    result (continuous, masked)."""
+    box = P.box
+    (Rx, _, _), (Ry, _, _), (Rz, _, _) = coarse_parts(box)
+    if Rx.shape[0] == 0 or Ry.shape[0] == 0 or Rz.shape[0] == 0:
+        return np.zeros_like(r)  # no interior vertex: no coarse space
+    gx_n, gy_n, gz_n = box.nx * box.N + 1, box.ny * box.N + 1, box.nz * box.N + 1
+    rg = P.to_global(r).reshape(gz_n, gy_n, gx_n)
+    rc = np.einsum("cz,by,ax,zyx->cba", Rz, Ry, Rx, rg)
+    zc = np.linalg.solve(coarse_operator(box), rc.reshape(-1)).reshape(rc.shape)
+    zg = np.einsum("cz,by,ax,cba->zyx", Rz, Ry, Rx, zc)
+    return P.to_local(zg.reshape(-1), masked=True)
+
+
+def precondition(P, r: np.ndarray, coarse: bool = False) -> np.ndarray:
+    """z = sum_e R_e^T A_e^-1 R_e r (+ R_0^T A_0^-1 R_0 r with ``coarse``) for a
+    continuous, masked L-vector r (oracle.Problem P); returns the L-vector z
+    (continuous, masked)."""
     box, N = P.box, P.N
     n = N + 1
     gx_n, gy_n, gz_n = box.nx * N + 1, box.ny * N + 1, box.nz * N + 1
@@ -135,6 +197,8 @@ def precondition(P, r: np.ndarray) -> np.ndarray:
                 zt = local_solve(fdm, rt)
                 zg[sub] += zt[loc]
     z = P.to_local(zg.reshape(-1), masked=True)
+    if coarse:
+        z = z + coarse_correction(P, r)
     return z
 
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libnekbone_gb300.so")
 NB_OK, NB_ERR_ARG, NB_ERR_CUDA, NB_ERR_OOM, NB_ERR_MESH, NB_ERR_STATE = 0, -1, -2, -3, -4, -5
 NB_NOT_CONVERGED, NB_STAGNATED, NB_BREAKDOWN, NB_FELL_BACK = 1, 2, 3, 4
 NB_FP64, NB_FP32, NB_TC_F16, NB_TC_BF16 = 0, 1, 2, 3
-NB_PC_NONE, NB_PC_JACOBI, NB_PC_LEARNED, NB_PC_SCHWARZ = 0, 1, 2, 3
+NB_PC_NONE, NB_PC_JACOBI, NB_PC_LEARNED, NB_PC_SCHWARZ, NB_PC_SCHWARZ2 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "ok", -1: "invalid argument", -2: "cuda error", -3: "out of memory",
                 -4: "invalid mesh", -5: "bad state", 1: "not converged", 2: "stagnated",
                 3: "breakdown", 4: "fell back"}
@@ -96,6 +96,7 @@ def _load():
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
         "nb_apply_vprec": (i32, [vp, i32, vp, vp]),
         "nb_schwarz_apply": (i32, [vp, vp, vp]),
+        "nb_schwarz2_apply": (i32, [vp, vp, vp]),
         "nb_cg_vprec": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(dbl)]),
         "nb_cg_mca": (i32, [vp, i32, i32, C.c_uint64, i32, i32, vp, vp, vp, C.POINTER(dbl)]),
     }
@@ -281,9 +282,11 @@ class Mesh:
         check(lib.nb_time_ax(self.h, prec, int(cg_step), variant, reps, fp, fb, C.byref(ms)))
         return ms.value
 
-    def schwarz_apply(self, r, z):
-        """z = M r with the overlapping Schwarz preconditioner (FP32)."""
-        check(lib.nb_schwarz_apply(self.h, self._vec(r, NB_FP32), self._vec(z, NB_FP32)))
+    def schwarz_apply(self, r, z, coarse=False):
+        """z = M r (FP32 L-vectors): one-level Schwarz, or with ``coarse`` the
+        two-level form (nb_schwarz2_apply)."""
+        f = lib.nb_schwarz2_apply if coarse else lib.nb_schwarz_apply
+        check(f(self.h, self._vec(r, NB_FP32), self._vec(z, NB_FP32)))
 
     def apply_vprec(self, t, u, w):
         """w = A u with every operation rounded to t mantissa bits (FP64)."""
@@ -462,5 +465,5 @@ class Model:
 __all__ = ["lib", "LIB_PATH", "Batch", "Model", "NbError", "Context", "Mesh", "default_opts", "check",
            "nb_opts", "nb_stats", "nb_version", "PREC_NAMES",
            "NB_FP64", "NB_FP32", "NB_TC_F16", "NB_TC_BF16", "NB_PC_NONE", "NB_PC_JACOBI",
-           "NB_PC_LEARNED", "NB_PC_SCHWARZ", "NB_OK", "NB_NOT_CONVERGED", "NB_STAGNATED", "NB_BREAKDOWN",
+           "NB_PC_LEARNED", "NB_PC_SCHWARZ", "NB_PC_SCHWARZ2", "NB_OK", "NB_NOT_CONVERGED", "NB_STAGNATED", "NB_BREAKDOWN",
            "NB_FELL_BACK"]

@@ -346,7 +346,7 @@ static nb_status check_opts(const nb_opts *o)
 {
     if (!o) return arg_error("opts is NULL");
     if (!prec_ok(o->prec)) return arg_error("opts.prec");
-    if (o->pc < NB_PC_NONE || o->pc > NB_PC_SCHWARZ) return arg_error("opts.pc");
+    if (o->pc < NB_PC_NONE || o->pc > NB_PC_SCHWARZ2) return arg_error("opts.pc");
     if (!(o->rtol > 0.0) || !(o->rtol < 1.0)) return arg_error("opts.rtol must be in (0,1)");
     if (o->maxiter < 0) return arg_error("opts.maxiter");
     if (o->prec != NB_FP64 && (!(o->inner_rtol > 0.0) || !(o->inner_rtol < 1.0)))
@@ -355,7 +355,7 @@ static nb_status check_opts(const nb_opts *o)
     if (o->restart != 0 && o->restart != 1) return arg_error("opts.restart must be 0 or 1");
     if (o->pc == NB_PC_LEARNED && o->prec == NB_FP64)
         return arg_error("the learned preconditioner runs inside refinement (prec != NB_FP64)");
-    if (o->pc == NB_PC_SCHWARZ && o->prec != NB_FP32)
+    if ((o->pc == NB_PC_SCHWARZ || o->pc == NB_PC_SCHWARZ2) && o->prec != NB_FP32)
         return arg_error("the Schwarz preconditioner runs inside FP32 refinement (prec = NB_FP32)");
     return NB_OK;
 }

@@ -1246,7 +1246,8 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
 nb_status schwarz_setup(nb_mesh *m);
 nb_status schwarz_gather(nb_mesh *m, const float *r, cudaStream_t s);
 nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *wold,
-                            CgScalars *sc, double *part, cudaStream_t s);
+                            CgScalars *sc, double *part, cudaStream_t s, bool coarse);
+nb_status schwarz_coarse_setup(nb_mesh *m);
 float *schwarz_rg(nb_mesh *m);
 
 // The inner solve of a refinement step with the Schwarz preconditioner (FP32,
@@ -1263,7 +1264,9 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         set_error("the Schwarz preconditioner runs in FP32 refinement steps with even n");
         return NB_ERR_ARG;
     }
+    const bool two = o->pc == NB_PC_SCHWARZ2;  // with the coarse-grid level
     NB_TRY(schwarz_setup(m));  // before any capture: it allocates once
+    if (two) NB_TRY(schwarz_coarse_setup(m));
     const int g = vec_grid(m->ctx, m->nL);
     const float *sgn = m->dinv32;
     float *x = (float *)ws.x, *r = (float *)ws.r, *p = (float *)ws.p, *w = (float *)ws.w;
@@ -1277,16 +1280,17 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     NB_TRY(schwarz_gather(m, r, s));
     m->launches += 3;
     auto step = [&](float *wcur, float *wold) -> nb_status {
-        NB_TRY(schwarz_solve_sum(m, r, z, wold, ws.scal, P0, s));
+        NB_TRY(schwarz_solve_sum(m, r, z, wold, ws.scal, P0, s, two));
         int nparts = 0;
         NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
         // w stays unassembled (the update folds the summation in; the sum
         // kernel forms (z, w_prev) over every copy)
         return fcg_update_folded(m, ws, x, r, p, wcur, P2, rg, s);
     };
-    constexpr int kPerStep = 4;  // local solves, their sum, operator, update
+    // local solves, (coarse restriction and solve,) their sum, operator, update
+    const int kPerStep = two ? 6 : 4;
     if (o->use_graph) {
-        const intptr_t key = (intptr_t)m->schwarz;
+        const intptr_t key = (intptr_t)m->schwarz + (two ? 1 : 0);
         if (!ws.exec2 || ws.graph2_key != key) {
             if (ws.exec2) NB_CUDA(cudaGraphExecDestroy(ws.exec2));
             if (ws.graph2) NB_CUDA(cudaGraphDestroy(ws.graph2));

@@ -36,8 +36,25 @@ struct SchwarzData {
     float *rg = nullptr;   // [nG] owner values of r
     float *zt = nullptr;   // [E][m][Mp][Mp] local solutions, [c][b][a], rows padded to Mp
     int grid_local = 1;    // blocks of k_sw_local
-    int grid_sum = 1;      // blocks of k_sw_sum (at most kMaxPartials / 2)
+    int grid_sum[2] = {1, 1};  // blocks of k_sw_sum without / with the coarse
+                               // level (at most kMaxPartials / 2)
+    // coarse level (two-level form): interior element vertices per direction,
+    // the 1D Galerkin eigenproblems Kc s = lam Mc s (S^T Mc S = I), the GLL
+    // points for the vertex hats, the y/x-restricted residual and the coarse
+    // solution
+    bool coarse = false;
+    int nc[3] = {0, 0, 0};
+    float *Sc = nullptr;    // [3][kCoarseDir^2], S[v][q] row-major per direction
+    float *lamc = nullptr;  // [3][kCoarseDir]
+    float *xi = nullptr;    // [N + 1]
+    float *t2 = nullptr;    // [gz][vy][vx]
+    float *zc = nullptr;    // [vz][vy][vx]
 };
+
+// Coarse level limits: interior vertices per direction, and in total (two
+// buffers of them in one block's shared memory).
+constexpr int kCoarseDir = 64;
+constexpr int kCoarseTotal = 24576;
 
 // Cyclic Jacobi eigenvalue iteration for a symmetric m x m matrix (Golub and
 // Van Loan, Section 8.5): C = Q diag(ev) Q^T, Q in columns.
@@ -311,11 +328,12 @@ k_sw_local(int64_t E, int nx, int ny, int nz, int N, const float *__restrict__ r
 // DOTS, also the partials of (z, w_prev) (w_prev unassembled) and (r, z), and the last
 // block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on the first
 // step) and rtz = (r, z).
-template <int n, bool DOTS>
+template <int n, bool DOTS, bool COARSE>
 __global__ void __launch_bounds__(256)
 k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
          const float *__restrict__ sgn, float *__restrict__ z, const float *__restrict__ r,
-         const float *__restrict__ wold, CgScalars *sc, double *__restrict__ part)
+         const float *__restrict__ wold, CgScalars *sc, double *__restrict__ part,
+         const float *__restrict__ zc, const float *__restrict__ xi)
 {
     constexpr int N = n - 1, n3 = n * n * n, Mp = SwCfg<n + 2>::Mp, ZS = SwCfg<n + 2>::ZS;
     // subdomains covering a node per direction: 2 for N >= 3 (3 for N = 2, 4 for N = 1)
@@ -330,6 +348,20 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
         const int eo = (int)e * ZS;
+        // coarse level: the coarse solution at the element's 8 vertices (0 on
+        // the boundary: interior vertex (ex + cx - 1, ...) of nx - 1 per row)
+        float zv[2][2][2];
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+            for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                for (int cx = 0; cx < 2; ++cx) {
+                    const int vx = ex + cx - 1, vy = ey + cy - 1, vz = ez + cz - 1;
+                    const bool in = COARSE && vx >= 0 && vx < nx - 1 && vy >= 0 && vy < ny - 1 &&
+                                    vz >= 0 && vz < nz - 1;
+                    zv[cz][cy][cx] = in ? zc[((int64_t)vz * (ny - 1) + vy) * (nx - 1) + vx] : 0.f;
+                }
 #pragma unroll
         for (int s = 0; s < QS; ++s) {
             const int q = threadIdx.x + 256 * s;
@@ -362,6 +394,16 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
                 for (int ty = 0; ty < KD; ++ty)
 #pragma unroll
                     for (int tx = 0; tx < KD; ++tx) sum += v[tz][ty][tx];
+            if (COARSE) {  // + R_0^T z_c: trilinear interpolation of the vertex values
+                const float ax = 0.5f * (1.f + xi[i]), ay = 0.5f * (1.f + xi[j]),
+                            az = 0.5f * (1.f + xi[k]);
+                const float y00 = zv[0][0][0] + ax * (zv[0][0][1] - zv[0][0][0]);
+                const float y01 = zv[0][1][0] + ax * (zv[0][1][1] - zv[0][1][0]);
+                const float y10 = zv[1][0][0] + ax * (zv[1][0][1] - zv[1][0][0]);
+                const float y11 = zv[1][1][0] + ax * (zv[1][1][1] - zv[1][1][0]);
+                const float z0 = y00 + ay * (y01 - y00), z1 = y10 + ay * (y11 - y10);
+                sum += z0 + az * (z1 - z0);
+            }
             sum = sg != 0.f ? sum : 0.f;  // masked (Dirichlet) copies are zero
             z[l] = sum;
             if (DOTS) {
@@ -400,16 +442,27 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
 template <bool DOTS>
 static nb_status sw_sum(int mode, int m, int sms, int *grid, int64_t E, int nx, int ny, int nz,
                         const float *zt, const float *sgn, float *z, const float *r,
-                        const float *wold, CgScalars *sc, double *part, cudaStream_t s)
+                        const float *wold, CgScalars *sc, double *part, cudaStream_t s,
+                        const float *zc = nullptr, const float *xi = nullptr)
 {
 #define NB_SWS(NN)                                                                                \
     if (mode == 0) {                                                                              \
-        int per_sm = 0;                                                                           \
-        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sw_sum<NN, true>, 256, 0)); \
-        *grid = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)sms * std::max(per_sm, 1))); \
+        int per_sm[2] = {0, 0};                                                                   \
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_sw_sum<NN, true, false>, \
+                                                              256, 0));                           \
+        NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_sw_sum<NN, true, true>, \
+                                                              256, 0));                           \
+        for (int c = 0; c < 2; ++c)                                                               \
+            grid[c] = (int)std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)sms *               \
+                                                                      std::max(per_sm[c], 1)));   \
         return NB_OK;                                                                             \
     }                                                                                             \
-    k_sw_sum<NN, DOTS><<<*grid, 256, 0, s>>>(E, nx, ny, nz, zt, sgn, z, r, wold, sc, part);        \
+    if (zc)                                                                                       \
+        k_sw_sum<NN, DOTS, true><<<grid[1], 256, 0, s>>>(E, nx, ny, nz, zt, sgn, z, r, wold, sc,  \
+                                                         part, zc, xi);                           \
+    else                                                                                          \
+        k_sw_sum<NN, DOTS, false><<<grid[0], 256, 0, s>>>(E, nx, ny, nz, zt, sgn, z, r, wold, sc, \
+                                                          part, zc, xi);                          \
     NB_CUDA(cudaGetLastError());                                                                  \
     return NB_OK
     switch (m - 2) {
@@ -429,6 +482,106 @@ static nb_status sw_sum(int mode, int m, int sms, int *grid, int64_t E, int nx, 
             return NB_ERR_ARG;
     }
 #undef NB_SWS
+}
+
+// Hat function of interior vertex v (0-based; its position is vertex v + 1)
+// at global GLL node g of one direction: (1 + xi_i)/2 on element v (g = v N + i),
+// (1 - xi_i)/2 on element v + 1 (g = (v + 1) N + i), 0 elsewhere.
+__device__ __forceinline__ float co_hat(const float *xi, int N, int v, int g)
+{
+    const int i0 = g - v * N;
+    if (i0 < 0 || i0 > 2 * N) return 0.f;
+    return i0 <= N ? 0.5f * (1.f + xi[i0]) : 0.5f * (1.f - xi[i0 - N]);
+}
+
+// Coarse restriction, x and y: t2[gz][vy][vx] = sum over the (2N + 1)^2 nodes
+// of the two hats' support of hat_vy(gy) hat_vx(gx) rg[gz][gy][gx] (rg holds
+// each global node's value once).
+__global__ void k_co_rxy(int gxn, int gyn, int gzn, int N, int ncx, int ncy,
+                         const float *__restrict__ xi, const float *__restrict__ rg,
+                         float *__restrict__ t2, const CgScalars *sc)
+{
+    if (sc && sc->done) return;
+    const int64_t total = (int64_t)gzn * ncy * ncx;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int vx = (int)(t % ncx), vy = (int)((t / ncx) % ncy), gz = (int)(t / ((int64_t)ncx * ncy));
+        float acc = 0.f;
+        for (int dy = 0; dy <= 2 * N; ++dy) {
+            const int gy = vy * N + dy;
+            const float hy = co_hat(xi, N, vy, gy);
+            const float *row = rg + ((int64_t)gz * gyn + gy) * gxn + vx * N;
+            float ax = 0.f;
+            for (int dx = 0; dx <= 2 * N; ++dx) ax += co_hat(xi, N, vx, vx * N + dx) * row[dx];
+            acc += hy * ax;
+        }
+        t2[t] = acc;
+    }
+}
+
+// One axis of a coarse tensor contraction in shared memory: out = sum over
+// the axis of M[a][q] in[..a..] (M row-major [nc][nc]); axis 0 = x (fastest).
+__device__ __forceinline__ void co_contract(const float *__restrict__ in, float *__restrict__ out,
+                                            const float *__restrict__ M, bool trans, int axis,
+                                            int nx, int ny, int nz)
+{
+    const int total = nx * ny * nz;
+    const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? nx : nx * ny);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int x = t % nx, y = (t / nx) % ny, z = t / (nx * ny);
+        const int q = axis == 0 ? x : (axis == 1 ? y : z);
+        const int base = t - q * stride;
+        float acc = 0.f;
+        // trans: out[q] = sum_a M[a][q] in[a] (S^T); else out[q] = sum_a M[q][a] in[a] (S)
+        for (int a = 0; a < na; ++a)
+            acc += (trans ? M[a * na + q] : M[q * na + a]) * in[base + a * stride];
+        out[t] = acc;
+    }
+}
+
+// Coarse solve in one block: the z restriction of t2, then A_0^-1 by fast
+// diagonalisation, (Sz(x)Sy(x)Sx) diag(1 / (lx + ly + lz)) (Sz(x)Sy(x)Sx)^T,
+// into zc.
+__global__ void k_co_solve(int gzn, int N, int ncx, int ncy, int ncz, const float *__restrict__ xi,
+                           const float *__restrict__ Sc, const float *__restrict__ lamc,
+                           const float *__restrict__ t2, float *__restrict__ zc,
+                           const CgScalars *sc)
+{
+    if (sc && sc->done) return;
+    extern __shared__ __align__(16) float co_smem[];
+    const int total = ncx * ncy * ncz;
+    float *A = co_smem, *B = co_smem + total;
+    const float *Sx = Sc, *Sy = Sc + kCoarseDir * kCoarseDir, *Sz = Sc + 2 * kCoarseDir * kCoarseDir;
+    const float *lx = lamc, *ly = lamc + kCoarseDir, *lz = lamc + 2 * kCoarseDir;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int vxy = t % (ncx * ncy), vz = t / (ncx * ncy);
+        float acc = 0.f;
+        for (int dz = 0; dz <= 2 * N; ++dz) {
+            const int gz = vz * N + dz;
+            acc += co_hat(xi, N, vz, gz) * t2[(int64_t)gz * ncx * ncy + vxy];
+        }
+        A[t] = acc;
+    }
+    __syncthreads();
+    co_contract(A, B, Sx, true, 0, ncx, ncy, ncz);
+    __syncthreads();
+    co_contract(B, A, Sy, true, 1, ncx, ncy, ncz);
+    __syncthreads();
+    co_contract(A, B, Sz, true, 2, ncx, ncy, ncz);
+    __syncthreads();
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int x = t % ncx, y = (t / ncx) % ncy, z = t / (ncx * ncy);
+        B[t] = B[t] / (lx[x] + ly[y] + lz[z]);
+    }
+    __syncthreads();
+    co_contract(B, A, Sz, false, 2, ncx, ncy, ncz);
+    __syncthreads();
+    co_contract(A, B, Sy, false, 1, ncx, ncy, ncz);
+    __syncthreads();
+    co_contract(B, A, Sx, false, 0, ncx, ncy, ncz);
+    __syncthreads();
+    for (int t = threadIdx.x; t < total; t += blockDim.x) zc[t] = A[t];
 }
 
 // Shared-memory limit and grid (resident blocks x SMs, at most one block
@@ -492,6 +645,11 @@ void schwarz_free(nb_mesh *m)
     cudaFree(d->lam);
     cudaFree(d->rg);
     cudaFree(d->zt);
+    cudaFree(d->Sc);
+    cudaFree(d->lamc);
+    cudaFree(d->xi);
+    cudaFree(d->t2);
+    cudaFree(d->zc);
     delete d;
     m->schwarz = nullptr;
 }
@@ -548,10 +706,158 @@ nb_status schwarz_setup(nb_mesh *m)
     nb_status st = sw_local(0, mm, m->ctx->sm_count, &d->grid_local, m->E, 0, 0, 0, 0, nullptr,
                             nullptr, nullptr, nullptr, nullptr, nullptr);
     if (st == NB_OK)
-        st = sw_sum<true>(0, mm, m->ctx->sm_count, &d->grid_sum, m->E, 0, 0, 0, nullptr, nullptr,
+        st = sw_sum<true>(0, mm, m->ctx->sm_count, d->grid_sum, m->E, 0, 0, 0, nullptr, nullptr,
                           nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (st != NB_OK) schwarz_free(m);
     return st;
+}
+
+// Generalised symmetric eigenproblem K s = lam M s of order m (M symmetric
+// positive definite): S with S^T M S = I, S^T K S = diag(lam), through the
+// Cholesky factor M = C C^T and cyclic Jacobi rotations on C^-1 K C^-T
+// (Golub and Van Loan, Section 8.7).  S row-major [i][mode].
+static bool gen_eig(int m, const std::vector<double> &K, const std::vector<double> &M,
+                    std::vector<double> &S, std::vector<double> &lam)
+{
+    std::vector<double> C((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j)
+        for (int i = j; i < m; ++i) {
+            double v = M[(size_t)i * m + j];
+            for (int k = 0; k < j; ++k) v -= C[(size_t)i * m + k] * C[(size_t)j * m + k];
+            if (i == j) {
+                if (!(v > 0.0)) return false;
+                C[(size_t)j * m + j] = sqrt(v);
+            } else {
+                C[(size_t)i * m + j] = v / C[(size_t)j * m + j];
+            }
+        }
+    // X = C^-1 K (forward substitution, column by column), W = C^-1 X^T
+    std::vector<double> X((size_t)m * m), W((size_t)m * m);
+    auto fsub = [&](const std::vector<double> &B, std::vector<double> &Y, bool transB) {
+        for (int c = 0; c < m; ++c)
+            for (int i = 0; i < m; ++i) {
+                double v = transB ? B[(size_t)c * m + i] : B[(size_t)i * m + c];
+                for (int k = 0; k < i; ++k) v -= C[(size_t)i * m + k] * Y[(size_t)k * m + c];
+                Y[(size_t)i * m + c] = v / C[(size_t)i * m + i];
+            }
+    };
+    fsub(K, X, false);
+    fsub(X, W, true);
+    for (int i = 0; i < m; ++i)  // symmetrise the rounding
+        for (int j = 0; j < i; ++j) {
+            const double a = 0.5 * (W[(size_t)i * m + j] + W[(size_t)j * m + i]);
+            W[(size_t)i * m + j] = W[(size_t)j * m + i] = a;
+        }
+    std::vector<double> Y;
+    jacobi_eig(m, W, lam, Y);  // W = Y diag(lam) Y^T
+    // S = C^-T Y (back substitution with C^T, column by column)
+    S.assign((size_t)m * m, 0.0);
+    for (int c = 0; c < m; ++c)
+        for (int i = m - 1; i >= 0; --i) {
+            double v = Y[(size_t)i * m + c];
+            for (int k = i + 1; k < m; ++k) v -= C[(size_t)k * m + i] * S[(size_t)k * m + c];
+            S[(size_t)i * m + c] = v / C[(size_t)i * m + i];
+        }
+    return true;
+}
+
+// The coarse level of the mesh (once): per direction the hats of the n_d - 1
+// interior vertices at the n_d N + 1 GLL nodes, the Galerkin 1D stiffness /
+// mass Kc = R1 Kf R1^T, Mc = R1 Mf R1^T with Kf, Mf the GLL stiffness / mass
+// assembled over the n_d elements of length 1 / n_d, and their generalised
+// eigenvectors.  A direction with one element has no interior vertex: no
+// coarse space (the correction is zero).
+static nb_status schwarz_setup_coarse(nb_mesh *m)
+{
+    SchwarzData *d = (SchwarzData *)m->schwarz;
+    if (d->coarse || d->Sc) return NB_OK;
+    const int N = m->N, n = N + 1;
+    const int cnt[3] = {m->nx, m->ny, m->nz};
+    int64_t total = 1;
+    for (int dir = 0; dir < 3; ++dir) {
+        d->nc[dir] = cnt[dir] - 1;
+        total *= d->nc[dir];
+        if (d->nc[dir] > kCoarseDir) {
+            set_error("two-level Schwarz: at most %d elements per direction", kCoarseDir + 1);
+            return NB_ERR_ARG;
+        }
+    }
+    if (total > kCoarseTotal) {
+        set_error("two-level Schwarz: at most %d interior element vertices", kCoarseTotal);
+        return NB_ERR_ARG;
+    }
+    std::vector<double> xi(n), w(n), D((size_t)n * n), K((size_t)n * n, 0.0);
+    NB_TRY(gll_host(N, xi.data(), w.data()));
+    deriv_host(N, xi.data(), D.data());
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s2 = 0.0;
+            for (int q = 0; q < n; ++q) s2 += w[q] * D[(size_t)q * n + i] * D[(size_t)q * n + j];
+            K[(size_t)i * n + j] = s2;
+        }
+    std::vector<float> Sh((size_t)3 * kCoarseDir * kCoarseDir, 0.f), lh((size_t)3 * kCoarseDir, 1.f);
+    for (int dir = 0; dir < 3 && total > 0; ++dir) {
+        const int nd = cnt[dir], nc = nd - 1, ng = nd * N + 1;
+        const double L = 1.0 / nd;
+        std::vector<double> Kf((size_t)ng * ng, 0.0), Mf((size_t)ng * ng, 0.0), R((size_t)nc * ng, 0.0);
+        for (int e = 0; e < nd; ++e)
+            for (int i = 0; i < n; ++i) {
+                Mf[(size_t)(e * N + i) * ng + e * N + i] += 0.5 * L * w[i];
+                for (int j = 0; j < n; ++j)
+                    Kf[(size_t)(e * N + i) * ng + e * N + j] += (2.0 / L) * K[(size_t)i * n + j];
+            }
+        for (int v = 0; v < nc; ++v)
+            for (int i = 0; i < n; ++i) {
+                R[(size_t)v * ng + v * N + i] = 0.5 * (1.0 + xi[i]);
+                R[(size_t)v * ng + (v + 1) * N + i] = 0.5 * (1.0 - xi[i]);
+            }
+        std::vector<double> Kc((size_t)nc * nc, 0.0), Mc((size_t)nc * nc, 0.0);
+        for (int a = 0; a < nc; ++a)
+            for (int b = 0; b < nc; ++b) {
+                double sk = 0.0, sm = 0.0;
+                for (int g = a * N; g <= (a + 2) * N; ++g)
+                    for (int h = b * N; h <= (b + 2) * N; ++h) {
+                        const double rr = R[(size_t)a * ng + g] * R[(size_t)b * ng + h];
+                        sk += rr * Kf[(size_t)g * ng + h];
+                        sm += rr * Mf[(size_t)g * ng + h];
+                    }
+                Kc[(size_t)a * nc + b] = sk;
+                Mc[(size_t)a * nc + b] = sm;
+            }
+        std::vector<double> S, lam;
+        if (!gen_eig(nc, Kc, Mc, S, lam)) {
+            set_error("two-level Schwarz: coarse mass matrix not positive definite");
+            return NB_ERR_ARG;
+        }
+        for (int a = 0; a < nc; ++a) {
+            lh[(size_t)dir * kCoarseDir + a] = (float)lam[a];
+            for (int q = 0; q < nc; ++q)
+                Sh[(size_t)dir * kCoarseDir * kCoarseDir + a * nc + q] = (float)S[(size_t)a * nc + q];
+        }
+    }
+    std::vector<float> xf(n);
+    for (int i = 0; i < n; ++i) xf[i] = (float)xi[i];
+    const int64_t gzn = (int64_t)m->nz * N + 1;
+    cudaError_t e = cudaMalloc(&d->Sc, sizeof(float) * Sh.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->lamc, sizeof(float) * lh.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->xi, sizeof(float) * n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d->t2, sizeof(float) * std::max<int64_t>(1, gzn * d->nc[1] * d->nc[0]));
+    if (e == cudaSuccess) e = cudaMalloc(&d->zc, sizeof(float) * std::max<int64_t>(1, total));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->Sc, Sh.data(), sizeof(float) * Sh.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->lamc, lh.data(), sizeof(float) * lh.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->xi, xf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_co_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * sizeof(float) * kCoarseTotal));
+    if (e != cudaSuccess) {
+        set_error("two-level Schwarz set-up: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
+    }
+    d->coarse = total > 0;
+    return NB_OK;
 }
 
 float *schwarz_rg(nb_mesh *m) { return ((SchwarzData *)m->schwarz)->rg; }
@@ -570,23 +876,45 @@ nb_status schwarz_gather(nb_mesh *m, const float *r, cudaStream_t s)
 // with sc, also the flexible-CG dots of z with r and w_prev (partials in
 // part, 2 x the sum's grid entries) and beta, rtz in sc.
 nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *wold,
-                            CgScalars *sc, double *part, cudaStream_t s)
+                            CgScalars *sc, double *part, cudaStream_t s, bool coarse)
 {
     SchwarzData *d = (SchwarzData *)m->schwarz;
     NB_TRY(sw_local(1, d->m, m->ctx->sm_count, &d->grid_local, m->E, m->nx, m->ny, m->nz, m->N,
                     d->rg, d->S, d->lam, d->zt, sc, s));
+    const float *zc = nullptr;
+    if (coarse && d->coarse) {  // R_0 r (x, y; then z and A_0^-1 in one block)
+        const int N = m->N, gxn = m->nx * N + 1, gyn = m->ny * N + 1, gzn = m->nz * N + 1;
+        const int64_t t2n = (int64_t)gzn * d->nc[1] * d->nc[0];
+        const int g = (int)std::min<int64_t>((t2n + 255) / 256, (int64_t)m->ctx->sm_count * 8);
+        k_co_rxy<<<std::max(g, 1), 256, 0, s>>>(gxn, gyn, gzn, N, d->nc[0], d->nc[1], d->xi, d->rg,
+                                                 d->t2, sc);
+        NB_CUDA(cudaGetLastError());
+        const int total = d->nc[0] * d->nc[1] * d->nc[2];
+        k_co_solve<<<1, 512, 2 * sizeof(float) * total, s>>>(gzn, N, d->nc[0], d->nc[1], d->nc[2],
+                                                              d->xi, d->Sc, d->lamc, d->t2, d->zc,
+                                                              sc);
+        NB_CUDA(cudaGetLastError());
+        zc = d->zc;
+    }
     if (sc)
-        return sw_sum<true>(1, d->m, 0, &d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32,
-                            z, r, wold, sc, part, s);
-    return sw_sum<false>(1, d->m, 0, &d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32, z,
-                         r, wold, sc, part, s);
+        return sw_sum<true>(1, d->m, 0, d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32,
+                            z, r, wold, sc, part, s, zc, d->xi);
+    return sw_sum<false>(1, d->m, 0, d->grid_sum, m->E, m->nx, m->ny, m->nz, d->zt, m->dinv32, z,
+                         r, wold, sc, part, s, zc, d->xi);
 }
 
-// z = M r for FP32 L-vectors r (continuous, masked).
-nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s)
+// Set-up of the coarse level for the two-level form (once per mesh).
+nb_status schwarz_coarse_setup(nb_mesh *m)
+{
+    NB_TRY(schwarz_setup(m));
+    return schwarz_setup_coarse(m);
+}
+
+// z = M r for FP32 L-vectors r (continuous, masked); coarse: two-level form.
+nb_status schwarz_apply(nb_mesh *m, const float *r, float *z, cudaStream_t s, bool coarse)
 {
     NB_TRY(schwarz_gather(m, r, s));
-    return schwarz_solve_sum(m, r, z, nullptr, nullptr, nullptr, s);
+    return schwarz_solve_sum(m, r, z, nullptr, nullptr, nullptr, s, coarse);
 }
 
 }  // namespace nb
@@ -605,7 +933,24 @@ extern "C" nb_status nb_schwarz_apply(nb_mesh *m, const float *r_dev, float *z_d
     }
     NB_CUDA(cudaSetDevice(m->ctx->device));
     NB_TRY(schwarz_setup(m));
-    NB_TRY(schwarz_apply(m, r_dev, z_dev, m->ctx->stream));
+    NB_TRY(schwarz_apply(m, r_dev, z_dev, m->ctx->stream, false));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_schwarz2_apply(nb_mesh *m, const float *r_dev, float *z_dev)
+{
+    if (!m || !r_dev || !z_dev) {
+        set_error("invalid argument: NULL mesh or vector");
+        return NB_ERR_ARG;
+    }
+    if (!m->gs_ready) {
+        set_error("call nb_setup_gs first");
+        return NB_ERR_STATE;
+    }
+    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_TRY(schwarz_coarse_setup(m));
+    NB_TRY(schwarz_apply(m, r_dev, z_dev, m->ctx->stream, true));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
     return NB_OK;
 }

@@ -727,7 +727,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         if (rel < o->rtol) { result = NB_OK; break; }
         if (outer == o->max_outer || used >= o->maxiter) { result = NB_NOT_CONVERGED; break; }
         if (rel > 0.5 * prev) {
-            if ((o->pc == NB_PC_LEARNED || o->pc == NB_PC_SCHWARZ) && !fell_back) {
+            if ((o->pc == NB_PC_LEARNED || o->pc == NB_PC_SCHWARZ || o->pc == NB_PC_SCHWARZ2) &&
+                !fell_back) {
                 fell_back = true;  // the learned steps stopped paying: Jacobi-PCG takes over
                 stagn = 0;
             } else if (++stagn >= 3) {
@@ -743,7 +744,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                            (float *)ws.x);
         NB_CUDA(cudaGetLastError());
         const int remaining = o->maxiter - used;
-        const bool use_learned = (o->pc == NB_PC_LEARNED || o->pc == NB_PC_SCHWARZ) && !fell_back;
+        const bool schwarz = o->pc == NB_PC_SCHWARZ || o->pc == NB_PC_SCHWARZ2;
+        const bool use_learned = (o->pc == NB_PC_LEARNED || schwarz) && !fell_back;
         // the inner solve only has to close the remaining gap to rtol (with a
         // factor 2 of margin), and never less than inner_rtol per step.  With
         // the direction kept (reliable update) the residual is replaced at
@@ -751,7 +753,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // true residual, and the iteration count stays that of FP64 PCG
         // (941 against 936 at E=4096, N=9; 6061 with replacements every 5
         // decades, where the recurrence drifts)
-        const int kind = !use_learned ? 1 : (o->pc == NB_PC_SCHWARZ ? 3 : 2);
+        const int kind = !use_learned ? 1 : (schwarz ? 2 + (int)o->pc : 2);
         const bool keep_dir = reliable;
         // resume only where the FP32 recurrence agreed with the true residual:
         // the FP64 residual dropped to at most 100x what the recurrence
@@ -765,7 +767,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         const bool odd = (prev_iters & 1) != 0;
         const double step_rtol = keep_dir ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
-        if (use_learned && o->pc == NB_PC_SCHWARZ) {
+        if (use_learned && schwarz) {
             // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
             k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, cap),
                                        o->record_history ? ws.hist : nullptr,

@@ -129,3 +129,89 @@ def test_fewer_iterations_than_jacobi():
     print(f"Jacobi {it_j} iterations, Schwarz {it_s}")
     assert rel < 1e-8
     assert it_s < 0.6 * it_j
+
+
+# ---- the coarse level (two-level additive Schwarz) ----
+
+@pytest.mark.parametrize("N", [2, 3, 7])
+def test_coarse_1d_matrices_are_the_q1_matrices(N):
+    """Galerkin products of the vertex hats with the GLL matrices: exact
+    integration of linear functions for N >= 2, i.e. the Q1 stiffness
+    (1/L) tridiag(-1, 2, -1) and consistent mass (L/6) tridiag(1, 4, 1)."""
+    n_d = 5
+    L = 1.0 / n_d
+    R1, Kc, Mc = schwarz.coarse_1d(N, n_d)
+    m = n_d - 1
+    T = np.diag(np.full(m, 2.0)) - np.diag(np.ones(m - 1), 1) - np.diag(np.ones(m - 1), -1)
+    S = np.diag(np.full(m, 4.0)) + np.diag(np.ones(m - 1), 1) + np.diag(np.ones(m - 1), -1)
+    np.testing.assert_allclose(Kc, T / L, atol=1e-11)
+    np.testing.assert_allclose(Mc, S * L / 6.0, atol=1e-13)
+    # the hats sum to 1 away from the boundary elements and are 0 on the boundary
+    assert R1[:, 0].max() == 0.0 and R1[:, -1].max() == 0.0
+    np.testing.assert_allclose(R1.sum(axis=0)[N:-N], 1.0, atol=1e-14)
+
+
+def _dense_global_operator(P):
+    """The assembled, masked fine operator on global vectors, column by column
+    through the oracle's apply (independent of the coarse code)."""
+    ng = P.box.n_global
+    A = np.zeros((ng, ng))
+    for j in range(ng):
+        e = np.zeros(ng)
+        e[j] = 1.0
+        A[:, j] = P.to_global(P.apply(P.to_local(e)))
+    return A
+
+
+def test_coarse_operator_is_the_galerkin_product():
+    box = Box(3, 3, 2, 3, 0.0)
+    P = oracle.Problem(box)
+    A = _dense_global_operator(P)
+    (Rx, _, _), (Ry, _, _), (Rz, _, _) = schwarz.coarse_parts(box)
+    R0 = np.kron(Rz, np.kron(Ry, Rx))
+    G = R0 @ A @ R0.T
+    A0 = schwarz.coarse_operator(box)
+    np.testing.assert_allclose(A0, G, atol=1e-11 * np.abs(G).max())
+
+
+def test_coarse_correction_is_exact_on_the_coarse_space():
+    """For v = R_0^T c on the undeformed box, R_0^T A_0^-1 R_0 A v = v."""
+    box = Box(4, 3, 3, 4, 0.0)
+    P = oracle.Problem(box)
+    (Rx, _, _), (Ry, _, _), (Rz, _, _) = schwarz.coarse_parts(box)
+    rng = np.random.default_rng(4)
+    c = rng.uniform(-1, 1, (Rz.shape[0], Ry.shape[0], Rx.shape[0]))
+    vg = np.einsum("cz,by,ax,cba->zyx", Rz, Ry, Rx, c).reshape(-1)
+    v = P.to_local(vg)
+    back = schwarz.coarse_correction(P, P.apply(v))
+    np.testing.assert_allclose(back, v, atol=1e-11 * np.abs(v).max())
+
+
+def test_two_level_is_symmetric_and_positive():
+    box = Box(3, 3, 2, 4, 0.05)
+    P = oracle.Problem(box)
+    u = P.to_local(rhs_global(box, 1))
+    v = P.to_local(rhs_global(box, 2))
+    Mu = schwarz.precondition(P, u, coarse=True)
+    Mv = schwarz.precondition(P, v, coarse=True)
+    a, b = P.glsc3(v, Mu), P.glsc3(u, Mv)
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+    assert P.glsc3(u, Mu) > P.glsc3(u, schwarz.precondition(P, u)) > 0
+
+
+def test_two_level_iterations_grow_little_with_the_element_count():
+    """One level: iterations grow with the number of subdomains per direction;
+    two levels: they stay nearly flat (and below one level)."""
+    its = {}
+    for k in (2, 6):
+        box = Box(k, k, k, 3, 0.05)
+        P = oracle.Problem(box)
+        b = P.to_local(rhs_global(box, 3))
+        for coarse in (False, True):
+            _, it, rel, _ = P.fcg(b, lambda r: schwarz.precondition(P, r, coarse=coarse),
+                                  tol=1e-8, maxit=2000)
+            assert rel < 1e-8
+            its[(k, coarse)] = it
+    print(its)
+    assert its[(6, True)] < its[(6, False)]
+    assert its[(6, True)] - its[(2, True)] < its[(6, False)] - its[(2, False)]
