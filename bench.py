@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
     ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned", "vprec",
-                                       "learned-step", "batched-step", "schwarz-step"],
+                                       "learned-step", "batched-step", "schwarz-step",
+                                       "schwarz2-step"],
                     default="full",
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture); "
@@ -466,8 +467,10 @@ def run_learned_step(args):
     model.attach(mesh)
     b = _rhs_local(nb, mesh, box, 0, dev)
     x = torch.zeros_like(b)
+    # one inner solve of exactly `steps` steps (restarted form, tight inner tolerance)
     o = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_LEARNED, rtol=1e-8, maxiter=args.steps,
-                        max_outer=1, use_graph=0 if args.no_graph else 1)
+                        max_outer=1, restart=1, inner_rtol=1e-12,
+                        use_graph=0 if args.no_graph else 1)
     st = mesh.solve(b, x, o)
     print(json.dumps({"mode": "learned-step", "iters": st["iters"], "ms": st["seconds"] * 1e3}),
           flush=True)
@@ -485,10 +488,13 @@ def run_schwarz_step(args):
     mesh = nb.Mesh.from_box(ctx, BOX)
     b = _rhs_local(nb, mesh, BOX, 0, dev)
     x = torch.zeros_like(b)
-    o = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_SCHWARZ, rtol=1e-10, maxiter=args.steps,
-                        max_outer=1, use_graph=0 if args.no_graph else 1)
+    pc = nb.NB_PC_SCHWARZ2 if args.mode == "schwarz2-step" else nb.NB_PC_SCHWARZ
+    # one inner solve of exactly `steps` steps (restarted form, tight inner tolerance)
+    o = nb.default_opts(prec=nb.NB_FP32, pc=pc, rtol=1e-10, maxiter=args.steps,
+                        max_outer=1, restart=1, inner_rtol=1e-12,
+                        use_graph=0 if args.no_graph else 1)
     st = mesh.solve(b, x, o)
-    print(json.dumps({"mode": "schwarz-step", "iters": st["iters"], "ms": st["seconds"] * 1e3}),
+    print(json.dumps({"mode": args.mode, "iters": st["iters"], "ms": st["seconds"] * 1e3}),
           flush=True)
     return 0
 
@@ -567,10 +573,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.mode in ("sweep", "batched", "learned", "vprec", "learned-step", "batched-step",
-                     "schwarz-step"):
+                     "schwarz-step", "schwarz2-step"):
         return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned,
                 "vprec": run_vprec, "learned-step": run_learned_step,
-                "batched-step": run_batched_step, "schwarz-step": run_schwarz_step}[args.mode](args)
+                "batched-step": run_batched_step, "schwarz-step": run_schwarz_step,
+                "schwarz2-step": run_schwarz_step}[args.mode](args)
     rank, world, local = dist_env()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -679,21 +686,26 @@ def main():
     t64 = statistics.median(fp64_ms)
     tm = statistics.median(step_ms)
     # the same mixed solve with the overlapping Schwarz preconditioner (the
-    # smoother of the paper's multigrid solveM)
-    osw = nb.default_opts(prec=nb.NB_FP32, pc=nb.NB_PC_SCHWARZ, rtol=RTOL)
-    xs = torch.zeros_like(b)
-    mesh.solve(b, xs, osw)
-    sw_ms, sw_stats = [], None
-    for _ in range(3):
-        flush.fill_(3)
-        xs.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sw_stats = mesh.solve(b, xs, osw)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        sw_ms.append(e0.elapsed_time(e1))
+    # smoother of the paper's multigrid solveM), one level and with the
+    # coarse-grid level
+    def time_pc(pc):
+        o_pc = nb.default_opts(prec=nb.NB_FP32, pc=pc, rtol=RTOL)
+        xs = torch.zeros_like(b)
+        mesh.solve(b, xs, o_pc)
+        ms, st = [], None
+        for _ in range(3):
+            flush.fill_(3)
+            xs.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = mesh.solve(b, xs, o_pc)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms), st
+    sw_t, sw_stats = time_pc(nb.NB_PC_SCHWARZ)
+    sw2_t, sw2_stats = time_pc(nb.NB_PC_SCHWARZ2)
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
 
     # energy to solution, mixed vs FP64 (outside the timed region; the GPU's
@@ -798,9 +810,11 @@ def main():
             "clocks": clk,
             "gpu_launches": launches,
             "time_to_solution_ms": {"mixed_fp32_refined": tm, "fp64_pcg": t64,
-                                    "mixed_schwarz": statistics.median(sw_ms)},
+                                    "mixed_schwarz": sw_t, "mixed_schwarz_two_level": sw2_t},
             "schwarz": {"iters": sw_stats["iters"], "outer": sw_stats["outer_iters"],
                         "rel_res": sw_stats["rel_res"], "status": sw_stats["status"]},
+            "schwarz_two_level": {"iters": sw2_stats["iters"], "outer": sw2_stats["outer_iters"],
+                                  "rel_res": sw2_stats["rel_res"], "status": sw2_stats["status"]},
             "gain_vs_fp64": (t64 - tm) / t64,
             "speedup_vs_fp64": t64 / tm,
             "iterations": {"mixed_inner": stats[-1]["iters"], "mixed_outer": stats[-1]["outer_iters"],

@@ -484,38 +484,38 @@ static nb_status sw_sum(int mode, int m, int sms, int *grid, int64_t E, int nx, 
 #undef NB_SWS
 }
 
-// Hat function of interior vertex v (0-based; its position is vertex v + 1)
-// at global GLL node g of one direction: (1 + xi_i)/2 on element v (g = v N + i),
-// (1 - xi_i)/2 on element v + 1 (g = (v + 1) N + i), 0 elsewhere.
-__device__ __forceinline__ float co_hat(const float *xi, int N, int v, int g)
-{
-    const int i0 = g - v * N;
-    if (i0 < 0 || i0 > 2 * N) return 0.f;
-    return i0 <= N ? 0.5f * (1.f + xi[i0]) : 0.5f * (1.f - xi[i0 - N]);
-}
-
-// Coarse restriction, x and y: t2[gz][vy][vx] = sum over the (2N + 1)^2 nodes
-// of the two hats' support of hat_vy(gy) hat_vx(gx) rg[gz][gy][gx] (rg holds
-// each global node's value once).
-__global__ void k_co_rxy(int gxn, int gyn, int gzn, int N, int ncx, int ncy,
-                         const float *__restrict__ xi, const float *__restrict__ rg,
-                         float *__restrict__ t2, const CgScalars *sc)
+// Coarse restriction, x and y, one block per plane gz: t1[gy][vx] = sum over
+// the 2N + 1 nodes of the hat's support of hat(gx) rg[gz][gy][gx] (rows read
+// by warps), then t2[gz][vy][vx] = sum over gy of hat(gy) t1[gy][vx].  Every
+// interior vertex's hat has the same 2N + 1 weights: (1 + xi_d)/2 for
+// d = 0..N, (1 - xi_(d - N))/2 for d = N..2N.  rg holds each global node's
+// value once.
+__global__ void k_co_rxy(int gxn, int gyn, int N, int ncx, int ncy, const float *__restrict__ xi,
+                         const float *__restrict__ rg, float *__restrict__ t2, const CgScalars *sc)
 {
     if (sc && sc->done) return;
-    const int64_t total = (int64_t)gzn * ncy * ncx;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int vx = (int)(t % ncx), vy = (int)((t / ncx) % ncy), gz = (int)(t / ((int64_t)ncx * ncy));
-        float acc = 0.f;
-        for (int dy = 0; dy <= 2 * N; ++dy) {
-            const int gy = vy * N + dy;
-            const float hy = co_hat(xi, N, vy, gy);
-            const float *row = rg + ((int64_t)gz * gyn + gy) * gxn + vx * N;
-            float ax = 0.f;
-            for (int dx = 0; dx <= 2 * N; ++dx) ax += co_hat(xi, N, vx, vx * N + dx) * row[dx];
-            acc += hy * ax;
+    extern __shared__ float co_rs[];
+    float *hw = co_rs;               // [2N + 1]
+    float *t1 = co_rs + 2 * N + 1;   // [gyn][ncx]
+    for (int d = threadIdx.x; d <= 2 * N; d += blockDim.x)
+        hw[d] = d <= N ? 0.5f * (1.f + xi[d]) : 0.5f * (1.f - xi[d - N]);
+    __syncthreads();
+    const int gz = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int gy = warp; gy < gyn; gy += nw) {
+        const float *row = rg + ((int64_t)gz * gyn + gy) * gxn;
+        for (int vx = lane; vx < ncx; vx += 32) {
+            float acc = 0.f;
+            for (int d = 0; d <= 2 * N; ++d) acc += hw[d] * row[vx * N + d];
+            t1[gy * ncx + vx] = acc;
         }
-        t2[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ncy * ncx; t += blockDim.x) {
+        const int vx = t % ncx, vy = t / ncx;
+        float acc = 0.f;
+        for (int d = 0; d <= 2 * N; ++d) acc += hw[d] * t1[(vy * N + d) * ncx + vx];
+        t2[((int64_t)gz * ncy + vy) * ncx + vx] = acc;
     }
 }
 
@@ -557,9 +557,9 @@ __global__ void k_co_solve(int gzn, int N, int ncx, int ncy, int ncz, const floa
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int vxy = t % (ncx * ncy), vz = t / (ncx * ncy);
         float acc = 0.f;
-        for (int dz = 0; dz <= 2 * N; ++dz) {
-            const int gz = vz * N + dz;
-            acc += co_hat(xi, N, vz, gz) * t2[(int64_t)gz * ncx * ncy + vxy];
+        for (int d = 0; d <= 2 * N; ++d) {
+            const float h = d <= N ? 0.5f * (1.f + xi[d]) : 0.5f * (1.f - xi[d - N]);
+            acc += h * t2[(int64_t)(vz * N + d) * ncx * ncy + vxy];
         }
         A[t] = acc;
     }
@@ -852,6 +852,10 @@ static nb_status schwarz_setup_coarse(nb_mesh *m)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_co_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2 * sizeof(float) * kCoarseTotal));
+    if (e == cudaSuccess)  // the x-restricted plane of k_co_rxy
+        e = cudaFuncSetAttribute(k_co_rxy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * (2 * N + 1 + (int64_t)(m->ny * N + 1) *
+                                                                      std::max(d->nc[0], 1))));
     if (e != cudaSuccess) {
         set_error("two-level Schwarz set-up: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
@@ -884,13 +888,11 @@ nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *w
     const float *zc = nullptr;
     if (coarse && d->coarse) {  // R_0 r (x, y; then z and A_0^-1 in one block)
         const int N = m->N, gxn = m->nx * N + 1, gyn = m->ny * N + 1, gzn = m->nz * N + 1;
-        const int64_t t2n = (int64_t)gzn * d->nc[1] * d->nc[0];
-        const int g = (int)std::min<int64_t>((t2n + 255) / 256, (int64_t)m->ctx->sm_count * 8);
-        k_co_rxy<<<std::max(g, 1), 256, 0, s>>>(gxn, gyn, gzn, N, d->nc[0], d->nc[1], d->xi, d->rg,
-                                                 d->t2, sc);
+        const size_t rs = sizeof(float) * (2 * N + 1 + (size_t)gyn * d->nc[0]);
+        k_co_rxy<<<gzn, 256, rs, s>>>(gxn, gyn, N, d->nc[0], d->nc[1], d->xi, d->rg, d->t2, sc);
         NB_CUDA(cudaGetLastError());
         const int total = d->nc[0] * d->nc[1] * d->nc[2];
-        k_co_solve<<<1, 512, 2 * sizeof(float) * total, s>>>(gzn, N, d->nc[0], d->nc[1], d->nc[2],
+        k_co_solve<<<1, 1024, 2 * sizeof(float) * total, s>>>(gzn, N, d->nc[0], d->nc[1], d->nc[2],
                                                               d->xi, d->Sc, d->lamc, d->t2, d->zc,
                                                               sc);
         NB_CUDA(cudaGetLastError());
