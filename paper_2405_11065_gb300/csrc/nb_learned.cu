@@ -1287,8 +1287,8 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         // kernel forms (z, w_prev) over every copy)
         return fcg_update_folded(m, ws, x, r, p, wcur, P2, rg, s);
     };
-    // local solves, (coarse restriction and solve,) their sum, operator, update
-    const int kPerStep = two ? 6 : 4;
+    // local solves, (coarse restrictions and solve,) their sum, operator, update
+    const int kPerStep = two ? 7 : 4;
     if (o->use_graph) {
         const intptr_t key = (intptr_t)m->schwarz + (two ? 1 : 0);
         if (!ws.exec2 || ws.graph2_key != key) {

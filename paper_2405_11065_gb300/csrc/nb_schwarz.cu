@@ -48,6 +48,7 @@ struct SchwarzData {
     float *lamc = nullptr;  // [3][kCoarseDir]
     float *xi = nullptr;    // [N + 1]
     float *t2 = nullptr;    // [gz][vy][vx]
+    float *rc = nullptr;    // [vz][vy][vx] restricted residual
     float *zc = nullptr;    // [vz][vy][vx]
 };
 
@@ -519,6 +520,24 @@ __global__ void k_co_rxy(int gxn, int gyn, int N, int ncx, int ncy, const float 
     }
 }
 
+// Coarse restriction, z: rc[vz][vy][vx] = sum over the 2N + 1 planes of the
+// hat's support of hat(gz) t2[gz][vy][vx] (one thread per coarse unknown).
+__global__ void k_co_rz(int N, int ncxy, int ncz, const float *__restrict__ xi,
+                        const float *__restrict__ t2, float *__restrict__ rc, const CgScalars *sc)
+{
+    if (sc && sc->done) return;
+    const int total = ncxy * ncz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int vxy = t % ncxy, vz = t / ncxy;
+        float acc = 0.f;
+        for (int d = 0; d <= 2 * N; ++d) {
+            const float h = d <= N ? 0.5f * (1.f + xi[d]) : 0.5f * (1.f - xi[d - N]);
+            acc += h * t2[(int64_t)(vz * N + d) * ncxy + vxy];
+        }
+        rc[t] = acc;
+    }
+}
+
 // One axis of a coarse tensor contraction in shared memory: out = sum over
 // the axis of M[a][q] in[..a..] (M row-major [nc][nc]); axis 0 = x (fastest).
 __device__ __forceinline__ void co_contract(const float *__restrict__ in, float *__restrict__ out,
@@ -540,13 +559,11 @@ __device__ __forceinline__ void co_contract(const float *__restrict__ in, float 
     }
 }
 
-// Coarse solve in one block: the z restriction of t2, then A_0^-1 by fast
-// diagonalisation, (Sz(x)Sy(x)Sx) diag(1 / (lx + ly + lz)) (Sz(x)Sy(x)Sx)^T,
-// into zc.
-__global__ void k_co_solve(int gzn, int N, int ncx, int ncy, int ncz, const float *__restrict__ xi,
-                           const float *__restrict__ Sc, const float *__restrict__ lamc,
-                           const float *__restrict__ t2, float *__restrict__ zc,
-                           const CgScalars *sc)
+// Coarse solve in one block: A_0^-1 rc by fast diagonalisation,
+// (Sz(x)Sy(x)Sx) diag(1 / (lx + ly + lz)) (Sz(x)Sy(x)Sx)^T, into zc.
+__global__ void k_co_solve(int ncx, int ncy, int ncz, const float *__restrict__ Sc,
+                           const float *__restrict__ lamc, const float *__restrict__ rc,
+                           float *__restrict__ zc, const CgScalars *sc)
 {
     if (sc && sc->done) return;
     extern __shared__ __align__(16) float co_smem[];
@@ -554,15 +571,7 @@ __global__ void k_co_solve(int gzn, int N, int ncx, int ncy, int ncz, const floa
     float *A = co_smem, *B = co_smem + total;
     const float *Sx = Sc, *Sy = Sc + kCoarseDir * kCoarseDir, *Sz = Sc + 2 * kCoarseDir * kCoarseDir;
     const float *lx = lamc, *ly = lamc + kCoarseDir, *lz = lamc + 2 * kCoarseDir;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int vxy = t % (ncx * ncy), vz = t / (ncx * ncy);
-        float acc = 0.f;
-        for (int d = 0; d <= 2 * N; ++d) {
-            const float h = d <= N ? 0.5f * (1.f + xi[d]) : 0.5f * (1.f - xi[d - N]);
-            acc += h * t2[(int64_t)(vz * N + d) * ncx * ncy + vxy];
-        }
-        A[t] = acc;
-    }
+    for (int t = threadIdx.x; t < total; t += blockDim.x) A[t] = rc[t];
     __syncthreads();
     co_contract(A, B, Sx, true, 0, ncx, ncy, ncz);
     __syncthreads();
@@ -649,6 +658,7 @@ void schwarz_free(nb_mesh *m)
     cudaFree(d->lamc);
     cudaFree(d->xi);
     cudaFree(d->t2);
+    cudaFree(d->rc);
     cudaFree(d->zc);
     delete d;
     m->schwarz = nullptr;
@@ -844,6 +854,7 @@ static nb_status schwarz_setup_coarse(nb_mesh *m)
     if (e == cudaSuccess)
         e = cudaMalloc(&d->t2, sizeof(float) * std::max<int64_t>(1, gzn * d->nc[1] * d->nc[0]));
     if (e == cudaSuccess) e = cudaMalloc(&d->zc, sizeof(float) * std::max<int64_t>(1, total));
+    if (e == cudaSuccess) e = cudaMalloc(&d->rc, sizeof(float) * std::max<int64_t>(1, total));
     if (e == cudaSuccess)
         e = cudaMemcpy(d->Sc, Sh.data(), sizeof(float) * Sh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -892,9 +903,11 @@ nb_status schwarz_solve_sum(nb_mesh *m, const float *r, float *z, const float *w
         k_co_rxy<<<gzn, 256, rs, s>>>(gxn, gyn, N, d->nc[0], d->nc[1], d->xi, d->rg, d->t2, sc);
         NB_CUDA(cudaGetLastError());
         const int total = d->nc[0] * d->nc[1] * d->nc[2];
-        k_co_solve<<<1, 1024, 2 * sizeof(float) * total, s>>>(gzn, N, d->nc[0], d->nc[1], d->nc[2],
-                                                              d->xi, d->Sc, d->lamc, d->t2, d->zc,
-                                                              sc);
+        k_co_rz<<<(total + 255) / 256, 256, 0, s>>>(N, d->nc[0] * d->nc[1], d->nc[2], d->xi, d->t2,
+                                                    d->rc, sc);
+        NB_CUDA(cudaGetLastError());
+        k_co_solve<<<1, 1024, 2 * sizeof(float) * total, s>>>(d->nc[0], d->nc[1], d->nc[2], d->Sc,
+                                                              d->lamc, d->rc, d->zc, sc);
         NB_CUDA(cudaGetLastError());
         zc = d->zc;
     }
