@@ -761,9 +761,10 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // next solve: restart)
         const bool agreed = outer > 0 && rel / rel_start <= 100.0 * prev_end;
         const bool resume = keep_dir && prev_ok && prev_kind == kind && agreed;
-        // a resumed solve that needs more than four times the previous
-        // solve's iterations (plus 100) stops, and the next step restarts
-        const int cap = resume ? 4 * prev_iters + 100 : remaining;
+        // a resumed solve that needs more than eight times the previous
+        // solve's iterations (plus 200) stops, and the next step restarts (the
+        // second solve, after the first 2 decades, typically takes 4x the first)
+        const int cap = resume ? 8 * prev_iters + 200 : remaining;
         const bool odd = (prev_iters & 1) != 0;
         const double step_rtol = keep_dir ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
