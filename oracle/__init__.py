@@ -33,6 +33,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 
 import numpy as np
 
@@ -54,10 +55,11 @@ class _Op(C.Structure):
 
 
 def lib():
-    """Load (building if needed) the C oracle."""
+    """Load (building if needed) the C oracle.  NBO_LIB, if set, names another
+    build of it (the mutation test's planted copies)."""
     global _lib
     if _lib is None:
-        L = C.CDLL(build_oracle())
+        L = C.CDLL(os.environ.get("NBO_LIB") or build_oracle())
         L.nbo_legendre.restype = C.c_double
         L.nbo_legendre.argtypes = [C.c_int, C.c_double]
         L.nbo_gll.restype = C.c_int
