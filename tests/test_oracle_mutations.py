@@ -112,3 +112,36 @@ def test_planted_mistakes_in_the_schwarz_oracle_fail_a_pin(monkeypatch):
     with pytest.raises(AssertionError):
         pins.test_coarse_operator_is_the_galerkin_product()
     monkeypatch.setattr(schwarz, "coarse_operator", good_coarse_operator)
+
+
+# ---- planted mistakes in the network oracle ----
+
+def test_planted_mistakes_in_the_network_oracle_fail_a_pin(monkeypatch):
+    import importlib.util
+    import numpy as np
+    from oracle import mlp
+    spec = importlib.util.spec_from_file_location(
+        "pins_mlp", os.path.join(ROOT, "tests", "test_oracle_mlp.py"))
+    pins = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(pins)
+    good_backward, good_grad = mlp.backward, mlp.gelu_grad
+
+    def output_use_dropped(params, X, T):  # W's gradient only through its input use
+        g = good_backward(params, X, T)
+        Y, (X_, Z, H) = mlp.forward(params, X)
+        dY = 2.0 * (Y - T) / Y.size
+        g["W"] = g["W"] - dY.T @ (H * params["a"])
+        return g
+
+    monkeypatch.setattr(mlp, "backward", output_use_dropped)
+    with pytest.raises(AssertionError):
+        pins.test_backward_matches_finite_differences((8, 4, 5))
+    monkeypatch.setattr(mlp, "backward", good_backward)
+
+    def tanh_term_sign(z):  # 0.5 (1 - t) instead of 0.5 (1 + t)
+        t = np.tanh(mlp._C * (z + 0.044715 * z ** 3))
+        return good_grad(z) - t
+
+    monkeypatch.setattr(mlp, "gelu_grad", tanh_term_sign)
+    with pytest.raises(AssertionError):
+        pins.test_backward_matches_finite_differences((8, 4, 5))
