@@ -16,7 +16,7 @@
 // iterates with the network being trained).  Being nonlinear, it is used
 // inside flexible CG (Notay 2000, one-vector truncation), with Jacobi-PCG as
 // the fallback when the flexible iteration fails and the FP64 residual of the
-// refinement as the judge of convergence.
+// refinement deciding convergence.
 //
 // Matrix products: BF16 operands on the tensor cores (mma.sync m16n8k16),
 // FP32 accumulation; master weights and Adam moments in FP32.

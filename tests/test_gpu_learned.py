@@ -1,7 +1,8 @@
 """The learned per-element preconditioner: GPU gradients against the FP64
 oracle's backward pass, the GPU training targets and the preconditioner
 against the oracle, and flexible CG with the trained network against
-Jacobi-PCG (the gain is measured and written to gpurun_out)."""
+Jacobi-PCG (the gain is measured and printed; written as JSON into the
+directory NB_RESULTS_DIR names, if set)."""
 import json
 import os
 
@@ -168,6 +169,8 @@ def test_learned_preconditioner_workload(nb, ctx):
         assert lrn["iters"] < jac["iters"]  # the network's gain over Jacobi
     summary = dict(pairs=npairs, params=model.nparam, final_train_loss=loss, results=out)
     print("learned workload:", json.dumps(summary))
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "learned_workload.json"), "w") as f:
-        json.dump(summary, f, indent=1)
+    out_dir = os.environ.get("NB_RESULTS_DIR")
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        with open(os.path.join(out_dir, "learned_workload.json"), "w") as f:
+            json.dump(summary, f, indent=1)
