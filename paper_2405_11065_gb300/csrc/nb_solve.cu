@@ -676,6 +676,7 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
 // residual, a resumed solve stagnates, and restarts are faster.
 constexpr double kReliableDrop = 1e-2;
 constexpr int kReliableMaxIters = 1000;
+constexpr int kReliableShort = 15;
 
 static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, double *x,
                                nb_stats *st, cudaStream_t s)
@@ -766,7 +767,12 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // second solve, after the first 2 decades, typically takes 4x the first)
         const int cap = resume ? 8 * prev_iters + 200 : remaining;
         const bool odd = (prev_iters & 1) != 0;
-        const double step_rtol = keep_dir ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
+        // after a short inner solve (a strong preconditioner: the recurrence
+        // has little room to drift) the next one may close inner_rtol again,
+        // which saves FP64 residuals
+        const bool short_prev = resume && prev_iters < kReliableShort;
+        const double step_rtol =
+            keep_dir && !short_prev ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
         if (use_learned && schwarz) {
             // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
