@@ -1,6 +1,7 @@
 """Mutation check of the oracle's pins: each plausible mistake below, planted
 by one textual change in a copy of the C oracle compiled into a temporary
-library, makes at least one pin of the GLL, mesh or operator tests fail.  The
+library, makes at least one pin of the GLL, mesh, operator or precision-study
+tests fail.  The
 committed oracle is never modified; the copies live in a temporary directory
 and are loaded through NBO_LIB in a child process."""
 import os
@@ -13,7 +14,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "nb_oracle.c")
 PINS = [os.path.join(ROOT, "tests", f)
-        for f in ("test_oracle_gll.py", "test_oracle_mesh.py", "test_oracle_operator.py")]
+        for f in ("test_oracle_gll.py", "test_oracle_mesh.py", "test_oracle_operator.py",
+                  "test_oracle_vprec.py")]
 
 MUTANTS = {
     "transposed derivative matrix": ("D[i * n + j] = v;", "D[j * n + i] = v;"),
@@ -31,6 +33,11 @@ MUTANTS = {
         "s += 2.0 * D[i * n + i] * D[j * n + j] * Ge[1 * n3 + q];",
         "s += D[i * n + i] * D[j * n + j] * Ge[1 * n3 + q];"),
     "sign of the deformation along y": ("X[1 * n3 + q] = y0 + d;", "X[1 * n3 + q] = y0 - d;"),
+    "VPREC ties rounded up instead of to even": (
+        "if (rem > half || (rem == half && ((b >> drop) & 1))) b += (uint64_t)1 << drop;",
+        "if (rem >= half) b += (uint64_t)1 << drop;"),
+    "MCA perturbation one bit too wide": ("const double r = x + ldexp(emu_u01(&m) - 0.5, e - t);",
+                                          "const double r = x + ldexp(emu_u01(&m) - 0.5, e - t + 1);"),
 }
 
 
