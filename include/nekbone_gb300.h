@@ -242,6 +242,12 @@ nb_status nb_time_ax(nb_mesh *mesh, nb_prec prec, int cg_step, int variant, int 
 /* Number of operator kernel variants available for (mesh order, prec). */
 int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
 
+/* Select operator variant `variant` (0 <= variant < nb_ax_variants) for
+ * later operator applications and solves in precision prec on this mesh,
+ * or -1 for the built-in default; the choice nb_autotune would otherwise
+ * make by timing.  Errors: NB_ERR_ARG (index out of range, bad prec). */
+nb_status nb_set_ax_variant(nb_mesh *mesh, nb_prec prec, int variant);
+
 /* Autotuner: time every operator variant for this mesh's order and
  * precision with nb_time_ax (cg_step = 1, `reps` launches each) and keep the
  * fastest for later calls.  *best_variant and *best_ms (may be NULL) receive

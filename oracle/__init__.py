@@ -14,7 +14,8 @@ the textbook spectral-element definition, cited at its C implementation in
 * coordinates of the deformed box and geometric factors (``geom``)
 * global numbering, multiplicity, Dirichlet mask, CSR of copies
 * the local operator ``ax`` and its diagonal, ``dssum`` + mask, ``glsc3``
-* Jacobi-PCG in Table 1 order (``Problem.pcg``) and flexible CG
+* Jacobi-PCG in Table 1 order (``Problem.pcg``; ``Problem.pcg_par`` the same
+  on all host cores) and flexible CG
   (``Problem.fcg``, Notay 2000) with a user-supplied preconditioner.
 * emulated reduced precision (Section 2, the VPREC backend; Section 4.2):
   ``vround`` rounds a binary64 value to t mantissa bits, and
@@ -89,6 +90,11 @@ def lib():
         L.nbo_pcg.restype = C.c_int
         L.nbo_pcg.argtypes = [C.POINTER(_Op), _dp, _dp, C.c_int, C.c_double, C.c_int,
                               C.c_void_p, C.POINTER(C.c_double)]
+        L.nbo_threads.restype = C.c_int
+        L.nbo_threads.argtypes = [C.c_int]
+        L.nbo_pcg_par.restype = C.c_int
+        L.nbo_pcg_par.argtypes = [C.POINTER(_Op), _ip, _ip, _dp, _dp, C.c_int, C.c_double,
+                                  C.c_int, C.c_void_p, C.POINTER(C.c_double)]
         L.nbo_vround.restype = C.c_double
         L.nbo_vround.argtypes = [C.c_double, C.c_int]
         L.nbo_apply_vprec.restype = None
@@ -209,6 +215,12 @@ def dssum(gid: np.ndarray, nG: int, u: np.ndarray, mask=None) -> np.ndarray:
     return out
 
 
+def threads(nt: int = 0) -> int:
+    """Host threads of the oracle's parallel loops (nt > 0 sets the count);
+    returns the count in force (1 without OpenMP)."""
+    return lib().nbo_threads(int(nt))
+
+
 def vround(x: float, t: int) -> float:
     """x rounded to t mantissa bits (round to nearest, ties to even)."""
     return lib().nbo_vround(float(x), int(t))
@@ -298,6 +310,24 @@ class Problem:
                            1 if precond == "jacobi" else 0, hist.ctypes.data, C.byref(rel))
         return x, it, rel.value, (hist[:it].copy() if history else None)
 
+    def pcg_par(self, b: np.ndarray, tol: float = 1e-10, maxit: int = 1000,
+                precond: str = "jacobi", x0=None, history: bool = False):
+        """``pcg`` on all host cores (``threads`` sets how many): the operator,
+        the summation and the vector updates give ``pcg``'s bits; the dot
+        products are summed in fixed chunks of 65536 terms, so the result does
+        not depend on the thread count and differs from ``pcg`` by the
+        rounding order of the dots only."""
+        if getattr(self, "_csr", None) is None:
+            self._csr = csr(self.gid, self.box.n_global)
+        off, loc = self._csr
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        hist = np.zeros(max(maxit, 1))
+        rel = C.c_double(0.0)
+        it = lib().nbo_pcg_par(C.byref(self._op), off, loc, b, x, maxit, tol,
+                               1 if precond == "jacobi" else 0, hist.ctypes.data, C.byref(rel))
+        return x, it, rel.value, (hist[:it].copy() if history else None)
+
     def fcg(self, b: np.ndarray, precond, tol: float = 1e-10, maxit: int = 1000,
             x0=None):
         """Flexible CG (Notay, SIAM J. Sci. Comput. 22, 2000) with one-vector
@@ -368,4 +398,5 @@ class Problem:
 
 
 __all__ = ["lib", "legendre", "gll", "deriv", "element_coords", "geom", "numbering",
-           "csr", "ax_local", "diag_local", "dssum", "glsc3", "vround", "inexact", "Problem"]
+           "csr", "ax_local", "diag_local", "dssum", "glsc3", "threads", "vround", "inexact",
+           "Problem"]

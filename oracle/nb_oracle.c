@@ -25,6 +25,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef long long i64;
 
@@ -295,8 +298,14 @@ void nbo_ax_local(i64 cnt, int N, const double *D, const double *G,
                   const double *u, double *w)
 {
     int n = N + 1, n3 = n * n * n;
+    /* Elements are independent: with OpenMP each thread takes a fixed
+     * contiguous range of them with its own scratch, so the result is the
+     * same bit for bit whatever the number of threads. */
+#pragma omp parallel
+    {
     double *wr = (double *)malloc(sizeof(double) * 3 * n3);
     double *ws = wr + n3, *wt = wr + 2 * n3;
+#pragma omp for schedule(static)
     for (i64 e = 0; e < cnt; ++e) {
         const double *ue = u + e * n3;
         const double *Ge = G + e * 6 * (i64)n3;
@@ -328,6 +337,7 @@ void nbo_ax_local(i64 cnt, int N, const double *D, const double *G,
                 }
     }
     free(wr);
+    }
 }
 
 /* Diagonal of the local operator, per element and node (i,j,k):
@@ -441,6 +451,111 @@ int nbo_pcg(const nbo_op *op, const double *b, double *x, int maxit, double tol,
         if (rel < tol) break;
     }
     if (iter > maxit) iter = maxit;
+    free(r);
+    if (relres) *relres = rel;
+    return iter;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same PCG on all host cores                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Threads used by the OpenMP loops (nt > 0 sets it); returns the count in
+ * force (1 when built without OpenMP). */
+int nbo_threads(int nt)
+{
+#ifdef _OPENMP
+    if (nt > 0) omp_set_num_threads(nt);
+    return omp_get_max_threads();
+#else
+    (void)nt;
+    return 1;
+#endif
+}
+
+/* Terms per fixed chunk of the parallel dot product. */
+#define NBO_CHUNK 65536
+
+/* glsc3 in fixed chunks of NBO_CHUNK consecutive terms: each chunk summed in
+ * ascending index, the chunk sums then added in ascending chunk order.  The
+ * chunking does not depend on the thread count, so neither does the result;
+ * it differs from nbo_glsc3's single running sum by rounding order only. */
+static double glsc3_chunked(const double *a, const double *b, const double *c, i64 n,
+                            double *csum)
+{
+    const i64 nc = (n + NBO_CHUNK - 1) / NBO_CHUNK;
+#pragma omp parallel for schedule(static)
+    for (i64 q = 0; q < nc; ++q) {
+        const i64 lo = q * NBO_CHUNK, hi = lo + NBO_CHUNK < n ? lo + NBO_CHUNK : n;
+        double s = 0.0;
+        for (i64 l = lo; l < hi; ++l) s += a[l] * b[l] * c[l];
+        csum[q] = s;
+    }
+    double s = 0.0;
+    for (i64 q = 0; q < nc; ++q) s += csum[q];
+    return s;
+}
+
+/* dssum + mask over the CSR of copies (nbo_csr): each global node's copies
+ * summed in ascending local index -- the order of nbo_dssum's scatter, so the
+ * result is bit-identical to it -- and written back; nodes in parallel. */
+static void dssum_csr(i64 nG, const i64 *off, const i64 *loc, const unsigned char *mask,
+                      double *u)
+{
+#pragma omp parallel for schedule(static)
+    for (i64 g = 0; g < nG; ++g) {
+        double s = 0.0;
+        for (i64 q = off[g]; q < off[g + 1]; ++q) s += u[loc[q]];
+        if (mask && !mask[g]) s = 0.0;
+        for (i64 q = off[g]; q < off[g + 1]; ++q) u[loc[q]] = s;
+    }
+}
+
+/* nbo_pcg with its loops spread over the host cores: the element operator,
+ * the per-node sums and the vector updates give the same bits as nbo_pcg's;
+ * the three dot products use glsc3_chunked.  off/loc: the CSR of nbo_csr. */
+int nbo_pcg_par(const nbo_op *op, const i64 *off, const i64 *loc, const double *b, double *x,
+                int maxit, double tol, int precond, double *hist, double *relres)
+{
+    const i64 n = op->nL;
+    double *r = (double *)malloc(sizeof(double) * 4 * n);
+    double *z = r + n, *p = r + 2 * n, *w = r + 3 * n;
+    double *csum = (double *)malloc(sizeof(double) * ((n + NBO_CHUNK - 1) / NBO_CHUNK + 1));
+    nbo_ax_local(op->E, op->N, op->D, op->G, x, w);
+    dssum_csr(op->nG, off, loc, op->mask, w);
+#pragma omp parallel for schedule(static)
+    for (i64 l = 0; l < n; ++l) {
+        r[l] = b[l] - w[l];
+        p[l] = 0.0;
+    }
+    double bnorm = sqrt(glsc3_chunked(b, op->c, b, n, csum));
+    if (bnorm == 0.0) bnorm = 1.0;
+    double rtz1 = 1.0, rtz2, rel = sqrt(glsc3_chunked(r, op->c, r, n, csum)) / bnorm;
+    int iter = 0;
+    for (iter = 1; iter <= maxit; ++iter) {
+#pragma omp parallel for schedule(static)
+        for (i64 l = 0; l < n; ++l) z[l] = precond == 1 ? op->dinv[l] * r[l] : r[l];
+        rtz2 = rtz1;
+        rtz1 = glsc3_chunked(r, op->c, z, n, csum);
+        const double beta = iter == 1 ? 0.0 : rtz1 / rtz2;
+#pragma omp parallel for schedule(static)
+        for (i64 l = 0; l < n; ++l) p[l] = beta * p[l] + z[l];
+        nbo_ax_local(op->E, op->N, op->D, op->G, p, w);
+        dssum_csr(op->nG, off, loc, op->mask, w);
+        const double pap = glsc3_chunked(w, op->c, p, n, csum);
+        const double alpha = rtz1 / pap;
+#pragma omp parallel for schedule(static)
+        for (i64 l = 0; l < n; ++l) {
+            x[l] = x[l] + alpha * p[l];
+            r[l] = r[l] - alpha * w[l];
+        }
+        const double rtr = glsc3_chunked(r, op->c, r, n, csum);
+        rel = sqrt(rtr) / bnorm;
+        if (hist) hist[iter - 1] = rel;
+        if (rel < tol) break;
+    }
+    if (iter > maxit) iter = maxit;
+    free(csum);
     free(r);
     if (relres) *relres = rel;
     return iter;

@@ -93,6 +93,7 @@ def _load():
         "nb_solve_host": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
         "nb_time_ax": (i32, [vp, i32, i32, i32, i32, vp, C.c_size_t, C.POINTER(dbl)]),
         "nb_ax_variants": (i32, [vp, i32]),
+        "nb_set_ax_variant": (i32, [vp, i32, i32]),
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
         "nb_apply_vprec": (i32, [vp, i32, vp, vp]),
         "nb_schwarz_apply": (i32, [vp, vp, vp]),
@@ -314,6 +315,10 @@ class Mesh:
 
     def ax_variants(self, prec) -> int:
         return lib.nb_ax_variants(self.h, prec)
+
+    def set_ax_variant(self, prec, variant=-1):
+        """Use operator variant ``variant`` (-1: the default) from now on."""
+        check(lib.nb_set_ax_variant(self.h, prec, int(variant)))
 
     def autotune(self, prec, reps=5, flush=None):
         v, ms = C.c_int(), C.c_double()

@@ -69,7 +69,7 @@ nb_status nb_create(nb_ctx **ctx, int device, void *cuda_stream)
     int count = 0;
     NB_CUDA(cudaGetDeviceCount(&count));
     if (device < 0 || device >= count) return arg_error("device index out of range");
-    NB_CUDA(cudaSetDevice(device));
+    NB_DEVICE_SCOPE(device);
     nb_ctx *c = new nb_ctx();
     c->device = device;
     cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -115,7 +115,7 @@ nb_status nb_destroy(nb_ctx *ctx)
 nb_status nb_mesh_destroy(nb_mesh *m)
 {
     if (!m) return NB_OK;
-    cudaSetDevice(m->ctx->device);
+    ::nb::DeviceGuard nb_device_guard_(m->ctx->device);
     cudaStreamSynchronize(m->ctx->stream);
     learned_free(m);
     schwarz_free(m);
@@ -148,7 +148,7 @@ nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double defor
     const int64_t nG = ((int64_t)nx * N + 1) * ((int64_t)ny * N + 1) * ((int64_t)nz * N + 1);
     if (nL >= (int64_t)1 << 31 || nG >= (int64_t)1 << 31)
         return arg_error("mesh too large for 32-bit local/global indices");
-    NB_CUDA(cudaSetDevice(ctx->device));
+    NB_DEVICE_SCOPE(ctx->device);
     nb_mesh *m = new nb_mesh();
     m->ctx = ctx;
     m->nx = nx;
@@ -178,7 +178,7 @@ nb_status nb_setup_gs(nb_mesh *m)
         set_error("nb_setup_gs before nb_setup_mesh");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     return build_gs(m);
 }
 
@@ -225,7 +225,7 @@ nb_status nb_get_maps(const nb_mesh *m, int32_t *gid, int32_t *mult, uint8_t *ma
                       int32_t *gs_row_gid, int32_t *gs_off, int32_t *gs_loc, uint8_t *gs_mask)
 {
     NB_TRY(need_gs(m));
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     if (gid) NB_CUDA(cudaMemcpy(gid, m->gid, sizeof(int32_t) * m->nL, cudaMemcpyDeviceToHost));
     if (mult) memcpy(mult, m->mult_host.data(), sizeof(int32_t) * m->nG);
     if (mask) memcpy(mask, m->mask_host.data(), m->nG);
@@ -246,7 +246,7 @@ nb_status nb_get_maps(const nb_mesh *m, int32_t *gid, int32_t *mult, uint8_t *ma
 nb_status nb_get_geom(const nb_mesh *m, double *G, double *dinv, double *c)
 {
     if (!m) return arg_error("mesh is NULL");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     if (G) NB_CUDA(cudaMemcpy(G, m->G64, sizeof(double) * 6 * m->nL, cudaMemcpyDeviceToHost));
     if (dinv || c) NB_TRY(need_gs(m));
     if (dinv) {
@@ -268,7 +268,7 @@ nb_status nb_to_local(nb_mesh *m, nb_prec prec, const void *ug, void *uL, int ma
 {
     NB_TRY(need_gs(m));
     if (!prec_ok(prec) || !ug || !uL) return arg_error("precision or NULL vector");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(to_local(m, prec, ug, uL, masked, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
     return NB_OK;
@@ -278,7 +278,7 @@ nb_status nb_to_global(nb_mesh *m, nb_prec prec, const void *uL, void *ug)
 {
     NB_TRY(need_gs(m));
     if (!prec_ok(prec) || !ug || !uL) return arg_error("precision or NULL vector");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(to_global(m, prec, uL, ug, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
     return NB_OK;
@@ -290,7 +290,7 @@ nb_status nb_ax(nb_mesh *m, nb_prec prec, int assemble, const void *u, void *w)
     if (!prec_ok(prec) || !u || !w) return arg_error("precision or NULL vector");
     if (u == w) return arg_error("u and w must not overlap");
     if (assemble) NB_TRY(need_gs(m));
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     NB_TRY(ax_local(m, prec, u, w, nullptr, nullptr, s));
     if (assemble) NB_TRY(dssum(m, prec, w, 1, s));
@@ -302,7 +302,7 @@ nb_status nb_dssum(nb_mesh *m, nb_prec prec, void *u, int masked)
 {
     NB_TRY(need_gs(m));
     if (!prec_ok(prec) || !u) return arg_error("precision or NULL vector");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(dssum(m, prec, u, masked, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
     return NB_OK;
@@ -312,7 +312,7 @@ nb_status nb_glsc3(nb_mesh *m, nb_prec prec, const void *a, const void *b, doubl
 {
     NB_TRY(need_gs(m));
     if (!prec_ok(prec) || !a || !b || !out) return arg_error("precision or NULL pointer");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     if (!m->red_out) {
         NB_CUDA(cudaMalloc(&m->red_out, sizeof(double) * 8));
@@ -369,7 +369,7 @@ nb_status nb_solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_
         set_error("no learned preconditioner attached to this mesh");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     if (st) st->history_len = 0;
     nb_status r = solve(m, o, b, x, st);
     if (r < 0) return r;
@@ -382,7 +382,7 @@ nb_status nb_solve_host(nb_mesh *m, const nb_opts *o, const double *bg, double *
     NB_TRY(need_gs(m));
     NB_TRY(check_opts(o));
     if (!bg || !xg) return arg_error("NULL host vector");
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     if (!m->b64) {
         NB_CUDA(cudaMalloc(&m->b64, sizeof(double) * m->nL));
@@ -428,7 +428,7 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
     if (!m || !ms_out || reps < 1 || !prec_ok(prec)) return arg_error("mesh, prec, reps or out");
     if (variant >= ax_variant_count(m, prec)) return arg_error("variant index");
     if (cg_step) NB_TRY(need_gs(m));
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     Workspace &ws = prec == NB_FP64 ? m->ws64 : m->ws32;
     NB_TRY(ensure_ws(m, ws, prec == NB_FP64 ? 8 : 4, 0));
@@ -467,6 +467,17 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
     return NB_OK;
 }
 
+extern "C" nb_status nb_set_ax_variant(nb_mesh *m, nb_prec prec, int variant)
+{
+    if (!m || !prec_ok(prec)) return arg_error("mesh or prec");
+    if (variant < -1 || variant >= ax_variant_count(m, prec)) return arg_error("variant index");
+    if (m->ax_cfg[prec].variant != variant) {
+        m->ax_cfg[prec].variant = variant;
+        ++m->ax_epoch;
+    }
+    return NB_OK;
+}
+
 extern "C" nb_status nb_autotune(nb_mesh *m, nb_prec prec, int reps, void *flush_dev,
                                  size_t flush_bytes, int *best_variant, double *best_ms)
 {
@@ -484,7 +495,10 @@ extern "C" nb_status nb_autotune(nb_mesh *m, nb_prec prec, int reps, void *flush
             best = v;
         }
     }
-    m->ax_cfg[prec].variant = best;
+    if (m->ax_cfg[prec].variant != best) {
+        m->ax_cfg[prec].variant = best;
+        ++m->ax_epoch;
+    }
     if (best_variant) *best_variant = best;
     if (best_ms) *best_ms = bms;
     return NB_OK;

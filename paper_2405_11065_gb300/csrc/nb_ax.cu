@@ -1,12 +1,17 @@
 // Host glue of the operator: precision and variant dispatch.
 //
 // Variants of the CUDA-core operator (chosen per mesh and precision by
-// nb_autotune, or by the default below):
-//   0, 1: k_ax_cc with the smaller / larger number of elements per block,
-//         every load issued by the computing threads;
-//   2:    k_ax_tma, element data streamed by bulk copies into a two-stage
-//         shared-memory ring (even n, when two stages fit in shared memory,
-//         and every vector 16-byte aligned).
+// nb_autotune, nb_set_ax_variant, or by the default below), numbered in this
+// order among those available for the mesh's order:
+//   k_ax_cc with the smaller / larger number of elements per block, every
+//         load issued by the computing threads (always available);
+//   k_ax_tma, element data streamed by bulk copies into a two-stage
+//         shared-memory ring, one thread per (i,j) column (even n, when two
+//         stages fit in shared memory);
+//   k_ax_pen with two / one stages of geometric factors, pencil passes
+//         (even n, when the stages and work arrays fit).
+// The bulk-copy variants need every vector 16-byte aligned; with an
+// unaligned vector the call falls back to the larger k_ax_cc group.
 #include <stdint.h>
 
 #include "nb_internal.h"
@@ -29,6 +34,14 @@ nb_status ax_tma_f64(int n, int mode, int sm_count, long long E, const double *G
                      CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s);
 bool ax_tma_available_f32(int n, bool pupd);
 bool ax_tma_available_f64(int n, bool pupd);
+nb_status ax_pen_f32(int n, int mode, int stages, int sm_count, long long E, const float *G,
+                     const float *u, float *w, const float *r, const float *dinv, float *p,
+                     CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s);
+nb_status ax_pen_f64(int n, int mode, int stages, int sm_count, long long E, const double *G,
+                     const double *u, double *w, const double *r, const double *dinv, double *p,
+                     CgScalars *scal, double *part, int *err, int *grid, cudaStream_t s);
+bool ax_pen_available_f32(int n, int stages);
+bool ax_pen_available_f64(int n, int stages);
 nb_status ax_tc(nb_mesh *m, nb_prec prec, bool pupd, const float *u, float *w, const float *r,
                 const float *dinv, float *p, CgScalars *scal, double *part, int *grid,
                 cudaStream_t s);
@@ -50,56 +63,104 @@ static bool tma_ok(const nb_mesh *m, nb_prec prec)
     return false;
 }
 
-int ax_variant_count(const nb_mesh *m, nb_prec prec)
+static bool pen_ok(const nb_mesh *m, nb_prec prec, int stages)
 {
-    if (prec == NB_FP64 || prec == NB_FP32) return tma_ok(m, prec) ? 3 : 2;
-    return 1;  // tensor-core kernel: one shape
+    if (prec == NB_FP32) return ax_pen_available_f32(m->n, stages);
+    if (prec == NB_FP64) return ax_pen_available_f64(m->n, stages);
+    return false;
 }
 
-// Default before any autotuning: the bulk-copy kernel where available, else
-// the larger element group, except FP64 at high order where two elements per
-// block spill registers.
-static int default_variant(const nb_mesh *m, nb_prec prec)
+enum AxKind { kCcSmall, kCcLarge, kTma, kPen2, kPen1 };
+
+// The variants available for the mesh's order and the precision, in index order.
+static int ax_kinds(const nb_mesh *m, nb_prec prec, AxKind out[5])
 {
-    if (tma_ok(m, prec)) return 2;
-    if (prec == NB_FP64 && m->n >= 12) return 0;
-    return 1;
+    if (prec != NB_FP64 && prec != NB_FP32) return 0;
+    int c = 0;
+    out[c++] = kCcSmall;
+    out[c++] = kCcLarge;
+    if (tma_ok(m, prec)) out[c++] = kTma;
+    if (pen_ok(m, prec, 2)) out[c++] = kPen2;
+    if (pen_ok(m, prec, 1)) out[c++] = kPen1;
+    return c;
+}
+
+int ax_variant_count(const nb_mesh *m, nb_prec prec)
+{
+    AxKind k[5];
+    const int c = ax_kinds(m, prec, k);
+    return c > 0 ? c : 1;  // tensor-core kernel: one shape
+}
+
+// Default before any autotuning or explicit choice.  FP32: the pencil kernel
+// with two stages where it fits, else with one, else the bulk-copy column
+// kernel, else the larger element group.  FP64 (bound by the FP64 pipe): the
+// bulk-copy column kernel, else the larger group, except at high order where
+// two elements per block spill registers.
+static AxKind default_kind(const nb_mesh *m, nb_prec prec)
+{
+    if (prec == NB_FP32) {
+        if (pen_ok(m, prec, 2)) return kPen2;
+        if (pen_ok(m, prec, 1)) return kPen1;
+    }
+    if (tma_ok(m, prec)) return kTma;
+    if (prec == NB_FP64 && m->n >= 12) return kCcSmall;
+    return kCcLarge;
 }
 
 static bool aligned16(const void *p) { return p == nullptr || ((uintptr_t)p & 15u) == 0; }
 
+static AxKind kind_of(const nb_mesh *m, nb_prec prec)
+{
+    AxKind k[5];
+    const int c = ax_kinds(m, prec, k);
+    const int v = m->ax_cfg[prec].variant;
+    if (v >= 0 && v < c) return k[v];
+    return default_kind(m, prec);
+}
+
+// mode: 0 plain operator, 1 fused Jacobi CG step, 2 fused flexible-CG step
+// (FP32 bulk-copy kinds only).
 template <typename T>
-static nb_status run_cc(nb_mesh *m, nb_prec prec, int v, bool pupd, const T *G, const T *u, T *w,
-                        const T *r, const T *dinv, T *p, CgScalars *scal, double *part,
+static nb_status run_cc(nb_mesh *m, nb_prec prec, AxKind kind, int mode, const T *G, const T *u,
+                        T *w, const T *r, const T *dinv, T *p, CgScalars *scal, double *part,
                         int *grid, cudaStream_t s)
 {
-    if (v == 2 && !(aligned16(u) && aligned16(w) && aligned16(r) && aligned16(dinv) &&
-                    aligned16(p)))
-        v = 1;  // the bulk copies need 16-byte aligned vectors
-    if (v == 2) {
-        if (prec == NB_FP64)
-            return ax_tma_f64(m->n, pupd ? 1 : 0, m->ctx->sm_count, m->E, (const double *)G,
+    const bool bulk = kind == kTma || kind == kPen2 || kind == kPen1;
+    if (bulk && !(aligned16(u) && aligned16(w) && aligned16(r) && aligned16(dinv) && aligned16(p)))
+        kind = kCcLarge;  // the bulk copies need 16-byte aligned vectors
+    constexpr bool f64 = sizeof(T) == 8;
+    if (kind == kTma) {
+        if (f64)
+            return ax_tma_f64(m->n, mode, m->ctx->sm_count, m->E, (const double *)G,
                               (const double *)u, (double *)w, (const double *)r,
                               (const double *)dinv, (double *)p, scal, part, m->kerr, grid, s);
-        return ax_tma_f32(m->n, pupd ? 1 : 0, m->ctx->sm_count, m->E, (const float *)G,
-                          (const float *)u,
+        return ax_tma_f32(m->n, mode, m->ctx->sm_count, m->E, (const float *)G, (const float *)u,
                           (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal,
                           part, m->kerr, grid, s);
     }
-    if (prec == NB_FP64)
-        return ax_cc_f64(m->n, v, pupd, m->ctx->sm_count, m->E, (const double *)G,
+    if (kind == kPen2 || kind == kPen1) {
+        const int stages = kind == kPen2 ? 2 : 1;
+        if (f64)
+            return ax_pen_f64(m->n, mode, stages, m->ctx->sm_count, m->E, (const double *)G,
+                              (const double *)u, (double *)w, (const double *)r,
+                              (const double *)dinv, (double *)p, scal, part, m->kerr, grid, s);
+        return ax_pen_f32(m->n, mode, stages, m->ctx->sm_count, m->E, (const float *)G,
+                          (const float *)u, (float *)w, (const float *)r, (const float *)dinv,
+                          (float *)p, scal, part, m->kerr, grid, s);
+    }
+    if (mode == 2) {
+        set_error("flexible-CG step needs a bulk-copy operator variant");
+        return NB_ERR_ARG;
+    }
+    const int v = kind == kCcSmall ? 0 : 1;
+    if (f64)
+        return ax_cc_f64(m->n, v, mode != 0, m->ctx->sm_count, m->E, (const double *)G,
                          (const double *)u, (double *)w, (const double *)r, (const double *)dinv,
                          (double *)p, scal, part, grid, s);
-    return ax_cc_f32(m->n, v, pupd, m->ctx->sm_count, m->E, (const float *)G, (const float *)u,
-                     (float *)w, (const float *)r, (const float *)dinv, (float *)p, scal, part,
-                     grid, s);
-}
-
-static int variant_of(const nb_mesh *m, nb_prec prec)
-{
-    const int v = m->ax_cfg[prec].variant;
-    if (v >= 0 && v < ax_variant_count(m, prec)) return v;
-    return default_variant(m, prec);
+    return ax_cc_f32(m->n, v, mode != 0, m->ctx->sm_count, m->E, (const float *)G,
+                     (const float *)u, (float *)w, (const float *)r, (const float *)dinv,
+                     (float *)p, scal, part, grid, s);
 }
 
 nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap_part,
@@ -107,11 +168,11 @@ nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap
 {
     switch (prec) {
         case NB_FP64:
-            return run_cc<double>(m, prec, variant_of(m, prec), false, m->G64, (const double *)u,
+            return run_cc<double>(m, prec, kind_of(m, prec), 0, m->G64, (const double *)u,
                                   (double *)w, nullptr, nullptr, nullptr, nullptr, pap_part,
                                   nparts, s);
         case NB_FP32:
-            return run_cc<float>(m, prec, variant_of(m, prec), false, m->G32, (const float *)u,
+            return run_cc<float>(m, prec, kind_of(m, prec), 0, m->G32, (const float *)u,
                                  (float *)w, nullptr, nullptr, nullptr, nullptr, pap_part, nparts,
                                  s);
         case NB_TC_F16:
@@ -128,11 +189,11 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
 {
     switch (prec) {
         case NB_FP64:
-            return run_cc<double>(m, prec, variant_of(m, prec), true, m->G64, nullptr,
+            return run_cc<double>(m, prec, kind_of(m, prec), 1, m->G64, nullptr,
                                   (double *)w, (const double *)r, (const double *)dinv,
                                   (double *)p, scal, pap_part, nparts, s);
         case NB_FP32:
-            return run_cc<float>(m, prec, variant_of(m, prec), true, m->G32, nullptr, (float *)w,
+            return run_cc<float>(m, prec, kind_of(m, prec), 1, m->G32, nullptr, (float *)w,
                                  (const float *)r, (const float *)dinv, (float *)p, scal,
                                  pap_part, nparts, s);
         case NB_TC_F16:
@@ -144,19 +205,26 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
     return NB_ERR_ARG;
 }
 
-bool ax_dir_step_available(const nb_mesh *m) { return tma_ok(m, NB_FP32); }
+bool ax_dir_step_available(const nb_mesh *m)
+{
+    return tma_ok(m, NB_FP32) || pen_ok(m, NB_FP32, 2) || pen_ok(m, NB_FP32, 1);
+}
 
 // The fused step of flexible CG in FP32: p = z + beta p, w = A_L p, and the
-// partials of p.w (the last block forms alpha = rtz / pap).
+// partials of p.w (the last block forms alpha = rtz / pap).  Runs the chosen
+// bulk-copy variant, or the best available one if a k_ax_cc group is chosen.
 nb_status ax_dir_step(nb_mesh *m, const float *z, float *p, float *w, CgScalars *scal,
                       double *pap_part, int *nparts, cudaStream_t s)
 {
     if (!ax_dir_step_available(m) || !(aligned16(z) && aligned16(p) && aligned16(w))) {
-        set_error("flexible-CG step needs the bulk-copy operator (even n, aligned vectors)");
+        set_error("flexible-CG step needs a bulk-copy operator (even n, aligned vectors)");
         return NB_ERR_ARG;
     }
-    return ax_tma_f32(m->n, 2, m->ctx->sm_count, m->E, m->G32, nullptr, w, z, nullptr, p, scal,
-                      pap_part, m->kerr, nparts, s);
+    AxKind kind = kind_of(m, NB_FP32);
+    if (kind != kTma && kind != kPen2 && kind != kPen1)
+        kind = pen_ok(m, NB_FP32, 2) ? kPen2 : pen_ok(m, NB_FP32, 1) ? kPen1 : kTma;
+    return run_cc<float>(m, NB_FP32, kind, 2, m->G32, nullptr, w, z, nullptr, p, scal, pap_part,
+                         nparts, s);
 }
 
 }  // namespace nb

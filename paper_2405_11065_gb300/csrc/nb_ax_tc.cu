@@ -296,14 +296,13 @@ static nb_status launch_tc(int sm_count, long long E, const float *G, const floa
 {
     auto kern = k_ax_tc<H, n, PUPD>;
     const size_t smem = 4096 * sizeof(H) + 3 * sizeof(float) * n * n * n;
-    static int grid_cache = 0;
-    static int sm_cached = 0;
-    if (grid_cache == 0 || sm_cached != sm_count) {
+    static int grid_cache_dev[kMaxDevices] = {};  // per device, as the smem attribute
+    int &grid_cache = device_slot(grid_cache_dev);
+    if (grid_cache == 0) {
         NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem));
         grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
-        sm_cached = sm_count;
     }
     int grid = (int)(E < grid_cache ? E : grid_cache);
     if (grid < 1) grid = 1;

@@ -284,14 +284,13 @@ nb_status launch_ax_tma(int sm_count, long long E, const T *G, const T *u, T *w,
     auto kern = k_ax_tma<T, n, MODE>;
     constexpr size_t smem = ax_tma_smem<T, n, MODE != 0>();
     constexpr int threads = tma_threads<n>();
-    static int grid_cache = 0;
-    static int sm_cached = 0;
-    if (grid_cache == 0 || sm_cached != sm_count) {
+    static int grid_cache_dev[kMaxDevices] = {};  // per device, as the smem attribute
+    int &grid_cache = device_slot(grid_cache_dev);
+    if (grid_cache == 0) {
         NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
         grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
-        sm_cached = sm_count;
     }
     int grid = (int)(E < grid_cache ? E : grid_cache);
     if (grid < 1) grid = 1;

@@ -776,7 +776,7 @@ using namespace nb;
 extern "C" nb_status nb_batch_destroy(nb_batch *B)
 {
     if (!B) return NB_OK;
-    cudaSetDevice(B->ctx->device);
+    ::nb::DeviceGuard nb_device_guard_(B->ctx->device);
     cudaStreamSynchronize(B->ctx->stream);
     for (nb_mesh *m : B->meshes) nb_mesh_destroy(m);
     free_bws(B->ws32);
@@ -802,7 +802,7 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
         return NB_ERR_ARG;
     }
     *out = nullptr;
-    NB_CUDA(cudaSetDevice(ctx->device));
+    NB_DEVICE_SCOPE(ctx->device);
     nb_batch *B = new nb_batch();
     B->ctx = ctx;
     B->nprob = nprob;
@@ -1001,7 +1001,7 @@ extern "C" nb_status nb_batch_to_local(nb_batch *B, const double *ug, double *uL
         set_error("invalid argument: NULL batch or vector");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(B->ctx->device));
+    NB_DEVICE_SCOPE(B->ctx->device);
     for (int p = 0; p < B->nprob; ++p)
         NB_TRY(to_local(B->meshes[p], NB_FP64, ug + B->g_off[p], uL + B->l_off[p], 1,
                         B->ctx->stream));
@@ -1015,7 +1015,7 @@ extern "C" nb_status nb_batch_autotune(nb_batch *B, int reps, void *flush, size_
         set_error("invalid argument: batch or reps");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(B->ctx->device));
+    NB_DEVICE_SCOPE(B->ctx->device);
     cudaStream_t s = B->ctx->stream;
     NB_TRY(ensure_bws(B, B->ws32, sizeof(float)));
     NB_TRY(set_active(B, std::vector<char>(B->nprob, 1), s));
@@ -1080,7 +1080,7 @@ extern "C" nb_status nb_batch_solve(nb_batch *B, const nb_opts *o, const double 
         set_error("invalid argument: rtol, maxiter or max_outer");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(B->ctx->device));
+    NB_DEVICE_SCOPE(B->ctx->device);
     cudaStream_t s = B->ctx->stream;
     const int np = B->nprob;
     cudaEvent_t t0, t1;

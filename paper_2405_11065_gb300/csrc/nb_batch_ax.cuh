@@ -149,14 +149,13 @@ nb_status launch_bax_tma(int sm_count, long long E, long long e_first, const int
     auto kern = k_bax_tma<T, n>;
     constexpr size_t smem = sizeof(T) * ((size_t)13 * n * n * n + 4 * n * n);
     constexpr int threads = tma_threads<n>();
-    static int grid_cache = 0;
-    static int sm_cached = 0;
-    if (grid_cache == 0 || sm_cached != sm_count) {
+    static int grid_cache_dev[kMaxDevices] = {};  // per device, as the smem attribute
+    int &grid_cache = device_slot(grid_cache_dev);
+    if (grid_cache == 0) {
         NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
         grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
-        sm_cached = sm_count;
     }
     if (E <= 0) return NB_OK;
     const int grid = (int)(E < grid_cache ? E : grid_cache);
@@ -325,16 +324,15 @@ nb_status launch_bax(int sm_count, long long E, long long e_first, const int32_t
     auto kern = k_bax<T, n, M, PUPD>;
     constexpr size_t smem = sizeof(T) * (size_t)M * (n * n * n + 3 * n * n);
     constexpr int threads = M * n * n;
-    static int grid_cache = 0;
-    static int sm_cached = 0;
-    if (grid_cache == 0 || sm_cached != sm_count) {
+    static int grid_cache_dev[kMaxDevices] = {};  // per device, as the smem attribute
+    int &grid_cache = device_slot(grid_cache_dev);
+    if (grid_cache == 0) {
         if (smem > 48 * 1024)
             NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
         int per_sm = 0;
         NB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
         grid_cache = (per_sm < 1 ? 1 : per_sm) * sm_count;
-        sm_cached = sm_count;
     }
     if (E <= 0) return NB_OK;
     const long long need = (E + M - 1) / M;

@@ -97,24 +97,23 @@ struct Pair2<double> {
 // kernel, so the sums are bit-identical to it.  Only the first node of a pair
 // can be on a lower x face and only the second on an upper one; the y / z
 // copies of both nodes are one vector load each.  No mask applied.
-template <typename T, int n>
-__device__ __forceinline__ void gs_sum_pair(const T *__restrict__ w, int64_t l, int i0, int j,
-                                            int k, int ex, int ey, int ez, int nx, int ny, int nz,
-                                            int64_t sx, int64_t sy, int64_t sz, T &wa, T &wb)
+// The sum of gs_sum_pair with its copy flags given: lxa / hxb the first
+// node on a lower x face / the second on an upper one (with a neighbour
+// there), ly, hy, lz, hz the pair on a lower / upper y or z face.
+template <typename T, typename I>
+__device__ __forceinline__ void gs_sum_pair_flags(const T *__restrict__ w, I l, bool lxa, bool hxb,
+                                                  int ly, int hy, int lz, int hz, I sx, I sy, I sz,
+                                                  T &wa, T &wb)
 {
     using V = typename Pair2<T>::type;
-    constexpr int N = n - 1;
-    const bool lxa = i0 == 0 && ex > 0, hxb = i0 + 1 == N && ex < nx - 1;
-    const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
-    const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
-    const int64_t l0 = l - ly * sy - lz * sz;
+    const I l0 = l - ly * sy - lz * sz;
     T va[2][2][2], vb[2][2][2];
 #pragma unroll
     for (int tz = 0; tz < 2; ++tz)
 #pragma unroll
         for (int ty = 0; ty < 2; ++ty) {
             const bool ok = tz <= lz + hz && ty <= ly + hy;
-            const int64_t o = l0 + ty * sy + tz * sz;
+            const I o = l0 + ty * sy + tz * sz;
             const V own = ok ? *reinterpret_cast<const V *>(w + o) : V{T(0), T(0)};
             const T pa = ok && lxa ? w[o - sx] : T(0);
             const T pb = ok && hxb ? w[o + 1 + sx] : T(0);
@@ -134,6 +133,18 @@ __device__ __forceinline__ void gs_sum_pair(const T *__restrict__ w, int64_t l, 
                 wa += va[tz][ty][tx];
                 wb += vb[tz][ty][tx];
             }
+}
+
+template <typename T, int n, typename I>
+__device__ __forceinline__ void gs_sum_pair(const T *__restrict__ w, I l, int i0, int j,
+                                            int k, int ex, int ey, int ez, int nx, int ny, int nz,
+                                            I sx, I sy, I sz, T &wa, T &wb)
+{
+    constexpr int N = n - 1;
+    const bool lxa = i0 == 0 && ex > 0, hxb = i0 + 1 == N && ex < nx - 1;
+    const int ly = j == 0 && ey > 0, hy = j == N && ey < ny - 1;
+    const int lz = k == 0 && ez > 0, hz = k == N && ez < nz - 1;
+    gs_sum_pair_flags<T, I>(w, l, lxa, hxb, ly, hy, lz, hz, sx, sy, sz, wa, wb);
 }
 
 }  // namespace nb

@@ -16,6 +16,46 @@ constexpr int kMaxN = 15;          // highest polynomial order supported
 constexpr int kMaxn = kMaxN + 1;   // GLL points per direction
 constexpr int kFinalizeThreads = 512;
 constexpr int kMaxPartials = 1 << 16;
+constexpr int kMaxDevices = 64;    // devices with their own launch-shape caches
+
+// The entry of a per-device cache for the calling thread's current device
+// (a scratch entry, never kept, beyond kMaxDevices).  Launch shapes that
+// depend on occupancy, and the shared-memory attribute set with them, are
+// per device.
+inline int &device_slot(int (&slots)[kMaxDevices])
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) {
+        static thread_local int spare;
+        spare = 0;
+        return spare;
+    }
+    return slots[d];
+}
+
+// Makes `device` current for the lifetime of the guard and restores the
+// caller's current device afterwards, so that a library call leaves the
+// calling thread's device as it found it.
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int device)
+    {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != device) err_ = cudaSetDevice(device);
+        else prev_ = -1;  // nothing to restore
+    }
+    ~DeviceGuard()
+    {
+        if (prev_ >= 0 && err_ == cudaSuccess) cudaSetDevice(prev_);
+    }
+    cudaError_t error() const { return err_; }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+
+  private:
+    int prev_ = -1;
+    cudaError_t err_ = cudaSuccess;
+};
 
 void set_error(const char *fmt, ...);
 
@@ -29,11 +69,36 @@ void set_error(const char *fmt, ...);
         }                                                                           \
     } while (0)
 
+// Enter `device` for the rest of the enclosing scope (see DeviceGuard).
+#define NB_DEVICE_SCOPE(device)                   \
+    ::nb::DeviceGuard nb_device_guard_(device);   \
+    NB_CUDA(nb_device_guard_.error())
+
 #define NB_TRY(expr)                     \
     do {                                 \
         nb_status s_ = (expr);           \
         if (s_ < 0) return s_;           \
     } while (0)
+
+// Division by a divisor fixed at launch time (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): for
+// 0 <= x < 2^31, x / d = (umulhi(x, m) + x) >> l with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1.
+struct FastDiv {
+    uint32_t m = 1, l = 0, d = 1;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div)
+    {
+        while ((1ull << l) < div) ++l;
+        m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ int div(int x) const
+    {
+        return (int)((__umulhi((uint32_t)x, m) + (uint32_t)x) >> l);
+    }
+#endif
+};
 
 // Device-resident scalars of one CG solve.  Every kernel of the iteration
 // reads alpha/beta from here, so a captured graph needs no host values.
@@ -81,9 +146,11 @@ struct Workspace {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_key = -1;           // which configuration the graph holds
+    int graph_epoch = -1;         // the mesh's ax_epoch at its capture
     cudaGraph_t graph2 = nullptr;       // flexible-CG iteration graph
     cudaGraphExec_t exec2 = nullptr;
     intptr_t graph2_key = 0;            // the model it was captured with
+    int graph2_epoch = -1;              // the mesh's ax_epoch at its capture
 };
 
 // Launch shape of the ax kernel for one (precision, order).
@@ -146,6 +213,12 @@ struct nb_mesh {
     double *red_out = nullptr;       // device scalar for glsc3/norms
     double *red_host = nullptr;      // pinned mirror
     nb::AxConfig ax_cfg[4];
+    int update_kind = 0;       // FP32 update with the folded summation, even n:
+                               // 1 element ranges (k_cg_update_el), 2 node pairs
+                               // (k_cg_update_pairs), 0 element ranges where an
+                               // element takes at most two rounds of 256 pairs
+    int ax_epoch = 0;          // bumped whenever an operator variant choice changes:
+                               // captured iteration graphs of an older epoch are stale
     int *kerr = nullptr;             // device flag: a pipelined kernel's wait timed out
     int64_t launches = 0;            // kernels issued by the current solve
     // learned preconditioner (optional)

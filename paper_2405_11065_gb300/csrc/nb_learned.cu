@@ -1181,7 +1181,7 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
         // the loop body is two steps (the roles of w and wprev swap between
         // them), repeated by a while node until the scalars say stop
         const intptr_t key = (intptr_t)md;
-        if (!ws.exec2 || ws.graph2_key != key) {
+        if (!ws.exec2 || ws.graph2_key != key || ws.graph2_epoch != m->ax_epoch) {
             if (ws.exec2) NB_CUDA(cudaGraphExecDestroy(ws.exec2));
             if (ws.graph2) NB_CUDA(cudaGraphDestroy(ws.graph2));
             ws.exec2 = nullptr;
@@ -1217,6 +1217,7 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
             NB_CUDA(cudaGraphInstantiate(&ws.exec2, gr, 0));
             ws.graph2 = gr;
             ws.graph2_key = key;
+            ws.graph2_epoch = m->ax_epoch;
         }
         NB_CUDA(cudaGraphLaunch(ws.exec2, s));
         NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
@@ -1291,7 +1292,7 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     const int kPerStep = two ? 7 : 4;
     if (o->use_graph) {
         const intptr_t key = (intptr_t)m->schwarz + (two ? 1 : 0);
-        if (!ws.exec2 || ws.graph2_key != key) {
+        if (!ws.exec2 || ws.graph2_key != key || ws.graph2_epoch != m->ax_epoch) {
             if (ws.exec2) NB_CUDA(cudaGraphExecDestroy(ws.exec2));
             if (ws.graph2) NB_CUDA(cudaGraphDestroy(ws.graph2));
             ws.exec2 = nullptr;
@@ -1327,6 +1328,7 @@ nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
             NB_CUDA(cudaGraphInstantiate(&ws.exec2, gr, 0));
             ws.graph2 = gr;
             ws.graph2_key = key;
+            ws.graph2_epoch = m->ax_epoch;
         }
         NB_CUDA(cudaGraphLaunch(ws.exec2, s));
         NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
@@ -1363,7 +1365,7 @@ extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t se
         return NB_ERR_ARG;
     }
     *out = nullptr;
-    NB_CUDA(cudaSetDevice(ctx->device));
+    NB_DEVICE_SCOPE(ctx->device);
     nb_model *md = new nb_model();
     md->ctx = ctx;
     md->N = N;
@@ -1404,7 +1406,7 @@ extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t se
 extern "C" nb_status nb_model_destroy(nb_model *md)
 {
     if (!md) return NB_OK;
-    cudaSetDevice(md->ctx->device);
+    ::nb::DeviceGuard nb_device_guard_(md->ctx->device);
     float *bufs[] = {md->W, md->grad, md->m, md->v, md->Z, md->H, md->Y, md->dY, md->dH,
                      md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
@@ -1421,7 +1423,7 @@ extern "C" nb_status nb_model_params(nb_model *md, float *get_host, const float 
         set_error("invalid argument: model is NULL");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(md->ctx->device));
+    NB_DEVICE_SCOPE(md->ctx->device);
     if (nparam) *nparam = md->nparam;
     if (set_host) {
         NB_CUDA(cudaMemcpy(md->W, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
@@ -1439,7 +1441,7 @@ extern "C" nb_status nb_model_grad(nb_model *md, const float *X, const float *T,
         set_error("invalid argument: model, batch or size");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(md->ctx->device));
+    NB_DEVICE_SCOPE(md->ctx->device);
     cudaStream_t s = md->ctx->stream;
     NB_TRY(model_scratch(md, B));
     double *dl = md->lpart + 4000;
@@ -1461,7 +1463,7 @@ extern "C" nb_status nb_model_train(nb_model *md, const float *X, const float *T
         set_error("invalid argument: training set-up");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(md->ctx->device));
+    NB_DEVICE_SCOPE(md->ctx->device);
     cudaStream_t s = md->ctx->stream;
     batch = std::min(batch, npairs);
     NB_TRY(model_scratch(md, batch));
@@ -1522,7 +1524,7 @@ extern "C" nb_status nb_learned_collect(nb_mesh *m, const double *b, int nsnap,
         set_error("use_learned needs an attached model");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     const size_t bytes = sizeof(double) * m->nL;
     const size_t smem = sizeof(double) * (7 * (size_t)m->n3 + (size_t)m->n * m->n);
@@ -1597,7 +1599,7 @@ extern "C" nb_status nb_learned_targets(nb_mesh *m, const double *r_dev, const i
         return NB_ERR_STATE;
     }
     if (count == 0) return NB_OK;
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     const size_t smem = sizeof(double) * (7 * (size_t)m->n3 + (size_t)m->n * m->n);
     NB_CUDA(cudaFuncSetAttribute(k_interior_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
@@ -1628,7 +1630,7 @@ extern "C" nb_status nb_learned_apply(nb_mesh *m, const float *r_dev, float *z_d
         set_error("invalid argument or no model attached");
         return NB_ERR_ARG;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(model_apply(m, (nb_model *)m->learned, r_dev, z_dev, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
     return NB_OK;

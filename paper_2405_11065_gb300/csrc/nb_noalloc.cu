@@ -81,7 +81,7 @@ extern "C" nb_status nb_glsc3_noalloc(nb_mesh *m, nb_prec prec, const void *a, c
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     const int grid = vec_grid(m->ctx, m->nL);
     if (grid > kNoAllocSlots) {
         set_error("nb_glsc3_noalloc: %d partial sums exceed the fixed scratch of %d", grid,

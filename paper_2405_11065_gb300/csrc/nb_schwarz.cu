@@ -946,7 +946,7 @@ extern "C" nb_status nb_schwarz_apply(nb_mesh *m, const float *r_dev, float *z_d
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(schwarz_setup(m));
     NB_TRY(schwarz_apply(m, r_dev, z_dev, m->ctx->stream, false));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
@@ -963,7 +963,7 @@ extern "C" nb_status nb_schwarz2_apply(nb_mesh *m, const float *r_dev, float *z_
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(schwarz_coarse_setup(m));
     NB_TRY(schwarz_apply(m, r_dev, z_dev, m->ctx->stream, true));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));

@@ -331,6 +331,185 @@ k_cg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T
     if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
+// k_cg_update_gs2 over node pairs instead of elements: the E n^3 / 2 pairs
+// are dealt to the threads of a persistent grid in turn (pair q to thread
+// q mod T), so every thread gets the same number of pairs to within one and
+// no wave of blocks runs part-empty at the end.  Each thread works on two
+// pairs at a time with all their loads issued first; the element of a pair
+// and its box coordinates come from multiplications by constants fixed at
+// launch (FastDiv).  32-bit indices (E n^3 < 2^31).  Same sums in the same
+// order as k_cg_update_gs2, so the result is bit-identical to it.
+template <typename T, int n>
+__global__ void __launch_bounds__(256)
+k_cg_update_pairs(int npairs, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
+                  CgScalars *__restrict__ sc, T *__restrict__ x, T *__restrict__ r,
+                  const T *__restrict__ p, const T *__restrict__ w, const T *__restrict__ dinv,
+                  double *__restrict__ part)
+{
+    static_assert(n % 2 == 0, "pairs of nodes need an even n");
+    using V = typename Pair2<T>::type;
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const int sx = n3 - N, sy = nx * n3 - N * n, sz = nx * ny * n3 - N * n2;
+    DotAcc<T> a, b;
+    struct Pair {
+        int l;
+        T wa, wb;
+        V xv, rv, pv, dv;
+    };
+    auto load = [&](int q, Pair &c) {
+        const int e = q / P, t = q - e * P;
+        const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
+        const int exy = dnx.div(e), ex = e - exy * nx;
+        const int ez = dny.div(exy), ey = exy - ez * ny;
+        c.l = e * n3 + k * n2 + j * n + i0;
+        gs_sum_pair<T, n, int>(w, c.l, i0, j, k, ex, ey, ez, nx, ny, nz, sx, sy, sz, c.wa, c.wb);
+        c.xv = *reinterpret_cast<const V *>(x + c.l);
+        c.rv = *reinterpret_cast<const V *>(r + c.l);
+        c.pv = *reinterpret_cast<const V *>(p + c.l);
+        c.dv = *reinterpret_cast<const V *>(dinv + c.l);
+    };
+    auto node = [&](T &xl, T &rl, T pl, T wl, T d) {
+        if (d == T(0)) wl = T(0);  // Dirichlet node
+        xl = xl + alpha * pl;
+        rl = rl - alpha * wl;
+        if (owner_copy(d)) {
+            a.add(rl * (d * rl));
+            b.add(rl * rl);
+        }
+    };
+    auto finish = [&](Pair &c) {
+        node(c.xv.x, c.rv.x, c.pv.x, c.wa, c.dv.x);
+        node(c.xv.y, c.rv.y, c.pv.y, c.wb, c.dv.y);
+        *reinterpret_cast<V *>(x + c.l) = c.xv;
+        *reinterpret_cast<V *>(r + c.l) = c.rv;
+    };
+    const int stride = gridDim.x * blockDim.x;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q + stride < npairs; q += 2 * stride) {
+        Pair c0, c1;
+        load(q, c0);
+        load(q + stride, c1);
+        finish(c0);
+        finish(c1);
+    }
+    if (q < npairs) {
+        Pair c0;
+        load(q, c0);
+        finish(c0);
+    }
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+}
+
+// The update with the folded summation over contiguous element ranges:
+// block b of a persistent grid takes elements [E b / G, E (b + 1) / G), and
+// thread t the node pairs t, t + 256, ... of each of them (R rounds).  The
+// pair's position in the element -- its local offset and which faces it lies
+// on -- is fixed per thread and computed once; per element only the box
+// coordinates and the neighbour tests change.  The rounds of one element are
+// loaded together before any is used.  Same sums in the same order as
+// k_cg_update_gs2 (bit-identical).  32-bit indices (E n^3 < 2^31).
+template <typename T, int n>
+__global__ void __launch_bounds__(256)
+k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
+               CgScalars *__restrict__ sc, T *__restrict__ x, T *__restrict__ r,
+               const T *__restrict__ p, const T *__restrict__ w, const T *__restrict__ dinv,
+               double *__restrict__ part)
+{
+    static_assert(n % 2 == 0, "pairs of nodes need an even n");
+    using V = typename Pair2<T>::type;
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
+    constexpr int R = (P + 255) / 256;  // rounds of 256 pairs per element
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
+    const int sx = n3 - N, sy = nx * n3 - N * n, sz = nx * ny * n3 - N * n2;
+    // the thread's pair slots: local offset and face flags (bit 0..5: lower x
+    // of the first node, upper x of the second, lower / upper y, lower / upper z)
+    int loc[R], fl[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int t = threadIdx.x + 256 * q;
+        const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
+        loc[q] = t < P ? k * n2 + j * n + i0 : -1;
+        fl[q] = (i0 == 0) | ((i0 + 1 == N) << 1) | ((j == 0) << 2) | ((j == N) << 3) |
+                ((k == 0) << 4) | ((k == N) << 5);
+    }
+    DotAcc<T> a, b;
+    auto node = [&](T &xl, T &rl, T pl, T wl, T d) {
+        if (d == T(0)) wl = T(0);  // Dirichlet node
+        xl = xl + alpha * pl;
+        rl = rl - alpha * wl;
+        if (owner_copy(d)) {
+            a.add(rl * (d * rl));
+            b.add(rl * rl);
+        }
+    };
+    const int e0 = (int)((int64_t)E * blockIdx.x / gridDim.x);
+    const int e1 = (int)((int64_t)E * (blockIdx.x + 1) / gridDim.x);
+    for (int e = e0; e < e1; ++e) {
+        const int exy = dnx.div(e), ex = e - exy * nx;
+        const int ez = dny.div(exy), ey = exy - ez * ny;
+        // neighbour present below / above in each direction, in the bit layout of fl
+        const int nb = (ex > 0) | ((ex < nx - 1) << 1) | ((ey > 0) << 2) | ((ey < ny - 1) << 3) |
+                       ((ez > 0) << 4) | ((ez < nz - 1) << 5);
+        T wa[R], wb[R];
+        V xv[R], rv[R], pv[R], dv[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (loc[q] < 0) continue;
+            const int l = e * n3 + loc[q], f = fl[q] & nb;
+            gs_sum_pair_flags<T, int>(w, l, (f & 1) != 0, (f & 2) != 0, (f >> 2) & 1,
+                                      (f >> 3) & 1, (f >> 4) & 1, (f >> 5) & 1, sx, sy, sz,
+                                      wa[q], wb[q]);
+            xv[q] = *reinterpret_cast<const V *>(x + l);
+            rv[q] = *reinterpret_cast<const V *>(r + l);
+            pv[q] = *reinterpret_cast<const V *>(p + l);
+            dv[q] = *reinterpret_cast<const V *>(dinv + l);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (loc[q] < 0) continue;
+            const int l = e * n3 + loc[q];
+            node(xv[q].x, rv[q].x, pv[q].x, wa[q], dv[q].x);
+            node(xv[q].y, rv[q].y, pv[q].y, wb[q], dv[q].y);
+            *reinterpret_cast<V *>(x + l) = xv[q];
+            *reinterpret_cast<V *>(r + l) = rv[q];
+        }
+    }
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+}
+
+// Grid of a pair kernel: one wave of its resident blocks (per device, from
+// the occupancy of its register count), and no more blocks than pairs need.
+template <typename K>
+static int update_pairs_grid(K kern, int sm_count, int npairs)
+{
+    static int per_sm_dev[kMaxDevices] = {};
+    int &per_sm = device_slot(per_sm_dev);
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    const int64_t need = ((int64_t)npairs + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count));
+}
+
 // k_cg_update_gs for n = N + 1 in FP32 (returns false where it is not
 // built).  FP64 keeps the separate summation: the folded sum adds every slot,
 // zeros included, which costs little on the FP32 pipe but measured slower
@@ -338,23 +517,45 @@ k_cg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T
 static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, double *part,
                              cudaStream_t s)
 {
-    // one wave: 8 blocks of 256 threads per SM (32 registers)
+    // one wave: 8 blocks of 256 threads per SM
     const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
+    // even n: the pair kernel over a full persistent grid (at most one pair
+    // per thread fewer or more anywhere)
+    const int npairs = (int)(m->nL / 2);
+    const FastDiv dnx((uint32_t)m->nx), dny((uint32_t)m->ny);
+    int pgrid = 0;
 #define NB_UGS(K, NN)                                                                           \
     case NN:                                                                                    \
         K<float, NN><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal, (float *)ws.x,    \
                                           (float *)ws.r, (const float *)ws.p,                   \
                                           (const float *)ws.w, dinv, part);                     \
         return true;
+#define NB_UGP(NN)                                                                              \
+    case NN:                                                                                    \
+        if (m->update_kind == 1 ||                                                              \
+            (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {               \
+            pgrid = update_pairs_grid(k_cg_update_el<float, NN>, m->ctx->sm_count,              \
+                                      (int)std::min<int64_t>(m->E * 256, npairs));              \
+            pgrid = (int)std::min<int64_t>(pgrid, m->E);                                        \
+            k_cg_update_el<float, NN><<<pgrid, 256, 0, s>>>(                                    \
+                (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
+                (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);           \
+        } else {                                                                                \
+            pgrid = update_pairs_grid(k_cg_update_pairs<float, NN>, m->ctx->sm_count, npairs);  \
+            k_cg_update_pairs<float, NN><<<pgrid, 256, 0, s>>>(                                 \
+                npairs, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x, (float *)ws.r,   \
+                (const float *)ws.p, (const float *)ws.w, dinv, part);                          \
+        }                                                                                       \
+        return true;
     switch (m->n) {
-        NB_UGS(k_cg_update_gs2, 2) NB_UGS(k_cg_update_gs, 3) NB_UGS(k_cg_update_gs2, 4)
-        NB_UGS(k_cg_update_gs, 5) NB_UGS(k_cg_update_gs2, 6) NB_UGS(k_cg_update_gs, 7)
-        NB_UGS(k_cg_update_gs2, 8) NB_UGS(k_cg_update_gs, 9) NB_UGS(k_cg_update_gs2, 10)
-        NB_UGS(k_cg_update_gs, 11) NB_UGS(k_cg_update_gs2, 12) NB_UGS(k_cg_update_gs, 13)
-        NB_UGS(k_cg_update_gs2, 14) NB_UGS(k_cg_update_gs, 15) NB_UGS(k_cg_update_gs2, 16)
+        NB_UGP(2) NB_UGS(k_cg_update_gs, 3) NB_UGP(4) NB_UGS(k_cg_update_gs, 5) NB_UGP(6)
+        NB_UGS(k_cg_update_gs, 7) NB_UGP(8) NB_UGS(k_cg_update_gs, 9) NB_UGP(10)
+        NB_UGS(k_cg_update_gs, 11) NB_UGP(12) NB_UGS(k_cg_update_gs, 13) NB_UGP(14)
+        NB_UGS(k_cg_update_gs, 15) NB_UGP(16)
         default:
             return false;
     }
+#undef NB_UGP
 #undef NB_UGS
 }
 
@@ -540,7 +741,7 @@ static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *di
                             int use_graph, int maxit, cudaStream_t s)
 {
     if (use_graph) {
-        if (ws.exec == nullptr || ws.graph_key != key) {
+        if (ws.exec == nullptr || ws.graph_key != key || ws.graph_epoch != m->ax_epoch) {
             if (ws.exec) {
                 NB_CUDA(cudaGraphExecDestroy(ws.exec));
                 ws.exec = nullptr;
@@ -578,6 +779,7 @@ static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *di
             NB_CUDA(cudaGraphInstantiate(&ws.exec, g, 0));
             ws.graph = g;
             ws.graph_key = key;
+            ws.graph_epoch = m->ax_epoch;
         }
         NB_CUDA(cudaGraphLaunch(ws.exec, s));
         return NB_OK;

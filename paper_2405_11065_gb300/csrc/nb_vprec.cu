@@ -273,7 +273,7 @@ static nb_status cg_emulated(nb_mesh *m, int mode, int t, uint64_t seed, int ite
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     cudaStream_t s = m->ctx->stream;
     const int64_t n = m->nL;
     const int vb = 256;
@@ -360,7 +360,7 @@ extern "C" nb_status nb_apply_vprec(nb_mesh *m, int t, const double *u_dev, doub
         set_error("call nb_setup_gs first");
         return NB_ERR_STATE;
     }
-    NB_CUDA(cudaSetDevice(m->ctx->device));
+    NB_DEVICE_SCOPE(m->ctx->device);
     EmuArgs ea = {0, t, 0ull, 0ull};
     NB_TRY(vp_apply(m, ea, u_dev, w_dev, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));

@@ -362,3 +362,33 @@ def test_reliable_update_keeps_fp64_iteration_count(nb, ctx):
     assert its[0] < its[1]
     with pytest.raises(nb.NbError):
         mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP32, restart=2))
+
+
+def test_variant_change_after_a_solve_takes_effect(nb, ctx):
+    """A solve captures its iteration in a CUDA graph; choosing another
+    operator variant afterwards must re-capture it.  The variants round
+    differently in FP32, so the solution bits tell which kernel ran: a solve
+    after switching from variant 0 to the last variant must give the bits of
+    a solve on a fresh mesh set to the last variant from the start."""
+    import torch
+    box = Box(3, 3, 2, 7, 0.05)
+    P = oracle.Problem(box)
+    b = _t(P.to_local(rhs_global(box, 6)))
+    m1 = nb.Mesh.from_box(ctx, box)
+    last = m1.ax_variants(nb.NB_FP32) - 1
+    assert last >= 2
+    x = torch.zeros_like(b)
+    m1.set_ax_variant(nb.NB_FP32, 0)
+    m1.solve(b, x, nb.default_opts(prec=nb.NB_FP32))
+    x0 = x.clone()
+    m1.set_ax_variant(nb.NB_FP32, last)
+    x.zero_()
+    m1.solve(b, x, nb.default_opts(prec=nb.NB_FP32))
+    m2 = nb.Mesh.from_box(ctx, box)
+    m2.set_ax_variant(nb.NB_FP32, last)
+    y = torch.zeros_like(b)
+    m2.solve(b, y, nb.default_opts(prec=nb.NB_FP32))
+    assert torch.equal(x, y)
+    assert not torch.equal(x0, y), "variants 0 and last give identical bits: no evidence"
+    with pytest.raises(nb.NbError):
+        m1.set_ax_variant(nb.NB_FP32, last + 1)
