@@ -50,6 +50,13 @@ struct SchwarzData {
     float *t2 = nullptr;    // [gz][vy][vx]
     float *rc = nullptr;    // [vz][vy][vx] restricted residual
     float *zc = nullptr;    // [vz][vy][vx]
+    // the same coarse level in FP64, for the outer correction of the
+    // refinement (schwarz_coarse_correct64)
+    double *Sc64 = nullptr, *lamc64 = nullptr, *xi64 = nullptr;
+    double *rg64 = nullptr;  // [nG] the FP64 residual on the global lattice
+    double *t1 = nullptr;    // [gz][gy][vx]
+    double *t2d = nullptr;   // [gz][vy][vx]
+    double *ca = nullptr, *cb = nullptr;  // [vz][vy][vx] coarse vectors
 };
 
 // Coarse level limits: interior vertices per direction, and in total (two
@@ -593,6 +600,130 @@ __global__ void k_co_solve(int ncx, int ncy, int ncz, const float *__restrict__ 
     for (int t = threadIdx.x; t < total; t += blockDim.x) zc[t] = A[t];
 }
 
+// ---------------------------------------------------------------------------
+// The coarse level in FP64, applied by the refinement to its FP64 residual
+// (schwarz_coarse_correct64): restriction along x, y, z, the coarse solve by
+// fast diagonalisation, and the trilinear prolongation to the local nodes.
+// One thread per output value throughout.
+// ---------------------------------------------------------------------------
+
+// Weight of the hat of an interior vertex at the d-th of the 2N + 1 GLL nodes
+// of its support: (1 + xi_d) / 2 on the element below the vertex, (1 - xi_(d-N))
+// / 2 on the element above.
+__device__ __forceinline__ double hat64(const double *xi, int N, int d)
+{
+    return d <= N ? 0.5 * (1.0 + xi[d]) : 0.5 * (1.0 - xi[d - N]);
+}
+
+// t1[gz][gy][vx] = sum_d hat(d) rg[gz][gy][vx N + d]
+__global__ void k_c64_rx(int64_t rows, int gxn, int N, int ncx, const double *__restrict__ xi,
+                         const double *__restrict__ rg, double *__restrict__ t1)
+{
+    const int64_t total = rows * ncx;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int vx = (int)(t % ncx);
+        const int64_t row = t / ncx;
+        const double *src = rg + row * gxn + (int64_t)vx * N;
+        double acc = 0.0;
+        for (int d = 0; d <= 2 * N; ++d) acc += hat64(xi, N, d) * src[d];
+        t1[t] = acc;
+    }
+}
+
+// out[o][v][q] = sum_d hat(d) in[o][v N + d][q] (the restriction along the
+// middle axis of in[o][g][q], g of length gn)
+__global__ void k_c64_rmid(int64_t outer, int gn, int nv, int nq, int N,
+                           const double *__restrict__ xi, const double *__restrict__ in,
+                           double *__restrict__ out)
+{
+    const int64_t total = outer * nv * nq;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t % nq), v = (int)((t / nq) % nv);
+        const int64_t o = t / ((int64_t)nq * nv);
+        const double *src = in + (o * gn + (int64_t)v * N) * nq + q;
+        double acc = 0.0;
+        for (int d = 0; d <= 2 * N; ++d) acc += hat64(xi, N, d) * src[(int64_t)d * nq];
+        out[t] = acc;
+    }
+}
+
+// One axis of the coarse fast-diagonalisation solve on [vz][vy][vx]:
+// out = S^T in (trans) or S in along the axis (0 = x), S[a][q] row-major
+// (kCoarseDir columns); with lam, the result is divided by lx + ly + lz.
+__global__ void k_c64_axis(int ncx, int ncy, int ncz, int axis, int trans,
+                           const double *__restrict__ S, const double *__restrict__ lam,
+                           const double *__restrict__ in, double *__restrict__ out)
+{
+    const int total = ncx * ncy * ncz;
+    const int na = axis == 0 ? ncx : (axis == 1 ? ncy : ncz);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? ncx : ncx * ncy);
+    const double *M = S + (size_t)axis * kCoarseDir * kCoarseDir;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int x = t % ncx, y = (t / ncx) % ncy, z = t / (ncx * ncy);
+        const int q = axis == 0 ? x : (axis == 1 ? y : z);
+        const int base = t - q * stride;
+        double acc = 0.0;
+        for (int a = 0; a < na; ++a)
+            acc += (trans ? M[a * na + q] : M[q * na + a]) * in[base + a * stride];
+        if (lam) acc /= lam[x] + lam[kCoarseDir + y] + lam[2 * kCoarseDir + z];
+        out[t] = acc;
+    }
+}
+
+// c = R_0^T zc at every local node (trilinear in the element's reference
+// coordinates from its 8 vertices; boundary vertices carry 0, so c vanishes
+// on the Dirichlet boundary), x += c, and c rounded to FP32 into c32.
+__global__ void k_c64_prolong(int64_t nL, int nx, int ny, int N, const double *__restrict__ xi,
+                              const double *__restrict__ zc, int ncx, int ncy, int ncz,
+                              double *__restrict__ x, float *__restrict__ c32)
+{
+    const int n = N + 1, n3 = n * n * n;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = l / n3;
+        const int q = (int)(l - e * n3), i = q % n, j = (q / n) % n, k = q / (n * n);
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        const double wx[2] = {0.5 * (1.0 - xi[i]), 0.5 * (1.0 + xi[i])};
+        const double wy[2] = {0.5 * (1.0 - xi[j]), 0.5 * (1.0 + xi[j])};
+        const double wz[2] = {0.5 * (1.0 - xi[k]), 0.5 * (1.0 + xi[k])};
+        double c = 0.0;
+        for (int cz = 0; cz < 2; ++cz) {
+            const int vz = ez + cz - 1;  // interior vertex index (vertex ez + cz)
+            if (vz < 0 || vz >= ncz) continue;
+            for (int by = 0; by < 2; ++by) {
+                const int vy = ey + by - 1;
+                if (vy < 0 || vy >= ncy) continue;
+                for (int ax = 0; ax < 2; ++ax) {
+                    const int vx = ex + ax - 1;
+                    if (vx < 0 || vx >= ncx) continue;
+                    c += wz[cz] * wy[by] * wx[ax] * zc[((int64_t)vz * ncy + vy) * ncx + vx];
+                }
+            }
+        }
+        x[l] += c;
+        c32[l] = (float)c;
+    }
+}
+
+// r64 -= w32 (the FP32 operator applied to the coarse correction) and the
+// partials of (r, c, r), c = 1/multiplicity.
+__global__ void k_c64_subnorm(int64_t nL, double *__restrict__ r64, const float *__restrict__ w32,
+                              const float *__restrict__ c, double *__restrict__ part)
+{
+    __shared__ double sred[32];
+    double a = 0.0;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double v = r64[l] - (double)w32[l];
+        r64[l] = v;
+        a += (double)c[l] * v * v;
+    }
+    const double t = block_sum(a, sred);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 // Shared-memory limit and grid (resident blocks x SMs, at most one block
 // per EPB elements) of k_sw_local<m>; set once per mesh, outside any capture.
 template <int m>
@@ -660,6 +791,14 @@ void schwarz_free(nb_mesh *m)
     cudaFree(d->t2);
     cudaFree(d->rc);
     cudaFree(d->zc);
+    cudaFree(d->Sc64);
+    cudaFree(d->lamc64);
+    cudaFree(d->xi64);
+    cudaFree(d->rg64);
+    cudaFree(d->t1);
+    cudaFree(d->t2d);
+    cudaFree(d->ca);
+    cudaFree(d->cb);
     delete d;
     m->schwarz = nullptr;
 }
@@ -806,6 +945,7 @@ static nb_status schwarz_setup_coarse(nb_mesh *m)
             K[(size_t)i * n + j] = s2;
         }
     std::vector<float> Sh((size_t)3 * kCoarseDir * kCoarseDir, 0.f), lh((size_t)3 * kCoarseDir, 1.f);
+    std::vector<double> Sh64(Sh.size(), 0.0), lh64(lh.size(), 1.0);
     for (int dir = 0; dir < 3 && total > 0; ++dir) {
         const int nd = cnt[dir], nc = nd - 1, ng = nd * N + 1;
         const double L = 1.0 / nd;
@@ -841,8 +981,11 @@ static nb_status schwarz_setup_coarse(nb_mesh *m)
         }
         for (int a = 0; a < nc; ++a) {
             lh[(size_t)dir * kCoarseDir + a] = (float)lam[a];
-            for (int q = 0; q < nc; ++q)
+            lh64[(size_t)dir * kCoarseDir + a] = lam[a];
+            for (int q = 0; q < nc; ++q) {
                 Sh[(size_t)dir * kCoarseDir * kCoarseDir + a * nc + q] = (float)S[(size_t)a * nc + q];
+                Sh64[(size_t)dir * kCoarseDir * kCoarseDir + a * nc + q] = S[(size_t)a * nc + q];
+            }
         }
     }
     std::vector<float> xf(n);
@@ -860,6 +1003,24 @@ static nb_status schwarz_setup_coarse(nb_mesh *m)
     if (e == cudaSuccess)
         e = cudaMemcpy(d->lamc, lh.data(), sizeof(float) * lh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d->xi, xf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    // FP64 copies for the outer coarse correction
+    const int64_t gxn = (int64_t)m->nx * N + 1, gyn = (int64_t)m->ny * N + 1;
+    if (e == cudaSuccess) e = cudaMalloc(&d->Sc64, sizeof(double) * Sh64.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->lamc64, sizeof(double) * lh64.size());
+    if (e == cudaSuccess) e = cudaMalloc(&d->xi64, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d->rg64, sizeof(double) * gxn * gyn * gzn);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d->t1, sizeof(double) * std::max<int64_t>(1, gzn * gyn * d->nc[0]));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d->t2d, sizeof(double) * std::max<int64_t>(1, gzn * d->nc[1] * d->nc[0]));
+    if (e == cudaSuccess) e = cudaMalloc(&d->ca, sizeof(double) * std::max<int64_t>(1, total));
+    if (e == cudaSuccess) e = cudaMalloc(&d->cb, sizeof(double) * std::max<int64_t>(1, total));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->Sc64, Sh64.data(), sizeof(double) * Sh64.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->lamc64, lh64.data(), sizeof(double) * lh64.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d->xi64, xi.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_co_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2 * sizeof(float) * kCoarseTotal));
@@ -923,6 +1084,54 @@ nb_status schwarz_coarse_setup(nb_mesh *m)
 {
     NB_TRY(schwarz_setup(m));
     return schwarz_setup_coarse(m);
+}
+
+// The coarse-grid correction in FP64 inside the refinement's outer step:
+// given the FP64 residual r64 = b - A x (continuous, masked), the coarse
+// correction c = R_0^T A_0^-1 R_0 r64 is computed in FP64 and added to x; r64
+// becomes r64 - A c with A c the FP32 operator (the inner solve's accuracy)
+// applied to c rounded to FP32 in c32_tmp, w32_tmp.  *norm_dev receives
+// (r, c, r) of the new r64.  The coarse level is the two-level
+// preconditioner's; the smooth error the FP32 inner solves leave in x has an
+// FP64 residual below what the stopping test resolves, and this correction
+// removes it.  No-op (returns false in *applied) without a coarse level.
+nb_status schwarz_coarse_correct64(nb_mesh *m, double *r64, double *x, float *c32_tmp,
+                                   float *w32_tmp, double *part, double *norm_dev,
+                                   bool *applied, cudaStream_t s)
+{
+    *applied = false;
+    NB_TRY(schwarz_coarse_setup(m));
+    SchwarzData *d = (SchwarzData *)m->schwarz;
+    if (!d->coarse) return NB_OK;
+    const int N = m->N, gxn = m->nx * N + 1, gyn = m->ny * N + 1, gzn = m->nz * N + 1;
+    const int ncx = d->nc[0], ncy = d->nc[1], ncz = d->nc[2], total = ncx * ncy * ncz;
+    auto blocks = [](int64_t cnt) { return (int)std::min<int64_t>((cnt + 255) / 256, 65535); };
+    NB_TRY(to_global(m, NB_FP64, r64, d->rg64, s));
+    k_c64_rx<<<blocks((int64_t)gzn * gyn * ncx), 256, 0, s>>>((int64_t)gzn * gyn, gxn, N, ncx,
+                                                             d->xi64, d->rg64, d->t1);
+    k_c64_rmid<<<blocks((int64_t)gzn * ncy * ncx), 256, 0, s>>>(gzn, gyn, ncy, ncx, N, d->xi64,
+                                                               d->t1, d->t2d);
+    k_c64_rmid<<<blocks(total), 256, 0, s>>>(1, gzn, ncz, ncx * ncy, N, d->xi64, d->t2d, d->ca);
+    // A_0^-1 = (Sz Sy Sx) diag(1 / (lx + ly + lz)) (Sz Sy Sx)^T
+    const int bt = blocks(total);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 0, 1, d->Sc64, nullptr, d->ca, d->cb);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 1, 1, d->Sc64, nullptr, d->cb, d->ca);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 2, 1, d->Sc64, d->lamc64, d->ca, d->cb);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 2, 0, d->Sc64, nullptr, d->cb, d->ca);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 1, 0, d->Sc64, nullptr, d->ca, d->cb);
+    k_c64_axis<<<bt, 256, 0, s>>>(ncx, ncy, ncz, 0, 0, d->Sc64, nullptr, d->cb, d->ca);
+    const int g = vec_grid(m->ctx, m->nL);
+    k_c64_prolong<<<g, kVecThreads, 0, s>>>(m->nL, m->nx, m->ny, N, d->xi64, d->ca, ncx, ncy, ncz,
+                                            x, c32_tmp);
+    NB_CUDA(cudaGetLastError());
+    NB_TRY(ax_local(m, NB_FP32, c32_tmp, w32_tmp, nullptr, nullptr, s));
+    NB_TRY(dssum(m, NB_FP32, w32_tmp, 1, s));
+    k_c64_subnorm<<<g, kVecThreads, 0, s>>>(m->nL, r64, w32_tmp, m->c32, part);
+    NB_CUDA(cudaGetLastError());
+    NB_TRY(sum_partials_dev(part, g, norm_dev, s));
+    m->launches += 14;
+    *applied = true;
+    return NB_OK;
 }
 
 // z = M r for FP32 L-vectors r (continuous, masked); coarse: two-level form.

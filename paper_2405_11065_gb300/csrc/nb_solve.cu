@@ -34,6 +34,9 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
                       bool odd, cudaStream_t s);
 nb_status fcg_schwarz(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o, bool keep,
                       bool odd, cudaStream_t s);
+nb_status schwarz_coarse_correct64(nb_mesh *m, double *r64, double *x, float *c32_tmp,
+                                   float *w32_tmp, double *part, double *norm_dev,
+                                   bool *applied, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -942,6 +945,24 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
             stagn = 0;
         }
         prev = rel;
+        // two-level Schwarz: the coarse-grid correction in FP64 on the FP64
+        // residual (x += R_0^T A_0^-1 R_0 r, r -= A that); the FP32 inner solves
+        // leave errors of FP32 size in the smoothest modes, whose residual the
+        // stopping test does not resolve
+        double rel_in = rel;
+        if (o->pc == NB_PC_SCHWARZ2 && !fell_back) {
+            bool applied = false;
+            NB_TRY(schwarz_coarse_correct64(m, m->r64, x, (float *)ws.x, (float *)ws.r, m->part64,
+                                            m->red_out + 1, &applied, s));
+            if (applied) {
+                NB_CUDA(cudaMemcpyAsync(m->red_host + 1, m->red_out + 1, sizeof(double),
+                                        cudaMemcpyDeviceToHost, s));
+                NB_CUDA(cudaStreamSynchronize(s));
+                rel_in = sqrt(m->red_host[1] / bn2);
+                if (!isfinite(rel_in)) { result = NB_BREAKDOWN; break; }
+                if (rel_in == 0.0) { rel = 0.0; result = NB_OK; break; }  // x is exact
+            }
+        }
         // inner solve on r32 = r64/||r64||, from zero
         k_demote<<<g, kVecThreads, 0, s>>>(m->nL, m->r64, m->red_out + 1, (float *)ws.r,
                                            (float *)ws.x);
@@ -975,7 +996,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         const bool short_prev = resume && prev_iters < kReliableShort;
         const double step_rtol =
             keep_dir && !short_prev ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
-        const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel));
+        const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel_in));
         if (use_learned && schwarz) {
             // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
             k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, cap),
@@ -1024,7 +1045,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         prev_ok = ws.scal_host->status == 0 && it > 0;
         prev_iters = it;
         prev_end = ws.scal_host->relres;  // the recurrence's drop over this solve
-        rel_start = rel;
+        rel_start = rel_in;
         const bool capped = resume && it >= cap && ws.scal_host->status == NB_NOT_CONVERGED;
         if (use_learned && ws.scal_host->status != 0 && !capped) {
             fell_back = true;  // the learned step failed: Jacobi-PCG from here on
