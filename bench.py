@@ -49,11 +49,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave the compact summary of the other workloads out of the line")
     ap.add_argument("--cpu-iters", type=int, default=40,
                     help="oracle iterations timed for the CPU baseline sample")
     ap.add_argument("--mode", choices=["full", "solve", "ax", "sweep", "batched", "learned", "vprec",
                                        "learned-step", "batched-step", "schwarz-step",
-                                       "schwarz2-step"],
+                                       "schwarz2-step", "extras"],
                     default="full",
                     help="solve: only the timed solves (for a kernel launch list); "
                          "ax: only a few launches of the operators (for a profiler capture); "
@@ -100,34 +102,69 @@ def oracle_iterations():
         return json.load(f)["mixed_16cube_n9"]
 
 
+def host_info():
+    """Host thread count and CPU model of the machine the bench runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count(), model
+
+
 def cpu_baseline(iters: int):
-    """The FP64 oracle as it stands, single-threaded on a host core: a
-    bounded sample of Jacobi-PCG iterations on the same problem, scaled to a
-    full solve with the oracle's own iteration count to 1e-10."""
+    """The FP64 oracle as it stands, on the host cores, on the same problem:
+    a full Jacobi-PCG solve to 1e-10 on all cores (measured, the reported
+    value), and a sample of `iters` iterations on one thread scaled to the
+    oracle's own iteration count.  Returns the baseline and the oracle's
+    solution continued to 1e-13 (the reference of the accuracy check)."""
     import oracle
     P = oracle.Problem(BOX)
     b = P.to_local(W.rhs_global(BOX, 0))
+    nproc, model = host_info()
+    n_all = oracle.threads()
+    oracle.threads(1)
     t0 = time.perf_counter()
     P.pcg(b, tol=0.0, maxit=iters)
-    dt = time.perf_counter() - t0
-    per_it = dt / iters
+    per_it1 = (time.perf_counter() - t0) / iters
+    oracle.threads(n_all)
+    t0 = time.perf_counter()
+    x, it, rel, _ = P.pcg_par(b, tol=RTOL, maxit=20000)
+    t_all = time.perf_counter() - t0
+    xo, _, rel_o, _ = P.pcg_par(b, tol=1e-13, maxit=20000, x0=x)
     full = oracle_iterations()
-    if full is None:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"{iters} oracle iterations, {per_it * 1e3:.1f} ms/iteration; "
-                          "iteration count to 1e-10 not yet recorded"}
-    t_solve = per_it * full["iterations"]
-    return {
-        "value": BOX.n_global / t_solve / 1e9,
+    one = {"ms_per_iteration": per_it1 * 1e3, "iterations_timed": iters}
+    if full is not None:
+        one["seconds_per_solve_extrapolated"] = per_it1 * full["iterations"]
+        one["value"] = BOX.n_global / one["seconds_per_solve_extrapolated"] / 1e9
+    base = {
+        "value": BOX.n_global / t_all / 1e9,
         "unit": UNIT,
-        "cores": 1,
+        "cores": n_all,
         "kind": "oracle",
-        "sample": (f"{iters} FP64 Jacobi-PCG iterations of the C oracle (1 thread) on the same "
-                   f"E=4096 N=9 problem, {per_it * 1e3:.1f} ms/iteration, scaled to the "
-                   f"{full['iterations']} iterations the oracle needs for 1e-10 "
-                   f"(oracle/iteration_counts.json): {t_solve:.1f} s per solve"),
-        "seconds_per_solve": t_solve,
+        "sample": (f"one full FP64 Jacobi-PCG solve to 1e-10 of the C oracle on {n_all} host "
+                   f"threads (OpenMP over elements, nodes and fixed chunks) on the same E=4096 "
+                   f"N=9 problem: {it} iterations in {t_all:.1f} s; also {iters} iterations on "
+                   f"1 thread: {per_it1 * 1e3:.1f} ms/iteration"),
+        "seconds_per_solve": t_all,
+        "iterations": it,
+        "one_thread": one,
+        "nproc": nproc,
+        "cpu_model": model,
     }
+    return base, xo
 
 
 class Clocks:
@@ -182,49 +219,91 @@ class Clocks:
                 "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def energy_per_solve(run, sync, device_uuid, seconds=2.0):
-    """Joules per call of run() (the paper's energy view): nvidia-smi samples
-    the board power every 50 ms during enough back-to-back calls to cover
-    about `seconds`; energy = mean power x wall time / calls."""
+class NvmlEnergy:
+    """The GPU's cumulative energy counter (NVML
+    nvmlDeviceGetTotalEnergyConsumption, millijoules since the driver loaded;
+    a read-only query) through the driver's own library."""
+
+    def __init__(self, device_uuid: str | None):
+        import ctypes as C
+        self.C = C
+        self.dev = None
+        try:
+            lib = C.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            dev = C.c_void_p()
+            if device_uuid:
+                ok = lib.nvmlDeviceGetHandleByUUID(device_uuid.encode(), C.byref(dev)) == 0
+            else:
+                ok = lib.nvmlDeviceGetHandleByIndex_v2(0, C.byref(dev)) == 0
+            if ok:
+                self.lib, self.dev = lib, dev
+        except Exception:
+            self.dev = None
+
+    def read_mj(self):
+        if self.dev is None:
+            return None
+        v = self.C.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.dev, self.C.byref(v)) != 0:
+            return None
+        return int(v.value)
+
+
+def energy_per_solve(run, sync, device_uuid, seconds=2.0, min_calls=10):
+    """Joules per call of run() (the paper's energy view): the GPU's energy
+    counter read before and after back-to-back calls (at least `min_calls`,
+    and enough to cover about `seconds`).  Without the counter: None."""
+    meter = NvmlEnergy(device_uuid)
+    if meter.read_mj() is None:
+        return None
     sync()
     t0 = time.perf_counter()
     run()
     sync()
-    reps = max(2, int(seconds / max(time.perf_counter() - t0, 1e-3)))
-    path = tempfile.mktemp(suffix=".csv")
-    args = ["nvidia-smi", "--query-gpu=power.draw", "--format=csv,noheader,nounits", "-lms", "50"]
-    if device_uuid:
-        args += ["-i", device_uuid]
-    try:
-        fh = open(path, "w")
-        proc = subprocess.Popen(args, stdout=fh, stderr=subprocess.DEVNULL)
-    except Exception:
-        return None
-    time.sleep(0.3)  # the sampler's first reading
+    reps = max(min_calls, int(seconds / max(time.perf_counter() - t0, 1e-3)))
+    e0 = meter.read_mj()
     t0 = time.perf_counter()
     for _ in range(reps):
         run()
     sync()
     wall = time.perf_counter() - t0
-    proc.terminate()
-    try:
-        proc.wait(timeout=5)
-    except Exception:
-        proc.kill()
-    fh.close()
-    watts = []
-    for line in open(path):
-        try:
-            watts.append(float(line.strip()))
-        except ValueError:
-            pass
-    os.unlink(path)
-    if len(watts) < 3:
+    e1 = meter.read_mj()
+    if e0 is None or e1 is None or e1 <= e0:
         return None
-    watts = watts[1:]  # drop the reading taken before the loop started
-    mean_w = statistics.mean(watts)
-    return {"joules_per_solve": mean_w * wall / reps, "solves": reps, "mean_watts": mean_w,
-            "samples": len(watts)}
+    joules = (e1 - e0) * 1e-3
+    return {"joules_per_solve": joules / reps, "solves": reps, "mean_watts": joules / wall,
+            "wall_s": wall}
+
+
+def fp64_peak_tflops(dev):
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM 4096^3 (2 n^3 flops), best
+    of 3 after a warm-up, CUDA events."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    bm = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, bm)
+    best = None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, bm)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, bm
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def l2_flush(buf, k):
+    """Evict L2 between timed steps: write `buf` (larger than L2), then read it
+    back so the writes' dirty lines are written back before the next step."""
+    buf.fill_(k & 0xFF)
+    buf.view(dtype=__import__("torch").int32).sum()
 
 
 def measured_peaks():
@@ -244,8 +323,9 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_tma.cuh", "paper_2405_11065_gb300/csrc/nb_ax_impl.cuh",
-              "paper_2405_11065_gb300/csrc/nb_ax.cu"]
+AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_pen.cuh", "paper_2405_11065_gb300/csrc/nb_ax_tma.cuh",
+              "paper_2405_11065_gb300/csrc/nb_ax_impl.cuh", "paper_2405_11065_gb300/csrc/nb_ax.cu",
+              "paper_2405_11065_gb300/csrc/nb_ax_f32.cu", "paper_2405_11065_gb300/csrc/nb_bulk.cuh"]
 
 
 def profiled_traffic(sha, kernel):
@@ -268,6 +348,10 @@ def profiled_traffic(sha, kernel):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands on all host
+    cores.  Each step is a bounded sample -- `per_step_iters` Jacobi-PCG
+    iterations of the parallel oracle on the E=4096 N=9 problem -- and the
+    value scales the mean step to the oracle's own iteration count to 1e-10."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -275,28 +359,33 @@ def run_reference(args):
     P = oracle.Problem(BOX)
     b = P.to_local(W.rhs_global(BOX, 0))
     full = oracle_iterations()
-    per_step_iters = 8
+    nproc, model = host_info()
+    cores = oracle.threads()
+    per_step_iters = 100
     for _ in range(args.warmup):
-        P.pcg(b, tol=0.0, maxit=2)
+        P.pcg_par(b, tol=0.0, maxit=10)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        P.pcg(b, tol=0.0, maxit=per_step_iters)
+        P.pcg_par(b, tol=0.0, maxit=per_step_iters)
         times.append(time.perf_counter() - t0)
-    per_it = sum(times) / (args.steps * per_step_iters)
-    t_solve = per_it * full["iterations"]
+    step_s = sum(times) / len(times)
+    t_solve = step_s / per_step_iters * full["iterations"]
     value = BOX.n_global / t_solve / 1e9
-    sample = (f"each step: {per_step_iters} FP64 Jacobi-PCG iterations of the C oracle "
-              f"(1 thread) on the E=4096 N=9 problem; scaled to the {full['iterations']} "
-              f"iterations the oracle needs for 1e-10")
+    sample = (f"each step: {per_step_iters} FP64 Jacobi-PCG iterations of the C oracle on "
+              f"{cores} host threads ({model}) on the E=4096 N=9 problem; value scaled to the "
+              f"{full['iterations']} iterations the oracle needs for 1e-10 "
+              f"({t_solve:.1f} s per solve)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "E": BOX.E, "N": BOX.N,
-                       "n_local": BOX.n_local, "n_global": BOX.n_global},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                       "n_local": BOX.n_local, "n_global": BOX.n_global,
+                       "step": f"{per_step_iters} oracle iterations"},
+            "seconds_per_solve_scaled": t_solve,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "nproc": nproc, "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -451,6 +540,110 @@ def run_learned(args):
     return 0
 
 
+def extra_workloads(nb, ctx, dev, flush, hbm_peak):
+    """The other workloads, compact, for the default line: the roofline sweep
+    at its largest size (E = 32^3 at N = 7 and 9), the 256-problem batch, and
+    the learned preconditioner against Jacobi on one held-out right-hand side."""
+    import torch
+    out = {}
+    sweep = []
+    for N in (7, 9):
+        box = W.Box(32, 32, 32, N, 0.05)
+        mesh = nb.Mesh.from_box(ctx, box)
+        nL = box.n_local
+        mesh.autotune(nb.NB_FP32, reps=2, flush=flush)
+        ms_ax = mesh.time_ax(nb.NB_FP32, cg_step=False, reps=5, flush=flush)
+        ms_cg = mesh.time_ax(nb.NB_FP32, cg_step=True, reps=5, flush=flush)
+        b = _rhs_local(nb, mesh, box, 0, dev)
+        x = torch.zeros_like(b)
+        o = nb.default_opts(prec=nb.NB_FP32, rtol=RTOL)
+        mesh.solve(b, x, o)
+        x.zero_()
+        st = mesh.solve(b, x, o)
+        sweep.append({"E": box.E, "N": N, "n_local": nL, "kernel": mesh.ax_variant_name(nb.NB_FP32),
+                      "ax_ms": ms_ax, "ax_hbm_frac": 32 * nL / (ms_ax * 1e-3) / 1e9 / hbm_peak,
+                      "cg_step_ms": ms_cg,
+                      "cg_step_hbm_frac": 44 * nL / (ms_cg * 1e-3) / 1e9 / hbm_peak,
+                      "mixed_solve_ms": st["seconds"] * 1e3, "iters": st["iters"],
+                      "rel_res": st["rel_res"], "status": st["status"]})
+        mesh.close()
+        del b, x
+        torch.cuda.empty_cache()
+    out["sweep_32cube"] = sweep
+
+    probs = W.batched_problems(256)
+    boxes = [bx for bx, _ in probs]
+    t0 = time.perf_counter()
+    batch = nb.Batch(ctx, boxes)
+    setup_s = time.perf_counter() - t0
+    batch.autotune(reps=2, flush=flush)
+    ug = torch.from_numpy(np.concatenate([W.rhs_global(bx, sd) for bx, sd in probs])).to(dev)
+    b = torch.empty(batch.n_local, dtype=torch.float64, device=dev)
+    batch.to_local(ug, b)
+    x = torch.zeros_like(b)
+    o = nb.default_opts(prec=nb.NB_FP32, maxiter=400000)
+    batch.solve(b, x, o)
+    x.zero_()
+    st = batch.solve(b, x, o)
+    iters = [p["iters"] for p in st["problems"]]
+    out["batched_256"] = {"problems": len(boxes), "n_local": batch.n_local,
+                          "n_global": batch.n_global, "setup_s": setup_s,
+                          "solve_ms": st["seconds"] * 1e3,
+                          "gdofs_solved_per_s": batch.n_global / st["seconds"] / 1e9,
+                          "batched_iterations": st["iters"], "max_problem_iters": max(iters),
+                          "median_problem_iters": float(np.median(iters)),
+                          "all_ok": all(p["status"] == 0 for p in st["problems"])}
+    batch.close()
+    del b, x, ug
+    torch.cuda.empty_cache()
+
+    box = W.LEARNED_16CUBE_N7
+    mesh = nb.Mesh.from_box(ctx, box)
+    model = nb.Model(ctx, box.N, 96, seed=7)
+    snaps = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 800]
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    for sd in W.TRAIN_SEEDS:
+        X, T = nb.Model.collect(mesh, _rhs_local(nb, mesh, box, sd, dev), snaps, 120, seed=sd)
+        Xs.append(X)
+        Ts.append(T)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    model.train(X, T, epochs=40, batch=256, lr=1e-3)
+    loss = model.train(X, T, epochs=20, batch=256, lr=3e-4)
+    model.attach(mesh)
+    train_s = time.perf_counter() - t0
+    sd = W.HELDOUT_SEEDS[0]
+    b = _rhs_local(nb, mesh, box, sd, dev)
+    row = {"E": box.E, "N": box.N, "pairs": int(X.shape[0]), "params": model.nparam,
+           "train_s": train_s, "final_loss": loss, "rtol": 1e-8, "heldout_seed": sd}
+    for name, pc in (("jacobi", nb.NB_PC_JACOBI), ("learned", nb.NB_PC_LEARNED)):
+        x = torch.zeros_like(b)
+        o = nb.default_opts(prec=nb.NB_FP32, pc=pc, rtol=1e-8)
+        mesh.solve(b, x, o)
+        ms = []
+        for _ in range(3):
+            x.zero_()
+            st = mesh.solve(b, x, o)
+            ms.append(st["seconds"] * 1e3)
+        row[name] = {"iters": st["iters"], "ms": statistics.median(ms), "status": st["status"],
+                     "rel_res": st["rel_res"]}
+    out["learned_16cube_N7"] = row
+    mesh.close()
+    return out
+
+
+def run_extras(args):
+    """Only the compact summary of the other workloads (one JSON line)."""
+    import torch
+    import paper_2405_11065_gb300 as nb
+    dev = torch.device("cuda", 0)
+    ctx = nb.Context(0)
+    flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
+    peak, _ = measured_peaks()
+    print(json.dumps({"mode": "extras", **extra_workloads(nb, ctx, dev, flush, peak)}), flush=True)
+    return 0
+
+
 def run_learned_step(args):
     """Profiling aid: `--steps` flexible-CG steps with the learned
     preconditioner on the learned workload's mesh (E=4096, N=7) and an
@@ -573,15 +766,15 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.mode in ("sweep", "batched", "learned", "vprec", "learned-step", "batched-step",
-                     "schwarz-step", "schwarz2-step"):
+                     "schwarz-step", "schwarz2-step", "extras"):
         return {"sweep": run_sweep, "batched": run_batched, "learned": run_learned,
                 "vprec": run_vprec, "learned-step": run_learned_step,
                 "batched-step": run_batched_step, "schwarz-step": run_schwarz_step,
-                "schwarz2-step": run_schwarz_step}[args.mode](args)
+                "schwarz2-step": run_schwarz_step, "extras": run_extras}[args.mode](args)
     rank, world, local = dist_env()
-    cpu = None
+    cpu, x_oracle = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_iters)  # host only, before the first GPU call
+        cpu, x_oracle = cpu_baseline(args.cpu_iters)  # host only, before the first GPU call
 
     import torch
     import paper_2405_11065_gb300 as nb
@@ -639,7 +832,7 @@ def main():
     stats = []
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(k & 0xFF)  # evict L2 between steps, outside the events
+        l2_flush(flush, k)  # evict L2 between steps, outside the events
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -674,7 +867,7 @@ def main():
     mesh.solve(b, x64, o64)
     fp64_ms, fp64_stats = [], None
     for _ in range(2):
-        flush.fill_(1)
+        l2_flush(flush, 1)
         x64.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -694,7 +887,7 @@ def main():
         mesh.solve(b, xs, o_pc)
         ms, st = [], None
         for _ in range(3):
-            flush.fill_(3)
+            l2_flush(flush, 3)
             xs.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -708,8 +901,14 @@ def main():
     sw2_t, sw2_stats = time_pc(nb.NB_PC_SCHWARZ2)
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
 
+    # the mixed solution against the oracle's (all host cores, to 1e-13)
+    oracle_diff = None
+    if x_oracle is not None:
+        xm = x.cpu().numpy()
+        oracle_diff = float(np.linalg.norm(xm - x_oracle) / np.linalg.norm(x_oracle))
+
     # energy to solution, mixed vs FP64 (outside the timed region; the GPU's
-    # own energy counter read by nvidia-smi before and after a run of solves)
+    # cumulative energy counter read before and after at least 10 solves)
     def _mixed():
         x.zero_()
         mesh.solve(b, x, opts)
@@ -724,8 +923,8 @@ def main():
     energy = {"mixed": en_m, "fp64": en_d,
               "reduction_vs_fp64": (1.0 - en_m["joules_per_solve"] / en_d["joules_per_solve"])
               if en_m and en_d else None,
-              "method": "board power sampled by nvidia-smi every 50 ms over back-to-back solves "
-                        "x their wall time"}
+              "method": "NVML total energy counter (nvmlDeviceGetTotalEnergyConsumption) "
+                        "read before and after >= 10 back-to-back solves"}
 
     # the paper's accuracy metric: AE_k = |r_m,k - r_d,k| between the residual
     # histories of an all-FP32 CG loop (the paper's mixed version, no
@@ -759,11 +958,17 @@ def main():
                      "variant": tune[pname]["variant"]}
     n = BOX.n
     ax["fp64"]["ax_gflops"] = (12 * n + 15) * nL / (ax["fp64"]["ax_ms"] * 1e-3) / 1e9
+    fp64_peak = fp64_peak_tflops(dev)
+    ax["fp64"]["fp64_peak_tflops_measured"] = fp64_peak
+    ax["fp64"]["fp64_peak_kind"] = "cuBLAS DGEMM 4096^3 on this GPU (best of 3)"
+    ax["fp64"]["frac_of_fp64_peak"] = ax["fp64"]["ax_gflops"] / (fp64_peak * 1e3)
+    ax["fp64"]["frac_of_fp64_nominal_1250_gflops"] = ax["fp64"]["ax_gflops"] / 1250.0
+    for pname, prec in (("fp32", nb.NB_FP32), ("fp64", nb.NB_FP64)):
+        ax[pname]["kernel"] = mesh.ax_variant_name(prec)
     sha = source_sha(AX_SOURCES)
     bytes_cg = 11 * 4 * nL
     achieved = bytes_cg / (ax["fp32"]["cg_step_ms"] * 1e-3) / 1e9
-    kname = ("k_ax_cc<float,%d,M,PUPD>" % n) if tune["fp32"]["variant"] in (0, 1) else \
-        ("k_ax_tma<float,%d,PUPD>" % n)
+    kname = mesh.ax_variant_name(nb.NB_FP32)
     traffic = profiled_traffic(sha, kname)
     roofline = {"kernel": kname + " (fused p-update + operator + pap, FP32)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -779,7 +984,7 @@ def main():
         mesh.solve_host(bh, xh, opts)
         e2e_ms = []
         for _ in range(max(2, min(args.steps, 5))):
-            flush.fill_(2)
+            l2_flush(flush, 2)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -792,6 +997,11 @@ def main():
                "h2d_bytes_per_step": 8 * BOX.n_global, "d2h_bytes_per_step": 8 * BOX.n_global,
                "ms_per_step": te, "status": outh["status"]}
 
+    # the other workloads, compact (outside the timed region; one replica only)
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = extra_workloads(nb, ctx, dev, flush, hbm_peak)
+
     launches = int(sum(s["launches"] for s in stats))
     value = whole_job_value(world, BOX.n_global, args.steps, max_ms)
     if rank == 0:
@@ -802,7 +1012,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "E": BOX.E, "N": BOX.N, "n_local": BOX.n_local,
                        "n_global": BOX.n_global, "deform": BOX.deform, "rhs": "U[-1,1) per unique node, seed = rank",
-                       "l2": "flushed between timed steps (512 MB write)",
+                       "l2": "flushed between timed steps (512 MB written, then read back)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -822,7 +1032,9 @@ def main():
             "rel_res": {"mixed": stats[-1]["rel_res"], "fp64": fp64_stats["rel_res"],
                         "mixed_recomputed": true_rel},
             "mixed_vs_fp64_solution_rel_diff": sol_diff,
+            "mixed_vs_oracle_solution_rel_diff": oracle_diff,
             "accuracy_ae_mae": accuracy, "energy": energy,
+            "other_workloads": extras,
             "all_steps_converged": ok,
             "ax": ax,
             "wall_s_timed_region": wall,

@@ -229,9 +229,11 @@ nb_status nb_solve_host(nb_mesh *mesh, const nb_opts *opts,
                         const double *bg_host, double *xg_host, nb_stats *stats);
 
 /* Measure the operator kernel: `reps` launches on the context's stream, each
- * bracketed by CUDA events, with `flush_bytes` of `flush_dev` overwritten
- * between launches (outside the events) to evict the L2 cache; flush_dev may
- * be NULL.  cg_step = 0 times ax (u -> w, the nb_ax kernel); cg_step = 1 times
+ * bracketed by CUDA events, with `flush_bytes` of `flush_dev` overwritten and
+ * then read back between launches (outside the events) to evict the L2 cache
+ * and write its dirty lines back, so every launch starts on a clean cache
+ * holding none of its data; flush_dev may be NULL (flush_bytes should exceed
+ * the L2 size).  cg_step = 0 times ax (u -> w, the nb_ax kernel); cg_step = 1 times
  * the fused CG-step kernel of the solver (p = dinv*r + beta*p, w = A_L p,
  * partial p.w) on the mesh's solve workspace.  variant: -1 for the current
  * choice, else a kernel variant index (see nb_autotune).  *ms_out = mean
@@ -247,6 +249,16 @@ int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
  * or -1 for the built-in default; the choice nb_autotune would otherwise
  * make by timing.  Errors: NB_ERR_ARG (index out of range, bad prec). */
 nb_status nb_set_ax_variant(nb_mesh *mesh, nb_prec prec, int variant);
+
+/* Kernel name of operator variant `variant` for (mesh order, prec), or of
+ * the variant in use with variant = -1 (a static string owned by the
+ * library; NULL for an index out of range, a NULL mesh or a bad prec). */
+const char *nb_ax_variant_name(const nb_mesh *mesh, nb_prec prec, int variant);
+
+/* Index of the operator variant that operator applications and solves in
+ * precision prec use now (the built-in default until one is chosen), or -1
+ * for a NULL mesh or a bad prec. */
+int nb_ax_variant_in_use(const nb_mesh *mesh, nb_prec prec);
 
 /* Autotuner: time every operator variant for this mesh's order and
  * precision with nb_time_ax (cg_step = 1, `reps` launches each) and keep the

@@ -94,6 +94,8 @@ def _load():
         "nb_time_ax": (i32, [vp, i32, i32, i32, i32, vp, C.c_size_t, C.POINTER(dbl)]),
         "nb_ax_variants": (i32, [vp, i32]),
         "nb_set_ax_variant": (i32, [vp, i32, i32]),
+        "nb_ax_variant_name": (C.c_char_p, [vp, i32, i32]),
+        "nb_ax_variant_in_use": (i32, [vp, i32]),
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
         "nb_apply_vprec": (i32, [vp, i32, vp, vp]),
         "nb_schwarz_apply": (i32, [vp, vp, vp]),
@@ -315,6 +317,14 @@ class Mesh:
 
     def ax_variants(self, prec) -> int:
         return lib.nb_ax_variants(self.h, prec)
+
+    def ax_variant_name(self, prec, variant=-1) -> str:
+        """Kernel name of a variant (-1: the one in use)."""
+        r = lib.nb_ax_variant_name(self.h, prec, int(variant))
+        return r.decode() if r else ""
+
+    def ax_variant_in_use(self, prec) -> int:
+        return lib.nb_ax_variant_in_use(self.h, prec)
 
     def set_ax_variant(self, prec, variant=-1):
         """Use operator variant ``variant`` (-1: the default) from now on."""

@@ -440,7 +440,10 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) st = NB_ERR_CUDA;
     for (int r = 0; st == NB_OK && r < reps; ++r) {
-        if (flush_dev && flush_bytes) cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, s);
+        if (flush_dev && flush_bytes) {
+            st = l2_flush(m->ctx, flush_dev, flush_bytes, r, s);
+            if (st != NB_OK) break;
+        }
         // beta = 0 and not done before every launch: the fused step's last
         // block may stop the scalars (pap <= 0 on arbitrary data), and a
         // stopped state would let the next launch return at once
@@ -465,6 +468,19 @@ extern "C" nb_status nb_time_ax(nb_mesh *m, nb_prec prec, int cg_step, int varia
     NB_CUDA(e);
     *ms_out = tot / reps;
     return NB_OK;
+}
+
+extern "C" const char *nb_ax_variant_name(const nb_mesh *m, nb_prec prec, int variant)
+{
+    if (!m || !prec_ok(prec)) return nullptr;
+    if (variant == -1) variant = ax_variant_in_use(m, prec);
+    return ax_variant_name(m, prec, variant);
+}
+
+extern "C" int nb_ax_variant_in_use(const nb_mesh *m, nb_prec prec)
+{
+    if (!m || !prec_ok(prec)) return -1;
+    return ax_variant_in_use(m, prec);
 }
 
 extern "C" nb_status nb_set_ax_variant(nb_mesh *m, nb_prec prec, int variant)

@@ -119,6 +119,35 @@ static AxKind kind_of(const nb_mesh *m, nb_prec prec)
     return default_kind(m, prec);
 }
 
+// Kernel name of variant v (NULL outside the range).
+const char *ax_variant_name(const nb_mesh *m, nb_prec prec, int v)
+{
+    AxKind k[5];
+    const int c = ax_kinds(m, prec, k);
+    if (c == 0) return v == 0 ? "k_ax_tc (mma.sync tensor-core contractions)" : nullptr;
+    if (v < 0 || v >= c) return nullptr;
+    switch (k[v]) {
+        case kCcSmall: return "k_ax_cc (smaller element group)";
+        case kCcLarge: return "k_ax_cc (larger element group)";
+        case kTma: return "k_ax_tma (column per thread, bulk-copy ring)";
+        case kPen2: return "k_ax_pen (pencil passes, two bulk-copy stages)";
+        case kPen1: return "k_ax_pen (pencil passes, one bulk-copy stage)";
+    }
+    return nullptr;
+}
+
+// Index of the variant in use for (mesh, prec) (the default when none is set).
+int ax_variant_in_use(const nb_mesh *m, nb_prec prec)
+{
+    AxKind k[5];
+    const int c = ax_kinds(m, prec, k);
+    if (c == 0) return 0;
+    const AxKind cur = kind_of(m, prec);
+    for (int v = 0; v < c; ++v)
+        if (k[v] == cur) return v;
+    return 0;
+}
+
 // mode: 0 plain operator, 1 fused Jacobi CG step, 2 fused flexible-CG step
 // (FP32 bulk-copy kinds only).
 template <typename T>

@@ -1032,7 +1032,7 @@ extern "C" nb_status nb_batch_autotune(nb_batch *B, int reps, void *flush, size_
         for (int v = 0; v < nv; ++v) {
             double tot = 0.0;
             for (int r = 0; r <= reps; ++r) {  // the first launch is a warm-up
-                if (flush && flush_bytes) cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+                if (flush && flush_bytes) NB_TRY(l2_flush(B->ctx, flush, flush_bytes, r, s));
                 cudaEventRecord(e0, s);
                 NB_TRY(bax_group<float>(B, gi, v, true, nullptr, (float *)B->ws32.w,
                                         (const float *)B->ws32.r, B->dinv32, (float *)B->ws32.p,

@@ -246,6 +246,9 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
                      void *w, CgScalars *scal, double *pap_part, int *nparts,
                      cudaStream_t s);
 int ax_variant_count(const nb_mesh *m, nb_prec prec);
+nb_status l2_flush(const nb_ctx *ctx, void *buf, size_t bytes, int pattern, cudaStream_t s);
+const char *ax_variant_name(const nb_mesh *m, nb_prec prec, int v);
+int ax_variant_in_use(const nb_mesh *m, nb_prec prec);
 
 // ---- gather-scatter and vectors (nb_vec.cu)
 nb_status dssum(nb_mesh *m, nb_prec prec, void *u, int masked, cudaStream_t s);
