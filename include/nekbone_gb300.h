@@ -250,6 +250,15 @@ int nb_ax_variants(const nb_mesh *mesh, nb_prec prec);
  * make by timing.  Errors: NB_ERR_ARG (index out of range, bad prec). */
 nb_status nb_set_ax_variant(nb_mesh *mesh, nb_prec prec, int variant);
 
+/* Kernel of the FP32 iteration's update with the folded direct-stiffness
+ * summation (x += alpha p, r -= alpha dssum(w), the next dots), for even
+ * N + 1: 0 the built-in choice (1 up to N = 9, else 2), 1 contiguous element
+ * ranges per block with the pair positions fixed per thread, 2 node pairs
+ * dealt round-robin over a persistent grid, 3 element ranges with x, r, p
+ * and dinv streamed by bulk copies into a two-stage shared-memory ring.  All
+ * sum in the same order (bit-identical results).  Errors: NB_ERR_ARG. */
+nb_status nb_set_update_variant(nb_mesh *mesh, int variant);
+
 /* Kernel name of operator variant `variant` for (mesh order, prec), or of
  * the variant in use with variant = -1 (a static string owned by the
  * library; NULL for an index out of range, a NULL mesh or a bad prec). */

@@ -94,6 +94,7 @@ def _load():
         "nb_time_ax": (i32, [vp, i32, i32, i32, i32, vp, C.c_size_t, C.POINTER(dbl)]),
         "nb_ax_variants": (i32, [vp, i32]),
         "nb_set_ax_variant": (i32, [vp, i32, i32]),
+        "nb_set_update_variant": (i32, [vp, i32]),
         "nb_ax_variant_name": (C.c_char_p, [vp, i32, i32]),
         "nb_ax_variant_in_use": (i32, [vp, i32]),
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
@@ -325,6 +326,10 @@ class Mesh:
 
     def ax_variant_in_use(self, prec) -> int:
         return lib.nb_ax_variant_in_use(self.h, prec)
+
+    def set_update_variant(self, variant=0):
+        """Kernel of the FP32 update with the folded summation (0: built-in)."""
+        check(lib.nb_set_update_variant(self.h, int(variant)))
 
     def set_ax_variant(self, prec, variant=-1):
         """Use operator variant ``variant`` (-1: the default) from now on."""

@@ -483,6 +483,16 @@ extern "C" int nb_ax_variant_in_use(const nb_mesh *m, nb_prec prec)
     return ax_variant_in_use(m, prec);
 }
 
+extern "C" nb_status nb_set_update_variant(nb_mesh *m, int variant)
+{
+    if (!m || variant < 0 || variant > 3) return arg_error("mesh or update variant");
+    if (m->update_kind != variant) {
+        m->update_kind = variant;
+        ++m->ax_epoch;  // captured iteration graphs hold the old kernel
+    }
+    return NB_OK;
+}
+
 extern "C" nb_status nb_set_ax_variant(nb_mesh *m, nb_prec prec, int variant)
 {
     if (!m || !prec_ok(prec)) return arg_error("mesh or prec");

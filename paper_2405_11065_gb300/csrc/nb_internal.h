@@ -215,8 +215,10 @@ struct nb_mesh {
     nb::AxConfig ax_cfg[4];
     int update_kind = 0;       // FP32 update with the folded summation, even n:
                                // 1 element ranges (k_cg_update_el), 2 node pairs
-                               // (k_cg_update_pairs), 0 element ranges where an
-                               // element takes at most two rounds of 256 pairs
+                               // (k_cg_update_pairs), 3 element ranges with
+                               // bulk-copied vectors (k_cg_update_tma), 0 element
+                               // ranges where an element takes at most two rounds
+                               // of 256 pairs, else node pairs (measured fastest)
     int ax_epoch = 0;          // bumped whenever an operator variant choice changes:
                                // captured iteration graphs of an older epoch are stale
     int *kerr = nullptr;             // device flag: a pipelined kernel's wait timed out

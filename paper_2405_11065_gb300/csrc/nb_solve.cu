@@ -24,6 +24,7 @@
 
 #include <algorithm>
 
+#include "nb_bulk.cuh"
 #include "nb_cg_dev.cuh"
 
 namespace nb {
@@ -497,15 +498,151 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
+// k_cg_update_el with the element's contiguous x, r, p and dinv blocks
+// streamed by bulk copies (cp.async.bulk) into a two-stage shared-memory ring,
+// two elements ahead: each thread first issues the loads of w over the
+// copies of its pairs (the only scattered reads), then waits for the ring,
+// then updates from shared memory and stores x and r.  Same sums in the same
+// order as k_cg_update_el.  Every wait is bounded (one second); a block that
+// times out sets *err and the solve's status, drains its copies and stops.
+template <int n>
+constexpr int upd_tma_vecs()
+{
+    return 4;  // x, r, p, dinv
+}
+
+template <int n>
+__global__ void __launch_bounds__(256)
+k_cg_update_tma(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
+                CgScalars *__restrict__ sc, float *__restrict__ x, float *__restrict__ r,
+                const float *__restrict__ p, const float *__restrict__ w,
+                const float *__restrict__ dinv, double *__restrict__ part, int *__restrict__ err)
+{
+    static_assert(n % 2 == 0, "pairs of nodes need an even n");
+    using V = float2;
+    constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
+    constexpr int R = (P + 255) / 256;
+    constexpr int NV = upd_tma_vecs<n>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *stage = reinterpret_cast<float *>(smem_raw);  // [2][NV][n3]: x, r, p, dinv
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ double sred[32];
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    const int sx = n3 - N, sy = nx * n3 - N * n, sz = nx * ny * n3 - N * n2;
+    int loc[R], fl[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int t = threadIdx.x + 256 * q;
+        const int i0 = 2 * (t % h), j = (t / h) % n, k = t / (h * n);
+        loc[q] = t < P ? k * n2 + j * n + i0 : -1;
+        fl[q] = (i0 == 0) | ((i0 + 1 == N) << 1) | ((j == 0) << 2) | ((j == N) << 3) |
+                ((k == 0) << 4) | ((k == N) << 5);
+    }
+    DotAcc<float> a, b;
+    const int e0 = (int)((int64_t)E * blockIdx.x / gridDim.x);
+    const int e1 = (int)((int64_t)E * (blockIdx.x + 1) / gridDim.x);
+    const int cnt = e1 - e0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {  // element e0 + t into stage t & 1
+        const int64_t off = (int64_t)(e0 + t) * n3;
+        float *dst = stage + (t & 1) * NV * n3;
+        constexpr uint32_t bytes = (uint32_t)(n3 * sizeof(float));
+        mbar_expect_tx(&bar[t & 1], NV * bytes);
+        bulk_g2s(dst + 0 * n3, x + off, bytes, &bar[t & 1]);
+        bulk_g2s(dst + 1 * n3, r + off, bytes, &bar[t & 1]);
+        bulk_g2s(dst + 2 * n3, p + off, bytes, &bar[t & 1]);
+        bulk_g2s(dst + 3 * n3, dinv + off, bytes, &bar[t & 1]);
+    };
+    if (threadIdx.x == 0) {
+        if (cnt > 0) issue(0);
+        if (cnt > 1) issue(1);
+    }
+    int t = 0;
+    for (; t < cnt; ++t) {
+        const int e = e0 + t;
+        const int exy = dnx.div(e), ex = e - exy * nx;
+        const int ez = dny.div(exy), ey = exy - ez * ny;
+        const int nb = (ex > 0) | ((ex < nx - 1) << 1) | ((ey > 0) << 2) | ((ey < ny - 1) << 3) |
+                       ((ez > 0) << 4) | ((ez < nz - 1) << 5);
+        float wa[R], wb[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (loc[q] < 0) continue;
+            const int f = fl[q] & nb;
+            gs_sum_pair_flags<float, int>(w, e * n3 + loc[q], (f & 1) != 0, (f & 2) != 0,
+                                          (f >> 2) & 1, (f >> 3) & 1, (f >> 4) & 1, (f >> 5) & 1,
+                                          sx, sy, sz, wa[q], wb[q]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+        if (__syncthreads_or(!ok)) break;
+        const float *sg = stage + (t & 1) * NV * n3;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (loc[q] < 0) continue;
+            const int lq = loc[q];
+            V xv = *reinterpret_cast<const V *>(sg + 0 * n3 + lq);
+            V rv = *reinterpret_cast<const V *>(sg + 1 * n3 + lq);
+            const V pv = *reinterpret_cast<const V *>(sg + 2 * n3 + lq);
+            const V dv = *reinterpret_cast<const V *>(sg + 3 * n3 + lq);
+            float wl[2] = {wa[q], wb[q]};
+            float *xs[2] = {&xv.x, &xv.y}, *rs[2] = {&rv.x, &rv.y};
+            const float ps[2] = {pv.x, pv.y}, ds[2] = {dv.x, dv.y};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (ds[u] == 0.f) wl[u] = 0.f;  // Dirichlet node
+                *xs[u] = *xs[u] + alpha * ps[u];
+                *rs[u] = *rs[u] - alpha * wl[u];
+                if (owner_copy(ds[u])) {
+                    a.add(*rs[u] * (ds[u] * *rs[u]));
+                    b.add(*rs[u] * *rs[u]);
+                }
+            }
+            const int64_t l = (int64_t)e * n3 + lq;
+            *reinterpret_cast<V *>(x + l) = xv;
+            *reinterpret_cast<V *>(r + l) = rv;
+        }
+        __syncthreads();  // stage t & 1 consumed
+        if (threadIdx.x == 0 && t + 2 < cnt) issue(t + 2);
+    }
+    if (t < cnt) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            sc->status = NB_BREAKDOWN;
+            sc->done = 1;
+            for (int tt = t; tt < t + 2 && tt < cnt; ++tt)
+                mbar_wait_bounded(&bar[tt & 1], (uint32_t)((tt >> 1) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    double ta = block_sum(a.value(), sred);
+    double tb = block_sum(b.value(), sred);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = ta;
+        part[gridDim.x + blockIdx.x] = tb;
+    }
+    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+}
+
 // Grid of a pair kernel: one wave of its resident blocks (per device, from
 // the occupancy of its register count), and no more blocks than pairs need.
-template <typename K>
-static int update_pairs_grid(K kern, int sm_count, int npairs)
+// (One cache per kernel: the template parameter is the kernel itself, not its
+// type, which kernels of different orders share.)
+template <auto kern>
+static int update_pairs_grid(int sm_count, int npairs, size_t smem = 0)
 {
     static int per_sm_dev[kMaxDevices] = {};
     int &per_sm = device_slot(per_sm_dev);
     if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess ||
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
     }
@@ -535,16 +672,24 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
         return true;
 #define NB_UGP(NN)                                                                              \
     case NN:                                                                                    \
-        if (m->update_kind == 1 ||                                                              \
-            (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {               \
-            pgrid = update_pairs_grid(k_cg_update_el<float, NN>, m->ctx->sm_count,              \
+        if (m->update_kind == 3) {                                                              \
+            constexpr size_t sm_ = 2 * upd_tma_vecs<NN>() * sizeof(float) * NN * NN * NN;       \
+            pgrid = update_pairs_grid<k_cg_update_tma<NN>>(m->ctx->sm_count,                    \
+                                      (int)std::min<int64_t>(m->E * 256, npairs), sm_);         \
+            pgrid = (int)std::min<int64_t>(pgrid, m->E);                                        \
+            k_cg_update_tma<NN><<<pgrid, 256, sm_, s>>>(                                        \
+                (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
+                (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part, m->kerr);  \
+        } else if (m->update_kind == 1 ||                                                       \
+                   (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {        \
+            pgrid = update_pairs_grid<k_cg_update_el<float, NN>>(m->ctx->sm_count,              \
                                       (int)std::min<int64_t>(m->E * 256, npairs));              \
             pgrid = (int)std::min<int64_t>(pgrid, m->E);                                        \
             k_cg_update_el<float, NN><<<pgrid, 256, 0, s>>>(                                    \
                 (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
                 (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);           \
         } else {                                                                                \
-            pgrid = update_pairs_grid(k_cg_update_pairs<float, NN>, m->ctx->sm_count, npairs);  \
+            pgrid = update_pairs_grid<k_cg_update_pairs<float, NN>>(m->ctx->sm_count, npairs);  \
             k_cg_update_pairs<float, NN><<<pgrid, 256, 0, s>>>(                                 \
                 npairs, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x, (float *)ws.r,   \
                 (const float *)ws.p, (const float *)ws.w, dinv, part);                          \

@@ -392,3 +392,32 @@ def test_variant_change_after_a_solve_takes_effect(nb, ctx):
     assert not torch.equal(x0, y), "variants 0 and last give identical bits: no evidence"
     with pytest.raises(nb.NbError):
         m1.set_ax_variant(nb.NB_FP32, last + 1)
+
+
+@pytest.mark.parametrize("box", [Box(3, 3, 2, 9, 0.05), Box(4, 3, 2, 7, 0.05), Box(2, 2, 3, 11, 0.05)],
+                         ids=lambda b: f"{b.nx}x{b.ny}x{b.nz}N{b.N}")
+def test_update_variants_are_bit_identical(nb, ctx, box):
+    """The kernels of the FP32 update with the folded summation (element
+    ranges, node pairs, bulk-copied element ranges) sum the copies of every
+    node in the same order: the mixed solve gives the same bits with each,
+    and reaches the oracle's solution."""
+    import torch
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    bl = P.to_local(rhs_global(box, 8))
+    b = _t(bl)
+    xs = []
+    for v in (1, 2, 3, 0):
+        mesh.set_update_variant(v)
+        x = torch.zeros_like(b)
+        out = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32))
+        assert out["status"] == 0, (v, out)
+        xs.append(x)
+    for x in xs[1:]:
+        assert torch.equal(x, xs[0])
+    xo, _, _, _ = P.pcg(bl, tol=1e-13, maxit=20000)
+    xg = xs[0].cpu().numpy()
+    assert P.true_relres(bl, xg) < 1.01e-10
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    with pytest.raises(nb.NbError):
+        mesh.set_update_variant(4)
