@@ -446,6 +446,75 @@ nb_status nb_schwarz_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
  * direction or 24576 interior vertices.  Used by NB_PC_SCHWARZ2. */
 nb_status nb_schwarz2_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
 
+/* ------------------------------------------------------------------------
+ * Slab partition along z and the CG iteration in split phases.  Nekbone runs
+ * its CG on MPI ranks that each own a set of elements (Section 4.1: dssum
+ * exchanges the shared nodes, glsc3 ends in a global sum; Section 7.2 /
+ * Table 5 scale it over ranks).  Here a box of nx x ny x nz elements is cut
+ * into z-slabs, one mesh per slab (on one or several GPUs, in one or several
+ * processes); the slabs share the node planes between them.  A driver runs
+ * Table 1's loop by calling, on every slab, nb_cg_step (then summing the
+ * slabs' p.w), the summation of w (nb_slab_face before nb_dssum, the
+ * neighbours' planes added with nb_slab_face_add after it), and nb_cg_update
+ * (then summing the slabs' dots); paper_2405_11065_gb300/slab.py is such a
+ * driver, in-process or over torch.distributed.
+ * ------------------------------------------------------------------------ */
+
+/* The slab z0 <= ez < z1 of the nx x ny x nz box of nb_setup_mesh (same
+ * arguments otherwise, the box's geometry and deformation): a mesh of
+ * nx x ny x (z1 - z0) elements.  After nb_setup_gs its Dirichlet boundary is
+ * the box's; the plane at z0 (if z0 > 0) and at z1 (if z1 < nz) are free
+ * interface planes, the lower one owned by the slab below (its copies are
+ * not owners in the dots), and the dot-product weights c count the copies
+ * on both sides.  Its Jacobi diagonal lacks the neighbours' part on the
+ * interface planes until nb_slab_finish_diag.
+ * Errors: NB_ERR_ARG (bounds, sizes), NB_ERR_MESH, NB_ERR_OOM. */
+nb_status nb_setup_slab(nb_ctx *ctx, int nx, int ny, int nz, int z0, int z1, int N,
+                        double deform, nb_mesh **out);
+
+/* Interface plane side (0: lower, 1: upper) of a slab: face_dev[gx + Gx gy]
+ * (Gx = nx N + 1, Gy = ny N + 1 values, device, precision's type) = the sum
+ * over the slab's copies of each plane node of the L-vector u_dev, taken
+ * before nb_dssum.  Errors: NB_ERR_ARG (no interface on that side). */
+nb_status nb_slab_face(nb_mesh *mesh, nb_prec prec, int side, const void *u_dev,
+                       void *face_dev);
+
+/* After nb_dssum: add the neighbouring slab's plane vector face_dev (its
+ * nb_slab_face on the shared plane) to every copy of the plane's free nodes
+ * of u_dev.  u then holds the box's direct-stiffness sum on this slab.
+ * Errors: NB_ERR_ARG. */
+nb_status nb_slab_face_add(nb_mesh *mesh, nb_prec prec, int side, void *u_dev,
+                           const void *face_dev);
+
+/* The slab's part of the assembled diagonal on interface plane `side`
+ * (FP64 plane vector, device). */
+nb_status nb_slab_diag_face(nb_mesh *mesh, int side, double *face_dev);
+
+/* Complete the Jacobi inverse diagonal with the neighbours' parts (their
+ * nb_slab_diag_face on the shared planes; NULL exactly where the slab has
+ * no interface).  Errors: NB_ERR_ARG, NB_ERR_STATE. */
+nb_status nb_slab_finish_diag(nb_mesh *mesh, const double *face_lo_dev,
+                              const double *face_hi_dev);
+
+/* One step of Table 1 on this mesh (lines 2-5 without the summation of w):
+ * p = Dinv r + beta p (solveM, add2s1), w = A_L p element by element, and
+ * *pap_host = sum of p.w over the mesh's local nodes in FP64 (for a
+ * continuous masked p the partial of glsc3(w, c, p) after summation).
+ * L-vectors on the device in the precision's type; p must hold the previous
+ * direction (zeros before the first step, with beta = 0).  Synchronises. */
+nb_status nb_cg_step(nb_mesh *mesh, nb_prec prec, double beta, const void *r_dev,
+                     void *p_dev, void *w_dev, double *pap_host);
+
+/* Lines 7-9: x += alpha p, r -= alpha w with w summed and masked, then
+ * dots_host[0] = (r, c, Dinv r) and dots_host[1] = (r, c, r) over this mesh
+ * (FP64 accumulation; on a slab the partials of the box's dots). */
+nb_status nb_cg_update(nb_mesh *mesh, nb_prec prec, double alpha, void *x_dev, void *r_dev,
+                       const void *p_dev, const void *w_dev, double *dots_host);
+
+/* dots_host[0] = (r, c, Dinv r), dots_host[1] = (r, c, r) of r on this mesh
+ * (the dots of the first iteration). */
+nb_status nb_cg_dots(nb_mesh *mesh, nb_prec prec, const void *r_dev, double *dots_host);
+
 /* nb_glsc3 for callers that cannot let a library allocate memory: a
  * framework whose caching allocator owns the device memory, a process under
  * a hard memory budget, or a latency-critical loop that must not pay for

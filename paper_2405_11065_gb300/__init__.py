@@ -95,6 +95,14 @@ def _load():
         "nb_ax_variants": (i32, [vp, i32]),
         "nb_set_ax_variant": (i32, [vp, i32, i32]),
         "nb_set_update_variant": (i32, [vp, i32]),
+        "nb_setup_slab": (i32, [vp, i32, i32, i32, i32, i32, i32, dbl, C.POINTER(vp)]),
+        "nb_slab_face": (i32, [vp, i32, i32, vp, vp]),
+        "nb_slab_face_add": (i32, [vp, i32, i32, vp, vp]),
+        "nb_slab_diag_face": (i32, [vp, i32, vp]),
+        "nb_slab_finish_diag": (i32, [vp, vp, vp]),
+        "nb_cg_step": (i32, [vp, i32, dbl, vp, vp, vp, C.POINTER(dbl)]),
+        "nb_cg_update": (i32, [vp, i32, dbl, vp, vp, vp, vp, C.POINTER(dbl)]),
+        "nb_cg_dots": (i32, [vp, i32, vp, C.POINTER(dbl)]),
         "nb_ax_variant_name": (C.c_char_p, [vp, i32, i32]),
         "nb_ax_variant_in_use": (i32, [vp, i32]),
         "nb_autotune": (i32, [vp, i32, i32, vp, C.c_size_t, C.POINTER(i32), C.POINTER(dbl)]),
@@ -172,9 +180,15 @@ class Context:
 class Mesh:
     """A box mesh with its gather-scatter set up (nb_setup_mesh + nb_setup_gs)."""
 
-    def __init__(self, ctx: Context, nx, ny, nz, N, deform=0.0, setup_gs=True):
+    def __init__(self, ctx: Context, nx, ny, nz, N, deform=0.0, setup_gs=True, slab=None):
+        """``slab=(z0, z1)``: the z-slab z0 <= ez < z1 of the box (nb_setup_slab)."""
         h = C.c_void_p()
-        check(lib.nb_setup_mesh(ctx.h, nx, ny, nz, N, float(deform), C.byref(h)))
+        if slab is None:
+            check(lib.nb_setup_mesh(ctx.h, nx, ny, nz, N, float(deform), C.byref(h)))
+        else:
+            check(lib.nb_setup_slab(ctx.h, nx, ny, nz, int(slab[0]), int(slab[1]), N,
+                                    float(deform), C.byref(h)))
+        self.slab = slab
         self.h = h
         self.ctx = ctx
         if setup_gs:
@@ -318,6 +332,42 @@ class Mesh:
 
     def ax_variants(self, prec) -> int:
         return lib.nb_ax_variants(self.h, prec)
+
+    # --- slabs and the split-phase CG (nb_slab_*, nb_cg_*)
+    def plane_size(self) -> int:
+        return (self.nx * self.N + 1) * (self.ny * self.N + 1)
+
+    def slab_face(self, prec, side, u, face):
+        check(lib.nb_slab_face(self.h, prec, int(side), self._vec(u, prec),
+                               self._vec(face, prec, self.plane_size())))
+
+    def slab_face_add(self, prec, side, u, face):
+        check(lib.nb_slab_face_add(self.h, prec, int(side), self._vec(u, prec),
+                                   self._vec(face, prec, self.plane_size())))
+
+    def slab_diag_face(self, side, face):
+        check(lib.nb_slab_diag_face(self.h, int(side), self._vec(face, NB_FP64, self.plane_size())))
+
+    def slab_finish_diag(self, face_lo=None, face_hi=None):
+        f = lambda t: None if t is None else self._vec(t, NB_FP64, self.plane_size())
+        check(lib.nb_slab_finish_diag(self.h, f(face_lo), f(face_hi)))
+
+    def cg_step(self, prec, beta, r, p, w) -> float:
+        out = C.c_double()
+        check(lib.nb_cg_step(self.h, prec, float(beta), self._vec(r, prec), self._vec(p, prec),
+                             self._vec(w, prec), C.byref(out)))
+        return out.value
+
+    def cg_update(self, prec, alpha, x, r, p, w):
+        out = (C.c_double * 2)()
+        check(lib.nb_cg_update(self.h, prec, float(alpha), self._vec(x, prec), self._vec(r, prec),
+                               self._vec(p, prec), self._vec(w, prec), out))
+        return out[0], out[1]
+
+    def cg_dots(self, prec, r):
+        out = (C.c_double * 2)()
+        check(lib.nb_cg_dots(self.h, prec, self._vec(r, prec), out))
+        return out[0], out[1]
 
     def ax_variant_name(self, prec, variant=-1) -> str:
         """Kernel name of a variant (-1: the one in use)."""

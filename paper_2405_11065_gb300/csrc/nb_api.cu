@@ -56,6 +56,22 @@ void schwarz_free(nb_mesh *m);  // nb_schwarz.cu
 
 using namespace nb;
 
+namespace nb {
+
+void ctx_retain(nb_ctx *c) { c->refs.fetch_add(1); }
+
+void ctx_release(nb_ctx *c)
+{
+    if (c->refs.fetch_sub(1) != 1) return;
+    if (c->own_stream) {
+        DeviceGuard g(c->device);
+        cudaStreamDestroy(c->own_stream);
+    }
+    delete c;
+}
+
+}  // namespace nb
+
 extern "C" {
 
 const char *nb_version(void) { return "nekbone-gb300 0.1 (sm_103a)"; }
@@ -107,8 +123,7 @@ nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream)
 nb_status nb_destroy(nb_ctx *ctx)
 {
     if (!ctx) return NB_OK;
-    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
-    delete ctx;
+    ::nb::ctx_release(ctx);
     return NB_OK;
 }
 
@@ -124,19 +139,25 @@ nb_status nb_mesh_destroy(nb_mesh *m)
     void *bufs[] = {m->D64, m->D32, m->G64, m->G32, m->gid, m->gs_off, m->gs_loc, m->gs_gid,
                     m->gs_mask, m->g_first, m->mask_g, m->c32, m->dinv64, m->dinv32,
                     m->ones64, m->ones32, m->r64, m->w64, m->x64, m->b64, m->g64, m->part64,
-                    m->red_out, m->kerr, m->gs_zero, m->gs_pair, m->gs_quad, m->gs_oct};
+                    m->red_out, m->kerr, m->gs_zero, m->gs_pair, m->gs_quad, m->gs_oct,
+                    m->diag_asm, m->scal_split};
     for (void *b : bufs) cudaFree(b);
     if (m->red_host) cudaFreeHost(m->red_host);
+    nb_ctx *ctx = m->ctx;
     delete m;
+    ::nb::ctx_release(ctx);
     return NB_OK;
 }
 
-nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double deform,
-                        nb_mesh **out)
+// A box of nx x ny x nz elements, or (nz_glob > nz) the slab of elements
+// z_off .. z_off + nz - 1 along z of a box of nz_glob elements.
+static nb_status setup_mesh_impl(nb_ctx *ctx, int nx, int ny, int nz, int z_off, int nz_glob,
+                                 int N, double deform, nb_mesh **out)
 {
     if (!ctx || !out) return arg_error("NULL ctx or out");
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return arg_error("element counts must be >= 1");
+    if (z_off < 0 || z_off + nz > nz_glob) return arg_error("slab outside the box");
     if (N < 1 || N > kMaxN) {
         set_error("order N=%d outside [1, %d]", N, kMaxN);
         return NB_ERR_MESH;
@@ -151,6 +172,7 @@ nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double defor
     NB_DEVICE_SCOPE(ctx->device);
     nb_mesh *m = new nb_mesh();
     m->ctx = ctx;
+    ::nb::ctx_retain(ctx);
     m->nx = nx;
     m->ny = ny;
     m->nz = nz;
@@ -158,6 +180,10 @@ nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double defor
     m->n = N + 1;
     m->n3 = m->n * m->n * m->n;
     m->deform = deform;
+    m->z_off = z_off;
+    m->nz_glob = nz_glob;
+    m->iface_lo = z_off > 0;
+    m->iface_hi = z_off + nz < nz_glob;
     m->E = E;
     m->nL = nL;
     m->nG = nG;
@@ -168,6 +194,22 @@ nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double defor
     }
     *out = m;
     return NB_OK;
+}
+
+nb_status nb_setup_mesh(nb_ctx *ctx, int nx, int ny, int nz, int N, double deform,
+                        nb_mesh **out)
+{
+    return setup_mesh_impl(ctx, nx, ny, nz, 0, nz, N, deform, out);
+}
+
+nb_status nb_setup_slab(nb_ctx *ctx, int nx, int ny, int nz, int z0, int z1, int N,
+                        double deform, nb_mesh **out)
+{
+    if (!(z0 >= 0 && z0 < z1 && z1 <= nz)) {
+        if (out) *out = nullptr;
+        return arg_error("slab bounds need 0 <= z0 < z1 <= nz");
+    }
+    return setup_mesh_impl(ctx, nx, ny, z1 - z0, z0, nz, N, deform, out);
 }
 
 nb_status nb_setup_gs(nb_mesh *m)
@@ -481,6 +523,80 @@ extern "C" int nb_ax_variant_in_use(const nb_mesh *m, nb_prec prec)
 {
     if (!m || !prec_ok(prec)) return -1;
     return ax_variant_in_use(m, prec);
+}
+
+extern "C" nb_status nb_slab_face(nb_mesh *m, nb_prec prec, int side, const void *u_dev,
+                                  void *face_dev)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !u_dev || !face_dev) return arg_error("precision or NULL vector");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    NB_TRY(slab_face(m, prec == NB_FP64 ? NB_FP64 : NB_FP32, side, u_dev, face_dev,
+                     m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_slab_face_add(nb_mesh *m, nb_prec prec, int side, void *u_dev,
+                                      const void *face_dev)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !u_dev || !face_dev) return arg_error("precision or NULL vector");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    NB_TRY(slab_face_add(m, prec == NB_FP64 ? NB_FP64 : NB_FP32, side, u_dev, face_dev,
+                         m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_slab_diag_face(nb_mesh *m, int side, double *face_dev)
+{
+    NB_TRY(need_gs(m));
+    if (!face_dev) return arg_error("NULL face vector");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    NB_TRY(slab_diag_face(m, side, face_dev, m->ctx->stream));
+    NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_slab_finish_diag(nb_mesh *m, const double *face_lo_dev,
+                                         const double *face_hi_dev)
+{
+    NB_TRY(need_gs(m));
+    NB_DEVICE_SCOPE(m->ctx->device);
+    return slab_finish_diag(m, face_lo_dev, face_hi_dev, m->ctx->stream);
+}
+
+extern "C" nb_status nb_cg_step(nb_mesh *m, nb_prec prec, double beta, const void *r_dev,
+                                void *p_dev, void *w_dev, double *pap_host)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !r_dev || !p_dev || !w_dev || !pap_host)
+        return arg_error("precision or NULL pointer");
+    if (!isfinite(beta)) return arg_error("beta is not finite");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    return split_step(m, prec, beta, r_dev, p_dev, w_dev, pap_host, m->ctx->stream);
+}
+
+extern "C" nb_status nb_cg_update(nb_mesh *m, nb_prec prec, double alpha, void *x_dev,
+                                  void *r_dev, const void *p_dev, const void *w_dev,
+                                  double *dots_host)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !x_dev || !r_dev || !p_dev || !w_dev || !dots_host)
+        return arg_error("precision or NULL pointer");
+    if (!isfinite(alpha)) return arg_error("alpha is not finite");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    return split_update(m, prec == NB_FP64 ? NB_FP64 : NB_FP32, alpha, x_dev, r_dev, p_dev, w_dev,
+                        dots_host, m->ctx->stream);
+}
+
+extern "C" nb_status nb_cg_dots(nb_mesh *m, nb_prec prec, const void *r_dev, double *dots_host)
+{
+    NB_TRY(need_gs(m));
+    if (!prec_ok(prec) || !r_dev || !dots_host) return arg_error("precision or NULL pointer");
+    NB_DEVICE_SCOPE(m->ctx->device);
+    return split_dots(m, prec == NB_FP64 ? NB_FP64 : NB_FP32, r_dev, dots_host, m->ctx->stream);
 }
 
 extern "C" nb_status nb_set_update_variant(nb_mesh *m, int variant)

@@ -789,7 +789,9 @@ extern "C" nb_status nb_batch_destroy(nb_batch *B)
     if (B->red_host) cudaFreeHost(B->red_host);
     if (B->act_host) cudaFreeHost(B->act_host);
     if (B->loops_host) cudaFreeHost(B->loops_host);
+    nb_ctx *ctx = B->ctx;
     delete B;
+    ctx_release(ctx);
     return NB_OK;
 }
 
@@ -805,6 +807,7 @@ extern "C" nb_status nb_batch_create(nb_ctx *ctx, int nprob, const int *nx, cons
     NB_DEVICE_SCOPE(ctx->device);
     nb_batch *B = new nb_batch();
     B->ctx = ctx;
+    ctx_retain(ctx);
     B->nprob = nprob;
     B->meshes.assign(nprob, nullptr);
     nb_status st = NB_OK;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -167,12 +168,29 @@ struct nb_ctx {
     int sm_count = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    // references: the caller's (dropped by nb_destroy) and one per mesh,
+    // batch and model built on the context, so that those can be destroyed
+    // after the context (in any order, e.g. by a garbage collector)
+    std::atomic<int> refs{1};
 };
+
+namespace nb {
+void ctx_retain(nb_ctx *c);
+void ctx_release(nb_ctx *c);
+}  // namespace nb
 
 struct nb_mesh {
     nb_ctx *ctx = nullptr;
     int nx = 0, ny = 0, nz = 0, N = 0, n = 0, n3 = 0;
     double deform = 0.0;
+    // z-slab of a larger box (nb_setup_slab): elements ez + z_off of a box of
+    // nz_glob elements along z; an interface plane below / above (shared with
+    // the neighbouring slab, not Dirichlet; the copies of the lower one are
+    // not owners).  A whole box: z_off = 0, nz_glob = nz, no interfaces.
+    int z_off = 0, nz_glob = 0;
+    bool iface_lo = false, iface_hi = false;
+    double *diag_asm = nullptr;  // [nL] slab-local assembled diagonal (slabs only)
+    nb::CgScalars *scal_split = nullptr;  // scalars of the split-phase CG calls
     int64_t E = 0, nL = 0, nG = 0;
     bool gs_ready = false;
     // geometry
@@ -236,6 +254,7 @@ nb_status gll_host(int N, double *xi, double *w);
 void deriv_host(int N, const double *xi, double *D);
 nb_status build_geometry(nb_mesh *m);
 nb_status build_gs(nb_mesh *m);
+nb_status slab_free(nb_mesh *m);
 
 // ---- operator (nb_ax.cu)
 nb_status upload_deriv_tables(int n, const double *D64);
@@ -249,6 +268,18 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
                      cudaStream_t s);
 int ax_variant_count(const nb_mesh *m, nb_prec prec);
 nb_status l2_flush(const nb_ctx *ctx, void *buf, size_t bytes, int pattern, cudaStream_t s);
+// ---- slabs and the split-phase CG (nb_slab.cu, nb_solve.cu)
+nb_status slab_face(nb_mesh *m, nb_prec prec, int side, const void *u, void *face, cudaStream_t s);
+nb_status slab_face_add(nb_mesh *m, nb_prec prec, int side, void *u, const void *face,
+                        cudaStream_t s);
+nb_status slab_diag_face(nb_mesh *m, int side, double *face, cudaStream_t s);
+nb_status slab_finish_diag(nb_mesh *m, const double *face_lo, const double *face_hi,
+                           cudaStream_t s);
+nb_status split_step(nb_mesh *m, nb_prec prec, double beta, const void *r, void *p, void *w,
+                     double *pap, cudaStream_t s);
+nb_status split_update(nb_mesh *m, nb_prec prec, double alpha, void *x, void *r, const void *p,
+                       const void *w, double out[2], cudaStream_t s);
+nb_status split_dots(nb_mesh *m, nb_prec prec, const void *r, double out[2], cudaStream_t s);
 const char *ax_variant_name(const nb_mesh *m, nb_prec prec, int v);
 int ax_variant_in_use(const nb_mesh *m, nb_prec prec);
 

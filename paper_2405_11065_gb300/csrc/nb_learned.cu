@@ -1368,6 +1368,7 @@ extern "C" nb_status nb_model_create(nb_ctx *ctx, int N, int hidden, uint64_t se
     NB_DEVICE_SCOPE(ctx->device);
     nb_model *md = new nb_model();
     md->ctx = ctx;
+    ctx_retain(ctx);
     md->N = N;
     md->d = (N + 1) * (N + 1) * (N + 1);
     md->h = hidden;
@@ -1412,7 +1413,9 @@ extern "C" nb_status nb_model_destroy(nb_model *md)
     for (float *b : bufs) cudaFree(b);
     cudaFree(md->lpart);
     cudaFree(md->Wb);
+    nb_ctx *ctx = md->ctx;
     delete md;
+    ctx_release(ctx);
     return NB_OK;
 }
 

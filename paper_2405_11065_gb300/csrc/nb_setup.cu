@@ -92,7 +92,10 @@ void deriv_host(int N, const double *xi, double *D)
 // shared memory, then per node the Jacobian matrix by the derivative matrix,
 // its determinant and inverse, and the six factors
 // G_ab = w_i w_j w_k J sum_d (dr_a/dx_d)(dr_b/dx_d).
-__global__ void k_geometry(int nx, int ny, int nz, int n, double amp, const double *__restrict__ xi,
+// The elements are ez = 0..nz-1 of the mesh, at position ez + zoff of a box
+// of nzg elements along z (a slab of it; zoff = 0, nzg = nz for a whole box).
+__global__ void k_geometry(int nx, int ny, int nz, int zoff, int nzg, int n, double amp,
+                           const double *__restrict__ xi,
                            const double *__restrict__ wq, const double *__restrict__ D,
                            double *__restrict__ G64, float *__restrict__ G32, int *bad)
 {
@@ -107,7 +110,7 @@ __global__ void k_geometry(int nx, int ny, int nz, int n, double amp, const doub
             int i = q % n, j = (q / n) % n, k = q / (n * n);
             double x0 = (ex + 0.5 * (1.0 + xi[i])) / nx;
             double y0 = (ey + 0.5 * (1.0 + xi[j])) / ny;
-            double z0 = (ez + 0.5 * (1.0 + xi[k])) / nz;
+            double z0 = (ez + zoff + 0.5 * (1.0 + xi[k])) / nzg;
             double d = amp * sin(pi * x0) * sin(pi * y0) * sin(pi * z0);
             X[q] = x0 + d;
             Y[q] = y0 + d;
@@ -191,9 +194,10 @@ nb_status build_geometry(nb_mesh *m)
     NB_CUDA(cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
-    int mx = std::max(m->nx, std::max(m->ny, m->nz));
-    k_geometry<<<grid, 256, smem, s>>>(m->nx, m->ny, m->nz, n, m->deform / mx, dxi, dw, m->D64,
-                                       m->G64, m->G32, dbad);
+    const int nzg = m->nz_glob > 0 ? m->nz_glob : m->nz;
+    int mx = std::max(m->nx, std::max(m->ny, nzg));
+    k_geometry<<<grid, 256, smem, s>>>(m->nx, m->ny, m->nz, m->z_off, nzg, n, m->deform / mx, dxi,
+                                       dw, m->D64, m->G64, m->G32, dbad);
     NB_CUDA(cudaGetLastError());
     int bad = 0;
     NB_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -233,7 +237,9 @@ nb_status build_gs(nb_mesh *m)
     }
     for (int64_t gz = 0; gz < Gz; ++gz)
         for (int64_t gy = 0; gy < Gy; ++gy) {
-            bool face = gz == 0 || gz == Gz - 1 || gy == 0 || gy == Gy - 1;
+            // an interface plane of a slab is not on the Dirichlet boundary
+            bool face = (gz == 0 && !m->iface_lo) || (gz == Gz - 1 && !m->iface_hi) || gy == 0 ||
+                        gy == Gy - 1;
             uint8_t *mrow = &m->mask_host[Gx * (gy + Gy * gz)];
             for (int64_t gx = 0; gx < Gx; ++gx)
                 mrow[gx] = (face || gx == 0 || gx == Gx - 1) ? 0 : 1;
@@ -260,7 +266,11 @@ nb_status build_gs(nb_mesh *m)
         int32_t r = row_of[g];
         if (r >= 0) rloc[fill[r]++] = (int32_t)l;
         if (first[g] < 0) first[g] = (int32_t)l;
-        c[l] = 1.0f / (float)m->mult_host[g];
+        // the global multiplicity of a slab's interface-plane node counts the
+        // neighbouring slab's copies too (as many as this slab's)
+        const int64_t gzl = g / (Gx * Gy);
+        const bool shared = (gzl == 0 && m->iface_lo) || (gzl == Gz - 1 && m->iface_hi);
+        c[l] = 1.0f / (float)(m->mult_host[g] * (shared ? 2 : 1));
     }
     cudaStream_t s = m->ctx->stream;
     m->gs_rows = rows;
@@ -340,6 +350,13 @@ nb_status build_gs(nb_mesh *m)
     m->gs_ready = true;
     nb_status st = local_diag(m, diag, s);
     if (st == NB_OK) st = dssum(m, NB_FP64, diag, 1, s);
+    if (st == NB_OK && (m->iface_lo || m->iface_hi)) {
+        // a slab keeps its own part of the diagonal: the interface planes
+        // still lack the neighbour's (nb_slab_finish_diag adds it)
+        if (cudaMalloc(&m->diag_asm, sizeof(double) * nL) != cudaSuccess) st = NB_ERR_OOM;
+        else if (cudaMemcpyAsync(m->diag_asm, diag, sizeof(double) * nL,
+                                 cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = NB_ERR_CUDA;
+    }
     if (st == NB_OK) st = finish_jacobi(m, diag, s);
     cudaError_t e1 = cudaStreamSynchronize(s);
     cudaFree(diag);

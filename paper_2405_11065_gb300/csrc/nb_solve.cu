@@ -1212,6 +1212,102 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
     return result;
 }
 
+// ---------------------------------------------------------------------------
+// The CG iteration in split phases, for drivers that combine several meshes
+// (the slabs of a partitioned box): each call does one step of Table 1 on
+// this mesh and returns its partial dot products; the caller sums them over
+// the meshes and passes alpha and beta back.
+// ---------------------------------------------------------------------------
+
+__global__ void k_split_scalars(CgScalars *sc, double alpha, double beta)
+{
+    sc->alpha = alpha;
+    sc->beta = beta;
+    sc->rtz = 1.0;
+    sc->rtz_old = 1.0;
+    sc->bnorm2 = 1.0;
+    sc->tol = 0.0;
+    sc->maxit = 0x7fffffff;
+    sc->iter = 0;
+    sc->done = 0;
+    sc->status = 0;
+    sc->hist = nullptr;
+    sc->hist_cap = 0;
+}
+
+static nb_status split_scalars(nb_mesh *m)
+{
+    if (!m->scal_split) {
+        NB_CUDA(cudaMalloc(&m->scal_split, sizeof(CgScalars)));
+        NB_CUDA(cudaMemset(m->scal_split, 0, sizeof(CgScalars)));
+    }
+    NB_TRY(ensure_fp64_bufs(m));
+    return NB_OK;
+}
+
+nb_status split_step(nb_mesh *m, nb_prec prec, double beta, const void *r, void *p, void *w,
+                     double *pap, cudaStream_t s)
+{
+    NB_TRY(split_scalars(m));
+    k_split_scalars<<<1, 1, 0, s>>>(m->scal_split, 0.0, beta);
+    NB_CUDA(cudaGetLastError());
+    const void *dinv = prec == NB_FP64 ? (const void *)m->dinv64 : (const void *)m->dinv32;
+    int nparts = 0;
+    NB_TRY(ax_cg_step(m, prec, r, dinv, p, w, m->scal_split, m->part64, &nparts, s));
+    NB_CUDA(cudaMemcpyAsync(m->red_host, &m->scal_split->pap, sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    *pap = m->red_host[0];
+    return NB_OK;
+}
+
+nb_status split_update(nb_mesh *m, nb_prec prec, double alpha, void *x, void *r, const void *p,
+                       const void *w, double out[2], cudaStream_t s)
+{
+    NB_TRY(split_scalars(m));
+    k_split_scalars<<<1, 1, 0, s>>>(m->scal_split, alpha, 0.0);
+    NB_CUDA(cudaGetLastError());
+    const int g = vec_grid(m->ctx, m->nL);
+    if (prec == NB_FP64)
+        k_cg_update<double><<<g, kVecThreads, 0, s>>>(m->nL, m->scal_split, (double *)x,
+                                                      (double *)r, (const double *)p,
+                                                      (const double *)w, m->dinv64, m->part64);
+    else
+        k_cg_update<float><<<g, kVecThreads, 0, s>>>(m->nL, m->scal_split, (float *)x,
+                                                     (float *)r, (const float *)p,
+                                                     (const float *)w, m->dinv32, m->part64);
+    NB_CUDA(cudaGetLastError());
+    NB_CUDA(cudaMemcpyAsync(m->red_host, &m->scal_split->rtz, sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(m->red_host + 1, &m->scal_split->rtr, sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    out[0] = m->red_host[0];
+    out[1] = m->red_host[1];
+    return NB_OK;
+}
+
+nb_status split_dots(nb_mesh *m, nb_prec prec, const void *r, double out[2], cudaStream_t s)
+{
+    NB_TRY(split_scalars(m));
+    const int g = vec_grid(m->ctx, m->nL);
+    if (prec == NB_FP64)
+        k_cg_init<double><<<g, kVecThreads, 0, s>>>(m->nL, (const double *)r, m->dinv64, nullptr,
+                                                    m->part64, 0);
+    else
+        k_cg_init<float><<<g, kVecThreads, 0, s>>>(m->nL, (const float *)r, m->dinv32, nullptr,
+                                                   m->part64, 0);
+    NB_CUDA(cudaGetLastError());
+    NB_TRY(sum_partials_dev(m->part64, g, m->red_out, s));
+    NB_TRY(sum_partials_dev(m->part64 + g, g, m->red_out + 1, s));
+    NB_CUDA(cudaMemcpyAsync(m->red_host, m->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                            s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    out[0] = m->red_host[0];
+    out[1] = m->red_host[1];
+    return NB_OK;
+}
+
 nb_status solve(nb_mesh *m, const nb_opts *o, const double *b, double *x, nb_stats *st)
 {
     cudaStream_t s = m->ctx->stream;

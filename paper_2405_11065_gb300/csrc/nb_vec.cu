@@ -236,15 +236,18 @@ nb_status local_diag(nb_mesh *m, double *diag, cudaStream_t s)
 // its global node (+ on the first local copy, - on the others): the solver's
 // dot products sum over owner copies instead of weighting every copy by
 // 1/multiplicity, and the preconditioner applies |value|.
+// The first copy of a global node owns it, except on a slab's lower
+// interface plane (global indices below lo_plane), which the slab below owns.
 __global__ void k_finish_jacobi(int64_t nL, const double *__restrict__ diag,
                                 const int32_t *__restrict__ gid,
-                                const int32_t *__restrict__ first, double *dinv64, float *dinv32,
-                                double *ones64, float *ones32)
+                                const int32_t *__restrict__ first, int64_t lo_plane,
+                                double *dinv64, float *dinv32, double *ones64, float *ones32)
 {
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
          l += (int64_t)gridDim.x * blockDim.x) {
         const double d = diag[l];
-        const double sgn = first[gid[l]] == (int32_t)l ? 1.0 : -1.0;
+        const int32_t g = gid[l];
+        const double sgn = first[g] == (int32_t)l && g >= lo_plane ? 1.0 : -1.0;
         const double v = sgn * (d != 0.0 ? 1.0 / d : 0.0);
         const double one = sgn * (d != 0.0 ? 1.0 : 0.0);
         dinv64[l] = v;
@@ -257,8 +260,10 @@ __global__ void k_finish_jacobi(int64_t nL, const double *__restrict__ diag,
 nb_status finish_jacobi(nb_mesh *m, double *diag, cudaStream_t s)
 {
     int grid = vec_grid(m->ctx, m->nL);
-    k_finish_jacobi<<<grid, kVecThreads, 0, s>>>(m->nL, diag, m->gid, m->g_first, m->dinv64,
-                                                 m->dinv32, m->ones64, m->ones32);
+    const int64_t lo_plane =
+        m->iface_lo ? ((int64_t)m->nx * m->N + 1) * ((int64_t)m->ny * m->N + 1) : 0;
+    k_finish_jacobi<<<grid, kVecThreads, 0, s>>>(m->nL, diag, m->gid, m->g_first, lo_plane,
+                                                 m->dinv64, m->dinv32, m->ones64, m->ones32);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }

@@ -421,3 +421,19 @@ def test_update_variants_are_bit_identical(nb, ctx, box):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
     with pytest.raises(nb.NbError):
         mesh.set_update_variant(4)
+
+
+def test_mesh_outlives_its_context(nb):
+    """A mesh keeps its context alive: destroying the context first (as a
+    garbage collector may) leaves the mesh usable and its destruction safe."""
+    import torch
+    c = nb.Context(0)
+    box = Box(2, 2, 2, 5, 0.05)
+    m = nb.Mesh.from_box(c, box)
+    c.close()
+    P = oracle.Problem(box)
+    b = _t(P.to_local(rhs_global(box, 1)))
+    x = torch.zeros_like(b)
+    out = m.solve(b, x, nb.default_opts(prec=nb.NB_FP64))
+    assert out["status"] == 0
+    m.close()
