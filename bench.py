@@ -61,6 +61,8 @@ def parse():
                          "ax: only a few launches of the operators (for a profiler capture); "
                          "sweep / batched / learned: the other workloads, one JSON line each")
     ap.add_argument("--prec", default="fp32", help="precision of --mode ax")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="operator variant of --mode ax (-1: the default)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default operator variants (profiler runs: timing under a "
                          "profiler would steer the autotuner)")
@@ -323,14 +325,18 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
+# device source of the FP32 fused-step kernels (the ncu summary's traffic is
+# valid while these are unchanged)
 AX_SOURCES = ["paper_2405_11065_gb300/csrc/nb_ax_pen.cuh", "paper_2405_11065_gb300/csrc/nb_ax_tma.cuh",
-              "paper_2405_11065_gb300/csrc/nb_ax_impl.cuh", "paper_2405_11065_gb300/csrc/nb_ax.cu",
-              "paper_2405_11065_gb300/csrc/nb_ax_f32.cu", "paper_2405_11065_gb300/csrc/nb_bulk.cuh"]
+              "paper_2405_11065_gb300/csrc/nb_ax_impl.cuh", "paper_2405_11065_gb300/csrc/nb_ax_f32.cu",
+              "paper_2405_11065_gb300/csrc/nb_bulk.cuh", "paper_2405_11065_gb300/csrc/nb_cg_dev.cuh",
+              "paper_2405_11065_gb300/csrc/nb_reduce.cuh"]
 
 
 def profiled_traffic(sha, kernel):
-    """DRAM bytes per launch of the FP32 CG-step operator from the committed
-    ncu summary, if it was taken on the current source of the same kernel."""
+    """DRAM bytes per launch of the FP32 fused-step kernel variant `kernel`
+    from the committed ncu summary (lines "- dram_bytes_per_launch[<kernel>]:
+    <bytes>"), if it was taken on the current device source."""
     p = os.path.join(ROOT, "profiles", "ax_fp32_cg_step_E4096_N9.md")
     if not os.path.exists(p):
         return None
@@ -339,10 +345,10 @@ def profiled_traffic(sha, kernel):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha") != sha or vals.get("kernel") != kernel:
+    if vals.get("kernel_source_sha") != sha:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[f"dram_bytes_per_launch[{kernel}]"])
     except (KeyError, ValueError):
         return None
 
@@ -794,10 +800,14 @@ def main():
     flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
     if args.mode == "ax":
         prec = nb.PREC_NAMES[args.prec]
+        if args.variant >= 0:
+            mesh.set_ax_variant(prec, args.variant)
         for _ in range(args.warmup):
             mesh.time_ax(prec, cg_step=True, reps=1, flush=flush)
         ms = mesh.time_ax(prec, cg_step=True, reps=max(args.steps, 1), flush=flush)
-        print(json.dumps({"mode": "ax", "prec": args.prec, "cg_step_ms": ms}), flush=True)
+        print(json.dumps({"mode": "ax", "prec": args.prec, "cg_step_ms": ms,
+                          "kernel": mesh.ax_variant_name(prec),
+                          "kernel_source_sha": source_sha(AX_SOURCES)}), flush=True)
         return 0
 
     # autotune the operator (per precision, this order) before timing
