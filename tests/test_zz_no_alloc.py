@@ -12,6 +12,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from workloads import Box
 
 pytestmark = pytest.mark.gpu
@@ -43,8 +44,14 @@ def test_noalloc_glsc3_matches_allocating_entry_point(nb, prec_name):
         st = nb.lib.nb_glsc3_noalloc(mesh.h, prec, C.c_void_p(a.data_ptr()),
                                      C.c_void_p(b.data_ptr()), C.byref(got))
         assert st == nb.NB_OK, nb.lib.nb_last_error()
-        scale = float(np.sum(np.abs(a.double().cpu().numpy() * b.double().cpu().numpy() * c)))
+        a64, b64 = a.double().cpu().numpy(), b.double().cpu().numpy()
+        scale = float(np.sum(np.abs(a64 * b64 * c)))
         assert abs(got.value - ref) <= 1e-13 * scale, (call, got.value, ref)
+        # and the oracle's glsc3 of the same values: FP64 to summation order,
+        # FP32 to the rounding of each product (2^-23 of its size)
+        ora = oracle.glsc3(a64, b64, c)
+        tol = 1e-13 if prec == nb.NB_FP64 else 2.0 ** -23
+        assert abs(got.value - ora) <= tol * scale, (call, got.value, ora)
     # NULL output is rejected without touching the device
     st = nb.lib.nb_glsc3_noalloc(mesh.h, prec, C.c_void_p(a.data_ptr()),
                                  C.c_void_p(b.data_ptr()), None)
