@@ -384,6 +384,20 @@ nb_status nb_learned_attach(nb_mesh *mesh, nb_model *model);
 /* Apply the attached preconditioner once: z = B(r), FP32 L-vectors. */
 nb_status nb_learned_apply(nb_mesh *mesh, const float *r_dev, float *z_dev);
 
+/* One application of the fused preconditioner step of the learned flexible CG
+ * (Sections 4.1 and 6: solveM and the two glsc3 that follow it, with the
+ * network of the learned preconditioner as solveM), the kernel the inner FP32
+ * solve runs every iteration: z = B(r) as nb_learned_apply, and in the same
+ * pass *zw = sum over every local copy of z * w_prev (w_prev the unassembled
+ * A p of the previous step) and *rz = (r, c, z) over owner copies.  r_dev,
+ * wprev_dev, z_dev: device FP32 L-vectors (r continuous and masked);
+ * zw / rz: host doubles.  Available for FP32 meshes with N in {1, 3, 5, 7}
+ * and hidden width <= 128 (else NB_ERR_ARG).  Errors: NB_ERR_ARG,
+ * NB_ERR_STATE (no model attached), NB_ERR_CUDA (also a timed-out wait inside
+ * the kernel). */
+nb_status nb_learned_step(nb_mesh *mesh, const float *r_dev, const float *wprev_dev,
+                          float *z_dev, double *zw, double *rz);
+
 /* ------------------------------------------------------------------------
  * Emulated reduced precision (Section 2: Verificarlo's VPREC backend
  * computes every floating-point operation in the original type and rounds

@@ -88,6 +88,8 @@ def _load():
         "nb_learned_targets": (i32, [vp, vp, vp, i32, vp, vp]),
         "nb_learned_attach": (i32, [vp, vp]),
         "nb_learned_apply": (i32, [vp, vp, vp]),
+        "nb_learned_step": (i32, [vp, vp, vp, vp, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
         "nb_default_opts": (None, [C.POINTER(nb_opts)]),
         "nb_solve": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
         "nb_solve_host": (i32, [vp, C.POINTER(nb_opts), vp, vp, C.POINTER(nb_stats)]),
@@ -530,6 +532,14 @@ class Model:
 
     def apply(self, mesh: "Mesh", r, z):
         check(lib.nb_learned_apply(mesh.h, _ptr(r), _ptr(z)))
+
+    def step(self, mesh: "Mesh", r, wprev, z):
+        """The fused preconditioner step of the learned flexible CG: z = B(r)
+        and the dots (z, w_prev) over every copy and (r, c, z); returns both."""
+        zw, rz = C.c_double(), C.c_double()
+        check(lib.nb_learned_step(mesh.h, _ptr(r), _ptr(wprev), _ptr(z), C.byref(zw),
+                                  C.byref(rz)))
+        return zw.value, rz.value
 
 
 __all__ = ["lib", "LIB_PATH", "Batch", "Model", "NbError", "Context", "Mesh", "default_opts", "check",

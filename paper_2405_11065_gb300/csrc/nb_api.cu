@@ -13,6 +13,7 @@
 namespace nb {
 
 static thread_local char g_err[512] = "";
+thread_local bool g_pdl = false;
 
 void set_error(const char *fmt, ...)
 {

@@ -101,7 +101,6 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     __shared__ __align__(8) uint64_t bar[S];
     __shared__ double sred[32];
 
-    if (PUPD && scal->done) return;  // the solve has stopped: leave p and w untouched
     const int tid = threadIdx.x;
     const bool act = tid < n2;
     // the same split serves the three pencil roles: k-pencil (i, j) =
@@ -110,7 +109,6 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     const int kcol = rr * n + q;       // k-pencil: node (q, rr, k) at k * KS + kcol
     const int jcol = rr * KS + q;      // j-pencil: node (q, j, rr) at jcol + j * n
     const int irow = rr * KS + q * n;  // i-pencil: node (i, q, rr) at irow + i
-    const T beta = PUPD ? (T)scal->beta : T(0);
     const long long mine = E > blockIdx.x ? (E - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
     if (tid == 0) {
@@ -130,6 +128,18 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     };
     if (tid == 0)
         for (long long t = 0; t < S && t < mine; ++t) issue(t);
+    // the geometric factors are constant: their first copies go out before
+    // the wait for the previous kernel (programmatic dependent launch)
+    pdl_wait();
+    __shared__ int sdone;
+    if (tid == 0) sdone = PUPD ? scal->done : 0;  // one reading for the whole block
+    __syncthreads();
+    if (sdone) {  // the solve has stopped: leave p and w untouched
+        if (tid == 0)
+            for (long long t = 0; t < S && t < mine; ++t) mbar_wait_bounded(&bar[t], 0);
+        return;
+    }
+    const T beta = PUPD ? (T)scal->beta : T(0);
 
     // the thread's k-pencil of the element's inputs, one element ahead
     T nr[n], nd[n], np[n];
@@ -246,6 +256,7 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             acc += (double)sdot;
         }
     }
+    pdl_trigger();
     if (t < mine) {
         // a wait timed out: record it, let this block's copies land, stop
         if (tid == 0) {
@@ -286,8 +297,7 @@ nb_status launch_ax_pen(int sm_count, long long E, const T *G, const T *u, T *w,
     int grid = (int)(E < grid_cache ? E : grid_cache);
     if (grid < 1) grid = 1;
     if (grid > kMaxPartials) grid = kMaxPartials;
-    kern<<<grid, threads, smem, s>>>(E, G, u, w, r, dinv, p, scal, part, err);
-    NB_CUDA(cudaGetLastError());
+    NB_CUDA(launch_pdl(kern, grid, threads, smem, s, E, G, u, w, r, dinv, p, scal, part, err));
     if (grid_io) *grid_io = grid;
     return NB_OK;
 }

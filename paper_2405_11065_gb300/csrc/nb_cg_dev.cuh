@@ -9,20 +9,40 @@
 
 namespace nb {
 
-// True in every thread of the block that arrived last; all partials written
-// before the calls of the other blocks are then visible.  Resets the ticket.
+// Programmatic dependent launch (see launch_pdl): wait until the previous
+// kernel of the stream has completed and its writes are visible (returns at
+// once for a launch without the attribute) ...
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+// ... and let the next kernel start its prologue once every block of this
+// one has called this (after its main work).
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// True in every thread of the block that arrived last; the partials that
+// thread 0 of each block wrote before its call are then visible to warp 0.
+// Resets the ticket.  Only thread 0 fences: a fence in every thread would wait for all
+// of the block's outstanding stores of the kernel's outputs, which the last
+// block does not read.
 __device__ __forceinline__ bool last_block(unsigned int *ticket)
 {
     __shared__ bool is_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned int t = atomicAdd(ticket, 1u);
         is_last = (t == gridDim.x - 1);
         if (is_last) *ticket = 0u;  // every block has taken its ticket
     }
     __syncthreads();
-    if (is_last) __threadfence();
+    // the partials are read by warp 0 (sum_partials up to 2048 of them; it
+    // fences every thread itself beyond that)
+    if (is_last && threadIdx.x < 32) __threadfence();
     return is_last;
 }
 
@@ -50,8 +70,8 @@ __device__ __forceinline__ void cg_finish_pap(CgScalars *sc, const double *part,
 __device__ __forceinline__ void cg_finish_iter(CgScalars *sc, const double *part, int cnt,
                                                double *sred)
 {
-    const double rtz = sum_partials(part, cnt, sred);
-    const double rtr = sum_partials(part + cnt, cnt, sred);
+    double rtz, rtr;
+    sum_partials2(part, part + cnt, cnt, sred, rtz, rtr);
     if (threadIdx.x == 0) {
         sc->rtz_old = sc->rtz;
         sc->rtz = rtz;

@@ -81,6 +81,44 @@ void set_error(const char *fmt, ...);
         if (s_ < 0) return s_;           \
     } while (0)
 
+// Programmatic dependent launch.  Inside a PdlScope the CG loops launch
+// their kernels that support it with the programmatic-serialization
+// attribute: such a kernel may start while the previous kernel of the stream
+// finishes (its last block's reductions, the launch latency) and runs its
+// independent prologue -- barrier set-up, bulk copies of constant data,
+// tensor-memory allocation -- before it waits (griddepcontrol.wait, pdl_wait)
+// for the previous kernel's completion.  Only kernels that wait before their
+// first dependent read are launched through launch_pdl.
+extern thread_local bool g_pdl;
+
+class PdlScope {
+  public:
+    explicit PdlScope(bool on) : prev_(g_pdl) { g_pdl = on; }
+    ~PdlScope() { g_pdl = prev_; }
+    PdlScope(const PdlScope &) = delete;
+    PdlScope &operator=(const PdlScope &) = delete;
+
+  private:
+    bool prev_;
+};
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Division by a divisor fixed at launch time (Granlund and Montgomery,
 // "Division by invariant integers using multiplication", 1994): for
 // 0 <= x < 2^31, x / d = (umulhi(x, m) + x) >> l with l = ceil(log2 d) and

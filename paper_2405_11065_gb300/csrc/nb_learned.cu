@@ -28,6 +28,7 @@
 
 #include "nb_bulk.cuh"
 #include "nb_cg_dev.cuh"
+#include "nb_tc.cuh"
 
 struct nb_model {
     nb_ctx *ctx = nullptr;
@@ -41,10 +42,10 @@ struct nb_model {
     int cap = 0;
     float *Z = nullptr, *H = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr, *nrm = nullptr;
     float *gpart = nullptr;  // per-block partials of the gain gradient
-    // BF16 copy of W for the fused preconditioner, [dp][h] with dp = d rounded
-    // up to 16 (zero rows); refreshed when the weights changed (step)
-    __nv_bfloat16 *Wb = nullptr;
-    int64_t wb_step = -1;
+    // BF16 shared-memory image of W for the fused preconditioner (core
+    // matrices, k_w_image); refreshed when the weights changed (step)
+    __nv_bfloat16 *Wimg = nullptr;
+    int64_t wimg_step = -1;
     float *X = nullptr;
     double *lpart = nullptr;
 };
@@ -496,298 +497,369 @@ static nb_status model_apply(nb_mesh *m, nb_model *md, const float *r, float *z,
 // fused preconditioner for the flexible CG: z, (z, w_prev), (r, z) in one pass
 // ---------------------------------------------------------------------------
 //
-// Tiles of 16 consecutive elements (one m16 row tile), persistent blocks of
-// 8 warps with the BF16 weights resident in shared memory ([dp][h+8], padded
-// rows so that the eight row addresses of each ldmatrix fall in distinct
-// bank groups).  Per tile: the tile's residual (16 d contiguous floats) by
-// one bulk copy into one of two buffers (the next tile's copy is issued when
-// a tile starts); row norms and X = r / |r| in BF16; H = a * gelu(X W) by
-// mma.sync (W as the col-major B operand through ldmatrix.trans); the
-// correction C = |r_e| (H W^T) on interior nodes (W rows as the B operand);
-// then one coalesced pass z = |dinv| r + C with the owner-copy partials of
-// (z, w_prev) and (r, z).  The last block forms the flexible-CG
-// beta = -(z, w_prev) / pap_prev (0 on the first step) and rtz = (r, z);
-// since r_k is orthogonal to p_(k-1), (r, p) = (r, z) and the operator's last
-// block forms alpha = rtz / pap.  Needs d a multiple of 4 (n even).
+// Both products of the network run on the fifth-generation tensor cores
+// (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in tensor
+// memory), transposed so that the weights are the M side and a tile of up to
+// 32 elements the N side:
+//     H^T (h x NT)  = W^T (h x d) X^T (d x NT)      A = W^T: MN-major view of W
+//     C^T (d x NT)  = W   (d x h) Hs^T (h x NT)     A = W chunks of 128 rows, K-major
+// with X = r_e / |r_e| in BF16 and Hs = a * gelu(H) in BF16.  One resident
+// copy of W serves both products: its image in shared memory is the core
+// matrices of W (8 nodes x 8 hidden units each, units contiguous), stored
+// unit-group-major, so that for the first product LBO (along K = nodes) is
+// 128 bytes and SBO (along M = units) is 16 dp bytes, and for the second LBO
+// (along K = units) is 16 dp bytes and SBO (along M = nodes) 128 bytes.
+// The first product reads 128 rows of W^T; rows beyond h fall on the
+// buffers after the image (their outputs are never read).
+//
+// One persistent CTA per SM (16 warps) takes a balanced contiguous range of
+// elements in tiles of up to 32.  All of a tile's HBM reads are requested at
+// its start: its residual rows by bulk copies into shared memory (rows padded
+// by 16 bytes, so that the column reads below spread over the banks), its
+// dinv and w_prev rows by bulk prefetches into L2.  Then:
+//   1. row norms from shared memory (a warp per element), and X = r / |r| in
+//      BF16 written in the order of the core-matrix image (each thread 4
+//      nodes of one element; a warp's stores are contiguous);
+//   2. one thread issues the first product, the tensor core signals an
+//      mbarrier; warps read H^T out of tensor memory (thread = hidden unit),
+//      apply the gain and GELU, and write Hs;
+//   3. one thread issues the second product; each warp then reads 32 nodes x
+//      all tile elements of C^T (thread = node), and for each element forms
+//      z = |dinv| r + |r_e| C on interior nodes (Jacobi elsewhere), stores z
+//      (32 consecutive nodes per warp: coalesced) and accumulates (z, w_prev)
+//      over every copy and (r, z) over owner copies.
+// The last block forms the flexible-CG beta = -(z, w_prev) / pap_prev (0 on
+// the first step) and rtz = (r, z); since r_k is orthogonal to p_(k-1),
+// (r, p) = (r, z) and the operator's last block forms alpha = rtz / pap.
+// Every wait is bounded (one second): on a timeout the kernel records an
+// error, stops the solve, waits (bounded) for its own copies and products,
+// frees its tensor memory and returns.
 
-constexpr int kLpcThreads = 256;
+constexpr int kLpcThreads = 512;
+constexpr int kLpcTile = 32;       // elements per tile: the N of both products
+constexpr int kLpcTmemCols = 256;  // H^T: 32 columns; C^T: 32 per 128-node chunk
 
-__host__ __device__ constexpr int lpc_dp(int d) { return (d + 15) / 16 * 16; }
+__host__ __device__ constexpr int lpc_dk(int d) { return (d + 15) / 16 * 16; }     // K of product 1
+__host__ __device__ constexpr int lpc_dp(int d) { return (d + 127) / 128 * 128; }  // M of product 2
+__host__ __device__ constexpr int lpc_hp(int h) { return (h + 15) / 16 * 16; }
+__host__ __device__ constexpr int lpc_rs(int d) { return 4 * d + 16; }  // bytes per staged row
 
+// Dynamic shared memory: the W image, the X tile, the Hs tile, the staged
+// residual rows, at least the 128 rows of W^T that the first product reads,
+// plus alignment slack.
 static size_t lpc_smem(int d, int h)
 {
-    const int dp = lpc_dp(d);
-    return sizeof(__nv_bfloat16) *
-               ((size_t)dp * (h + 8) + 16 * (size_t)(dp + 8) + 16 * (size_t)(h + 8)) +
-           sizeof(float) * (3 * 16 * (size_t)d + 16 + h);
+    const size_t img = 2 * (size_t)lpc_hp(h) * lpc_dp(d);
+    const size_t used = img + 2 * (size_t)kLpcTile * lpc_dk(d) +
+                        2 * (size_t)kLpcTile * lpc_hp(h) + (size_t)kLpcTile * lpc_rs(d);
+    const size_t wt_span = 2 * (size_t)128 * lpc_dp(d);
+    return std::max(used, wt_span) + 1024;
 }
 
 static bool lpc_fits(int d, int h)
 {
-    return d % 4 == 0 && h % 16 == 0 && h <= 128 && d <= 512 && lpc_smem(d, h) <= 227 * 1024;
+    return d % 4 == 0 && d <= 512 && h >= 1 && h <= 128 && lpc_smem(d, h) <= 227 * 1024;
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t a[4], const void *p)
+// The shared-memory image of W (d x h, FP32, row-major) in BF16: core matrix
+// (node group g, unit group c) at element offset (c dp/8 + g) 64, rows of 8
+// units; zero beyond d and h.
+__global__ void k_w_image(int d, int h, const float *__restrict__ W,
+                          __nv_bfloat16 *__restrict__ img)
 {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
-                 : "r"(s));
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t b[2], const void *p)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-                 : "=r"(b[0]), "=r"(b[1])
-                 : "r"(s));
-}
-
-__device__ __forceinline__ void ldsm_x2_t(uint32_t b[2], const void *p)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
-                 : "=r"(b[0]), "=r"(b[1])
-                 : "r"(s));
-}
-
-__global__ void k_w_bf16(int d, int dp, int h, const float *__restrict__ W,
-                         __nv_bfloat16 *__restrict__ Wb)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dp * h; i += gridDim.x * blockDim.x)
-        Wb[i] = __float2bfloat16_rn(i < d * h ? W[i] : 0.f);
+    const int dp = lpc_dp(d), hp = lpc_hp(h);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dp * hp;
+         i += gridDim.x * blockDim.x) {
+        const int q = i / hp, u = i - q * hp;  // node, unit
+        const float v = q < d && u < h ? W[(size_t)q * h + u] : 0.f;
+        img[((u >> 3) * (dp >> 3) + (q >> 3)) * 64 + (q & 7) * 8 + (u & 7)] =
+            __float2bfloat16_rn(v);
+    }
 }
 
 template <int n>
 __global__ void __launch_bounds__(kLpcThreads, 1)
-k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
-      const float *__restrict__ wold, float *__restrict__ z, const __nv_bfloat16 *__restrict__ Wb,
-      const float *__restrict__ gain, CgScalars *sc, double *__restrict__ part, int *err)
+k_lpc_tc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
+         const float *__restrict__ wold, float *__restrict__ z,
+         const __nv_bfloat16 *__restrict__ Wimg, const float *__restrict__ gain, CgScalars *sc,
+         double *__restrict__ part, int *err)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int d = n * n * n, dp = lpc_dp(d), xs = dp + 8;
-    const int hs = h + 8;
-    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [dp][hs]
-    __nv_bfloat16 *Xs = Ws + (size_t)dp * hs;                          // [16][xs]
-    __nv_bfloat16 *Hs = Xs + 16 * xs;                                  // [16][hs]
-    float *Rbuf = reinterpret_cast<float *>(Hs + 16 * hs);             // [2][16][d] (bulk copies)
-    float *Cs = Rbuf + 2 * 16 * d;                                     // [16][d]
-    float *nrm = Cs + 16 * d;                                          // [16]
-    float *as = nrm + 16;                                              // [h]
-    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int d = n * n * n, dk = lpc_dk(d), dp = lpc_dp(d), NT = kLpcTile, NQ = dp / 128;
+    constexpr int RS = lpc_rs(d) / 4;  // staged row stride in floats
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int hp = lpc_hp(h);
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(sm);  // W image (hp x dp)
+    __nv_bfloat16 *Xs = Ws + (size_t)hp * dp;                    // [NT][dk] K-major
+    __nv_bfloat16 *Hs = Xs + (size_t)NT * dk;                    // [NT][hp] K-major
+    float *Rs = reinterpret_cast<float *>(Hs + (size_t)NT * hp); // [NT][RS] residual rows
+    __shared__ __align__(8) uint64_t bar[4];  // W image, product 1, product 2, residual rows
+    __shared__ uint32_t tslot;
+    __shared__ float snrm[NT], sinv[NT];
     __shared__ double sred[32];
-    __shared__ int sbad;
-    if (sc->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, tq = lane & 3;
-    const int tiles = (E + 15) / 16;
-    // tile number u of this block (u = 0, 1, ...) goes to buffer u & 1
-    auto issue = [&](int u) {
-        const int e0 = (blockIdx.x + u * gridDim.x) * 16, rows = min(16, E - e0);
-        const uint32_t bytes = (uint32_t)(sizeof(float) * rows * d);  // multiple of 16: d % 4 == 0
-        mbar_expect_tx(&bar[u & 1], bytes);
-        bulk_g2s(Rbuf + (u & 1) * 16 * d, r + (size_t)e0 * d, bytes, &bar[u & 1]);
+    const int e_beg = (int)((int64_t)E * blockIdx.x / gridDim.x);
+    const int e_end = (int)((int64_t)E * (blockIdx.x + 1) / gridDim.x);
+    const uint32_t img_bytes = 2u * (uint32_t)hp * dp;
+    // a tile's residual rows into Rs (bar[3]): warp 0, one row per lane after
+    // lane 0 has announced the bytes
+    auto request = [&](int t0, int cnt) {
+        if (lane == 0) mbar_expect_tx(&bar[3], (uint32_t)(4 * d * cnt));
+        __syncwarp();
+        for (int e = lane; e < cnt; e += 32)
+            bulk_g2s(Rs + (size_t)e * RS, r + (size_t)(t0 + e) * d, 4u * d, &bar[3]);
     };
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
-        sbad = 0;
-        if ((int)blockIdx.x < tiles) issue(0);
-    }
-    // the weights: 16-byte chunks of each row into the padded rows, four
-    // loads in flight per thread
-    const int chunks = h / 8, nchunk = dp * chunks;
-    for (int c0 = tid; c0 < nchunk; c0 += 4 * blockDim.x) {
-        uint4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = c0 + u * blockDim.x;
-            if (c < nchunk) {
-                const int row = c / chunks, col = (c - row * chunks) * 8;
-                v[u] = *reinterpret_cast<const uint4 *>(Wb + (size_t)row * h + col);
-            }
+    // prologue (weights, barriers, tensor memory: nothing the previous kernel
+    // writes), then the wait for it (programmatic dependent launch)
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+            mbar_init_fence();
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = c0 + u * blockDim.x;
-            if (c < nchunk) {
-                const int row = c / chunks, col = (c - row * chunks) * 8;
-                *reinterpret_cast<uint4 *>(Ws + (size_t)row * hs + col) = v[u];
-            }
-        }
+        __syncwarp();
+        if (lane == 0) mbar_expect_tx(&bar[0], img_bytes);
+        __syncwarp();
+        for (uint32_t o = 16384u * lane; o < img_bytes; o += 16384u * 32)
+            bulk_g2s(reinterpret_cast<unsigned char *>(Ws) + o,
+                     reinterpret_cast<const unsigned char *>(Wimg) + o,
+                     img_bytes - o < 16384u ? img_bytes - o : 16384u, &bar[0]);
     }
-    for (int c = tid; c < h; c += blockDim.x) as[c] = gain[c];
-    auto interior = [](int q) {  // n is a compile-time constant: no divisions
+    if (warp == 1) tc::tmem_alloc(&tslot, kLpcTmemCols);
+    // thread roles in tensor memory: lanes 32 (warp % 4) + lane
+    const int sp = warp & 3, grp = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * sp) << 16;
+    const int unit = 32 * sp + lane;  // hidden unit of the GELU pass
+    const float gu = unit < h ? gain[unit] : 0.f;
+    // epilogue node of this thread (chunk grp of 128 nodes)
+    const int q = 128 * grp + 32 * sp + lane;
+    const bool q_in = grp < NQ && q < d;
+    bool inside = false;
+    if (q_in) {
         const int i = q % n, j = (q / n) % n, k = q / (n * n);
-        return q < d && i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1;
-    };
+        inside = i > 0 && i < n - 1 && j > 0 && j < n - 1 && k > 0 && k < n - 1;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    pdl_wait();
+    __shared__ int sdone;
+    if (tid == 0) sdone = sc->done;  // one reading for the whole block
+    __syncthreads();
+    if (sdone) {  // the solve has stopped: let the weight copy land, free, leave
+        if (tid == 0) mbar_wait_bounded(&bar[0], 0);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 1) tc::tmem_dealloc(tmem, kLpcTmemCols);
+        return;
+    }
+    if (warp == 0 && e_beg < e_end) request(e_beg, min(NT, e_end - e_beg));
+    const uint32_t ws_a = smem_u32(Ws), xs_a = smem_u32(Xs), hs_a = smem_u32(Hs);
+    constexpr uint32_t id1 = tc::idesc_bf16(128, NT, true, false);
+    constexpr uint32_t id2 = tc::idesc_bf16(128, NT, false, false);
     DotAcc<float> zw, rz;
-    int u = 0;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++u) {
-        const int e0 = tile * 16, rows = min(16, E - e0);
-        float *Rs = Rbuf + (u & 1) * 16 * d;
-        __syncthreads();  // the previous tile is done with every buffer (and Ws is loaded)
-        // the next tile's residual into the other buffer, free since tile u-1 ended
-        if (tid == 0 && tile + (int)gridDim.x < tiles) issue(u + 1);
-        for (int q = tid; q < 16 * d; q += blockDim.x) Cs[q] = 0.f;
-        const bool ok = mbar_wait_bounded(&bar[u & 1], (uint32_t)((u >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) sbad = 1;
+    bool bad = false;
+    int it = 0;
+    for (int t0 = e_beg; t0 < e_end; t0 += NT, ++it) {
+        const int cnt = min(NT, e_end - t0);
+        const uint32_t ph = (uint32_t)(it & 1);
+        if (__syncthreads_or(warp == 0 && !mbar_wait_bounded(&bar[3], ph))) {
+            bad = true;
             break;
         }
-        // 1. row norms, X = r / |r| (warp w: rows w and w + 8)
-        for (int rr = warp; rr < 16; rr += kLpcThreads / 32) {
-            float ss = 0.f;
-            if (rr < rows)
-                for (int q = lane; q < d; q += 32) ss += Rs[rr * d + q] * Rs[rr * d + q];
+        // 1. row norms (warp per element; zero beyond the tile's elements)
+        {
+            constexpr int NW = kLpcThreads / 32, R4 = (d / 4 + 31) / 32;
+            float ss[NT / NW];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            const float nv = sqrtf(ss);
-            const float inv = nv > 0.f ? 1.0f / nv : 0.f;
-            for (int q = lane; q < dp; q += 32)
-                Xs[rr * xs + q] = __float2bfloat16_rn((rr < rows && q < d) ? Rs[rr * d + q] * inv : 0.f);
-            if (lane == 0) nrm[rr] = rr < rows ? nv : 0.f;
+            for (int m = 0; m < NT / NW; ++m) {
+                const int e = warp + m * NW;
+                ss[m] = 0.f;
+#pragma unroll
+                for (int u = 0; u < R4; ++u) {
+                    const int c = lane + 32 * u;
+                    if (e < cnt && c < d / 4) {
+                        const float4 v =
+                            *reinterpret_cast<const float4 *>(Rs + (size_t)e * RS + 4 * c);
+                        ss[m] += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NT / NW; ++m) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ss[m] += __shfl_xor_sync(0xffffffffu, ss[m], o);
+                if (lane == 0) {
+                    const int e = warp + m * NW;
+                    const float nv = sqrtf(ss[m]);
+                    snrm[e] = nv;
+                    sinv[e] = nv > 0.f ? 1.0f / nv : 0.f;
+                }
+            }
         }
         __syncthreads();
-        // 2. H = a * gelu(X W): warp w takes the column tiles w and w + 8 (h <= 128),
-        //    both accumulated in one pass over k (independent mma chains)
+        //    X in BF16: chunk i = 4 nodes of one element, at element offset 4 i
+        //    of the image (core c = i / 16: element group c / (dk/8), node
+        //    group c % (dk/8); row (i % 16) / 2, half i % 2)
+#pragma unroll
+        for (int i = tid; i < NT * dk / 4; i += kLpcThreads) {
+            const int c = i >> 4, rr = (i & 15) >> 1;
+            const int e = (c / (dk / 8)) * 8 + rr;
+            const int k = (c % (dk / 8)) * 8 + (i & 1) * 4;
+            uint2 pk = make_uint2(0u, 0u);
+            if (e < cnt && k < d) {
+                const float4 v = *reinterpret_cast<const float4 *>(Rs + (size_t)e * RS + k);
+                const float inv = sinv[e];
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x * inv, v.y * inv);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(v.z * inv, v.w * inv);
+                pk.x = *reinterpret_cast<uint32_t *>(&lo);
+                pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            }
+            *reinterpret_cast<uint2 *>(Xs + 4 * (size_t)i) = pk;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // 2. H^T = W^T X^T (tensor memory columns [0, NT))
+        if (tid == 0) {
+            bool ok = true;
+            if (it == 0) ok = mbar_wait_bounded(&bar[0], 0);
+            if (ok) {
+                tc::fence_after_sync();
+#pragma unroll 1
+                for (int ks = 0; ks < dk / 16; ++ks)
+                    tc::mma_bf16(tmem, tc::sdesc(ws_a + 256u * ks, 128u, 16u * dp),
+                                 tc::sdesc(xs_a + 256u * ks, 128u, 16u * dk), id1, ks > 0);
+                tc::commit(&bar[1]);
+            } else {
+                atomicExch(err, 1);
+            }
+        }
+        if (__syncthreads_or(warp == 0 && !mbar_wait_bounded(&bar[1], ph))) {
+            bad = true;
+            break;
+        }
+        tc::fence_after_sync();
+        // Hs = a * gelu(H): thread = hidden unit, elements 8 grp .. 8 grp + 7
         {
-            constexpr int NW = kLpcThreads / 32;
-            const int nts = h / 8;
-            const bool two = warp + NW < nts;
-            if (warp < nts) {
-                float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
-                const int mi = lane >> 3, ri = lane & 7;
-#pragma unroll 4
-                for (int k0 = 0; k0 < dp; k0 += 16) {
-                    uint32_t a[4], b0[2], b1[2];
-                    ldsm_x4(a, Xs + ((mi & 1) * 8 + ri) * xs + k0 + (mi >> 1) * 8);
-                    const __nv_bfloat16 *wrow = Ws + (size_t)(k0 + (mi & 1) * 8 + ri) * hs;
-                    ldsm_x2_t(b0, wrow + warp * 8);
-                    mma_bf16(acc0, a, b0);
-                    if (two) {
-                        ldsm_x2_t(b1, wrow + (warp + NW) * 8);
-                        mma_bf16(acc1, a, b1);
+            float hv[8];
+            tc::ld_x8(tmem + lane_base + 8u * grp, hv);
+            tc::wait_ld();
+            if (unit < hp) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int e = 8 * grp + j;
+                    const float val = unit < h ? gu * gelu_f(hv[j]) : 0.f;
+                    Hs[tc::kmajor_off(e, unit, hp / 8)] = __float2bfloat16_rn(val);
+                }
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // 3. C^T = W Hs^T, chunk mq of 128 nodes into columns NT (1 + mq)
+        if (tid == 0) {
+#pragma unroll 1
+            for (int mq = 0; mq < NQ; ++mq)
+#pragma unroll 1
+                for (int ks = 0; ks < hp / 16; ++ks)
+                    tc::mma_bf16(tmem + (uint32_t)(NT * (1 + mq)),
+                                 tc::sdesc(ws_a + 2u * ks * 16u * dp + 2048u * mq, 16u * dp, 128u),
+                                 tc::sdesc(hs_a + 256u * ks, 128u, 16u * hp), id2, ks > 0);
+            tc::commit(&bar[2]);
+        }
+        // the epilogue's dinv and w_prev of this thread's node for the whole
+        // tile, in flight while the product runs
+        float dv[NT], wv[NT];
+        if (q_in) {
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+                if (j < cnt) {
+                    const size_t o = (size_t)(t0 + j) * d + q;
+                    dv[j] = dinv[o];
+                    wv[j] = wold[o];
+                }
+        }
+        if (__syncthreads_or(warp == 0 && !mbar_wait_bounded(&bar[2], ph))) {
+            bad = true;
+            break;
+        }
+        tc::fence_after_sync();
+        if (grp < NQ) {  // warp-uniform: the loads below are warp-collective
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float c[NT / 2];
+                tc::ld_x16(tmem + lane_base + (uint32_t)(NT * (1 + grp) + half * (NT / 2)), c);
+                tc::wait_ld();
+                if (q_in) {
+                    // two elements per compensated addition: their products
+                    // summed in FP32 first
+#pragma unroll
+                    for (int j = 0; j < NT / 2; j += 2) {
+                        float tzw = 0.f, trz = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < 2; ++jj) {
+                            const int e = half * (NT / 2) + j + jj;
+                            if (e < cnt) {
+                                const float rv = Rs[(size_t)e * RS + q];
+                                float zv = fabsf(dv[e]) * rv;
+                                if (inside) zv += c[j + jj] * snrm[e];
+                                z[(size_t)(t0 + e) * d + q] = zv;
+                                tzw = fmaf(zv, wv[e], tzw);
+                                if (!signbit(dv[e])) trz = fmaf(rv, zv, trz);
+                            }
+                        }
+                        zw.add(tzw);
+                        rz.add(trz);
                     }
                 }
-#pragma unroll
-                for (int hh = 0; hh < 4; ++hh) {
-                    const int row = g + 8 * (hh >> 1), col = warp * 8 + 2 * tq + (hh & 1);
-                    Hs[row * hs + col] = __float2bfloat16_rn(as[col] * gelu_f(acc0[hh]));
-                    if (two) {
-                        const int c1 = col + NW * 8;
-                        Hs[row * hs + c1] = __float2bfloat16_rn(as[c1] * gelu_f(acc1[hh]));
-                    }
-                }
             }
         }
-        __syncthreads();  // Hs complete
-        // 3. C = |r_e| (H W^T) on interior nodes: warp w takes the column tiles
-        //    w, w + 8, ... that hold an interior node, all accumulated in one
-        //    pass over k
-        {
-            constexpr int NW = kLpcThreads / 32, NT = (dp / 8 + NW - 1) / NW;
-            float acc[NT][4];
-            bool use[NT];
-#pragma unroll
-            for (int m = 0; m < NT; ++m) {
-                const int nt = warp + m * NW;
-                bool any = false;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) any |= nt < dp / 8 && interior(nt * 8 + c);
-                use[m] = any;
-#pragma unroll
-                for (int hh = 0; hh < 4; ++hh) acc[m][hh] = 0.f;
-            }
-            const int mi = lane >> 3, ri = lane & 7;
-            for (int k0 = 0; k0 < h; k0 += 16) {
-                uint32_t a[4];
-                ldsm_x4(a, Hs + ((mi & 1) * 8 + ri) * hs + k0 + (mi >> 1) * 8);
-#pragma unroll
-                for (int m = 0; m < NT; ++m) {
-                    if (!use[m]) continue;
-                    uint32_t b[2];
-                    ldsm_x2(b, Ws + (size_t)((warp + m * NW) * 8 + ri) * hs + k0 + (mi & 1) * 8);
-                    mma_bf16(acc[m], a, b);
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < NT; ++m) {
-                if (!use[m]) continue;
-#pragma unroll
-                for (int hh = 0; hh < 4; ++hh) {
-                    const int rr = g + 8 * (hh >> 1);
-                    const int q = (warp + m * NW) * 8 + 2 * tq + (hh & 1);
-                    if (rr < rows && interior(q)) Cs[rr * d + q] = acc[m][hh] * nrm[rr];
-                }
-            }
-        }
-        __syncthreads();  // Cs complete
-        // 4. z = |dinv| r + C over the tile, four nodes per 16-byte access
-        const int n4 = rows * d / 4;
-        const float4 *dv4 = reinterpret_cast<const float4 *>(dinv + (size_t)e0 * d);
-        const float4 *wo4 = reinterpret_cast<const float4 *>(wold + (size_t)e0 * d);
-        float4 *z4 = reinterpret_cast<float4 *>(z + (size_t)e0 * d);
-        const float4 *r4 = reinterpret_cast<const float4 *>(Rs);
-        const float4 *c4 = reinterpret_cast<const float4 *>(Cs);
-        for (int q0 = tid; q0 < n4; q0 += 4 * blockDim.x) {  // four float4 of each in flight
-            float4 dv[4], wv[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int q = q0 + k * blockDim.x;
-                if (q < n4) {
-                    dv[k] = dv4[q];
-                    wv[k] = wo4[q];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int q = q0 + k * blockDim.x;
-                if (q >= n4) continue;
-                const float4 rv = r4[q], cv = c4[q];
-                float4 zv;
-                zv.x = fabsf(dv[k].x) * rv.x + cv.x;
-                zv.y = fabsf(dv[k].y) * rv.y + cv.y;
-                zv.z = fabsf(dv[k].z) * rv.z + cv.z;
-                zv.w = fabsf(dv[k].w) * rv.w + cv.w;
-                z4[q] = zv;
-                // (z, w_prev) over every copy: w_prev is the unassembled
-                // A_L p (z continuous); (r, z) over owner copies
-                zw.add(zv.x * wv[k].x);
-                zw.add(zv.y * wv[k].y);
-                zw.add(zv.z * wv[k].z);
-                zw.add(zv.w * wv[k].w);
-                if (!signbit(dv[k].x)) rz.add(rv.x * zv.x);
-                if (!signbit(dv[k].y)) rz.add(rv.y * zv.y);
-                if (!signbit(dv[k].z)) rz.add(rv.z * zv.z);
-                if (!signbit(dv[k].w)) rz.add(rv.w * zv.w);
-            }
-        }
+        // the tile's buffers and tensor memory are free again; the next
+        // tile's residual rows may land in Rs
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp == 0 && t0 + NT < e_end) request(t0 + NT, min(NT, e_end - t0 - NT));
     }
-    __syncthreads();
-    if (sbad) {  // a residual tile never arrived: record it, let the copies land, stop
+    pdl_trigger();
+    if (bad) {
+        // a copy or a product never completed: record it, stop the solve, let
+        // what is in flight land, free the tensor memory
         if (tid == 0) {
             atomicExch(err, 1);
             sc->status = NB_BREAKDOWN;
             sc->done = 1;
-            mbar_wait_bounded(&bar[u & 1], (uint32_t)((u >> 1) & 1));
-            if ((int)blockIdx.x + (u + 1) * (int)gridDim.x < tiles)
-                mbar_wait_bounded(&bar[(u + 1) & 1], (uint32_t)(((u + 1) >> 1) & 1));
+            mbar_wait_bounded(&bar[0], 0);
+            mbar_wait_bounded(&bar[1], (uint32_t)(it & 1));
+            mbar_wait_bounded(&bar[2], (uint32_t)(it & 1));
+            mbar_wait_bounded(&bar[3], (uint32_t)(it & 1));
         }
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 1) tc::tmem_dealloc(tmem, kLpcTmemCols);
         return;
     }
-    const double tzw = block_sum(zw.value(), sred);
-    const double trz = block_sum(rz.value(), sred);
+    if (e_beg >= e_end && tid == 0) mbar_wait_bounded(&bar[0], 0);  // no tile: the copy lands
+    const double tzw = block_sum_acc(zw, sred);
+    const double trz = block_sum_acc(rz, sred);
     if (tid == 0) {
         part[blockIdx.x] = tzw;
         part[gridDim.x + blockIdx.x] = trz;
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, kLpcTmemCols);
     if (last_block(&sc->tick_upd)) {
-        const double szw = sum_partials(part, gridDim.x, sred);
-        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
+        double szw, srz;
+        sum_partials2(part, part + gridDim.x, gridDim.x, sred, szw, srz);
         if (tid == 0) {
             sc->beta = sc->pap_prev > 0.0 ? -szw / sc->pap_prev : 0.0;  // 0: first step
+            sc->fcg_zw = szw;
             sc->rtz = srz;
             sc->rp = srz;
             if (!isfinite(sc->beta) || !isfinite(srz)) {
@@ -800,10 +872,10 @@ k_lpc(int E, int h, const float *__restrict__ r, const float *__restrict__ dinv,
 
 // The block's partial of (r, c, r); the last block: pap_prev, rtr, the
 // iteration count, the relative residual (history) and the stopping tests.
-__device__ __forceinline__ void fcg_step_finish(CgScalars *sc, double mine, double *part,
-                                                double *sred)
+__device__ __forceinline__ void fcg_step_finish(CgScalars *sc, const DotAcc<float> &mine,
+                                                double *part, double *sred)
 {
-    const double t = block_sum(mine, sred);
+    const double t = block_sum_acc(mine, sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     if (!last_block(&sc->tick_upd)) return;
     const double rtr = sum_partials(part, gridDim.x, sred);
@@ -844,6 +916,7 @@ k_fcg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *sc, float *__rest
     static_assert(n % 2 == 0, "pairs of nodes need an even n");
     constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
     __shared__ double sred[32];
+    pdl_wait();  // the previous kernel's alpha, w and p (programmatic dependent launch)
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
     const int64_t sx = n3 - N, sy = (int64_t)nx * n3 - N * n, sz = (int64_t)nx * ny * n3 - N * n2;
@@ -876,7 +949,8 @@ k_fcg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *sc, float *__rest
             *reinterpret_cast<float2 *>(r + l) = rv;
         }
     }
-    fcg_step_finish(sc, acc.value(), part, sred);
+    pdl_trigger();
+    fcg_step_finish(sc, acc, part, sred);
 }
 
 // k_fcg_update_gs2 for the mesh's order (even n <= 16; the flexible-CG paths
@@ -892,9 +966,9 @@ static nb_status fcg_update_folded(nb_mesh *m, Workspace &ws, float *x, float *r
             k_fcg_update_gs2<NN, true><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal,   \
                                                             x, r, p, w, sgn, part, rg, m->gid);   \
         else                                                                                      \
-            k_fcg_update_gs2<NN, false><<<grid, 256, 0, s>>>(m->E, m->nx, m->ny, m->nz, ws.scal,  \
-                                                             x, r, p, w, sgn, part, nullptr,      \
-                                                             nullptr);                            \
+            NB_CUDA(launch_pdl(k_fcg_update_gs2<NN, false>, grid, 256, 0, s, m->E, m->nx, m->ny,  \
+                               m->nz, ws.scal, x, r, p, w, sgn, part, (float *)nullptr,           \
+                               (const int32_t *)nullptr));                                        \
         break;
     switch (m->n) {
         NB_FU(2) NB_FU(4) NB_FU(6) NB_FU(8) NB_FU(10) NB_FU(12) NB_FU(14) NB_FU(16)
@@ -907,16 +981,16 @@ static nb_status fcg_update_folded(nb_mesh *m, Workspace &ws, float *x, float *r
     return NB_OK;
 }
 
-// k_lpc for the orders it is built for (d = n^3 <= 512, n even).
+// k_lpc_tc for the orders it is built for (d = n^3 <= 512, n even).
 static bool lpc_order(int n) { return n == 2 || n == 4 || n == 6 || n == 8; }
 
 static nb_status lpc_attr(int n, size_t smem)
 {
     switch (n) {
-        case 2: NB_CUDA(cudaFuncSetAttribute(k_lpc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
-        case 4: NB_CUDA(cudaFuncSetAttribute(k_lpc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
-        case 6: NB_CUDA(cudaFuncSetAttribute(k_lpc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
-        case 8: NB_CUDA(cudaFuncSetAttribute(k_lpc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 2: NB_CUDA(cudaFuncSetAttribute(k_lpc_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 4: NB_CUDA(cudaFuncSetAttribute(k_lpc_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 6: NB_CUDA(cudaFuncSetAttribute(k_lpc_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
+        case 8: NB_CUDA(cudaFuncSetAttribute(k_lpc_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); break;
         default: set_error("fused preconditioner unavailable for n=%d", n); return NB_ERR_ARG;
     }
     return NB_OK;
@@ -924,10 +998,12 @@ static nb_status lpc_attr(int n, size_t smem)
 
 static nb_status launch_lpc(int n, int grid, size_t smem, cudaStream_t s, int E, int h,
                             const float *r, const float *dinv, const float *wold, float *z,
-                            const __nv_bfloat16 *Wb, const float *gain, CgScalars *sc,
+                            const __nv_bfloat16 *Wimg, const float *gain, CgScalars *sc,
                             double *part, int *err)
 {
-#define NB_LPC(NN) k_lpc<NN><<<grid, kLpcThreads, smem, s>>>(E, h, r, dinv, wold, z, Wb, gain, sc, part, err)
+#define NB_LPC(NN)                                                                           \
+    NB_CUDA(launch_pdl(k_lpc_tc<NN>, grid, kLpcThreads, smem, s, E, h, r, dinv, wold, z, Wimg, \
+                       gain, sc, part, err))
     switch (n) {
         case 2: NB_LPC(2); break;
         case 4: NB_LPC(4); break;
@@ -940,14 +1016,16 @@ static nb_status launch_lpc(int n, int grid, size_t smem, cudaStream_t s, int E,
     return NB_OK;
 }
 
-static nb_status ensure_wb(nb_model *md, cudaStream_t s)
+// The BF16 shared-memory image of W for k_lpc_tc, rebuilt when the weights
+// changed (training step).
+static nb_status ensure_wimg(nb_model *md, cudaStream_t s)
 {
-    const int dp = lpc_dp(md->d);
-    if (!md->Wb) NB_CUDA(cudaMalloc(&md->Wb, sizeof(__nv_bfloat16) * (size_t)dp * md->h));
-    if (md->wb_step != md->step || md->wb_step < 0) {
-        k_w_bf16<<<64, 256, 0, s>>>(md->d, dp, md->h, md->W, md->Wb);
+    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)lpc_hp(md->h) * lpc_dp(md->d);
+    if (!md->Wimg) NB_CUDA(cudaMalloc(&md->Wimg, bytes));
+    if (md->wimg_step != md->step || md->wimg_step < 0) {
+        k_w_image<<<64, 256, 0, s>>>(md->d, md->h, md->W, md->Wimg);
         NB_CUDA(cudaGetLastError());
-        md->wb_step = md->step;
+        md->wimg_step = md->step;
     }
     return NB_OK;
 }
@@ -965,7 +1043,7 @@ __global__ void k_fdot(int64_t n, const float *__restrict__ a, const float *__re
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         if (!signbit(sgn[i])) acc.add(a[i] * b[i]);
-    const double t = block_sum(acc.value(), sred);
+    const double t = block_sum_acc(acc, sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -991,7 +1069,7 @@ __global__ void k_fcg_p(int64_t n, CgScalars *sc, const double *__restrict__ par
         p[i] = pv;
         if (!signbit(sgn[i])) acc.add(r[i] * pv);
     }
-    const double t = block_sum(acc.value(), sred);
+    const double t = block_sum_acc(acc, sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -1029,7 +1107,7 @@ __global__ void k_fcg_update(int64_t n, CgScalars *sc, const double *__restrict_
         r[i] = rv;
         if (!signbit(sgn[i])) acc.add(rv * rv);
     }
-    const double t = block_sum(acc.value(), sred);
+    const double t = block_sum_acc(acc, sred);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -1120,7 +1198,7 @@ static nb_status fcg_prepare(nb_mesh *m, Workspace &ws, bool keep, bool odd, cud
 
 // The inner solve of a refinement step: ws.r holds the scaled residual, ws.x
 // starts at zero.  One flexible-CG step is three kernels when the fused forms
-// apply (k_lpc; the operator's direction form with alpha; k_fcg_update_gs2
+// apply (k_lpc_tc; the operator's direction form with alpha; k_fcg_update_gs2
 // with the summation folded in), otherwise the general path below.  Captured in a graph
 // with a while node (two steps per body), or host-launched with the stopping
 // state checked every few steps (all kernels skip their work once it is set).
@@ -1142,9 +1220,9 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     const bool fast = prec == NB_FP32 && ax_dir_step_available(m) && lpc_order(m->n) &&
                       lpc_fits(md->d, md->h);
     const size_t lsm = lpc_smem(md->d, md->h);
-    const int lgrid = std::max(1, std::min((int)((m->E + 15) / 16), m->ctx->sm_count));
+    const int lgrid = std::max(1, (int)std::min<int64_t>(m->E, m->ctx->sm_count));
     if (fast) {
-        NB_TRY(ensure_wb(md, s));  // outside any capture: refreshed in place when W changed
+        NB_TRY(ensure_wimg(md, s));  // outside any capture: refreshed in place when W changed
         NB_TRY(lpc_attr(m->n, lsm));
     }
     keep = keep && fast;
@@ -1156,12 +1234,13 @@ nb_status fcg_learned(nb_mesh *m, nb_prec prec, Workspace &ws, const nb_opts *o,
     // one flexible-CG step; w receives A p, wprev holds the previous A p
     auto step = [&](float *wcur, float *wold) -> nb_status {
         if (fast) {
-            NB_TRY(launch_lpc(m->n, lgrid, lsm, s, (int)m->E, md->h, r, sgn, wold, z, md->Wb,
+            PdlScope pdl(true);  // the three kernels wait for their predecessor themselves
+            NB_TRY(launch_lpc(m->n, lgrid, lsm, s, (int)m->E, md->h, r, sgn, wold, z, md->Wimg,
                               md->a, ws.scal, P0, m->kerr));
             int nparts = 0;
             NB_TRY(ax_dir_step(m, z, p, wcur, ws.scal, P1, &nparts, s));
             // w stays unassembled: the update folds the summation in, and
-            // k_lpc forms (z, w_prev) over every copy
+            // k_lpc_tc forms (z, w_prev) over every copy
             return fcg_update_folded(m, ws, x, r, p, wcur, P2, nullptr, s);
         }
         NB_TRY(model_apply(m, md, r, z, s));
@@ -1412,7 +1491,7 @@ extern "C" nb_status nb_model_destroy(nb_model *md)
                      md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
     cudaFree(md->lpart);
-    cudaFree(md->Wb);
+    cudaFree(md->Wimg);
     nb_ctx *ctx = md->ctx;
     delete md;
     ctx_release(ctx);
@@ -1430,7 +1509,7 @@ extern "C" nb_status nb_model_params(nb_model *md, float *get_host, const float 
     if (nparam) *nparam = md->nparam;
     if (set_host) {
         NB_CUDA(cudaMemcpy(md->W, set_host, sizeof(float) * md->nparam, cudaMemcpyHostToDevice));
-        md->wb_step = -1;  // the BF16 copy of the fused preconditioner is stale
+        md->wimg_step = -1;  // the BF16 image of the fused preconditioner is stale
     }
     if (get_host)
         NB_CUDA(cudaMemcpy(get_host, md->W, sizeof(float) * md->nparam, cudaMemcpyDeviceToHost));
@@ -1636,5 +1715,47 @@ extern "C" nb_status nb_learned_apply(nb_mesh *m, const float *r_dev, float *z_d
     NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(model_apply(m, (nb_model *)m->learned, r_dev, z_dev, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
+    return NB_OK;
+}
+
+extern "C" nb_status nb_learned_step(nb_mesh *m, const float *r_dev, const float *wprev_dev,
+                                     float *z_dev, double *zw, double *rz)
+{
+    if (!m || !r_dev || !wprev_dev || !z_dev || !zw || !rz) {
+        set_error("invalid argument: NULL pointer");
+        return NB_ERR_ARG;
+    }
+    nb_model *md = (nb_model *)m->learned;
+    if (!md || !m->gs_ready) {
+        set_error("no model attached or no gather-scatter set up");
+        return NB_ERR_STATE;
+    }
+    if (!lpc_order(m->n) || !lpc_fits(md->d, md->h)) {
+        set_error("the fused preconditioner needs N in {1,3,5,7} and hidden width <= 128");
+        return NB_ERR_ARG;
+    }
+    NB_DEVICE_SCOPE(m->ctx->device);
+    cudaStream_t s = m->ctx->stream;
+    Workspace &ws = m->ws32;
+    NB_TRY(ensure_ws(m, ws, 4, 0));
+    NB_TRY(ensure_wimg(md, s));
+    const size_t lsm = lpc_smem(md->d, md->h);
+    NB_TRY(lpc_attr(m->n, lsm));
+    NB_CUDA(cudaMemsetAsync(ws.scal, 0, sizeof(CgScalars), s));
+    NB_CUDA(cudaMemsetAsync(m->kerr, 0, sizeof(int), s));
+    const int grid = std::max(1, (int)std::min<int64_t>(m->E, m->ctx->sm_count));
+    NB_TRY(launch_lpc(m->n, grid, lsm, s, (int)m->E, md->h, r_dev, m->dinv32, wprev_dev, z_dev,
+                      md->Wimg, md->a, ws.scal, ws.part, m->kerr));
+    m->launches += 1;
+    int kerr = 0;
+    NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaMemcpyAsync(&kerr, m->kerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_CUDA(cudaStreamSynchronize(s));
+    if (kerr || ws.scal_host->status != 0) {
+        set_error("fused preconditioner: a wait inside the kernel timed out");
+        return NB_ERR_CUDA;
+    }
+    *zw = ws.scal_host->fcg_zw;
+    *rz = ws.scal_host->rtz;
     return NB_OK;
 }

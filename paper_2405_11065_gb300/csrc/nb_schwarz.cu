@@ -424,15 +424,15 @@ k_sw_sum(int64_t E, int nx, int ny, int nz, const float *__restrict__ zt,
         }
     }
     if (!DOTS) return;
-    const double tzw = block_sum(zw.value(), sred);
-    const double trz = block_sum(rz.value(), sred);
+    const double tzw = block_sum_acc(zw, sred);
+    const double trz = block_sum_acc(rz, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = tzw;
         part[gridDim.x + blockIdx.x] = trz;
     }
     if (last_block(&sc->tick_upd)) {
-        const double szw = sum_partials(part, gridDim.x, sred);
-        const double srz = sum_partials(part + gridDim.x, gridDim.x, sred);
+        double szw, srz;
+        sum_partials2(part, part + gridDim.x, gridDim.x, sred, szw, srz);
         if (threadIdx.x == 0) {
             sc->beta = sc->pap_prev > 0.0 ? -szw / sc->pap_prev : 0.0;  // 0: first step
             sc->rtz = srz;

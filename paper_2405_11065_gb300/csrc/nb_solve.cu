@@ -87,8 +87,8 @@ __global__ void k_cg_init(int64_t nL, const T *__restrict__ r, const T *__restri
             b.add(rl * rl);
         }
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -199,8 +199,8 @@ __global__ void k_cg_update(int64_t nL, CgScalars *__restrict__ sc, T *__restric
         x[l] = xl;
         r[l] = rl;
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -273,8 +273,8 @@ k_cg_update_gs(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T 
             r[l] = rl;
         }
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -326,8 +326,8 @@ k_cg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *__restrict__ sc, T
             *reinterpret_cast<V *>(r + l) = rv;
         }
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -404,8 +404,8 @@ k_cg_update_pairs(int npairs, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         load(q, c0);
         finish(c0);
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -433,8 +433,6 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
     constexpr int R = (P + 255) / 256;  // rounds of 256 pairs per element
     __shared__ double sred[32];
-    if (sc->done) return;
-    const T alpha = (T)sc->alpha;
     const int sx = n3 - N, sy = nx * n3 - N * n, sz = nx * ny * n3 - N * n2;
     // the thread's pair slots: local offset and face flags (bit 0..5: lower x
     // of the first node, upper x of the second, lower / upper y, lower / upper z)
@@ -447,6 +445,9 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         fl[q] = (i0 == 0) | ((i0 + 1 == N) << 1) | ((j == 0) << 2) | ((j == N) << 3) |
                 ((k == 0) << 4) | ((k == N) << 5);
     }
+    pdl_wait();  // the previous kernel's alpha, w and p (programmatic dependent launch)
+    if (sc->done) return;
+    const T alpha = (T)sc->alpha;
     DotAcc<T> a, b;
     auto node = [&](T &xl, T &rl, T pl, T wl, T d) {
         if (d == T(0)) wl = T(0);  // Dirichlet node
@@ -489,8 +490,9 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
             *reinterpret_cast<V *>(r + l) = rv[q];
         }
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    pdl_trigger();
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -621,8 +623,8 @@ k_cg_update_tma(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         __syncthreads();
         return;
     }
-    double ta = block_sum(a.value(), sred);
-    double tb = block_sum(b.value(), sred);
+    double ta = block_sum_acc(a, sred);
+    double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = ta;
         part[gridDim.x + blockIdx.x] = tb;
@@ -685,7 +687,7 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
             pgrid = update_pairs_grid<k_cg_update_el<float, NN>>(m->ctx->sm_count,              \
                                       (int)std::min<int64_t>(m->E * 256, npairs));              \
             pgrid = (int)std::min<int64_t>(pgrid, m->E);                                        \
-            k_cg_update_el<float, NN><<<pgrid, 256, 0, s>>>(                                    \
+            launch_pdl(k_cg_update_el<float, NN>, pgrid, 256, 0, s,                             \
                 (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
                 (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);           \
         } else {                                                                                \
@@ -821,10 +823,15 @@ static int cg_body_kernels(const nb_mesh *m, nb_prec prec)
 // The launches of one iteration (see the file comment): operator (its last
 // block computes alpha), gather-scatter, update (its last block computes
 // beta and the stopping test), and inside a graph the loop condition.
+// use_cond: 1 in a graph, ending the body with the loop condition; 2 in a
+// graph, an iteration followed by another one of the same body; 0 launched
+// from the host.  In FP32 the operator and the update go out with
+// programmatic dependent launch.
 template <typename T>
 static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
                          cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
 {
+    PdlScope pdl(sizeof(T) == 4);
     int nparts = 0;
     NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
     double *up = ws.part + kMaxPartials;
@@ -837,13 +844,31 @@ static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
                                                  (const T *)ws.p, (const T *)ws.w, dinv, up);
     }
     NB_CUDA(cudaGetLastError());
-    if (use_cond) {
+    if (use_cond == 1) {
         k_cg_cond<<<1, 1, 0, s>>>(ws.scal, h);
         NB_CUDA(cudaGetLastError());
-    } else {
+    } else if (use_cond == 0) {
         m->launches += cg_body_kernels(m, prec) - 1;
     }
     return NB_OK;
+}
+
+// Iterations per captured loop body: two in FP32, so that the second
+// operator follows the first update inside the body (a programmatic
+// dependent launch); the kernels of an iteration after convergence return at
+// once.
+template <typename T>
+constexpr int cg_body_iters()
+{
+    return sizeof(T) == 4 ? 2 : 1;
+}
+
+// Kernel launches of a graph-run inner solve, from the executed loop bodies.
+static int64_t graph_launches(const nb_mesh *m, nb_prec prec, const CgScalars &h)
+{
+    const int per_iter = cg_body_kernels(m, prec) - 1;  // without the condition
+    const int iters = prec == NB_FP64 ? 1 : 2;
+    return (int64_t)std::max(h.loops, 1) * (iters * per_iter + 1);
 }
 
 // Initial scalars from ws.r: p = 0, rtz, rtr, relres, done.
@@ -912,7 +937,9 @@ static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *di
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             NB_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed));
-            nb_status st = cg_body<T>(m, prec, ws, dinv, h, 1, s);
+            nb_status st = NB_OK;
+            for (int i = 0; i < cg_body_iters<T>() && st == NB_OK; ++i)
+                st = cg_body<T>(m, prec, ws, dinv, h, i + 1 == cg_body_iters<T>() ? 1 : 2, s);
             cudaGraph_t captured = nullptr;
             cudaError_t ce = cudaStreamEndCapture(s, &captured);
             if (st != NB_OK) {
@@ -1007,7 +1034,7 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
     const double bn2 = m->red_host[0] > 0 ? m->red_host[0] : 1.0;
     if (st) {
         if (o->use_graph)
-            m->launches += cg_body_kernels(m, NB_FP64) * (int64_t)std::max(h.iter, 1);
+            m->launches += graph_launches(m, NB_FP64, h);
         st->iters = h.iter;
         st->outer_iters = 0;
         st->launches = m->launches;
@@ -1175,8 +1202,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         const int it = ws.scal_host->iter;
-        if (o->use_graph && !use_learned)
-            m->launches += cg_body_kernels(m, o->prec) * (int64_t)std::max(it, 1);
+        if (o->use_graph && !use_learned) m->launches += graph_launches(m, o->prec, *ws.scal_host);
         if (o->record_history) {
             copy_history(ws, it, hist_off, st, s);
             hist_off += it;

@@ -94,6 +94,68 @@ def test_preconditioner_matches_oracle_forward(nb, ctx):
     assert err < 3e-2
 
 
+def _bf16(a):
+    """Round to BF16 (nearest even), as the kernels' __float2bfloat16_rn."""
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float32)).bfloat16().double().numpy()
+
+
+@pytest.mark.parametrize("nx,ny,nz,N,h", [
+    (3, 2, 2, 7, 96),      # 12 elements: one per block
+    (6, 5, 4, 5, 40),      # N = 5: padded K (224) and M (256); hidden width not a multiple of 16
+    (16, 16, 16, 7, 96),   # the learned workload's mesh: 26-27 elements per block
+    (18, 18, 16, 7, 96),   # 34-35 elements per block: a full tile and a ragged one
+    (18, 18, 16, 5, 48),
+])
+def test_fused_step_matches_oracle(nb, ctx, nx, ny, nz, N, h):
+    """The fused preconditioner step of the learned flexible CG (tensor-core
+    products, the z pass and its two dot products) element by element against
+    the FP64 oracle network, and against the same arithmetic with the
+    kernel's two BF16 roundings (inputs X and hidden activations) emulated."""
+    import torch
+    box = Box(nx, ny, nz, N, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    model = nb.Model(ctx, N, h, seed=3)
+    p = mlp.init_params(box.n ** 3, h, seed=11)
+    rng = np.random.default_rng(12)
+    p["W"] = p["W"] * 2.0
+    p["a"] = rng.uniform(0.5, 1.5, h)
+    p = {k: _bf16(v) for k, v in p.items()}  # weights exact in BF16
+    model.set_params(p)
+    model.attach(mesh)
+    r = P.to_local(rhs_global(box, 5)).astype(np.float32).astype(np.float64)
+    wprev = rng.uniform(-1, 1, box.n_local).astype(np.float32).astype(np.float64)
+    rt = torch.from_numpy(r.astype(np.float32)).cuda()
+    wt = torch.from_numpy(wprev.astype(np.float32)).cuda()
+    zt = torch.full_like(rt, float("nan"))
+    zw, rz = model.step(mesh, rt, wt, zt)
+    z = zt.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(z))
+    # the FP64 oracle network
+    ref = mlp.precondition_interior(p, P, r)
+    err = np.max(np.abs(z - ref)) / np.max(np.abs(ref))
+    # the same with X and a * gelu(H) rounded to BF16
+    n3 = box.n ** 3
+    R = r.reshape(-1, n3)
+    nrm = np.linalg.norm(R, axis=1)
+    X = _bf16(R / np.where(nrm > 0, nrm, 1.0)[:, None])
+    Hs = _bf16(p["a"] * mlp.gelu(X @ p["W"]))
+    corr = (Hs @ p["W"].T) * nrm[:, None] * mlp.interior_mask(N)[None, :]
+    emu = P.dinv * r + corr.reshape(-1)
+    err_emu = np.max(np.abs(z - emu)) / np.max(np.abs(emu))
+    # the in-kernel dot products against FP64 sums of the kernel's own z
+    zw_ref = float(np.dot(z, wprev))
+    rz_ref = float(np.sum(P.c * r * z))
+    dz = abs(zw - zw_ref) / np.sum(np.abs(z * wprev))
+    dr = abs(rz - rz_ref) / abs(rz_ref)
+    print(f"E={box.E} N={N} h={h}: z vs FP64 oracle {err:.2e}, vs BF16-emulated {err_emu:.2e}; "
+          f"(z, w_prev) {dz:.1e}, (r, z) {dr:.1e}")
+    assert err < 3e-2
+    assert err_emu < 2e-3
+    assert dz < 1e-6 and dr < 1e-6
+
+
 def _rhs(nb, mesh, box, seed):
     import torch
     bg = torch.from_numpy(rhs_global(box, seed)).cuda()
