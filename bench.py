@@ -546,12 +546,34 @@ def run_learned(args):
     return 0
 
 
-def extra_workloads(nb, ctx, dev, flush, hbm_peak):
-    """The other workloads, compact, for the default line: the roofline sweep
-    at its largest size (E = 32^3 at N = 7 and 9), the 256-problem batch, and
-    the learned preconditioner against Jacobi on one held-out right-hand side."""
+def small_fp64(nb, ctx, dev):
+    """The plain FP64 Jacobi-PCG workload: 2x2x2 affine box, N = 7, right-hand
+    side U[-1,1) per unique node from seed 0; the relative residual after 100
+    iterations, then the solve continued to 1e-10."""
     import torch
-    out = {}
+    box = W.SMALL_FP64
+    mesh = nb.Mesh.from_box(ctx, box)
+    b = _rhs_local(nb, mesh, box, 0, dev)
+    x = torch.zeros_like(b)
+    s100 = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64, rtol=1e-30, maxiter=100))
+    x.zero_()
+    mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64, rtol=RTOL))  # warm-up
+    x.zero_()
+    full = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP64, rtol=RTOL))
+    mesh.close()
+    return {"E": box.E, "N": box.N, "n_global": box.n_global, "deform": box.deform,
+            "rel_res_after_100": s100["rel_res"], "iters_to_1e-10": full["iters"],
+            "rel_res": full["rel_res"], "ms_to_1e-10": full["seconds"] * 1e3,
+            "status": full["status"]}
+
+
+def extra_workloads(nb, ctx, dev, flush, hbm_peak):
+    """The other workloads, compact, for the default line: the plain FP64
+    PCG on the 2x2x2 box, the roofline sweep at its largest size (E = 32^3 at
+    N = 7 and 9), the 256-problem batch, and the learned preconditioner
+    against Jacobi on one held-out right-hand side."""
+    import torch
+    out = {"fp64_2cube_N7": small_fp64(nb, ctx, dev)}
     sweep = []
     for N in (7, 9):
         box = W.Box(32, 32, 32, N, 0.05)

@@ -101,8 +101,10 @@ typedef struct {
                            inner solves stay below 1000 iterations and resumed
                            ones converge (else it falls back to restarts).  The
                            same holds for the flexible CG of the learned (fused
-                           form) and Schwarz preconditioners; the batch always
-                           restarts. */
+                           form) and Schwarz preconditioners, except that with
+                           the Schwarz preconditioners an inner solve that follows
+                           one of fewer than 15 iterations closes inner_rtol
+                           itself; the batch always restarts. */
 } nb_opts;
 
 typedef struct {

@@ -256,7 +256,7 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             acc += (double)sdot;
         }
     }
-    pdl_trigger();
+    if (PUPD && scal->pdl_early) pdl_trigger();
     if (t < mine) {
         // a wait timed out: record it, let this block's copies land, stop
         if (tid == 0) {

@@ -18,7 +18,9 @@ __device__ __forceinline__ void pdl_wait()
 }
 
 // ... and let the next kernel start its prologue once every block of this
-// one has called this (after its main work).
+// one has called this (after its main work; without the call the next kernel
+// starts as this one's blocks exit).  The loop kernels call it where the
+// solve's scalars ask for it (CgScalars::pdl_early).
 __device__ __forceinline__ void pdl_trigger()
 {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");

@@ -102,6 +102,14 @@ class PdlScope {
     bool prev_;
 };
 
+// Whether the CG loop's kernels should let their successor launch as soon as
+// their main work is done, rather than as their blocks exit.  Measured: the
+// early start hides the last block's scalar step where blocks have few
+// elements (E = 4096, N = 9: 62.5 against 63.5 ms per solve); on larger meshes
+// the successor's early blocks take SM slots from the persistent grids of the
+// previous kernel's last wave (E = 32768, N = 7: 376 against 297 ms).
+inline int pdl_early_for(int64_t E, int sm_count) { return E <= 32 * (int64_t)sm_count ? 1 : 0; }
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, Args... args)
@@ -159,6 +167,8 @@ struct CgScalars {
     int status;       // 0 running/converged, NB_NOT_CONVERGED, NB_BREAKDOWN
     int hist_cap;     // capacity of hist
     int loops;        // executions of the graph's loop body (hard stop at maxit + 1)
+    int pdl_early;    // 1: the loop's kernels let the next one launch after their main
+                      // work (programmatic dependent launch; small meshes, see pdl_early_for)
     double *hist;     // device history (relres per iteration) or nullptr
     unsigned int tick_ax;   // blocks of the operator kernel done (last block finalises)
     unsigned int tick_upd;  // blocks of the update kernel done

@@ -18,8 +18,9 @@
 // the fallback when the flexible iteration fails and the FP64 residual of the
 // refinement deciding convergence.
 //
-// Matrix products: BF16 operands on the tensor cores (mma.sync m16n8k16),
-// FP32 accumulation; master weights and Adam moments in FP32.
+// Matrix products: BF16 operands on the fifth-generation tensor cores
+// (tcgen05.mma, FP32 accumulators in tensor memory); master weights and Adam
+// moments in FP32.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -55,10 +56,12 @@ namespace nb {
 // ---------------------------------------------------------------------------
 // BF16 tensor-core matrix product: C = op(A) op(B) (+ epilogue)
 //   A: M x K (TA: stored K x M), B: K x N (TB: stored N x K), FP32 in memory,
-//   rounded to BF16 when staged in shared memory; FP32 accumulation.
+//   rounded to BF16 when staged in shared memory; FP32 accumulation in
+//   tensor memory (tcgen05.mma, issued by one thread, completion on an
+//   mbarrier).
 // ---------------------------------------------------------------------------
 
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+constexpr int GBM = 128, GBN = 64, GBK = 32;  // tile: the MMA's M and N, K per stage
 
 enum GemmEpi { EPI_STORE = 0, EPI_GELU_GAIN = 1, EPI_ADD = 2, EPI_PRECOND = 3 };
 
@@ -93,77 +96,102 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
+// One 128 x 64 tile of C per CTA (4 warps).  Per K stage of 32 the threads
+// stage op(A) (128 x 32) and op(B)^T (64 x 32) as BF16 in the K-major
+// core-matrix layout (two buffers; a buffer is rewritten once the MMAs that
+// read it have signalled their mbarrier), thread 0 issues two MMAs of K = 16.
+// Warp w then reads the accumulator rows 32 w .. 32 w + 31 (its tensor-memory
+// lanes) and applies the epilogue.  Every wait is bounded (one second); on a
+// timeout the kernel sets *err, skips the epilogue and frees its tensor
+// memory.
 template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int *err)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];  // transposed: Bs[n][k]
+    __shared__ __align__(1024) __nv_bfloat16 As[2][GBM * GBK];
+    __shared__ __align__(1024) __nv_bfloat16 Bs[2][GBN * GBK];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gq = lane >> 2, tq = lane & 3;
     const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4] = {};
-    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tslot, 64);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t idesc = tc::idesc_bf16(GBM, GBN, false, false);
+    const int nk = (g.K + GBK - 1) / GBK;
+    bool ok = true;
+    for (int kc = 0; kc < nk; ++kc) {
+        const int buf = kc & 1, k0 = kc * GBK;
+        // the MMAs of stage kc - 2 read this buffer
+        if (kc >= 2 && __syncthreads_or(tid == 0 && !mbar_wait_bounded(&bar[buf], ((kc - 2) >> 1) & 1))) {
+            ok = false;
+            break;
+        }
+        // op(A)[m][k]: consecutive threads along the stored row
         for (int q = tid; q < GBM * GBK; q += 128) {
             int mm, kk;
             if (TA) { mm = q % GBM; kk = q / GBM; } else { kk = q % GBK; mm = q / GBK; }
             const int gm = m0 + mm, gk = k0 + kk;
             float v = 0.f;
             if (gm < g.M && gk < g.K) v = TA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
-            As[mm][kk] = __float2bfloat16_rn(v);
+            As[buf][tc::kmajor_off(mm, kk, GBK / 8)] = __float2bfloat16_rn(v);
         }
+        // op(B)^T[n][k] = op(B)[k][n]
         for (int q = tid; q < GBN * GBK; q += 128) {
             int nn, kk;
             if (TB) { kk = q % GBK; nn = q / GBK; } else { nn = q % GBN; kk = q / GBN; }
             const int gn = n0 + nn, gk = k0 + kk;
             float v = 0.f;
             if (gn < g.N && gk < g.K) v = TB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
-            Bs[nn][kk] = __float2bfloat16_rn(v);
+            Bs[buf][tc::kmajor_off(nn, kk, GBK / 8)] = __float2bfloat16_rn(v);
         }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
         __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(As[buf]), b0 = smem_u32(Bs[buf]);
 #pragma unroll
-        for (int ks = 0; ks < GBK; ks += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = wm + mt * 16 + gq;
-                a[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r0][ks + 2 * tq]);
-                a[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][ks + 2 * tq]);
-                a[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r0][ks + 2 * tq + 8]);
-                a[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r0 + 8][ks + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int c0 = wn + nt * 8 + gq;
-                b[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[c0][ks + 2 * tq]);
-                b[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[c0][ks + 2 * tq + 8]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt], b[nt]);
+            for (int ks = 0; ks < GBK / 16; ++ks)
+                tc::mma_bf16(tmem, tc::sdesc(a0 + 256u * ks, 128u, 16u * GBK),
+                             tc::sdesc(b0 + 256u * ks, 128u, 16u * GBK), idesc, kc > 0 || ks > 0);
+            tc::commit(&bar[buf]);
         }
-        __syncthreads();
     }
+    // the last stage's commit covers every MMA issued before it
+    if (ok && nk > 0 &&
+        __syncthreads_or(tid == 0 && !mbar_wait_bounded(&bar[(nk - 1) & 1], ((nk - 1) >> 1) & 1)))
+        ok = false;
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bar[b], 0);  // let the MMAs land
+        }
+    } else {
+        tc::fence_after_sync();
+        const int row = m0 + 32 * warp + lane;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+        for (int c0 = 0; c0 < GBN; c0 += 16) {
+            float acc[16];
+            if (nk > 0) {
+                tc::ld_x16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, acc);
+                tc::wait_ld();
+            } else {
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+                for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+            }
+            if (row >= g.M) continue;
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-                const int row = m0 + wm + mt * 16 + gq + 8 * (hh >> 1);
-                const int col = n0 + wn + nt * 8 + 2 * tq + (hh & 1);
-                if (row >= g.M || col >= g.N) continue;
-                float v = acc[mt][nt][hh];
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + j;
+                if (col >= g.N) continue;
+                const float v = acc[j];
                 const size_t o = (size_t)row * g.ldc + col;
                 if (EPI == EPI_GELU_GAIN) {
                     if (g.C) g.C[o] = v;
@@ -183,13 +211,52 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                     g.C[o] = v;
                 }
             }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// Error flag of the product kernel (device memory, zero while no wait timed out).
+static int *gemm_err()
+{
+    static int *flag_dev[kMaxDevices] = {};
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return nullptr;
+    if (!flag_dev[d]) {
+        if (cudaMalloc(&flag_dev[d], sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(flag_dev[d], 0, sizeof(int)) != cudaSuccess) return nullptr;
+    }
+    return flag_dev[d];
+}
+
+// After a synchronisation: NB_ERR_CUDA (and the flag cleared) if a product's
+// wait timed out since the last check.
+static nb_status gemm_check()
+{
+    int *err = gemm_err();
+    if (!err) return NB_OK;
+    int v = 0;
+    NB_CUDA(cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) {
+        cudaMemset(err, 0, sizeof(int));
+        set_error("matrix product: a wait inside the kernel timed out");
+        return NB_ERR_CUDA;
+    }
+    return NB_OK;
 }
 
 template <bool TA, bool TB, int EPI>
 static nb_status gemm(const GemmArgs &a, cudaStream_t s)
 {
+    int *err = gemm_err();
+    if (!err) {
+        set_error("matrix product: no device error flag");
+        return NB_ERR_CUDA;
+    }
     dim3 grid((a.N + GBN - 1) / GBN, (a.M + GBM - 1) / GBM);
-    k_gemm_bf16<TA, TB, EPI><<<grid, 128, 0, s>>>(a);
+    k_gemm_tc<TA, TB, EPI><<<grid, 128, 0, s>>>(a, err);
     NB_CUDA(cudaGetLastError());
     return NB_OK;
 }
@@ -410,6 +477,10 @@ constexpr int kBackBlocks = 64;  // blocks of k_tied_back (partials of the gain 
 
 static nb_status model_scratch(nb_model *md, int rows)
 {
+    if (!gemm_err()) {  // allocated here, before any graph capture
+        set_error("matrix product: no device error flag");
+        return NB_ERR_OOM;
+    }
     if (rows <= md->cap) return NB_OK;
     float *bufs[] = {md->Z, md->H, md->Y, md->dY, md->dH, md->nrm, md->X, md->gpart};
     for (float *b : bufs) cudaFree(b);
@@ -826,7 +897,7 @@ k_lpc_tc(int E, int h, const float *__restrict__ r, const float *__restrict__ di
         tc::fence_after_sync();
         if (warp == 0 && t0 + NT < e_end) request(t0 + NT, min(NT, e_end - t0 - NT));
     }
-    pdl_trigger();
+    if (sc->pdl_early) pdl_trigger();
     if (bad) {
         // a copy or a product never completed: record it, stop the solve, let
         // what is in flight land, free the tensor memory
@@ -949,7 +1020,7 @@ k_fcg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *sc, float *__rest
             *reinterpret_cast<float2 *>(r + l) = rv;
         }
     }
-    pdl_trigger();
+    if (sc->pdl_early) pdl_trigger();
     fcg_step_finish(sc, acc, part, sred);
 }
 
@@ -1534,6 +1605,7 @@ extern "C" nb_status nb_model_grad(nb_model *md, const float *X, const float *T,
         NB_CUDA(cudaMemcpyAsync(grad_host, md->grad, sizeof(float) * md->nparam,
                                 cudaMemcpyDeviceToHost, s));
     NB_CUDA(cudaStreamSynchronize(s));
+    NB_TRY(gemm_check());
     if (loss_host) *loss_host = l / ((double)B * md->d);
     return NB_OK;
 }
@@ -1574,6 +1646,7 @@ extern "C" nb_status nb_model_train(nb_model *md, const float *X, const float *T
         }
     }
     NB_CUDA(cudaStreamSynchronize(s));
+    NB_TRY(gemm_check());
     if (final_loss) *final_loss = lcnt ? lsum / lcnt : 0.0;
     return NB_OK;
 }
@@ -1715,7 +1788,7 @@ extern "C" nb_status nb_learned_apply(nb_mesh *m, const float *r_dev, float *z_d
     NB_DEVICE_SCOPE(m->ctx->device);
     NB_TRY(model_apply(m, (nb_model *)m->learned, r_dev, z_dev, m->ctx->stream));
     NB_CUDA(cudaStreamSynchronize(m->ctx->stream));
-    return NB_OK;
+    return gemm_check();
 }
 
 extern "C" nb_status nb_learned_step(nb_mesh *m, const float *r_dev, const float *wprev_dev,

@@ -43,8 +43,10 @@ nb_status schwarz_coarse_correct64(nb_mesh *m, double *r64, double *x, float *c3
 // kernels
 // ---------------------------------------------------------------------------
 
-__global__ void k_cg_setup(CgScalars *sc, double tol, int maxit, double *hist, int hist_cap)
+__global__ void k_cg_setup(CgScalars *sc, double tol, int maxit, double *hist, int hist_cap,
+                           int pdl_early)
 {
+    sc->pdl_early = pdl_early;
     sc->tol = tol;
     sc->maxit = maxit;
     sc->hist = hist;
@@ -490,7 +492,7 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
             *reinterpret_cast<V *>(r + l) = rv[q];
         }
     }
-    pdl_trigger();
+    if (sc->pdl_early) pdl_trigger();
     double ta = block_sum_acc(a, sred);
     double tb = block_sum_acc(b, sred);
     if (threadIdx.x == 0) {
@@ -877,7 +879,7 @@ static nb_status cg_start(nb_mesh *m, Workspace &ws, const T *dinv, double tol, 
                           int bnorm_from_r, bool hist, cudaStream_t s)
 {
     k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tol, maxit, hist ? ws.hist : nullptr,
-                               hist ? ws.hist_cap : 0);
+                               hist ? ws.hist_cap : 0, pdl_early_for(m->E, m->ctx->sm_count));
     NB_CUDA(cudaGetLastError());
     const int g = vec_grid(m->ctx, m->nL);
     k_cg_init<T><<<g, kVecThreads, 0, s>>>(m->nL, (const T *)ws.r, dinv, (T *)ws.p,
@@ -896,7 +898,7 @@ static nb_status cg_resume(nb_mesh *m, Workspace &ws, const T *dinv, double tol,
                            bool hist, double c, cudaStream_t s)
 {
     k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tol, maxit, hist ? ws.hist : nullptr,
-                               hist ? ws.hist_cap : 0);
+                               hist ? ws.hist_cap : 0, pdl_early_for(m->E, m->ctx->sm_count));
     NB_CUDA(cudaGetLastError());
     const int g = vec_grid(m->ctx, m->nL);
     k_cg_init<T><<<g, kVecThreads, 0, s>>>(m->nL, (const T *)ws.r, dinv, (T *)ws.p,
@@ -1162,10 +1164,11 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // second solve, after the first 2 decades, typically takes 4x the first)
         const int cap = resume ? 8 * prev_iters + 200 : remaining;
         const bool odd = (prev_iters & 1) != 0;
-        // after a short inner solve (a strong preconditioner: the recurrence
-        // has little room to drift) the next one may close inner_rtol again,
-        // which saves FP64 residuals
-        const bool short_prev = resume && prev_iters < kReliableShort;
+        // with the Schwarz preconditioners, after a short inner solve (the
+        // recurrence has little room to drift) the next one may close
+        // inner_rtol again, which saves FP64 residuals (measured there: the
+        // two-level solve needs 4 refinement steps instead of 5)
+        const bool short_prev = resume && schwarz && prev_iters < kReliableShort;
         const double step_rtol =
             keep_dir && !short_prev ? std::max(o->inner_rtol, kReliableDrop) : o->inner_rtol;
         const double tau = std::min(0.5, std::max(step_rtol, 0.5 * o->rtol / rel_in));
@@ -1173,7 +1176,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
             // flexible CG with the Schwarz preconditioner (nb_schwarz.cu)
             k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau, std::min(remaining, cap),
                                        o->record_history ? ws.hist : nullptr,
-                                       o->record_history ? ws.hist_cap : 0);
+                                       o->record_history ? ws.hist_cap : 0,
+                                       pdl_early_for(m->E, m->ctx->sm_count));
             NB_CUDA(cudaGetLastError());
             NB_TRY(fcg_schwarz(m, o->prec, ws, o, resume, odd, s));
         } else if (use_learned) {
@@ -1182,7 +1186,8 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
             k_cg_setup<<<1, 1, 0, s>>>(ws.scal, tau,
                                        std::min(std::min(remaining, cap), kLearnedBudget),
                                        o->record_history ? ws.hist : nullptr,
-                                       o->record_history ? ws.hist_cap : 0);
+                                       o->record_history ? ws.hist_cap : 0,
+                                       pdl_early_for(m->E, m->ctx->sm_count));
             NB_CUDA(cudaGetLastError());
             NB_TRY(fcg_learned(m, o->prec, ws, o, resume, odd, s));
         } else {

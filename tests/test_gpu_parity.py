@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import Box, rhs_global
+from workloads import SMALL_FP64, Box, rhs_global
 
 pytestmark = pytest.mark.gpu
 
@@ -186,6 +186,35 @@ def test_fp64_pcg_matches_oracle(case, nb):
     k = min(len(h), len(histo), 20)
     np.testing.assert_allclose(h[:k], histo[:k], rtol=1e-8)
     assert P.true_relres(b, xg) < 1e-11
+
+
+def test_small_fp64_workload_as_specified(nb, ctx):
+    """The plain FP64 Jacobi-PCG workload: the 2x2x2 affine box, N = 7,
+    right-hand side U[-1,1) per unique node from seed 0, 100 iterations, then
+    continued to a relative residual of 1e-10.  The residual history of the
+    100 iterations follows the oracle's, and the solve to 1e-10 takes the
+    oracle's iteration count and reaches its solution."""
+    import torch
+    box = SMALL_FP64
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 0))
+    _, it100, rel100, h100 = P.pcg(b, tol=1e-30, maxit=100, history=True)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, rtol=1e-30, maxiter=100),
+                     history_cap=100)
+    assert out["iters"] == 100 == it100
+    h = np.asarray(out["history"])
+    np.testing.assert_allclose(h[:60], h100[:60], rtol=1e-6)
+    assert 0.5 < h[99] / h100[99] < 2.0, (h[99], h100[99])
+    xo, ito, _, _ = P.pcg(b, tol=1e-10, maxit=1000)
+    x.zero_()
+    full = mesh.solve(_t(b), x, nb.default_opts(prec=nb.NB_FP64, rtol=1e-10))
+    assert full["status"] == 0 and abs(full["iters"] - ito) <= 1, (full["iters"], ito)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    print(f"2x2x2 N=7 FP64 PCG: after 100 iterations {h[99]:.3e} (oracle {h100[99]:.3e}); "
+          f"to 1e-10 in {full['iters']} iterations (oracle {ito})")
 
 
 @pytest.mark.parametrize("prec", ["fp32"])
