@@ -217,3 +217,46 @@ def dense_local_operator(fdm) -> np.ndarray:
             np.kron(Az, np.kron(By, Bx)))
     act = (az[:, None, None] & ay[None, :, None] & ax[None, None, :]).reshape(-1)
     return full[np.ix_(act, act)], act
+
+
+# --------------------------------------------------------------------------
+# an intermediate p-level (a study of the multigrid's middle levels)
+# --------------------------------------------------------------------------
+
+def p_interpolation(N_c: int, N_f: int, n_el: int) -> np.ndarray:
+    """Interpolation from the global GLL lattice of order N_c to that of order
+    N_f along one direction of n_el elements: in each element the Lagrange
+    basis of the N_c + 1 GLL points evaluated at the N_f + 1 GLL points
+    (element end points shared, so continuous fields stay continuous).
+    Shape (n_el N_f + 1, n_el N_c + 1)."""
+    xc, _ = gll(N_c)
+    xf, _ = gll(N_f)
+    L = np.ones((N_f + 1, N_c + 1))
+    for j in range(N_c + 1):
+        for k in range(N_c + 1):
+            if k != j:
+                L[:, j] *= (xf - xc[k]) / (xc[j] - xc[k])
+    J = np.zeros((n_el * N_f + 1, n_el * N_c + 1))
+    for e in range(n_el):
+        J[e * N_f:e * N_f + N_f + 1, e * N_c:e * N_c + N_c + 1] = L
+    return J
+
+
+def precondition_three_level(P, Pm, r: np.ndarray) -> np.ndarray:
+    """Three-level additive form: the two-level preconditioner of P (order N)
+    plus J S_m J^T r, S_m the one-level Schwarz preconditioner of the same
+    box at the intermediate order N_m (oracle.Problem Pm), J the lattice
+    interpolation from order N_m to N (p_interpolation per direction), the
+    restricted residual masked on the coarse lattice's Dirichlet boundary."""
+    box, bm = P.box, Pm.box
+    gx, gy, gz = box.nx * box.N + 1, box.ny * box.N + 1, box.nz * box.N + 1
+    Jx = p_interpolation(bm.N, box.N, box.nx)
+    Jy = p_interpolation(bm.N, box.N, box.ny)
+    Jz = p_interpolation(bm.N, box.N, box.nz)
+    z = precondition(P, r, coarse=True)
+    rg = P.to_global(r).reshape(gz, gy, gx)
+    rm = np.einsum("zc,yb,xa,zyx->cba", Jz, Jy, Jx, rg)
+    zm = precondition(Pm, Pm.to_local(rm.reshape(-1), masked=True), coarse=False)
+    zmg = Pm.to_global(zm).reshape(rm.shape)
+    zg = np.einsum("zc,yb,xa,cba->zyx", Jz, Jy, Jx, zmg)
+    return z + P.to_local(zg.reshape(-1), masked=True)

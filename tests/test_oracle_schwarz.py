@@ -215,3 +215,47 @@ def test_two_level_iterations_grow_little_with_the_element_count():
     print(its)
     assert its[(6, True)] < its[(6, False)]
     assert its[(6, True)] - its[(2, True)] < its[(6, False)] - its[(2, False)]
+
+
+@pytest.mark.parametrize("Nc,Nf", [(1, 5), (3, 7), (4, 9)])
+def test_p_interpolation_is_exact_on_the_coarse_polynomials(Nc, Nf):
+    """The lattice interpolation from order Nc to Nf reproduces, element by
+    element, every polynomial of degree <= Nc (so it is the identity on the
+    coarse space), has rows summing to one, and keeps the element end points."""
+    n_el = 3
+    J = schwarz.p_interpolation(Nc, Nf, n_el)
+    assert J.shape == (n_el * Nf + 1, n_el * Nc + 1)
+    xc, _ = oracle.gll(Nc)
+    xf, _ = oracle.gll(Nf)
+    # global coordinates of both lattices on [0, n_el]
+    gc = np.concatenate([e + (xc[:-1] + 1) / 2 for e in range(n_el)] + [[n_el]])
+    gf = np.concatenate([e + (xf[:-1] + 1) / 2 for e in range(n_el)] + [[n_el]])
+    for e in range(n_el):  # a piecewise polynomial of degree Nc, different per element
+        for k in range(Nc + 1):
+            f = lambda x: (x - e) ** k
+            sel_c = slice(e * Nc, e * Nc + Nc + 1)
+            sel_f = slice(e * Nf, e * Nf + Nf + 1)
+            np.testing.assert_allclose(J[sel_f, sel_c] @ f(gc[sel_c]), f(gf[sel_f]), atol=1e-12)
+    np.testing.assert_allclose(J.sum(axis=1), 1.0, atol=1e-13)
+    for e in range(n_el + 1):
+        assert J[e * Nf, e * Nc] == pytest.approx(1.0, abs=1e-14)
+
+
+def test_three_level_is_symmetric_and_adds_the_middle_level():
+    """The three-level form is symmetric on continuous vectors, and with the
+    intermediate order equal to the fine one (J the identity) it is the
+    two-level form plus one more one-level Schwarz term."""
+    box = Box(3, 2, 2, 4, 0.05)
+    P = oracle.Problem(box)
+    Pm = oracle.Problem(Box(3, 2, 2, 2, 0.05))
+    rng = np.random.default_rng(4)
+    r = P.to_local(rng.uniform(-1, 1, box.n_global))
+    s = P.to_local(rng.uniform(-1, 1, box.n_global))
+    zr = schwarz.precondition_three_level(P, Pm, r)
+    zs = schwarz.precondition_three_level(P, Pm, s)
+    a, b = P.to_global(s) @ P.to_global(zr), P.to_global(r) @ P.to_global(zs)
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert P.to_global(r) @ P.to_global(zr) > 0
+    same = schwarz.precondition_three_level(P, P, r)
+    expect = schwarz.precondition(P, r, coarse=True) + schwarz.precondition(P, r)
+    np.testing.assert_allclose(same, expect, atol=1e-12 * np.max(np.abs(expect)))
