@@ -421,9 +421,12 @@ k_cg_update_pairs(int npairs, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
 // pair's position in the element -- its local offset and which faces it lies
 // on -- is fixed per thread and computed once; per element only the box
 // coordinates and the neighbour tests change.  The rounds of one element are
-// loaded together before any is used.  Same sums in the same order as
-// k_cg_update_gs2 (bit-identical).  32-bit indices (E n^3 < 2^31).
-template <typename T, int n>
+// loaded together before any is used.  With PIPE the next element's loads
+// are issued before the current element is finished (more registers, fewer
+// resident blocks: it pays where the blocks have few elements).  Same sums in
+// the same order as k_cg_update_gs2 (bit-identical).  32-bit indices
+// (E n^3 < 2^31).
+template <typename T, int n, bool PIPE>
 __global__ void __launch_bounds__(256)
 k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
                CgScalars *__restrict__ sc, T *__restrict__ x, T *__restrict__ r,
@@ -462,34 +465,59 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     };
     const int e0 = (int)((int64_t)E * blockIdx.x / gridDim.x);
     const int e1 = (int)((int64_t)E * (blockIdx.x + 1) / gridDim.x);
-    for (int e = e0; e < e1; ++e) {
+    // one element's loads: the summed w of the thread's pairs and x, r, p, dinv
+    struct Buf {
+        T wa[R], wb[R];
+        V xv[R], rv[R], pv[R], dv[R];
+    };
+    auto load = [&](int e, Buf &B) {
         const int exy = dnx.div(e), ex = e - exy * nx;
         const int ez = dny.div(exy), ey = exy - ez * ny;
         // neighbour present below / above in each direction, in the bit layout of fl
         const int nb = (ex > 0) | ((ex < nx - 1) << 1) | ((ey > 0) << 2) | ((ey < ny - 1) << 3) |
                        ((ez > 0) << 4) | ((ez < nz - 1) << 5);
-        T wa[R], wb[R];
-        V xv[R], rv[R], pv[R], dv[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             if (loc[q] < 0) continue;
             const int l = e * n3 + loc[q], f = fl[q] & nb;
             gs_sum_pair_flags<T, int>(w, l, (f & 1) != 0, (f & 2) != 0, (f >> 2) & 1,
                                       (f >> 3) & 1, (f >> 4) & 1, (f >> 5) & 1, sx, sy, sz,
-                                      wa[q], wb[q]);
-            xv[q] = *reinterpret_cast<const V *>(x + l);
-            rv[q] = *reinterpret_cast<const V *>(r + l);
-            pv[q] = *reinterpret_cast<const V *>(p + l);
-            dv[q] = *reinterpret_cast<const V *>(dinv + l);
+                                      B.wa[q], B.wb[q]);
+            B.xv[q] = *reinterpret_cast<const V *>(x + l);
+            B.rv[q] = *reinterpret_cast<const V *>(r + l);
+            B.pv[q] = *reinterpret_cast<const V *>(p + l);
+            B.dv[q] = *reinterpret_cast<const V *>(dinv + l);
         }
+    };
+    auto finish = [&](int e, Buf &B) {
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             if (loc[q] < 0) continue;
             const int l = e * n3 + loc[q];
-            node(xv[q].x, rv[q].x, pv[q].x, wa[q], dv[q].x);
-            node(xv[q].y, rv[q].y, pv[q].y, wb[q], dv[q].y);
-            *reinterpret_cast<V *>(x + l) = xv[q];
-            *reinterpret_cast<V *>(r + l) = rv[q];
+            node(B.xv[q].x, B.rv[q].x, B.pv[q].x, B.wa[q], B.dv[q].x);
+            node(B.xv[q].y, B.rv[q].y, B.pv[q].y, B.wb[q], B.dv[q].y);
+            *reinterpret_cast<V *>(x + l) = B.xv[q];
+            *reinterpret_cast<V *>(r + l) = B.rv[q];
+        }
+    };
+    if constexpr (PIPE) {
+        // software pipeline: the next element's loads are in flight while this
+        // one is finished (w is read-only here; x and r of different elements)
+        Buf A, Bn;
+        int e = e0;
+        if (e < e1) load(e, A);
+        for (; e < e1; e += 2) {
+            if (e + 1 < e1) load(e + 1, Bn);
+            finish(e, A);
+            if (e + 1 >= e1) break;
+            if (e + 2 < e1) load(e + 2, A);
+            finish(e + 1, Bn);
+        }
+    } else {
+        for (int e = e0; e < e1; ++e) {
+            Buf A;
+            load(e, A);
+            finish(e, A);
         }
     }
     if (sc->pdl_early) pdl_trigger();
@@ -654,6 +682,12 @@ static int update_pairs_grid(int sm_count, int npairs, size_t smem = 0)
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count));
 }
 
+// The element-range update pipelines its element loop up to 100 elements per
+// SM.  Measured (mixed solves): E=4096 N=9 61.3 against 63.6 ms, N=7 25.5
+// against 27.1 ms, E=13824 N=7 108.1 against 110.2 ms; at E=32768 the plain
+// loop's higher occupancy wins (N=9 783 against 825 ms).
+static bool update_pipelined(const nb_mesh *m) { return m->E <= 100 * (int64_t)m->ctx->sm_count; }
+
 // k_cg_update_gs for n = N + 1 in FP32 (returns false where it is not
 // built).  FP64 keeps the separate summation: the folded sum adds every slot,
 // zeros included, which costs little on the FP32 pipe but measured slower
@@ -686,12 +720,21 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
                 (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part, m->kerr);  \
         } else if (m->update_kind == 1 ||                                                       \
                    (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {        \
-            pgrid = update_pairs_grid<k_cg_update_el<float, NN>>(m->ctx->sm_count,              \
-                                      (int)std::min<int64_t>(m->E * 256, npairs));              \
-            pgrid = (int)std::min<int64_t>(pgrid, m->E);                                        \
-            launch_pdl(k_cg_update_el<float, NN>, pgrid, 256, 0, s,                             \
-                (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
-                (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);           \
+            if (update_pipelined(m)) {                                                          \
+                pgrid = update_pairs_grid<k_cg_update_el<float, NN, true>>(m->ctx->sm_count,    \
+                                          (int)std::min<int64_t>(m->E * 256, npairs));          \
+                pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
+                launch_pdl(k_cg_update_el<float, NN, true>, pgrid, 256, 0, s,                   \
+                    (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
+                    (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
+            } else {                                                                            \
+                pgrid = update_pairs_grid<k_cg_update_el<float, NN, false>>(m->ctx->sm_count,   \
+                                          (int)std::min<int64_t>(m->E * 256, npairs));          \
+                pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
+                launch_pdl(k_cg_update_el<float, NN, false>, pgrid, 256, 0, s,                  \
+                    (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
+                    (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
+            }                                                                                   \
         } else {                                                                                \
             pgrid = update_pairs_grid<k_cg_update_pairs<float, NN>>(m->ctx->sm_count, npairs);  \
             k_cg_update_pairs<float, NN><<<pgrid, 256, 0, s>>>(                                 \
