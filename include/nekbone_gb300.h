@@ -117,6 +117,12 @@ typedef struct {
     double *history_host;   /* caller-provided, history_cap entries, or NULL */
     int history_cap;
     int64_t launches;       /* kernels launched by the solve (graph nodes included) */
+    nb_prec final_prec;     /* precision of the last inner solve: opts.prec, or a higher one
+                               when the refinement raised it (precision adaptivity: after
+                               two refinement steps in which the FP64 residual did not
+                               halve, the inner solves go from the tensor-core precisions
+                               to NB_FP32, and from NB_FP32 to FP64 PCG; NB_STAGNATED only
+                               when FP64 inner solves stall too) */
 } nb_stats;
 
 /* Library version string. */

@@ -43,7 +43,7 @@ class nb_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("rel_res", C.c_double),
                 ("seconds", C.c_double), ("status", C.c_int), ("history_len", C.c_int),
                 ("history_host", C.POINTER(C.c_double)), ("history_cap", C.c_int),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("final_prec", C.c_int)]
 
 
 def _load():
@@ -275,7 +275,7 @@ class Mesh:
         r = check(lib.nb_solve(self.h, C.byref(opts), self._vec(b, NB_FP64), self._vec(x, NB_FP64),
                                C.byref(st)), allow_positive=not raise_on_outcome)
         out = dict(status=r, iters=st.iters, outer_iters=st.outer_iters, rel_res=st.rel_res,
-                   seconds=st.seconds, launches=st.launches)
+                   seconds=st.seconds, launches=st.launches, final_prec=st.final_prec)
         if hist is not None:
             out["history"] = hist[:st.history_len].copy()
         return out

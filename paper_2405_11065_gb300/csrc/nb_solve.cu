@@ -794,6 +794,25 @@ __global__ void k_demote(int64_t nL, const double *__restrict__ r64, const doubl
     }
 }
 
+// The FP64 inner solve's start: r = r64, x = 0.
+__global__ void k_stage64(int64_t nL, const double *__restrict__ r64, double *__restrict__ r,
+                          double *__restrict__ x)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        r[l] = r64[l];
+        x[l] = 0.0;
+    }
+}
+
+// x += d in FP64.
+__global__ void k_add64(int64_t nL, const double *__restrict__ d, double *__restrict__ x)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x)
+        x[l] += d[l];
+}
+
 // Solution update in FP64: x += s * d.
 __global__ void k_promote(int64_t nL, const double *__restrict__ s2, const float *__restrict__ d,
                           double *__restrict__ x)
@@ -1086,6 +1105,7 @@ static nb_status solve_fp64(nb_mesh *m, const nb_opts *o, const double *b, doubl
         st->rel_res = sqrt(m->red_host[1] / bn2);
         st->status = (nb_status)h.status;
         st->history_len = 0;
+        st->final_prec = NB_FP64;
     }
     if (o->record_history) copy_history(ws, h.iter, 0, st, s);
     return (nb_status)h.status;
@@ -1128,6 +1148,10 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
     bool reliable = !o->restart;
     nb_status result = NB_NOT_CONVERGED;
     bool fell_back = false;
+    // precision adaptivity: the inner solves' precision, raised one step
+    // (tensor-core 16-bit contractions -> FP32 -> FP64) when the FP64
+    // residual stops dropping at the current one
+    nb_prec inner = o->prec;
     constexpr int kLearnedBudget = 3000;  // flexible-CG iterations per refinement step
     for (outer = 0; outer <= o->max_outer; ++outer) {
         // FP64 residual r = b - A x (skipped product for the zero start)
@@ -1154,7 +1178,16 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                 !fell_back) {
                 fell_back = true;  // the learned steps stopped paying: Jacobi-PCG takes over
                 stagn = 0;
-            } else if (++stagn >= 3) {
+            } else if (inner != NB_FP64 && ++stagn >= 2) {
+                // two steps without progress: the inner precision cannot
+                // resolve the correction any more (its operator error times
+                // the condition number is near one); raise it one step, and
+                // restart the inner solves in the new precision
+                inner = inner == NB_FP32 ? NB_FP64 : NB_FP32;
+                stagn = 0;
+                reliable = false;
+                prev_ok = false;
+            } else if (inner == NB_FP64 && ++stagn >= 3) {
                 result = NB_STAGNATED;
                 break;
             }
@@ -1167,7 +1200,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         // leave errors of FP32 size in the smoothest modes, whose residual the
         // stopping test does not resolve
         double rel_in = rel;
-        if (o->pc == NB_PC_SCHWARZ2 && !fell_back) {
+        if (o->pc == NB_PC_SCHWARZ2 && !fell_back && inner == NB_FP32) {
             bool applied = false;
             NB_TRY(schwarz_coarse_correct64(m, m->r64, x, (float *)ws.x, (float *)ws.r, m->part64,
                                             m->red_out + 1, &applied, s));
@@ -1180,11 +1213,36 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                 if (rel_in == 0.0) { rel = 0.0; result = NB_OK; break; }  // x is exact
             }
         }
+        const int remaining = o->maxiter - used;
+        if (inner == NB_FP64) {
+            // the precision raised to FP64: PCG in FP64 on A d = r64 to the
+            // step's tolerance, then x += d
+            Workspace &w64 = m->ws64;
+            NB_TRY(ensure_ws(m, w64, 8, 0));
+            const double *dinv64 = o->pc == NB_PC_NONE ? m->ones64 : m->dinv64;
+            const double tau64 = std::min(0.5, std::max(o->inner_rtol, 0.5 * o->rtol / rel_in));
+            k_stage64<<<g, kVecThreads, 0, s>>>(m->nL, m->r64, (double *)w64.r, (double *)w64.x);
+            NB_CUDA(cudaGetLastError());
+            NB_TRY(cg_start<double>(m, w64, dinv64, tau64, remaining, 1, false, s));
+            NB_TRY(cg_iterate<double>(m, NB_FP64, w64, dinv64, 10 + (int)NB_PC_JACOBI,
+                                      o->use_graph, remaining, s));
+            k_add64<<<g, kVecThreads, 0, s>>>(m->nL, (const double *)w64.x, x);
+            NB_CUDA(cudaGetLastError());
+            NB_CUDA(cudaMemcpyAsync(w64.scal_host, w64.scal, sizeof(CgScalars),
+                                    cudaMemcpyDeviceToHost, s));
+            NB_CUDA(cudaStreamSynchronize(s));
+            const int it64 = w64.scal_host->iter;
+            m->launches += 2 + (o->use_graph ? graph_launches(m, NB_FP64, *w64.scal_host) : 0);
+            used += it64;
+            prev_kind = 0;
+            prev_ok = false;
+            if (w64.scal_host->status == NB_BREAKDOWN && it64 == 0) { result = NB_BREAKDOWN; break; }
+            continue;
+        }
         // inner solve on r32 = r64/||r64||, from zero
         k_demote<<<g, kVecThreads, 0, s>>>(m->nL, m->r64, m->red_out + 1, (float *)ws.r,
                                            (float *)ws.x);
         NB_CUDA(cudaGetLastError());
-        const int remaining = o->maxiter - used;
         const bool schwarz = o->pc == NB_PC_SCHWARZ || o->pc == NB_PC_SCHWARZ2;
         const bool use_learned = (o->pc == NB_PC_LEARNED || schwarz) && !fell_back;
         // the inner solve only has to close the remaining gap to rtol (with a
@@ -1222,7 +1280,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                        o->record_history ? ws.hist_cap : 0,
                                        pdl_early_for(m->E, m->ctx->sm_count));
             NB_CUDA(cudaGetLastError());
-            NB_TRY(fcg_schwarz(m, o->prec, ws, o, resume, odd, s));
+            NB_TRY(fcg_schwarz(m, inner, ws, o, resume, odd, s));
         } else if (use_learned) {
             // flexible CG with the learned preconditioner (nb_learned.cu), on a
             // bounded budget; Jacobi-PCG takes over if it fails
@@ -1232,14 +1290,14 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                        o->record_history ? ws.hist_cap : 0,
                                        pdl_early_for(m->E, m->ctx->sm_count));
             NB_CUDA(cudaGetLastError());
-            NB_TRY(fcg_learned(m, o->prec, ws, o, resume, odd, s));
+            NB_TRY(fcg_learned(m, inner, ws, o, resume, odd, s));
         } else {
             if (resume)
                 NB_TRY(cg_resume<float>(m, ws, dinv, tau, std::min(remaining, cap), o->record_history,
                                         sqrt(s2_prev / m->red_host[1]), s));
             else
                 NB_TRY(cg_start<float>(m, ws, dinv, tau, remaining, 1, o->record_history, s));
-            NB_TRY(cg_iterate<float>(m, o->prec, ws, dinv, 20 * (int)o->prec + (int)o->pc,
+            NB_TRY(cg_iterate<float>(m, inner, ws, dinv, 20 * (int)inner + (int)o->pc,
                                      o->use_graph, remaining, s));
         }
         s2_prev = m->red_host[1];
@@ -1250,7 +1308,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         const int it = ws.scal_host->iter;
-        if (o->use_graph && !use_learned) m->launches += graph_launches(m, o->prec, *ws.scal_host);
+        if (o->use_graph && !use_learned) m->launches += graph_launches(m, inner, *ws.scal_host);
         if (o->record_history) {
             copy_history(ws, it, hist_off, st, s);
             hist_off += it;
@@ -1281,6 +1339,7 @@ static nb_status solve_refined(nb_mesh *m, const nb_opts *o, const double *b, do
         st->launches = m->launches;
         st->rel_res = rel;
         st->status = result;
+        st->final_prec = inner;
         if (o->record_history) st->history_len = std::min(hist_off, st->history_cap);
     }
     return result;

@@ -466,3 +466,50 @@ def test_mesh_outlives_its_context(nb):
     out = m.solve(b, x, nb.default_opts(prec=nb.NB_FP64))
     assert out["status"] == 0
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["tc_bf16", "tc_f16"])
+def test_tensor_core_refinement_reaches_the_oracle(nb, ctx, prec):
+    """Refinement whose inner solves use the 16-bit tensor-core contractions
+    (about 5e-3 / 5e-4 relative operator error) still reduces the FP64
+    residual every step here and reaches the FP64 oracle's solution; the
+    precision it finished in is reported."""
+    import torch
+    box = Box(8, 8, 8, 7, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 0))
+    xo, _, _, _ = P.pcg(b, tol=1e-13, maxit=5000)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.PREC_NAMES[prec], rtol=1e-10))
+    print(f"{prec} inner solves: status {out['status']}, final precision {out['final_prec']}, "
+          f"{out['iters']} iterations, {out['outer_iters']} refinement steps")
+    assert out["status"] == nb.NB_OK, out
+    xg = x.cpu().numpy()
+    assert P.true_relres(b, xg) < 1.01e-10
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tc_bf16"])
+def test_precision_adaptivity_reaches_fp64_inner_solves(nb, ctx, prec):
+    """Asked for a residual below what FP64 resolves, the refinement stalls at
+    the FP64 residual's rounding floor; each stall raises the inner precision
+    one step (tensor-core -> FP32 -> FP64 PCG), and only when the FP64 inner
+    solves stall too does the solve end as stagnated -- with the solution at
+    the oracle's."""
+    import torch
+    box = Box(3, 3, 3, 5, 0.05)
+    mesh = nb.Mesh.from_box(ctx, box)
+    P = oracle.Problem(box)
+    b = P.to_local(rhs_global(box, 1))
+    xo, _, _, _ = P.pcg(b, tol=1e-14, maxit=5000)
+    x = torch.zeros(box.n_local, dtype=torch.float64, device="cuda")
+    out = mesh.solve(_t(b), x, nb.default_opts(prec=nb.PREC_NAMES[prec], rtol=1e-16,
+                                               max_outer=80, maxiter=100000))
+    print(f"{prec}, rtol 1e-16: status {out['status']}, final precision {out['final_prec']}, "
+          f"rel_res {out['rel_res']:.2e}, {out['outer_iters']} refinement steps")
+    assert out["status"] == nb.NB_STAGNATED, out
+    assert out["final_prec"] == nb.NB_FP64
+    assert out["rel_res"] < 1e-13
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
