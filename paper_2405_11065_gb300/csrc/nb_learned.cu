@@ -1026,9 +1026,17 @@ k_fcg_update_gs2(int64_t E, int nx, int ny, int nz, CgScalars *sc, float *__rest
 
 // k_fcg_update_gs2 for the mesh's order (even n <= 16; the flexible-CG paths
 // that use it need an even n).
+bool launch_fcg_update_el(nb_mesh *m, Workspace &ws, float *x, float *r, const float *p,
+                          const float *w, double *part, float *rg, cudaStream_t s);
+
 static nb_status fcg_update_folded(nb_mesh *m, Workspace &ws, float *x, float *r, const float *p,
                                    const float *w, double *part, float *rg, cudaStream_t s)
 {
+    // element ranges where built (even n <= 10), else one block per element
+    if (launch_fcg_update_el(m, ws, x, r, p, w, part, rg, s)) {
+        NB_CUDA(cudaGetLastError());
+        return NB_OK;
+    }
     const int grid = (int)std::min<int64_t>(m->E, (int64_t)m->ctx->sm_count * 8);
     const float *sgn = m->dinv32;
 #define NB_FU(NN)                                                                                 \

@@ -415,7 +415,38 @@ k_cg_update_pairs(int npairs, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
-// The update with the folded summation over contiguous element ranges:
+// Flexible CG: rtr from the update's partials, pap_prev, the iteration count,
+// the relative residual (history) and the stopping tests (the same step as
+// the flexible-CG update kernels of the learned and Schwarz paths).  Called by
+// the whole last block.
+__device__ __forceinline__ void fcg_finish_iter(CgScalars *sc, const double *part, int cnt,
+                                                double *sred)
+{
+    const double rtr = sum_partials(part, cnt, sred);
+    if (threadIdx.x == 0) {
+        sc->pap_prev = sc->pap;
+        sc->rtr = rtr;
+        const int it = sc->iter + 1;
+        sc->iter = it;
+        const double bn = sc->bnorm2 > 0.0 ? sc->bnorm2 : 1.0;
+        const double rel = sqrt(rtr / bn);
+        sc->relres = rel;
+        if (sc->hist && it <= sc->hist_cap) sc->hist[it - 1] = rel;
+        if (!isfinite(rel)) {
+            sc->done = 1;
+            sc->status = NB_BREAKDOWN;
+        } else if (rel < sc->tol) {
+            sc->done = 1;
+        } else if (it >= sc->maxit) {
+            sc->done = 1;
+            sc->status = NB_NOT_CONVERGED;
+        }
+    }
+}
+
+// The update with the folded summation over contiguous element ranges (FLEX
+// 0: Jacobi CG, its (r, dinv r) and (r, r) with beta in the last block; 1:
+// flexible CG, (r, r) and the flexible-CG stopping step):
 // block b of a persistent grid takes elements [E b / G, E (b + 1) / G), and
 // thread t the node pairs t, t + 256, ... of each of them (R rounds).  The
 // pair's position in the element -- its local offset and which faces it lies
@@ -426,7 +457,7 @@ k_cg_update_pairs(int npairs, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
 // resident blocks: it pays where the blocks have few elements).  Same sums in
 // the same order as k_cg_update_gs2 (bit-identical).  32-bit indices
 // (E n^3 < 2^31).
-template <typename T, int n, bool PIPE>
+template <typename T, int n, bool PIPE, int FLEX>
 __global__ void __launch_bounds__(256)
 k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
                CgScalars *__restrict__ sc, T *__restrict__ x, T *__restrict__ r,
@@ -459,7 +490,7 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         xl = xl + alpha * pl;
         rl = rl - alpha * wl;
         if (owner_copy(d)) {
-            a.add(rl * (d * rl));
+            if (FLEX == 0) a.add(rl * (d * rl));
             b.add(rl * rl);
         }
     };
@@ -521,13 +552,19 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         }
     }
     if (sc->pdl_early) pdl_trigger();
-    double ta = block_sum_acc(a, sred);
-    double tb = block_sum_acc(b, sred);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = ta;
-        part[gridDim.x + blockIdx.x] = tb;
+    if constexpr (FLEX == 0) {
+        double ta = block_sum_acc(a, sred);
+        double tb = block_sum_acc(b, sred);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = ta;
+            part[gridDim.x + blockIdx.x] = tb;
+        }
+        if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+    } else {
+        const double tb = block_sum_acc(b, sred);
+        if (threadIdx.x == 0) part[blockIdx.x] = tb;
+        if (last_block(&sc->tick_upd)) fcg_finish_iter(sc, part, gridDim.x, sred);
     }
-    if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
 }
 
 // k_cg_update_el with the element's contiguous x, r, p and dinv blocks
@@ -721,17 +758,17 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
         } else if (m->update_kind == 1 ||                                                       \
                    (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {        \
             if (update_pipelined(m)) {                                                          \
-                pgrid = update_pairs_grid<k_cg_update_el<float, NN, true>>(m->ctx->sm_count,    \
+                pgrid = update_pairs_grid<k_cg_update_el<float, NN, true, 0>>(m->ctx->sm_count, \
                                           (int)std::min<int64_t>(m->E * 256, npairs));          \
                 pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
-                launch_pdl(k_cg_update_el<float, NN, true>, pgrid, 256, 0, s,                   \
+                launch_pdl(k_cg_update_el<float, NN, true, 0>, pgrid, 256, 0, s,                \
                     (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
                     (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
             } else {                                                                            \
-                pgrid = update_pairs_grid<k_cg_update_el<float, NN, false>>(m->ctx->sm_count,   \
+                pgrid = update_pairs_grid<k_cg_update_el<float, NN, false, 0>>(m->ctx->sm_count,\
                                           (int)std::min<int64_t>(m->E * 256, npairs));          \
                 pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
-                launch_pdl(k_cg_update_el<float, NN, false>, pgrid, 256, 0, s,                  \
+                launch_pdl(k_cg_update_el<float, NN, false, 0>, pgrid, 256, 0, s,               \
                     (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
                     (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
             }                                                                                   \
@@ -752,6 +789,48 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
     }
 #undef NB_UGP
 #undef NB_UGS
+}
+
+template <int NN, bool PIPE, int FLEX>
+static cudaError_t launch_update_el(nb_mesh *m, CgScalars *sc, float *x, float *r, const float *p,
+                                   const float *w, const float *dinv, double *part, cudaStream_t s)
+{
+    const int npairs = (int)(m->nL / 2);
+    int pgrid = update_pairs_grid<k_cg_update_el<float, NN, PIPE, FLEX>>(
+        m->ctx->sm_count, (int)std::min<int64_t>(m->E * 256, npairs));
+    pgrid = (int)std::min<int64_t>(pgrid, m->E);
+    const FastDiv dnx((uint32_t)m->nx), dny((uint32_t)m->ny);
+    return launch_pdl(k_cg_update_el<float, NN, PIPE, FLEX>, pgrid, 256, 0, s, (int)m->E, m->nx,
+                      m->ny, m->nz, dnx, dny, sc, x, r, p, w, dinv, part);
+}
+
+// The flexible-CG update over element ranges: x, r with the summation of w
+// folded in, (r, r) and the stopping step.  False (nothing launched) where the
+// element-range form is not used: odd n, more than two rounds of 256 node
+// pairs per element (n > 10), and with rg, the Schwarz path's scatter of the
+// new r.  Measured: the learned flexible CG at E=4096, N=7 28.7 against
+// 30.3 ms; the Schwarz solve at N=9 39.8 against 39.1 ms with the scatter in
+// this kernel, so that path keeps the one-block-per-element kernel.
+bool launch_fcg_update_el(nb_mesh *m, Workspace &ws, float *x, float *r, const float *p,
+                          const float *w, double *part, float *rg, cudaStream_t s)
+{
+    if (rg) return false;
+    const bool pipe = update_pipelined(m);
+    const float *dinv = m->dinv32;
+    cudaError_t e = cudaSuccess;
+#define NB_FEL(NN)                                                                               \
+    case NN:                                                                                     \
+        e = pipe ? launch_update_el<NN, true, 1>(m, ws.scal, x, r, p, w, dinv, part, s)          \
+                 : launch_update_el<NN, false, 1>(m, ws.scal, x, r, p, w, dinv, part, s);        \
+        break;
+    switch (m->n) {
+        NB_FEL(2) NB_FEL(4) NB_FEL(6) NB_FEL(8) NB_FEL(10)
+        default:
+            return false;
+    }
+#undef NB_FEL
+    (void)e;  // a launch error is reported by the caller's cudaGetLastError
+    return true;
 }
 
 // The while-node condition of the captured iteration.  It counts executions
