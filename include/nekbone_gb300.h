@@ -267,6 +267,15 @@ nb_status nb_set_ax_variant(nb_mesh *mesh, nb_prec prec, int variant);
  * sum in the same order (bit-identical results).  Errors: NB_ERR_ARG. */
 nb_status nb_set_update_variant(nb_mesh *mesh, int variant);
 
+/* Deferred x steps of the FP32 Jacobi iteration, where the update is variant
+ * 1 and the operator the pencil kernel: the iteration alternates two
+ * direction buffers, the first iteration of each pair skips x += alpha p and
+ * the second applies both steps in the same order (same bits).  mode -1 the
+ * built-in rule (where x, r, the two directions, w and dinv, 24 bytes per
+ * local node, exceed the L2 cache), 0 never, 1 wherever those kernels run.
+ * Costs one more L-vector of workspace.  Errors: NB_ERR_ARG (mode). */
+nb_status nb_set_x_deferral(nb_mesh *mesh, int mode);
+
 /* Kernel name of operator variant `variant` for (mesh order, prec), or of
  * the variant in use with variant = -1 (a static string owned by the
  * library; NULL for an index out of range, a NULL mesh or a bad prec). */

@@ -97,6 +97,7 @@ def _load():
         "nb_ax_variants": (i32, [vp, i32]),
         "nb_set_ax_variant": (i32, [vp, i32, i32]),
         "nb_set_update_variant": (i32, [vp, i32]),
+        "nb_set_x_deferral": (i32, [vp, i32]),
         "nb_setup_slab": (i32, [vp, i32, i32, i32, i32, i32, i32, dbl, C.POINTER(vp)]),
         "nb_slab_face": (i32, [vp, i32, i32, vp, vp]),
         "nb_slab_face_add": (i32, [vp, i32, i32, vp, vp]),
@@ -382,6 +383,11 @@ class Mesh:
     def set_update_variant(self, variant=0):
         """Kernel of the FP32 update with the folded summation (0: built-in)."""
         check(lib.nb_set_update_variant(self.h, int(variant)))
+
+    def set_x_deferral(self, mode=-1):
+        """Deferred x steps of the FP32 Jacobi iteration: -1 by size (the
+        built-in rule), 0 never, 1 wherever the kernels allow it."""
+        check(lib.nb_set_x_deferral(self.h, int(mode)))
 
     def set_ax_variant(self, prec, variant=-1):
         """Use operator variant ``variant`` (-1: the default) from now on."""

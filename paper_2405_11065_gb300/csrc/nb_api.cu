@@ -43,6 +43,7 @@ static void free_ws(Workspace &ws)
     cudaFree(ws.w);
     cudaFree(ws.z);
     cudaFree(ws.aux);
+    cudaFree(ws.p2);
     cudaFree(ws.part);
     cudaFree(ws.scal);
     cudaFree(ws.hist);
@@ -90,6 +91,7 @@ nb_status nb_create(nb_ctx **ctx, int device, void *cuda_stream)
     nb_ctx *c = new nb_ctx();
     c->device = device;
     cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, device);
     if (e != cudaSuccess) {
         delete c;
         NB_CUDA(e);
@@ -606,6 +608,16 @@ extern "C" nb_status nb_set_update_variant(nb_mesh *m, int variant)
     if (m->update_kind != variant) {
         m->update_kind = variant;
         ++m->ax_epoch;  // captured iteration graphs hold the old kernel
+    }
+    return NB_OK;
+}
+
+extern "C" nb_status nb_set_x_deferral(nb_mesh *m, int mode)
+{
+    if (!m || mode < -1 || mode > 1) return arg_error("mesh or x deferral mode");
+    if (m->x_defer != mode) {
+        m->x_defer = mode;
+        ++m->ax_epoch;  // captured iteration graphs hold the old form
     }
     return NB_OK;
 }

@@ -234,6 +234,28 @@ nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, 
     return NB_ERR_ARG;
 }
 
+// The fused FP32 Jacobi CG step with the previous direction read from p_prev
+// and the new one written to p (distinct buffers; the pencil kernel only).
+bool ax_cg_step_from_available(const nb_mesh *m)
+{
+    const AxKind k = kind_of(m, NB_FP32);
+    return (k == kPen2 || k == kPen1) && pen_ok(m, NB_FP32, k == kPen2 ? 2 : 1);
+}
+
+nb_status ax_cg_step_from(nb_mesh *m, const float *r, const float *dinv, const float *p_prev,
+                          float *p, float *w, CgScalars *scal, double *pap_part, int *nparts,
+                          cudaStream_t s)
+{
+    if (!ax_cg_step_from_available(m) || p_prev == nullptr || p_prev == p ||
+        !(aligned16(r) && aligned16(dinv) && aligned16(p_prev) && aligned16(p) && aligned16(w))) {
+        set_error("CG step from a second direction buffer needs the pencil operator");
+        return NB_ERR_ARG;
+    }
+    const AxKind kind = kind_of(m, NB_FP32);
+    return ax_pen_f32(m->n, 1, kind == kPen2 ? 2 : 1, m->ctx->sm_count, m->E, m->G32, p_prev, w,
+                      r, dinv, p, scal, pap_part, m->kerr, nparts, s);
+}
+
 bool ax_dir_step_available(const nb_mesh *m)
 {
     return tma_ok(m, NB_FP32) || pen_ok(m, NB_FP32, 2) || pen_ok(m, NB_FP32, 1);

@@ -41,7 +41,9 @@
 //
 // Forms (MODE) as k_ax_tma: 0 the plain operator w = A_L u; 1 the fused
 // Jacobi CG step p = |dinv| r + beta p, w = A_L p, partials of p.w and
-// alpha in the last block; 2 the fused flexible-CG step p = z + beta p.
+// alpha in the last block; 2 the fused flexible-CG step p = z + beta p.  In
+// forms 1 and 2 the previous direction is read from u where u is given (the
+// solver then alternates two direction buffers) and from p itself otherwise.
 // Every wait on an mbarrier is bounded (one second); a block that times out
 // sets *err, drains its own copies and exits.
 #pragma once
@@ -142,6 +144,7 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
     const T beta = PUPD ? (T)scal->beta : T(0);
 
     // the thread's k-pencil of the element's inputs, one element ahead
+    const T *pin = PUPD && uin != nullptr ? uin : p;  // the previous direction
     T nr[n], nd[n], np[n];
     auto fetch = [&](long long t) {
         const size_t b = (size_t)(blockIdx.x + t * gridDim.x) * n3 + tid;
@@ -150,7 +153,7 @@ k_ax_pen(long long E, const T *__restrict__ G, const T *__restrict__ uin, T *__r
             if (PUPD) {
                 nr[k] = r[b + k * n2];
                 nd[k] = MODE == 1 ? dinv[b + k * n2] : T(1);
-                np[k] = p[b + k * n2];
+                np[k] = pin[b + k * n2];
             } else {
                 nr[k] = uin[b + k * n2];
             }

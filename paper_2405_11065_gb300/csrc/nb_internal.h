@@ -161,6 +161,8 @@ struct CgScalars {
     double fcg_zw;    // flexible CG: (z, c, w_prev)
     double pap_prev;  // flexible CG: previous (p, c, A p)
     double rp;        // flexible CG: (r, c, p)
+    double alpha_x;   // alpha of the iteration whose x step is deferred
+    int x_pending;    // 1: x still lacks alpha_x times the other direction buffer
     int iter;         // iterations done
     int maxit;        // iteration limit
     int done;         // 1 when the loop must stop
@@ -187,6 +189,7 @@ struct Workspace {
     int elt = 0;                  // bytes per value (4 or 8)
     void *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr;
     void *aux = nullptr;          // flexible CG: previous A p
+    void *p2 = nullptr;           // Jacobi CG with deferred x steps: the second direction
     double *part = nullptr;       // per-block partial sums (kMaxPartials * 3)
     CgScalars *scal = nullptr;    // device scalars
     CgScalars *scal_host = nullptr;  // pinned mirror
@@ -214,6 +217,7 @@ struct AxConfig {
 struct nb_ctx {
     int device = 0;
     int sm_count = 0;
+    int l2_bytes = 0;  // L2 cache size
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
     // references: the caller's (dropped by nb_destroy) and one per mesh,
@@ -285,6 +289,7 @@ struct nb_mesh {
                                // bulk-copied vectors (k_cg_update_tma), 0 element
                                // ranges where an element takes at most two rounds
                                // of 256 pairs, else node pairs (measured fastest)
+    int x_defer = -1;          // deferred x steps: -1 by size, 0 never, 1 where possible
     int ax_epoch = 0;          // bumped whenever an operator variant choice changes:
                                // captured iteration graphs of an older epoch are stale
     int *kerr = nullptr;             // device flag: a pipelined kernel's wait timed out
@@ -314,6 +319,13 @@ nb_status ax_local(nb_mesh *m, nb_prec prec, const void *u, void *w, double *pap
 nb_status ax_cg_step(nb_mesh *m, nb_prec prec, const void *r, const void *dinv, void *p,
                      void *w, CgScalars *scal, double *pap_part, int *nparts,
                      cudaStream_t s);
+// The same step in FP32 with the previous direction read from p_prev and the
+// new one written to p (two buffers that the iteration alternates); only
+// where the pencil operator is the FP32 variant in use.
+bool ax_cg_step_from_available(const nb_mesh *m);
+nb_status ax_cg_step_from(nb_mesh *m, const float *r, const float *dinv, const float *p_prev,
+                          float *p, float *w, CgScalars *scal, double *pap_part, int *nparts,
+                          cudaStream_t s);
 int ax_variant_count(const nb_mesh *m, nb_prec prec);
 nb_status l2_flush(const nb_ctx *ctx, void *buf, size_t bytes, int pattern, cudaStream_t s);
 // ---- slabs and the split-phase CG (nb_slab.cu, nb_solve.cu)

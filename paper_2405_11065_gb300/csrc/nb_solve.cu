@@ -59,6 +59,7 @@ __global__ void k_cg_setup(CgScalars *sc, double tol, int maxit, double *hist, i
     sc->loops = 0;
     sc->tick_ax = 0u;
     sc->tick_upd = 0u;
+    sc->x_pending = 0;
 }
 
 // The weighted dot products glsc3(a, c, b) of the iteration, for continuous
@@ -457,13 +458,22 @@ __device__ __forceinline__ void fcg_finish_iter(CgScalars *sc, const double *par
 // resident blocks: it pays where the blocks have few elements).  Same sums in
 // the same order as k_cg_update_gs2 (bit-identical).  32-bit indices
 // (E n^3 < 2^31).
-template <typename T, int n, bool PIPE, int FLEX>
-__global__ void __launch_bounds__(256)
+// XM, the x step of Jacobi CG: 0 x += alpha p every iteration; 1 none (the
+// even iteration of a pair: x, p are not read; the last block keeps alpha
+// as alpha_x and marks the step pending); 2 x += alpha_x p2 + alpha p (the
+// odd iteration: p2 the even iteration's direction, the two additions in
+// the order of two single steps, so x is bit-identical to XM = 0).  A pair
+// moves 16 + 32 bytes per local node in the update instead of 2 x 28.  The
+// odd form with two rounds of pairs and the pipeline is held to three
+// resident blocks per SM (80 registers at n = 10; 100 unbounded, i.e. two).
+template <typename T, int n, bool PIPE, int FLEX, int XM = 0>
+__global__ void __launch_bounds__(256, PIPE && XM == 2 && n * n * n / 2 > 256 ? 3 : 0)
 k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
                CgScalars *__restrict__ sc, T *__restrict__ x, T *__restrict__ r,
-               const T *__restrict__ p, const T *__restrict__ w, const T *__restrict__ dinv,
-               double *__restrict__ part)
+               const T *__restrict__ p, const T *__restrict__ p2, const T *__restrict__ w,
+               const T *__restrict__ dinv, double *__restrict__ part)
 {
+    static_assert(XM == 0 || FLEX == 0, "deferred x steps are a Jacobi CG form");
     static_assert(n % 2 == 0, "pairs of nodes need an even n");
     using V = typename Pair2<T>::type;
     constexpr int N = n - 1, n2 = n * n, n3 = n2 * n, h = n / 2, P = n3 / 2;
@@ -484,10 +494,12 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     pdl_wait();  // the previous kernel's alpha, w and p (programmatic dependent launch)
     if (sc->done) return;
     const T alpha = (T)sc->alpha;
+    const T alpha_x = XM == 2 ? (T)sc->alpha_x : T(0);
     DotAcc<T> a, b;
-    auto node = [&](T &xl, T &rl, T pl, T wl, T d) {
+    auto node = [&](T &xl, T &rl, T pl, T p2l, T wl, T d) {
         if (d == T(0)) wl = T(0);  // Dirichlet node
-        xl = xl + alpha * pl;
+        if (XM == 2) xl = xl + alpha_x * p2l;
+        if (XM != 1) xl = xl + alpha * pl;
         rl = rl - alpha * wl;
         if (owner_copy(d)) {
             if (FLEX == 0) a.add(rl * (d * rl));
@@ -496,10 +508,11 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
     };
     const int e0 = (int)((int64_t)E * blockIdx.x / gridDim.x);
     const int e1 = (int)((int64_t)E * (blockIdx.x + 1) / gridDim.x);
-    // one element's loads: the summed w of the thread's pairs and x, r, p, dinv
+    // one element's loads: the summed w of the thread's pairs and x, r, p,
+    // (p2,) dinv
     struct Buf {
         T wa[R], wb[R];
-        V xv[R], rv[R], pv[R], dv[R];
+        V xv[R], rv[R], pv[R], p2v[R], dv[R];
     };
     auto load = [&](int e, Buf &B) {
         const int exy = dnx.div(e), ex = e - exy * nx;
@@ -514,9 +527,12 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
             gs_sum_pair_flags<T, int>(w, l, (f & 1) != 0, (f & 2) != 0, (f >> 2) & 1,
                                       (f >> 3) & 1, (f >> 4) & 1, (f >> 5) & 1, sx, sy, sz,
                                       B.wa[q], B.wb[q]);
-            B.xv[q] = *reinterpret_cast<const V *>(x + l);
+            if (XM != 1) {
+                B.xv[q] = *reinterpret_cast<const V *>(x + l);
+                B.pv[q] = *reinterpret_cast<const V *>(p + l);
+            }
+            if (XM == 2) B.p2v[q] = *reinterpret_cast<const V *>(p2 + l);
             B.rv[q] = *reinterpret_cast<const V *>(r + l);
-            B.pv[q] = *reinterpret_cast<const V *>(p + l);
             B.dv[q] = *reinterpret_cast<const V *>(dinv + l);
         }
     };
@@ -525,9 +541,9 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
         for (int q = 0; q < R; ++q) {
             if (loc[q] < 0) continue;
             const int l = e * n3 + loc[q];
-            node(B.xv[q].x, B.rv[q].x, B.pv[q].x, B.wa[q], B.dv[q].x);
-            node(B.xv[q].y, B.rv[q].y, B.pv[q].y, B.wb[q], B.dv[q].y);
-            *reinterpret_cast<V *>(x + l) = B.xv[q];
+            node(B.xv[q].x, B.rv[q].x, B.pv[q].x, B.p2v[q].x, B.wa[q], B.dv[q].x);
+            node(B.xv[q].y, B.rv[q].y, B.pv[q].y, B.p2v[q].y, B.wb[q], B.dv[q].y);
+            if (XM != 1) *reinterpret_cast<V *>(x + l) = B.xv[q];
             *reinterpret_cast<V *>(r + l) = B.rv[q];
         }
     };
@@ -559,11 +575,34 @@ k_cg_update_el(int E, int nx, int ny, int nz, FastDiv dnx, FastDiv dny,
             part[blockIdx.x] = ta;
             part[gridDim.x + blockIdx.x] = tb;
         }
-        if (last_block(&sc->tick_upd)) cg_finish_iter(sc, part, gridDim.x, sred);
+        if (last_block(&sc->tick_upd)) {
+            cg_finish_iter(sc, part, gridDim.x, sred);
+            if (XM != 0 && threadIdx.x == 0) {
+                if (XM == 1) sc->alpha_x = sc->alpha;
+                sc->x_pending = XM == 1;
+            }
+        }
     } else {
         const double tb = block_sum_acc(b, sred);
         if (threadIdx.x == 0) part[blockIdx.x] = tb;
         if (last_block(&sc->tick_upd)) fcg_finish_iter(sc, part, gridDim.x, sred);
+    }
+}
+
+// The x step a Jacobi CG solve with deferred x steps still owes when it stops
+// after the even iteration of a pair: x += alpha_x p2, and the last direction
+// p2 into p (where a resumed solve reads it).  Nothing when none is pending.
+template <typename T>
+__global__ void k_x_flush(int64_t nL, const CgScalars *__restrict__ sc, T *__restrict__ x,
+                          T *__restrict__ p, const T *__restrict__ p2)
+{
+    if (!sc->x_pending) return;
+    const T a = (T)sc->alpha_x;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nL;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const T pl = p2[l];
+        x[l] = x[l] + a * pl;
+        p[l] = pl;
     }
 }
 
@@ -729,7 +768,23 @@ static bool update_pipelined(const nb_mesh *m) { return m->E <= 100 * (int64_t)m
 // built).  FP64 keeps the separate summation: the folded sum adds every slot,
 // zeros included, which costs little on the FP32 pipe but measured slower
 // than the separate kernel on the FP64 pipe.
-static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, double *part,
+template <int NN, bool PIPE>
+static cudaError_t launch_update_el_xm(nb_mesh *m, Workspace &ws, int xm, const float *dinv,
+                                       double *part, cudaStream_t s);
+
+// Whether the FP32 Jacobi update is the element-range kernel: even n, by
+// choice (variant 1) or by default up to two rounds of 256 node pairs per
+// element (n <= 10).
+static bool update_el_used(const nb_mesh *m)
+{
+    const int n = m->n, rounds = (n * n * n / 2 + 255) / 256;
+    return n % 2 == 0 && n >= 2 && n <= 16 &&
+           (m->update_kind == 1 || (m->update_kind == 0 && rounds <= 2));
+}
+
+// xm: the x step form of the element-range kernel (0 where x is updated every
+// iteration; 1, 2 the even and odd iteration of a pair with deferred x steps).
+static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, double *part, int xm,
                              cudaStream_t s)
 {
     // one wave: 8 blocks of 256 threads per SM
@@ -755,23 +810,11 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
             k_cg_update_tma<NN><<<pgrid, 256, sm_, s>>>(                                        \
                 (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,               \
                 (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part, m->kerr);  \
-        } else if (m->update_kind == 1 ||                                                       \
-                   (m->update_kind == 0 && ((NN) * (NN) * (NN) / 2 + 255) / 256 <= 2)) {        \
-            if (update_pipelined(m)) {                                                          \
-                pgrid = update_pairs_grid<k_cg_update_el<float, NN, true, 0>>(m->ctx->sm_count, \
-                                          (int)std::min<int64_t>(m->E * 256, npairs));          \
-                pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
-                launch_pdl(k_cg_update_el<float, NN, true, 0>, pgrid, 256, 0, s,                \
-                    (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
-                    (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
-            } else {                                                                            \
-                pgrid = update_pairs_grid<k_cg_update_el<float, NN, false, 0>>(m->ctx->sm_count,\
-                                          (int)std::min<int64_t>(m->E * 256, npairs));          \
-                pgrid = (int)std::min<int64_t>(pgrid, m->E);                                    \
-                launch_pdl(k_cg_update_el<float, NN, false, 0>, pgrid, 256, 0, s,               \
-                    (int)m->E, m->nx, m->ny, m->nz, dnx, dny, ws.scal, (float *)ws.x,           \
-                    (float *)ws.r, (const float *)ws.p, (const float *)ws.w, dinv, part);       \
-            }                                                                                   \
+        } else if (update_el_used(m)) {                                                         \
+            if (update_pipelined(m))                                                            \
+                launch_update_el_xm<NN, true>(m, ws, xm, dinv, part, s);                        \
+            else                                                                                \
+                launch_update_el_xm<NN, false>(m, ws, xm, dinv, part, s);                       \
         } else {                                                                                \
             pgrid = update_pairs_grid<k_cg_update_pairs<float, NN>>(m->ctx->sm_count, npairs);  \
             k_cg_update_pairs<float, NN><<<pgrid, 256, 0, s>>>(                                 \
@@ -791,17 +834,31 @@ static bool launch_update_gs(nb_mesh *m, Workspace &ws, const float *dinv, doubl
 #undef NB_UGS
 }
 
-template <int NN, bool PIPE, int FLEX>
+template <int NN, bool PIPE, int FLEX, int XM = 0>
 static cudaError_t launch_update_el(nb_mesh *m, CgScalars *sc, float *x, float *r, const float *p,
-                                   const float *w, const float *dinv, double *part, cudaStream_t s)
+                                   const float *p2, const float *w, const float *dinv,
+                                   double *part, cudaStream_t s)
 {
     const int npairs = (int)(m->nL / 2);
-    int pgrid = update_pairs_grid<k_cg_update_el<float, NN, PIPE, FLEX>>(
+    int pgrid = update_pairs_grid<k_cg_update_el<float, NN, PIPE, FLEX, XM>>(
         m->ctx->sm_count, (int)std::min<int64_t>(m->E * 256, npairs));
     pgrid = (int)std::min<int64_t>(pgrid, m->E);
     const FastDiv dnx((uint32_t)m->nx), dny((uint32_t)m->ny);
-    return launch_pdl(k_cg_update_el<float, NN, PIPE, FLEX>, pgrid, 256, 0, s, (int)m->E, m->nx,
-                      m->ny, m->nz, dnx, dny, sc, x, r, p, w, dinv, part);
+    return launch_pdl(k_cg_update_el<float, NN, PIPE, FLEX, XM>, pgrid, 256, 0, s, (int)m->E,
+                      m->nx, m->ny, m->nz, dnx, dny, sc, x, r, p, p2, w, dinv, part);
+}
+
+// The Jacobi update over element ranges with x step form xm (see
+// k_cg_update_el).
+template <int NN, bool PIPE>
+static cudaError_t launch_update_el_xm(nb_mesh *m, Workspace &ws, int xm, const float *dinv,
+                                       double *part, cudaStream_t s)
+{
+    float *x = (float *)ws.x, *r = (float *)ws.r;
+    const float *p = (const float *)ws.p, *p2 = (const float *)ws.p2, *w = (const float *)ws.w;
+    if (xm == 1) return launch_update_el<NN, PIPE, 0, 1>(m, ws.scal, x, r, p, p2, w, dinv, part, s);
+    if (xm == 2) return launch_update_el<NN, PIPE, 0, 2>(m, ws.scal, x, r, p, p2, w, dinv, part, s);
+    return launch_update_el<NN, PIPE, 0, 0>(m, ws.scal, x, r, p, nullptr, w, dinv, part, s);
 }
 
 // The flexible-CG update over element ranges: x, r with the summation of w
@@ -820,8 +877,8 @@ bool launch_fcg_update_el(nb_mesh *m, Workspace &ws, float *x, float *r, const f
     cudaError_t e = cudaSuccess;
 #define NB_FEL(NN)                                                                               \
     case NN:                                                                                     \
-        e = pipe ? launch_update_el<NN, true, 1>(m, ws.scal, x, r, p, w, dinv, part, s)          \
-                 : launch_update_el<NN, false, 1>(m, ws.scal, x, r, p, w, dinv, part, s);        \
+        e = pipe ? launch_update_el<NN, true, 1>(m, ws.scal, x, r, p, nullptr, w, dinv, part, s) \
+                 : launch_update_el<NN, false, 1>(m, ws.scal, x, r, p, nullptr, w, dinv, part, s);\
         break;
     switch (m->n) {
         NB_FEL(2) NB_FEL(4) NB_FEL(6) NB_FEL(8) NB_FEL(10)
@@ -969,17 +1026,29 @@ static int cg_body_kernels(const nb_mesh *m, nb_prec prec)
 // use_cond: 1 in a graph, ending the body with the loop condition; 2 in a
 // graph, an iteration followed by another one of the same body; 0 launched
 // from the host.  In FP32 the operator and the update go out with
-// programmatic dependent launch.
+// programmatic dependent launch.  xm (FP32, see defer_x): 0 one direction
+// buffer, x stepped every iteration; 1 the even iteration of a pair (p read,
+// p2 written, no x step); 2 the odd one (p2 read, p written, both x steps).
 template <typename T>
 static nb_status cg_body(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv,
-                         cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
+                         cudaGraphConditionalHandle h, int use_cond, int xm, cudaStream_t s)
 {
     PdlScope pdl(sizeof(T) == 4);
     int nparts = 0;
-    NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
+    if (xm != 0) {
+        float *pa = (float *)ws.p, *pb = (float *)ws.p2;
+        NB_TRY(ax_cg_step_from(m, (const float *)ws.r, (const float *)dinv, xm == 1 ? pa : pb,
+                               xm == 1 ? pb : pa, (float *)ws.w, ws.scal, ws.part, &nparts, s));
+    } else {
+        NB_TRY(ax_cg_step(m, prec, ws.r, dinv, ws.p, ws.w, ws.scal, ws.part, &nparts, s));
+    }
     double *up = ws.part + kMaxPartials;
     bool folded = false;
-    if constexpr (sizeof(T) == 4) folded = launch_update_gs(m, ws, (const float *)dinv, up, s);
+    if constexpr (sizeof(T) == 4) folded = launch_update_gs(m, ws, (const float *)dinv, up, xm, s);
+    if (!folded && xm != 0) {
+        set_error("deferred x steps need the element-range update");
+        return NB_ERR_ARG;
+    }
     if (!folded) {
         NB_TRY(dssum(m, prec, ws.w, 1, s));
         const int g = vec_grid(m->ctx, m->nL);
@@ -1051,10 +1120,11 @@ static nb_status cg_resume(nb_mesh *m, Workspace &ws, const T *dinv, double tol,
     return NB_OK;
 }
 
-// Run iterations until the device scalars say stop.
+// The loop of cg_iterate: a captured graph with a device-side loop
+// condition, or chunks of iterations launched from the host.
 template <typename T>
-static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv, int key,
-                            int use_graph, int maxit, cudaStream_t s)
+static nb_status cg_loop(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv, int key,
+                         int use_graph, int maxit, bool defer, cudaStream_t s)
 {
     if (use_graph) {
         if (ws.exec == nullptr || ws.graph_key != key || ws.graph_epoch != m->ax_epoch) {
@@ -1082,7 +1152,8 @@ static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *di
                                                   cudaStreamCaptureModeRelaxed));
             nb_status st = NB_OK;
             for (int i = 0; i < cg_body_iters<T>() && st == NB_OK; ++i)
-                st = cg_body<T>(m, prec, ws, dinv, h, i + 1 == cg_body_iters<T>() ? 1 : 2, s);
+                st = cg_body<T>(m, prec, ws, dinv, h, i + 1 == cg_body_iters<T>() ? 1 : 2,
+                                defer ? 1 + i : 0, s);
             cudaGraph_t captured = nullptr;
             cudaError_t ce = cudaStreamEndCapture(s, &captured);
             if (st != NB_OK) {
@@ -1102,14 +1173,55 @@ static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *di
         NB_CUDA(cudaGraphLaunch(ws.exec, s));
         return NB_OK;
     }
-    // host-driven: launch a chunk of iterations, then look at the flag
+    // host-driven: launch a chunk of iterations, then look at the flag (an
+    // even number: with deferred x steps every chunk is whole pairs)
     const int chunk = 16;
     for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
-        for (int t = 0; t < chunk; ++t) NB_TRY(cg_body<T>(m, prec, ws, dinv, 0, 0, s));
+        for (int t = 0; t < chunk; ++t)
+            NB_TRY(cg_body<T>(m, prec, ws, dinv, 0, 0, defer ? 1 + (t & 1) : 0, s));
         NB_CUDA(cudaMemcpyAsync(ws.scal_host, ws.scal, sizeof(CgScalars), cudaMemcpyDeviceToHost,
                                 s));
         NB_CUDA(cudaStreamSynchronize(s));
         if (ws.scal_host->done) break;
+    }
+    return NB_OK;
+}
+
+// Jacobi CG in FP32 with the pencil operator and the element-range update
+// defers the x step over pairs of iterations where the loop's vectors do not
+// fit in L2: the operator alternates two direction buffers, so that the even
+// iteration's update reads neither x nor p and the odd one applies both steps
+// (16 + 32 instead of 2 x 28 bytes per local node in the update).  Measured
+// (mixed solves): E=13824 N=9 254.4 against 271.3 ms, E=32768 N=7 290.8
+// against 297.2 ms; where x, r, p, w and dinv stay in L2 the sixth vector
+// costs more than it saves (E=4096 N=9 61.3 against 59.8 ms), so the rule is
+// the six vectors' 24 bytes per local node against the L2 size
+// (nb_set_x_deferral overrides it).
+static bool defer_x(const nb_mesh *m, nb_prec prec, const Workspace &ws)
+{
+    if (m->x_defer == 0 || prec != NB_FP32 || ws.elt != 4 || !update_el_used(m) ||
+        !ax_cg_step_from_available(m))
+        return false;
+    return m->x_defer == 1 || (double)24 * m->nL > (double)m->ctx->l2_bytes;
+}
+
+// Run iterations until the device scalars say stop.
+template <typename T>
+static nb_status cg_iterate(nb_mesh *m, nb_prec prec, Workspace &ws, const T *dinv, int key,
+                            int use_graph, int maxit, cudaStream_t s)
+{
+    const bool defer = sizeof(T) == 4 && defer_x(m, prec, ws);
+    if (defer && ws.p2 == nullptr) {
+        NB_CUDA(cudaMalloc(&ws.p2, (size_t)ws.elt * ws.nL));
+        NB_CUDA(cudaMemsetAsync(ws.p2, 0, (size_t)ws.elt * ws.nL, s));
+    }
+    NB_TRY(cg_loop<T>(m, prec, ws, dinv, key, use_graph, maxit, defer, s));
+    if (defer) {
+        const int g = vec_grid(m->ctx, m->nL);
+        k_x_flush<float><<<g, kVecThreads, 0, s>>>(m->nL, ws.scal, (float *)ws.x, (float *)ws.p,
+                                                   (const float *)ws.p2);
+        NB_CUDA(cudaGetLastError());
+        m->launches += 1;
     }
     return NB_OK;
 }

@@ -452,6 +452,51 @@ def test_update_variants_are_bit_identical(nb, ctx, box):
         mesh.set_update_variant(4)
 
 
+@pytest.mark.parametrize("box", [Box(3, 3, 2, 9, 0.05), Box(4, 3, 2, 7, 0.05)],
+                         ids=lambda b: f"{b.nx}x{b.ny}x{b.nz}N{b.N}")
+@pytest.mark.parametrize("use_graph", [1, 0], ids=["graph", "host"])
+@pytest.mark.parametrize("maxiter", [7, 8, 10000])
+def test_deferred_x_steps_give_the_single_step_bits(nb, ctx, box, use_graph, maxiter):
+    """Jacobi CG with the element-range update defers the x step over pairs of
+    iterations (two direction buffers): its solution has the bits of the
+    node-pair update, which steps x every iteration.  maxiter 7 stops the
+    solve after the first iteration of a pair (the pending step is applied
+    after the loop), 8 after the second; 10000 converges.  (The built-in rule
+    defers only where the loop's vectors exceed L2; mode 1 forces it here.)"""
+    import torch
+    mesh = nb.Mesh.from_box(ctx, box)
+    mesh.set_x_deferral(1)
+    P = oracle.Problem(box)
+    b = _t(P.to_local(rhs_global(box, 11)))
+    res = {}
+    for v in (1, 2):
+        mesh.set_update_variant(v)
+        x = torch.zeros_like(b)
+        out = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32, use_graph=use_graph,
+                                               maxiter=maxiter))
+        res[v] = (x, out)
+    (x1, o1), (x2, o2) = res[1], res[2]
+    assert o1["status"] == o2["status"], (o1, o2)
+    assert (o1["status"] == 0) == (maxiter > 100), o1
+    assert o1["iters"] == o2["iters"] and o1["outer_iters"] == o2["outer_iters"]
+    assert torch.equal(x1, x2)
+    # one step-completing launch after each inner solve of the deferred form
+    assert 0 < o1["launches"] - o2["launches"] <= max(o1["outer_iters"], 1), (o1, o2)
+    if maxiter > 100:
+        assert P.true_relres(P.to_local(rhs_global(box, 11)), x1.cpu().numpy()) < 1.01e-10
+    # mode 0 and the built-in rule (a mesh this small fits in L2) step x every
+    # iteration: the same bits, no completing launch
+    for mode in (0, -1):
+        mesh.set_x_deferral(mode)
+        mesh.set_update_variant(1)
+        x = torch.zeros_like(b)
+        o = mesh.solve(b, x, nb.default_opts(prec=nb.NB_FP32, use_graph=use_graph,
+                                             maxiter=maxiter))
+        assert torch.equal(x, x1) and o["launches"] == o2["launches"], (mode, o, o2)
+    with pytest.raises(nb.NbError):
+        mesh.set_x_deferral(2)
+
+
 def test_mesh_outlives_its_context(nb):
     """A mesh keeps its context alive: destroying the context first (as a
     garbage collector may) leaves the mesh usable and its destruction safe."""
