@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default operator variants (profiler runs: timing under a "
                          "profiler would steer the autotuner)")
+    ap.add_argument("--edge", type=int, default=0,
+                    help="--mode solve / ax only: an edge^3 deformed box of order --order instead "
+                         "of the 16^3, N=9 workload (profiling other mesh sizes)")
+    ap.add_argument("--order", type=int, default=9, help="polynomial order with --edge")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the iteration's kernels from the host instead of one CUDA graph "
                          "(same kernels; lets a profiler list them one by one)")
@@ -814,9 +818,14 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)  # legacy default stream: events are ordered
     ctx = nb.Context(local)                  # with the library's own blocking stream
-    mesh = nb.Mesh.from_box(ctx, BOX)
-    bg = torch.from_numpy(W.rhs_global(BOX, rank)).to(dev)
-    b = torch.empty(BOX.n_local, dtype=torch.float64, device=dev)
+    box = BOX
+    if args.edge:
+        if args.mode not in ("solve", "ax"):
+            raise SystemExit("--edge applies to --mode solve and --mode ax only")
+        box = W.Box(args.edge, args.edge, args.edge, args.order, BOX.deform)
+    mesh = nb.Mesh.from_box(ctx, box)
+    bg = torch.from_numpy(W.rhs_global(box, rank)).to(dev)
+    b = torch.empty(box.n_local, dtype=torch.float64, device=dev)
     mesh.to_local(nb.NB_FP64, bg, b, masked=True)
     x = torch.zeros_like(b)
     flush = torch.empty(W.l2_flush_bytes(), dtype=torch.uint8, device=dev)
