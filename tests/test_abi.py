@@ -61,6 +61,8 @@ def test_argument_validation_without_gpu(nb):
     assert lib.nb_setup_gs(None) == nb.NB_ERR_ARG
     assert lib.nb_ax(None, 0, 0, None, None) == nb.NB_ERR_ARG
     assert lib.nb_solve(None, None, None, None, None) == nb.NB_ERR_ARG
+    assert lib.nb_set_update_variant(None, 0) == nb.NB_ERR_ARG
+    assert lib.nb_set_x_deferral(None, -1) == nb.NB_ERR_ARG
     assert b"invalid argument" in lib.nb_last_error()
     assert lib.nb_destroy(None) == nb.NB_OK
     assert lib.nb_mesh_destroy(None) == nb.NB_OK
