@@ -26,9 +26,11 @@ the textbook spectral-element definition, cited at its C implementation in
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, exactness properties, an independently assembled dense
-matrix with a direct solve, or brute force; none is "parity unpinned" except
-the flexible-CG path with a nonlinear (learned) preconditioner, whose only
-pin is its reduction to PCG for a linear preconditioner.
+matrix with a direct solve, or brute force; none is "parity unpinned".  The
+flexible CG is pinned by its reduction to PCG for a linear preconditioner
+and, for a nonlinear one, by the properties every step keeps (residual
+orthogonal to the last direction, consecutive directions A-conjugate, A-norm
+error not growing) and its limit, the dense direct solution.
 """
 from __future__ import annotations
 

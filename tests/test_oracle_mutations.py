@@ -1,9 +1,9 @@
-"""Mutation check of the oracle's pins: each plausible mistake below, planted
-by one textual change in a copy of the C oracle compiled into a temporary
-library, makes at least one pin of the GLL, mesh, operator or precision-study
-tests fail.  The
-committed oracle is never modified; the copies live in a temporary directory
-and are loaded through NBO_LIB in a child process."""
+"""Mutation check of the oracle's pins: each plausible mistake below makes at
+least one pin fail.  In the C oracle a mistake is one textual change in a
+copy compiled into a temporary library (loaded through NBO_LIB in a child
+process); in the Python parts (Schwarz, network, flexible CG) it is a changed
+copy of one function patched in for the test.  The committed oracle is never
+modified."""
 import os
 import shutil
 import subprocess
@@ -152,3 +152,46 @@ def test_planted_mistakes_in_the_network_oracle_fail_a_pin(monkeypatch):
     monkeypatch.setattr(mlp, "gelu_grad", tanh_term_sign)
     with pytest.raises(AssertionError):
         pins.test_backward_matches_finite_differences((8, 4, 5))
+
+
+# ---- planted mistakes in the flexible CG ----
+
+FCG_MUTANTS = {
+    "wrong sign of the flexible-CG beta": ("beta = -self.glsc3(z, w) / pap_prev",
+                                           "beta = self.glsc3(z, w) / pap_prev"),
+    "flexible-CG beta dropped": ("p = z + beta * p", "p = z + 0.0 * beta * p"),
+    "residual updated without alpha": ("r = r - alpha * w", "r = r - w"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FCG_MUTANTS))
+def test_planted_mistakes_in_the_flexible_cg_fail_a_pin(name, monkeypatch):
+    """One textual change in a copy of Problem.fcg (the committed oracle is
+    untouched): the step-by-step pin of flexible CG under a nonlinear
+    preconditioner fails, while the unchanged copy passes it."""
+    import importlib.util
+    import inspect
+    import math
+    import textwrap
+
+    import numpy as np
+
+    import oracle
+    from workloads import Box
+    spec = importlib.util.spec_from_file_location(
+        "pins_operator", os.path.join(ROOT, "tests", "test_oracle_operator.py"))
+    pins = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(pins)
+    src = textwrap.dedent(inspect.getsource(oracle.Problem.fcg))
+    old, new = FCG_MUTANTS[name]
+    assert src.count(old) == 1
+    box = Box(2, 2, 1, 5, 0.05)
+    for text, fails in ((src, False), (src.replace(old, new), True)):
+        ns = {"np": np, "math": math}
+        exec(text, ns)
+        monkeypatch.setattr(oracle.Problem, "fcg", ns["fcg"])
+        if fails:
+            with pytest.raises(AssertionError):
+                pins.test_flexible_cg_with_a_nonlinear_preconditioner(box)
+        else:
+            pins.test_flexible_cg_with_a_nonlinear_preconditioner(box)

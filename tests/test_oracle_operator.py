@@ -138,6 +138,51 @@ def test_assembled_operator_spd_and_direct_solve(box):
         assert np.linalg.norm(xp - xf) <= 1e-12 * np.linalg.norm(xp)
 
 
+@pytest.mark.parametrize("box", [Box(2, 2, 1, 5, 0.05), Box(2, 2, 2, 3, 0.05)])
+def test_flexible_cg_with_a_nonlinear_preconditioner(box):
+    """Flexible CG with one-vector truncation (Notay 2000), driven by a
+    nonlinear preconditioner, keeps at every step what holds for any
+    preconditioner: the new residual is orthogonal to the last direction
+    (exact line search), consecutive directions are A-conjugate (the choice
+    of beta), so the A-norm of the error never grows; and it converges to
+    the dense direct solution.  The iterate after k steps comes from a run
+    stopped there (the iteration is deterministic), the direction of step k
+    is x_k - x_(k-1), and no quantity is taken from the routine's internals."""
+    P = oracle.Problem(box)
+    A, free = _assembled_dense(P)
+    bg = rhs_global(box, 5)
+    b = P.to_local(bg)
+    xg = np.zeros(box.n_global)
+    xg[free] = np.linalg.solve(A, bg[free])
+    xstar = P.to_local(xg)
+
+    def B(r):  # pointwise in a continuous, masked r: continuous and masked
+        s = math.sqrt(P.glsc3(r, r) / max(len(free), 1)) or 1.0
+        return P.dinv * (r + 0.5 * s * np.tanh(r / s))
+
+    def inner_a(u, v):
+        return P.glsc3(u, P.apply(v))
+
+    K = 14
+    X = [np.zeros_like(b)] + [P.fcg(b, B, tol=0.0, maxit=k)[0] for k in range(1, K + 1)]
+    err = [inner_a(xstar - x, xstar - x) for x in X]
+    for k in range(1, K + 1):
+        d = X[k] - X[k - 1]
+        r = b - P.apply(X[k])
+        assert abs(P.glsc3(r, d)) <= 1e-8 * math.sqrt(P.glsc3(r, r) * P.glsc3(d, d)), k
+        assert err[k] <= err[k - 1] * (1 + 1e-12), k
+        if k >= 2:
+            dp = X[k - 1] - X[k - 2]
+            assert abs(inner_a(d, dp)) <= 1e-8 * math.sqrt(inner_a(d, d) * inner_a(dp, dp)), k
+    assert err[K] < 1e-3 * err[0]
+    # the preconditioner is not a linear one in disguise: the iterates leave PCG's
+    xp, _, _, _ = P.pcg(b, tol=0.0, maxit=5)
+    assert np.linalg.norm(X[5] - xp) > 1e-4 * np.linalg.norm(xp)
+    x, _, rel, _ = P.fcg(b, B, tol=1e-12, maxit=500)
+    assert rel < 1e-12
+    assert np.linalg.norm(x - xstar) <= 1e-9 * np.linalg.norm(xstar)
+
+
 def test_linear_function_annihilated_at_interior_nodes():
     box = Box(2, 2, 1, 4, 0.0)
     P = oracle.Problem(box)
