@@ -497,6 +497,36 @@ def test_deferred_x_steps_give_the_single_step_bits(nb, ctx, box, use_graph, max
         mesh.set_x_deferral(2)
 
 
+def test_x_deferral_rule_by_size(nb, ctx):
+    """The built-in rule defers the x steps where the loop's six vectors (24 B
+    per local node) exceed L2 -- an 8000-element N=9 mesh, 192 MB -- and not
+    where they fit (a 2x2x2 mesh); either way the bits are those of x stepped
+    every iteration."""
+    import torch
+    big = Box(20, 20, 20, 9, 0.05)
+    mesh = nb.Mesh.from_box(ctx, big)
+    b = torch.from_numpy(rhs_global(big, 3)).to("cuda")
+    bl = torch.empty(big.n_local, dtype=torch.float64, device="cuda")
+    mesh.to_local(nb.NB_FP64, b, bl, masked=True)
+    res = {}
+    for mode in (0, -1):
+        mesh.set_x_deferral(mode)
+        x = torch.zeros_like(bl)
+        res[mode] = (x, mesh.solve(bl, x, nb.default_opts(prec=nb.NB_FP32)))
+    (x0, o0), (xa, oa) = res[0], res[-1]
+    assert o0["status"] == oa["status"] == 0 and o0["iters"] == oa["iters"]
+    assert torch.equal(x0, xa)
+    assert 0 < oa["launches"] - o0["launches"] <= oa["outer_iters"], (o0, oa)
+    small = Box(2, 2, 2, 9, 0.05)
+    m2 = nb.Mesh.from_box(ctx, small)
+    b2 = _t(oracle.Problem(small).to_local(rhs_global(small, 3)))
+    launches = []
+    for mode in (0, -1):
+        m2.set_x_deferral(mode)
+        launches.append(m2.solve(b2, torch.zeros_like(b2), nb.default_opts(prec=nb.NB_FP32))["launches"])
+    assert launches[0] == launches[1]
+
+
 def test_mesh_outlives_its_context(nb):
     """A mesh keeps its context alive: destroying the context first (as a
     garbage collector may) leaves the mesh usable and its destruction safe."""
