@@ -42,7 +42,7 @@ WORKLOAD = ("mixed-precision Jacobi-PCG (FP32 operator and vectors, FP64 dots, F
 RTOL = 1e-10
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -73,7 +73,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the iteration's kernels from the host instead of one CUDA graph "
                          "(same kernels; lets a profiler list them one by one)")
-    return ap.parse_args()
+    a = ap.parse_args(argv)
+    if a.edge and a.mode not in ("solve", "ax"):
+        ap.error("--edge applies to --mode solve and --mode ax only")
+    return a
 
 
 def dist_env():
@@ -818,10 +821,8 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)  # legacy default stream: events are ordered
     ctx = nb.Context(local)                  # with the library's own blocking stream
-    box = BOX
+    box = BOX  # --edge (solve and ax modes only, checked in parse): another box size
     if args.edge:
-        if args.mode not in ("solve", "ax"):
-            raise SystemExit("--edge applies to --mode solve and --mode ax only")
         box = W.Box(args.edge, args.edge, args.edge, args.order, BOX.deform)
     mesh = nb.Mesh.from_box(ctx, box)
     bg = torch.from_numpy(W.rhs_global(box, rank)).to(dev)

@@ -1,6 +1,6 @@
 """The multi-rank path of the benchmark on CPU: two gloo ranks agree on the
 slowest rank's time and on the whole-job throughput (replicas, weak
-scaling)."""
+scaling); and the benchmark's argument checks."""
 import os
 import socket
 
@@ -49,3 +49,15 @@ def test_single_process_is_its_own_max():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.whole_job_value(1, 2000, 2, 4.0) == pytest.approx(2000 * 2 / 4e-3 / 1e9)
+
+
+def test_edge_option_only_with_the_profiling_modes():
+    """--edge (another box size) is accepted by the solve and ax modes only,
+    so that the bench line always measures the stated workload."""
+    import bench
+    a = bench.parse(["--mode", "solve", "--edge", "24", "--order", "7"])
+    assert (a.edge, a.order) == (24, 7)
+    assert bench.parse([]).edge == 0
+    for mode in ("full", "sweep", "batched"):
+        with pytest.raises(SystemExit):
+            bench.parse(["--mode", mode, "--edge", "24"])
